@@ -1,0 +1,295 @@
+#!/usr/bin/env python3
+"""Exact reverse k-MIPS throughput and latency at |Q|=1M, |P|=500k, d=50, k=10.
+
+One step = one batch of ``--nq`` queries (bit copies of random items, k=10)
+through the whole online path (block filter, per-user filter, exact recheck /
+verification, emit) via ``rmips_query_batch`` with device-resident inputs and
+outputs.  The index (Algorithm 1) is built once before timing.  Prints one JSON
+line on rank 0.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2110_07131_gb300 import datagen  # noqa: E402
+
+METRIC = "exact reverse k-MIPS queries/s and p50/p99 ms at |Q|=1M |P|=500k d=50 k=10"
+SEED = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--m", type=int, default=500_000)
+    ap.add_argument("--d", type=int, default=50)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--k-max", type=int, default=25)
+    ap.add_argument("--nq", type=int, default=1000, help="queries per step")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--p-prime", type=int, default=0, help="0 = bounds over all of P")
+    ap.add_argument("--block-size", type=int, default=32)
+    ap.add_argument("--plain-queries", type=int, default=400)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU baseline time")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    return {"workload": f"reverse k-MIPS |Q|={a.n} |P|={a.m} d={a.d} k={a.k} (k_max={a.k_max}), "
+                        f"MF-like lognormal-norm synthetic vectors, queries = random items of P",
+            "n_users": a.n, "n_items": a.m, "d": a.d, "k": a.k, "k_max": a.k_max,
+            "queries_per_step": a.nq, "index": "full-P" if a.p_prime == 0 else f"P'={a.p_prime}",
+            "block_size": a.block_size, "filter_precision": a.precision,
+            "l2": "inputs larger than L2 (Q 200 MB fp32 + bounds 200 MB); no flush between steps"}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU oracle timing
+def oracle_sample(Q, P, q, k, seconds, rng):
+    """Time the CPU oracle deciding a random user sample for one query.
+
+    Returns (queries/s equivalent, users sampled, seconds, cores)."""
+    from oracle import rmips_oracle as O
+    n = Q.shape[0]
+    users = rng.choice(n, 256, replace=False)
+    t0 = time.perf_counter()
+    O.decide_users(Q, P, q, k, users)
+    t = time.perf_counter() - t0
+    s = int(min(n, max(256, 256 * seconds / max(t, 1e-3))))
+    users = rng.choice(n, s, replace=False)
+    t0 = time.perf_counter()
+    O.decide_users(Q, P, q, k, users)
+    t = time.perf_counter() - t0
+    return (s / n) / t, s, t, os.cpu_count()
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    Q, P = datagen.make_problem(a.n, a.m, a.d, SEED)
+    qs, _ = datagen.queries_from_items(P, a.steps + a.warmup, SEED)
+    rng = np.random.default_rng(0)
+    from oracle import rmips_oracle as O
+    per_step = max(64, int(a.n * 0.0005))
+    for w in range(a.warmup):
+        O.decide_users(Q, P, qs[w], a.k, rng.choice(a.n, 64, replace=False))
+    times = []
+    for s in range(a.steps):
+        users = rng.choice(a.n, per_step, replace=False)
+        t0 = time.perf_counter()
+        O.decide_users(Q, P, qs[a.warmup + s], a.k, users)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    qps = a.steps * (per_step / a.n) / tot
+    sample = (f"each step: the oracle decides {per_step} random users of one query (fraction "
+              f"{per_step / a.n:.2e} of a query) over all {a.m} items in float64 numpy")
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(a),
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ours(a):
+    import torch
+    from paper_2110_07131_gb300 import rmips
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    Q, P = datagen.make_problem(a.n, a.m, a.d, SEED)
+    t0 = time.perf_counter()
+    index = rmips.rmips_build_index(Q, P, k_max=a.k_max, block_size=a.block_size, p_prime=a.p_prime,
+                                    precision=a.precision)
+    build_s = time.perf_counter() - t0
+    info = index.info()
+
+    total_q = (a.warmup + a.steps) * a.nq
+    qs, _ = datagen.queries_from_items(P, total_q, SEED + 7919 * rank)
+    ks = np.full(a.nq, a.k, np.int32)
+    dqs = torch.from_numpy(qs).to(dev)
+    dks = torch.from_numpy(ks).to(dev)
+    cap = 64 << 20
+    dout = torch.empty(cap, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        sl = dqs[i * a.nq:(i + 1) * a.nq]
+        _, offs = rmips.rmips_query_batch(index, sl, dks, out=dout, stream=stream)
+        return int(offs[-1])
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    rmips.rmips_profile_enable(index, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    results = 0
+    for i in range(a.steps):
+        results += step(a.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = rmips.rmips_profile_read(index)
+    rmips.rmips_profile_enable(index, False)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.barrier()
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = a.steps * a.nq * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    hq = np.ascontiguousarray(qs[:a.nq])
+    e2e_steps = max(2, min(a.steps, 5))
+    rmips.rmips_query_batch(index, hq, ks)
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        ids, offs = rmips.rmips_query_batch(index, hq, ks)
+        d2h += ids.nbytes + offs.nbytes
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": a.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(hq.nbytes + ks.nbytes),
+           "d2h_bytes_per_step": int(d2h // e2e_steps)}
+
+    # plain path: one query per call, host buffers, per-call latency
+    lat = []
+    for j in range(a.plain_queries):
+        t1 = time.perf_counter()
+        rmips.rmips_query(index, qs[j], a.k)
+        lat.append((time.perf_counter() - t1) * 1e3)
+    lat_s = np.array(lat[5:] if len(lat) > 10 else lat)
+    plain = {"qps": 1e3 / lat_s.mean(), "p50_ms": float(np.percentile(lat_s, 50)),
+             "p99_ms": float(np.percentile(lat_s, 99)), "queries": int(len(lat_s)),
+             "api": "rmips_query, host q and host ids, one query per call"}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    launches = prof["filter_launches"] or 1
+    per_launch_bytes = prof["filter_alg_bytes"] / launches
+    per_launch_ms = prof["filter_ms"] / launches
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": "k_filter (Lemmas 1-3, TMA-staged rows)",
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "peak_source": peak_src, "traffic": None,
+                "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": per_launch_ms * 1e3,
+                "filter_share_of_step": prof["filter_ms"] / ms if ms > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision, "data": "synthetic",
+            "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
+            "gpu_launches": a.steps * (1 + 3 * a.nq),
+            "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain,
+            "batch_latency_ms": ms_max / a.steps,
+            "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
+            "index_incomplete_users": info["incomplete"],
+            "users_returned_per_query": results / (a.steps * a.nq),
+            "alpha_blocks_pruned": (prof["blocks_pruned"] / prof["blocks_total"]) if prof["blocks_total"] else None,
+            "users_tested_per_query": prof["users_tested"] / launches}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rng = np.random.default_rng(1)
+        qps, s, t, cores = oracle_sample(Q, P, qs[0], a.k, a.cpu_seconds, rng)
+        line["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one query, {s} random users decided over all {a.m} items "
+                                          f"in float64 numpy ({t:.1f} s), scaled to queries/s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    index.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * rmips.h -- C ABI of librmips: exact reverse k-MIPS on one NVIDIA GB300 GPU.
+ *
+ * Problem (Definition 2, "Reverse k-MIPS problem", of Amagata & Hara,
+ * "Reverse Maximum Inner Product Search", RecSys 2021): given a query item
+ * vector q, a user set Q, an item set P and k, return every user u in Q whose
+ * k-MIPS result over P + {q} contains q.  Ties between q and an item are
+ * resolved in q's favour:
+ *
+ *     u is returned  <=>  #{ p in P : u.p > u.q } < k
+ *
+ * with the inner products taken in exact arithmetic on the float32 inputs.
+ * The returned set is exactly that set on every precision path; reduced
+ * precision only changes how many users need the exact recheck.
+ *
+ * Method (Simpfer, Section 4): an offline index (Algorithm 1) keeps, per
+ * user, bounds on its j-th largest inner product over P (j = 1..k_max) and
+ * groups norm-sorted users into blocks; a query prunes whole blocks
+ * (Lemma 3), decides most remaining users in O(1) (Lemmas 1 and 2), and
+ * verifies the rest against P (Algorithm 2, Corollaries 1 and 2) with an
+ * exact tie-breaking recheck.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major float32, [rows][d], caller-owned, and may live in
+ *    host or device memory (detected with cudaPointerGetAttributes).  The
+ *    library never keeps a caller pointer after the call returns.
+ *  - Ids are 0-based row numbers of the caller's original Q.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that return counts or host results synchronise that stream.
+ *  - Every call returns an rmips_status; on failure no output is partially
+ *    written unless stated, and rmips_last_error() gives a message.
+ *  - An index is immutable after build.  Concurrent queries on one index are
+ *    safe from different host threads (each call takes its own workspace).
+ */
+#ifndef RMIPS_H
+#define RMIPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rmips_index rmips_index;
+
+typedef enum {
+  RMIPS_OK = 0,
+  RMIPS_ERR_ARG = 1,        /* bad pointer, size, option or segment */
+  RMIPS_ERR_K_RANGE = 2,    /* k < 1 or k > k_max (the paper rebuilds the
+                               index for k > k_max, Section 4.1) */
+  RMIPS_ERR_NONFINITE = 3,  /* NaN or Inf in Q, P or a query */
+  RMIPS_ERR_OOM = 4,        /* device or pinned host allocation failed */
+  RMIPS_ERR_CAPACITY = 5,   /* output buffer too small; the required size
+                               is reported, nothing is written */
+  RMIPS_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
+  RMIPS_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+  RMIPS_ERR_INTERNAL = 8    /* a device-side consistency check failed */
+} rmips_status;
+
+/* Arithmetic of the online filter (the index always keeps float32 copies). */
+enum { RMIPS_FP32 = 0, RMIPS_BF16 = 1, RMIPS_FP16 = 2 };
+
+typedef struct {
+  int32_t k_max;      /* largest k a query may use; 1..28 (Section 2: the
+                         method's only parameter, 25 in Section 5) */
+  int32_t block_size; /* users per block (Definition 4); 32, 64, 128 or 256;
+                         0 selects 32 */
+  int64_t p_prime;    /* |P'| of Algorithm 1: 0 (or >= |P|) builds the bounds
+                         over all of P ("full-P"); otherwise over the first
+                         p_prime items in descending norm, as in the paper */
+  int32_t precision;  /* RMIPS_FP32, RMIPS_BF16 or RMIPS_FP16 */
+  int32_t reserved;   /* must be 0 */
+} rmips_build_opts;
+
+/* Optional restriction of a query to a subset of users. */
+typedef struct {
+  int32_t kind;       /* 0: all users, 1: ids in [begin, end), 2: id list */
+  int32_t reserved;   /* must be 0 */
+  int64_t begin, end; /* kind 1 */
+  const int64_t* ids; /* kind 2: host array of n_ids distinct ids */
+  int64_t n_ids;
+} rmips_segment;
+
+typedef struct {
+  int64_t n, m;          /* |Q|, |P| */
+  int32_t d, k_max;
+  int32_t block_size, precision;
+  int64_t n_blocks;
+  int64_t p_prime;       /* items the bounds were built over */
+  int64_t incomplete;    /* users whose candidate list could not be proven
+                            complete (they fall back to a full scan) */
+  int64_t device_bytes;  /* index footprint in device memory */
+  double build_ms;       /* wall time of rmips_build_index */
+} rmips_index_info;
+
+typedef struct {
+  int64_t blocks_total, blocks_pruned;   /* Lemma 3 */
+  int64_t users_tested;                  /* users of unpruned blocks */
+  int64_t yes_fast;                      /* decided yes without a scan */
+  int64_t todo;                          /* sent to recheck / Algorithm 2 */
+  int64_t exact_calls;                   /* exact (integer) tie decisions */
+  int64_t result;                        /* users returned */
+} rmips_query_stats;
+
+/*
+ * rmips_build_index -- Algorithm 1 (Section 4.1, "Pre-processing").
+ *
+ * Q: n x d users, P: m x d items (float32, host or device).  Computes the
+ * norms, sorts users and items by descending norm (ties by ascending id),
+ * computes for every user bounds lo_j <= v_j <= hi_j on its j-th largest
+ * inner product v_j over P' (j = 1..k_max), and the block arrays
+ * L^j(B) = min_{u in B} lo_j(u) (Equation 1).  The index owns device copies
+ * of everything it needs; the caller may free Q and P on return.
+ * Errors: ARG (null pointer, n < 1, m < 1, d < 1 or d > 128, bad opts),
+ * NONFINITE, OOM, CUDA.  On error *out is NULL.
+ */
+rmips_status rmips_build_index(const float* Q, int64_t n, const float* P, int64_t m,
+                               int32_t d, const rmips_build_opts* opts, void* stream,
+                               rmips_index** out);
+
+/*
+ * rmips_query -- Algorithm 3 (Section 4.3, "Simpfer") for one query.
+ *
+ * q: d floats (host or device).  k: 1..k_max.  seg: NULL for all users.
+ * out_ids: capacity int64 slots (host or device); receives the result ids in
+ * ascending order.  *out_count (host) receives the result size, also when
+ * the status is RMIPS_ERR_CAPACITY (then nothing is written to out_ids).
+ * Synchronises `stream`.  Errors: ARG, K_RANGE, NONFINITE, CAPACITY, CUDA.
+ */
+rmips_status rmips_query(rmips_index* index, const float* q, int32_t k,
+                         const rmips_segment* seg, int64_t* out_ids, int64_t capacity,
+                         int64_t* out_count, void* stream);
+
+/*
+ * rmips_query_batch -- many queries in one call.
+ *
+ * qs: nq x d (host or device), ks: nq values of k (host or device), segs:
+ * NULL or nq segments (host).  Results are concatenated in query order into
+ * out_ids (capacity slots, host or device); out_offsets (host, nq + 1
+ * entries) receives the CSR offsets, so query j's ids are
+ * out_ids[out_offsets[j] .. out_offsets[j+1]).  On RMIPS_ERR_CAPACITY the
+ * offsets are still filled (out_offsets[nq] is the size needed) and out_ids
+ * is left unspecified.  Synchronises `stream`.
+ */
+rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
+                               const int32_t* ks, const rmips_segment* segs,
+                               int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
+                               void* stream);
+
+/* Per-kernel timing of the filter kernel (Lemmas 1-3), for roofline reports. */
+typedef struct {
+  int64_t filter_launches;   /* filter launches since profiling was enabled */
+  double filter_ms;          /* summed CUDA-event durations of those launches,
+                                events recorded on the launching stream */
+  double filter_alg_bytes;   /* algorithmic bytes they had to move: 8 bytes of
+                                block header and L^k(B) per block, plus per
+                                tested user its row (d x element size), its
+                                (lo, hi) pair (8 bytes), its norm (4 bytes,
+                                P' index only) and 4 bytes per listed user */
+  int64_t users_tested;      /* users of unpruned blocks */
+  int64_t blocks_pruned;     /* blocks pruned by Lemma 3 */
+  int64_t blocks_total;      /* blocks examined */
+} rmips_profile;
+
+/* Turns filter timing on (resetting the counters) or off.  While on, every
+   query records a CUDA event pair around each filter launch. */
+rmips_status rmips_profile_enable(rmips_index* index, int32_t enable);
+
+/* Reads the accumulated filter timing. */
+rmips_status rmips_profile_read(const rmips_index* index, rmips_profile* out);
+
+/* Sizes and build statistics of an index. */
+rmips_status rmips_index_get_info(const rmips_index* index, rmips_index_info* out);
+
+/* Counters of the most recent rmips_query on this index (host thread safe,
+   but "most recent" is only meaningful without concurrent queries). */
+rmips_status rmips_last_query_stats(const rmips_index* index, rmips_query_stats* out);
+
+/*
+ * rmips_index_export -- copy one index array to host memory (for tests and
+ * inspection).  field: 0 permQ (int32 [n], sorted position -> original id),
+ * 1 permP (int32 [m]), 2 lower bounds (float [k_max][n], sorted positions),
+ * 3 upper bounds (float [k_max][n]), 4 block minima L^j(B) (float
+ * [k_max][n_blocks]), 5 block headers (float [n_blocks], upper bound of the
+ * first user's norm), 6 user norms rounded up (float [n]), 7 item norms
+ * rounded up (float [m]), 8 incomplete flags (uint8 [n]).
+ * bytes must equal the field's size.  Synchronises the index's device.
+ */
+rmips_status rmips_index_export(const rmips_index* index, int32_t field, void* host_dst,
+                                int64_t bytes);
+
+/* Releases every device and host resource of the index.  NULL is ignored. */
+void rmips_free_index(rmips_index* index);
+
+/* Static description of a status code. */
+const char* rmips_status_string(rmips_status status);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* rmips_last_error(void);
+
+/*
+ * rmips_exact_sign_host -- sign of u.a - u.b in exact arithmetic, computed on
+ * the host with the same integer accumulator the device recheck uses.
+ * Returns -1, 0 or +1.  Exposed so the tie-breaking arithmetic can be checked
+ * without a GPU.  Ordinary host function; d in 1..256.
+ */
+int32_t rmips_exact_sign_host(const float* u, const float* a, const float* b, int32_t d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMIPS_H */

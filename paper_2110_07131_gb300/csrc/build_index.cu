@@ -1,0 +1,420 @@
+// Offline index build: Algorithm 1 ("Pre-processing of Simpfer", Section 4.1).
+//
+//  1. norms of every user and item (float64, squares summed in index order);
+//  2. users and items sorted by descending norm, ties by ascending id;
+//  3. for every user, its top-KC items by float32 inner product over P'
+//     (the first p' sorted items; all of P for a full-P index), kept with a
+//     running threshold (one user per thread, items streamed through shared
+//     memory);
+//  4. the KC candidates re-dotted in float64 with a rounding bound, giving
+//     lo_j <= v_j <= hi_j for the j-th largest inner product v_j, and a proof
+//     that no item outside the candidates can reach the k_max-th place;
+//  5. blocks of consecutive users with L^j(B) = min lo_j (Equation 1).
+#include <chrono>
+#include <climits>
+#include <cmath>
+
+#include "rmips_internal.cuh"
+
+namespace rmips {
+namespace {
+
+constexpr float kInf = __builtin_huge_valf();
+
+// --- 1. norms ----------------------------------------------------------------
+__global__ void k_norms(const float* __restrict__ X, int64_t rows, int64_t rows_pad, int d,
+                        float* __restrict__ nrm_up, unsigned long long* __restrict__ key,
+                        int32_t* __restrict__ ids, int* __restrict__ bad) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= rows_pad) return;
+  if (r >= rows) {
+    key[r] = ~0ull;
+    ids[r] = INT_MAX;
+    return;
+  }
+  const float* x = X + r * d;
+  double acc = 0.0;
+  bool fin = true;
+  for (int i = 0; i < d; ++i) {
+    float v = x[i];
+    fin = fin && isfinite(v);
+    double dv = (double)v;
+    acc = fma(dv, dv, acc);   // dv*dv is exact, so this equals acc + dv*dv rounded once
+  }
+  if (!fin) atomicOr(bad, 1);
+  double s = sqrt(acc);
+  // Upper bound of the exact norm: the float64 value is within (d/2 + 2) ulps.
+  nrm_up[r] = __double2float_ru(__dmul_ru(s, 1.0 + (d + 8) * 0x1p-52));
+  key[r] = ~(unsigned long long)__double_as_longlong(s);   // s >= 0: ascending key = descending norm
+  ids[r] = (int32_t)r;
+}
+
+// --- 2. sort: bitonic network over (key, id), both ascending ----------------------
+__global__ void k_bitonic(unsigned long long* __restrict__ key, int32_t* __restrict__ id, int64_t N2,
+                          int64_t j, int64_t kk) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N2) return;
+  int64_t p = i ^ j;
+  if (p <= i) return;
+  unsigned long long a = key[i], b = key[p];
+  int32_t ia = id[i], ib = id[p];
+  bool gt = (a > b) || (a == b && ia > ib);
+  bool up = (i & kk) == 0;
+  if (gt == up) {
+    key[i] = b; key[p] = a;
+    id[i] = ib; id[p] = ia;
+  }
+}
+
+// --- gather rows / norms into sorted order ----------------------------------------
+__global__ void k_gather(const float* __restrict__ src, const int32_t* __restrict__ perm, int64_t rows, int d,
+                         float* __restrict__ dst, const float* __restrict__ nsrc, float* __restrict__ ndst) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= rows * d) return;
+  int64_t r = e / d;
+  int c = (int)(e - r * d);
+  int64_t o = perm[r];
+  dst[e] = src[o * d + c];
+  if (c == 0) ndst[r] = nsrc[o];
+}
+
+__device__ __forceinline__ void store_rn(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_rn(__half* p, float v) { *p = __float2half_rn(v); }
+
+template <class H>
+__global__ void k_to_half(const float* __restrict__ src, int64_t count, H* __restrict__ dst) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  store_rn(dst + e, src[e]);
+}
+
+// --- 3. top-KC candidates per user (float32, one user per thread) -----------------
+// Items stream through shared memory in tiles of TP, stored transposed so that
+// every thread reads the same float4 (a broadcast) holding component i of four
+// consecutive items.  The KC best (value, position) pairs of each thread live
+// in a shared-memory column; an item is inserted only when strictly above the
+// current minimum, so every item left out has a value <= the final minimum.
+constexpr int TP = 64;
+constexpr int TS = TP + 4;
+constexpr int TOPK_THREADS = 128;
+
+template <int DP>
+__global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__ Qs, const float* __restrict__ Ps,
+                                                       int64_t n, int64_t pp, int d, float* __restrict__ cval,
+                                                       int32_t* __restrict__ cid) {
+  extern __shared__ __align__(16) float topk_smem[];
+  float* tile = topk_smem;                                                   // [DP][TS]
+  float (*lv)[TOPK_THREADS] = reinterpret_cast<float (*)[TOPK_THREADS]>(topk_smem + DP * TS);
+  int32_t (*li)[TOPK_THREADS] =
+      reinterpret_cast<int32_t (*)[TOPK_THREADS]>(topk_smem + DP * TS + RMIPS_KC * TOPK_THREADS);
+  const int t = threadIdx.x;
+  const int64_t u = blockIdx.x * (int64_t)TOPK_THREADS + t;
+  float ur[DP];
+#pragma unroll
+  for (int i = 0; i < DP; ++i) ur[i] = (u < n && i < d) ? Qs[u * d + i] : 0.f;
+#pragma unroll
+  for (int s = 0; s < RMIPS_KC; ++s) {
+    lv[s][t] = -kInf;
+    li[s][t] = -1;
+  }
+  float thr = -kInf;
+  int minslot = 0;
+  for (int64_t p0 = 0; p0 < pp; p0 += TP) {
+    __syncthreads();
+    for (int e = t; e < DP * TP; e += TOPK_THREADS) {
+      int i = e / TP, j = e % TP;
+      int64_t p = p0 + j;
+      tile[i * TS + j] = (i < d && p < pp) ? Ps[p * d + i] : 0.f;
+    }
+    __syncthreads();
+    const int jmax = (int)((pp - p0) < TP ? (pp - p0) : TP);
+    for (int j = 0; j < jmax; j += 4) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int i = 0; i < DP; ++i) {
+        float4 pv = *reinterpret_cast<const float4*>(&tile[i * TS + j]);
+        a0 = fmaf(ur[i], pv.x, a0);
+        a1 = fmaf(ur[i], pv.y, a1);
+        a2 = fmaf(ur[i], pv.z, a2);
+        a3 = fmaf(ur[i], pv.w, a3);
+      }
+      float av[4] = {a0, a1, a2, a3};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (j + r < jmax && av[r] > thr) {
+          lv[minslot][t] = av[r];
+          li[minslot][t] = (int32_t)(p0 + j + r);
+          thr = lv[0][t];
+          minslot = 0;
+          for (int s = 1; s < RMIPS_KC; ++s) {
+            float v = lv[s][t];
+            if (v < thr) { thr = v; minslot = s; }
+          }
+        }
+      }
+    }
+  }
+  if (u < n) {
+    for (int s = 0; s < RMIPS_KC; ++s) {
+      cval[u * RMIPS_KC + s] = lv[s][t];
+      cid[u * RMIPS_KC + s] = li[s][t];
+    }
+  }
+}
+
+// Bitonic sort of one value per lane, descending across the warp.
+__device__ __forceinline__ double warp_sort_desc(double x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      double y = __shfl_xor_sync(0xffffffffu, x, j);
+      bool keep_max = (((lane & j) == 0) == ((lane & k) == 0));
+      x = keep_max ? fmax(x, y) : fmin(x, y);
+    }
+  }
+  return x;
+}
+
+// --- 4. float64 re-dot, bounds, completeness proof (one warp per user) ------------
+__global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict__ Ps,
+                           const float* __restrict__ cval, const int32_t* __restrict__ cid,
+                           const float* __restrict__ unorm, float pn0, int64_t n, int64_t pp, int d,
+                           int dp, int k_max, int full_p, float2* __restrict__ Lb,
+                           int32_t* __restrict__ cand, uint8_t* __restrict__ incomp,
+                           unsigned long long* __restrict__ n_incomplete) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const float v = cval[w * RMIPS_KC + lane];
+  const int32_t id = cid[w * RMIPS_KC + lane];
+  double lo = -INFINITY, hi = -INFINITY;
+  if (id >= 0) {
+    const float* u = Qs + w * d;
+    const float* p = Ps + (int64_t)id * d;
+    double s = 0.0, a = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double x = (double)u[i], y = (double)p[i];
+      s = fma(x, y, s);
+      a = fma(fabs(x), fabs(y), a);
+    }
+    double beta = __dmul_ru(a, 2.0 * (d + 2) * 0x1p-53);
+    lo = __dsub_rd(s, beta);
+    hi = __dadd_ru(s, beta);
+  }
+  const double lo_s = warp_sort_desc(lo);
+  const double hi_s = warp_sort_desc(hi);
+  const double v_s = warp_sort_desc(id >= 0 ? (double)v : -INFINITY);
+  // Items never kept have float32 value <= the KC-th kept value t_K; each float32
+  // value is within E = (dp + 2) 2^-24 ||u|| max||p|| of the exact one, so if
+  // t_K + E <= t_kmax - E, no item outside the list can exceed the k_max-th
+  // largest exact value among the kept ones.
+  bool complete = pp <= RMIPS_KC;
+  if (!complete) {
+    double tk = __shfl_sync(0xffffffffu, v_s, k_max - 1);
+    double tK = __shfl_sync(0xffffffffu, v_s, RMIPS_KC - 1);
+    double E = __dmul_ru(__dmul_ru((double)(dp + 2) * 0x1p-24, (double)unorm[w]), (double)pn0);
+    complete = __dadd_ru(tK, E) <= __dsub_rd(tk, E);
+  }
+  if (lane < k_max) {
+    float flo = __double2float_rd(lo_s);
+    float fhi = (full_p && complete) ? __double2float_ru(hi_s) : kInf;
+    Lb[(int64_t)lane * n + w] = make_float2(flo, fhi);
+  }
+  if (full_p) {
+    cand[w * RMIPS_KC + lane] = id;
+    if (lane == 0) {
+      incomp[w] = complete ? 0 : 1;
+      if (!complete) atomicAdd(n_incomplete, 1ull);
+    }
+  }
+}
+
+// --- 5. blocks (Equation 1) --------------------------------------------------------
+__global__ void k_blocks(const float2* __restrict__ Lb, const float* __restrict__ unorm, int64_t n, int bs,
+                         int64_t nb, int k_max, float* __restrict__ LB, float* __restrict__ hdr) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nb * k_max) return;
+  int j = (int)(e / nb);
+  int64_t b = e - (int64_t)j * nb;
+  int64_t lo = b * bs, hi = lo + bs < n ? lo + bs : n;
+  float mn = kInf;
+  for (int64_t i = lo; i < hi; ++i) mn = fminf(mn, Lb[(int64_t)j * n + i].x);
+  LB[(int64_t)j * nb + b] = mn;
+  if (j == 0) hdr[b] = unorm[lo];
+}
+
+inline unsigned grid_for(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+rmips_status sort_by_norm(const float* X, int64_t rows, int d, cudaStream_t st, float* nrm_up,
+                          int32_t* order, int* d_bad) {
+  int64_t N2 = 1;
+  while (N2 < rows) N2 <<= 1;
+  unsigned long long* key = nullptr;
+  int32_t* ids = nullptr;
+  RMIPS_TRY_CUDA(cudaMallocAsync((void**)&key, N2 * sizeof(unsigned long long), st));
+  RMIPS_TRY_CUDA(cudaMallocAsync((void**)&ids, N2 * sizeof(int32_t), st));
+  k_norms<<<grid_for(N2, 256), 256, 0, st>>>(X, rows, N2, d, nrm_up, key, ids, d_bad);
+  for (int64_t kk = 2; kk <= N2; kk <<= 1)
+    for (int64_t j = kk >> 1; j > 0; j >>= 1)
+      k_bitonic<<<grid_for(N2, 256), 256, 0, st>>>(key, ids, N2, j, kk);
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(order, ids, rows * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  RMIPS_TRY_CUDA(cudaFreeAsync(key, st));
+  RMIPS_TRY_CUDA(cudaFreeAsync(ids, st));
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  return RMIPS_OK;
+}
+
+template <int DP>
+cudaError_t launch_topk(const float* Qs, const float* Ps, int64_t n, int64_t pp, int d, float* cval,
+                        int32_t* cid, cudaStream_t st) {
+  const size_t smem = (size_t)(DP * TS + 2 * RMIPS_KC * TOPK_THREADS) * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_topk<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_topk<DP><<<grid_for(n, TOPK_THREADS), TOPK_THREADS, smem, st>>>(Qs, Ps, n, pp, d, cval, cid);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace rmips
+
+using namespace rmips;
+
+extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float* P, int64_t m, int32_t d,
+                                          const rmips_build_opts* opts, void* stream, rmips_index** out) {
+  if (out) *out = nullptr;
+  if (!Q || !P || !out || !opts) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  if (n < 1 || m < 1 || d < 1 || d > RMIPS_DMAX || n > INT_MAX / 2 || m > INT_MAX / 2) {
+    set_error("n, m must be >= 1 and < 2^30, d in [1, 128]");
+    return RMIPS_ERR_ARG;
+  }
+  int bs = opts->block_size == 0 ? 32 : opts->block_size;
+  if (opts->k_max < 1 || opts->k_max > RMIPS_KMAX_LIMIT || !(bs == 32 || bs == 64 || bs == 128 || bs == 256) ||
+      opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 || opts->reserved != 0) {
+    set_error("invalid build options (k_max 1..28, block_size 32/64/128/256, precision 0..2)");
+    return RMIPS_ERR_ARG;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  rmips_index* idx = new rmips_index();
+  idx->n = n; idx->m = m; idx->d = d; idx->k_max = opts->k_max; idx->bs = bs;
+  idx->precision = opts->precision;
+  idx->pp = (opts->p_prime == 0 || opts->p_prime >= m) ? m : opts->p_prime;
+  idx->full_p = idx->pp == m ? 1 : 0;
+  idx->nb = (n + bs - 1) / bs;
+  cudaGetDevice(&idx->device);
+
+  auto fail = [&](rmips_status s) { rmips_free_index(idx); return s; };
+  const bool q_dev = is_device_ptr(Q), p_dev = is_device_ptr(P);
+  float *Qin = nullptr, *Pin = nullptr, *qn = nullptr, *pn = nullptr, *cval = nullptr;
+  int32_t* cid = nullptr;
+  int *d_bad = nullptr;
+  unsigned long long* d_incomp = nullptr;
+  rmips_status s = RMIPS_OK;
+#define TRY(expr)                                                                  \
+  do {                                                                             \
+    cudaError_t e__ = (expr);                                                      \
+    if (e__ != cudaSuccess) {                                                      \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));              \
+      s = (e__ == cudaErrorMemoryAllocation) ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;     \
+      goto cleanup;                                                                \
+    }                                                                              \
+  } while (0)
+  {
+    const int64_t pad = 32 * (int64_t)d;  // one spare chunk so bulk copies of the tail stay in bounds
+    TRY(dalloc(idx, &idx->Qs, n * d + pad));
+    TRY(dalloc(idx, &idx->Ps, m * d + pad));
+    TRY(cudaMemsetAsync(idx->Qs + n * d, 0, pad * sizeof(float), st));
+    TRY(cudaMemsetAsync(idx->Ps + m * d, 0, pad * sizeof(float), st));
+    TRY(dalloc(idx, &idx->unorm, n));
+    TRY(dalloc(idx, &idx->pnorm, m));
+    TRY(dalloc(idx, &idx->permQ, n));
+    TRY(dalloc(idx, &idx->permP, m));
+    TRY(dalloc(idx, &idx->Lb, (size_t)idx->k_max * n));
+    TRY(dalloc(idx, &idx->LB, (size_t)idx->k_max * idx->nb));
+    TRY(dalloc(idx, &idx->hdr, idx->nb));
+    if (idx->full_p) {
+      TRY(dalloc(idx, &idx->cand, (size_t)n * RMIPS_KC));
+      TRY(dalloc(idx, &idx->incomp, n));
+    }
+    TRY(cudaMallocAsync((void**)&qn, n * sizeof(float), st));
+    TRY(cudaMallocAsync((void**)&pn, m * sizeof(float), st));
+    TRY(cudaMallocAsync((void**)&d_bad, 16, st));
+    TRY(cudaMallocAsync((void**)&d_incomp, 16, st));
+    TRY(cudaMemsetAsync(d_bad, 0, 16, st));
+    TRY(cudaMemsetAsync(d_incomp, 0, 16, st));
+    const float* Qsrc = Q;
+    const float* Psrc = P;
+    if (!q_dev) {
+      TRY(cudaMallocAsync((void**)&Qin, n * d * sizeof(float), st));
+      TRY(cudaMemcpyAsync(Qin, Q, n * d * sizeof(float), cudaMemcpyHostToDevice, st));
+      Qsrc = Qin;
+    }
+    if (!p_dev) {
+      TRY(cudaMallocAsync((void**)&Pin, m * d * sizeof(float), st));
+      TRY(cudaMemcpyAsync(Pin, P, m * d * sizeof(float), cudaMemcpyHostToDevice, st));
+      Psrc = Pin;
+    }
+    // 1-2: norms and sort
+    s = sort_by_norm(Qsrc, n, d, st, qn, idx->permQ, d_bad);
+    if (s != RMIPS_OK) goto cleanup;
+    s = sort_by_norm(Psrc, m, d, st, pn, idx->permP, d_bad);
+    if (s != RMIPS_OK) goto cleanup;
+    k_gather<<<grid_for(n * d, 256), 256, 0, st>>>(Qsrc, idx->permQ, n, d, idx->Qs, qn, idx->unorm);
+    k_gather<<<grid_for(m * d, 256), 256, 0, st>>>(Psrc, idx->permP, m, d, idx->Ps, pn, idx->pnorm);
+    TRY(cudaGetLastError());
+    int h_bad = 0;
+    TRY(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(&idx->pn0, idx->pnorm, sizeof(float), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    if (h_bad) { set_error("non-finite value in Q or P"); s = RMIPS_ERR_NONFINITE; goto cleanup; }
+    if (idx->precision != RMIPS_FP32) {
+      TRY(dalloc(idx, (uint16_t**)&idx->Qh, n * d + pad));
+      TRY(cudaMemsetAsync((uint16_t*)idx->Qh + n * d, 0, pad * 2, st));
+      if (idx->precision == RMIPS_BF16)
+        k_to_half<__nv_bfloat16><<<grid_for(n * d, 256), 256, 0, st>>>(idx->Qs, n * d, (__nv_bfloat16*)idx->Qh);
+      else
+        k_to_half<__half><<<grid_for(n * d, 256), 256, 0, st>>>(idx->Qs, n * d, (__half*)idx->Qh);
+    }
+    // 3: candidates
+    TRY(cudaMallocAsync((void**)&cval, (size_t)n * RMIPS_KC * sizeof(float), st));
+    TRY(cudaMallocAsync((void**)&cid, (size_t)n * RMIPS_KC * sizeof(int32_t), st));
+    int dp;
+    if (d <= 16) { dp = 16; TRY(launch_topk<16>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    else if (d <= 32) { dp = 32; TRY(launch_topk<32>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    else if (d <= 52) { dp = 52; TRY(launch_topk<52>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    else if (d <= 64) { dp = 64; TRY(launch_topk<64>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    else { dp = 128; TRY(launch_topk<128>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    // 4: bounds
+    k_finalize<<<grid_for(n * 32, 256), 256, 0, st>>>(idx->Qs, idx->Ps, cval, cid, idx->unorm, idx->pn0, n,
+                                                      idx->pp, d, dp, idx->k_max, idx->full_p, idx->Lb,
+                                                      idx->cand, idx->incomp, d_incomp);
+    // 5: blocks
+    k_blocks<<<grid_for(idx->nb * idx->k_max, 256), 256, 0, st>>>(idx->Lb, idx->unorm, n, bs, idx->nb,
+                                                                   idx->k_max, idx->LB, idx->hdr);
+    TRY(cudaGetLastError());
+    unsigned long long h_incomp = 0;
+    TRY(cudaMemcpyAsync(&h_incomp, d_incomp, sizeof(h_incomp), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    idx->incomplete = (int64_t)h_incomp;
+  }
+cleanup:
+  if (Qin) cudaFreeAsync(Qin, st);
+  if (Pin) cudaFreeAsync(Pin, st);
+  if (qn) cudaFreeAsync(qn, st);
+  if (pn) cudaFreeAsync(pn, st);
+  if (cval) cudaFreeAsync(cval, st);
+  if (cid) cudaFreeAsync(cid, st);
+  if (d_bad) cudaFreeAsync(d_bad, st);
+  if (d_incomp) cudaFreeAsync(d_incomp, st);
+#undef TRY
+  if (s != RMIPS_OK) return fail(s);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("stream synchronisation failed after build");
+    return fail(RMIPS_ERR_CUDA);
+  }
+  idx->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = idx;
+  return RMIPS_OK;
+}

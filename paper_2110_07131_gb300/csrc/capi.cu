@@ -1,0 +1,203 @@
+// C ABI glue: errors, workspaces, index inspection and release.
+#include <cstdio>
+
+#include "rmips_internal.cuh"
+
+namespace rmips {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error state of the query
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void destroy_workspace(Workspace* ws) {
+  if (!ws) return;
+  cudaFree(ws->yes);
+  cudaFree(ws->todo);
+  cudaFree(ws->bitmap);
+  cudaFree(ws->ctr);
+  cudaFree(ws->dq);
+  cudaFree(ws->dk);
+  cudaFree(ws->dqn);
+  cudaFree(ws->deps);
+  cudaFree(ws->doffs);
+  cudaFree(ws->dout);
+  cudaFreeHost(ws->h_ctr);
+  cudaFreeHost(ws->h_offs);
+  cudaFreeHost(ws->h_out);
+  for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
+  delete ws;
+}
+
+Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
+  {
+    std::lock_guard<std::mutex> lk(idx->mu);
+    if (!idx->pool.empty()) {
+      Workspace* ws = idx->pool.back();
+      idx->pool.pop_back();
+      return ws;
+    }
+  }
+  Workspace* ws = new Workspace();
+  const int64_t n = idx->n;
+  const int64_t nw = n / 32 + 1;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ws->yes, n * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ws->todo, n * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ws->bitmap, nw * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ws->ctr, C_NCOUNTERS * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(ws->bitmap, 0, nw * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(ws->ctr, 0, C_NCOUNTERS * sizeof(long long));
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_ctr, C_NCOUNTERS * sizeof(long long), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_out, n * sizeof(long long), cudaHostAllocMapped);
+  if (e == cudaSuccess) ws->cap_hout = n;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
+    *st = e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
+    destroy_workspace(ws);
+    return nullptr;
+  }
+  return ws;
+}
+
+void release_workspace(rmips_index* idx, Workspace* ws) {
+  std::lock_guard<std::mutex> lk(idx->mu);
+  idx->pool.push_back(ws);
+}
+
+}  // namespace rmips
+
+using namespace rmips;
+
+extern "C" const char* rmips_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* rmips_status_string(rmips_status s) {
+  switch (s) {
+    case RMIPS_OK: return "ok";
+    case RMIPS_ERR_ARG: return "invalid argument";
+    case RMIPS_ERR_K_RANGE: return "k outside [1, k_max]";
+    case RMIPS_ERR_NONFINITE: return "non-finite input";
+    case RMIPS_ERR_OOM: return "out of memory";
+    case RMIPS_ERR_CAPACITY: return "output capacity too small";
+    case RMIPS_ERR_TIMEOUT: return "device wait timed out";
+    case RMIPS_ERR_CUDA: return "CUDA runtime error";
+    case RMIPS_ERR_INTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+extern "C" rmips_status rmips_index_get_info(const rmips_index* idx, rmips_index_info* out) {
+  if (!idx || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  rmips_index_info i{};
+  i.n = idx->n;
+  i.m = idx->m;
+  i.d = idx->d;
+  i.k_max = idx->k_max;
+  i.block_size = idx->bs;
+  i.precision = idx->precision;
+  i.n_blocks = idx->nb;
+  i.p_prime = idx->pp;
+  i.incomplete = idx->incomplete;
+  i.device_bytes = idx->device_bytes;
+  i.build_ms = idx->build_ms;
+  *out = i;
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_last_query_stats(const rmips_index* idx, rmips_query_stats* out) {
+  if (!idx || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  rmips_index* m = const_cast<rmips_index*>(idx);
+  std::lock_guard<std::mutex> lk(m->mu);
+  *out = m->last_stats;
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_index_export(const rmips_index* idx, int32_t field, void* dst, int64_t bytes) {
+  if (!idx || !dst) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  const void* src = nullptr;
+  int64_t need = 0;
+  std::vector<float2> tmp;
+  switch (field) {
+    case 0: src = idx->permQ; need = idx->n * 4; break;
+    case 1: src = idx->permP; need = idx->m * 4; break;
+    case 2: case 3: need = (int64_t)idx->k_max * idx->n * 4; break;
+    case 4: src = idx->LB; need = (int64_t)idx->k_max * idx->nb * 4; break;
+    case 5: src = idx->hdr; need = idx->nb * 4; break;
+    case 6: src = idx->unorm; need = idx->n * 4; break;
+    case 7: src = idx->pnorm; need = idx->m * 4; break;
+    case 8: src = idx->incomp; need = idx->full_p ? idx->n : 0; break;
+    default: set_error("unknown field"); return RMIPS_ERR_ARG;
+  }
+  if (bytes != need) { set_error("byte count does not match the field size"); return RMIPS_ERR_ARG; }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != idx->device) cudaSetDevice(idx->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    if (field == 2 || field == 3) {
+      tmp.resize((size_t)idx->k_max * idx->n);
+      e = cudaMemcpy(tmp.data(), idx->Lb, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost);
+      float* f = (float*)dst;
+      for (size_t i = 0; i < tmp.size(); ++i) f[i] = field == 2 ? tmp[i].x : tmp[i].y;
+    } else if (need > 0) {
+      e = cudaMemcpy(dst, src, need, cudaMemcpyDeviceToHost);
+    }
+  }
+  if (prev != idx->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return RMIPS_ERR_CUDA; }
+  return RMIPS_OK;
+}
+
+extern "C" void rmips_free_index(rmips_index* idx) {
+  if (!idx) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != idx->device) cudaSetDevice(idx->device);
+  cudaDeviceSynchronize();
+  for (Workspace* ws : idx->pool) destroy_workspace(ws);
+  idx->pool.clear();
+  cudaFree(idx->Qs);
+  cudaFree(idx->Qh);
+  cudaFree(idx->Ps);
+  cudaFree(idx->unorm);
+  cudaFree(idx->pnorm);
+  cudaFree(idx->permQ);
+  cudaFree(idx->permP);
+  cudaFree(idx->Lb);
+  cudaFree(idx->cand);
+  cudaFree(idx->incomp);
+  cudaFree(idx->LB);
+  cudaFree(idx->hdr);
+  if (prev != idx->device) cudaSetDevice(prev);
+  delete idx;
+}
+
+extern "C" int32_t rmips_exact_sign_host(const float* u, const float* a, const float* b, int32_t d) {
+  if (!u || !a || !b || d < 1 || d > 256) return 0;
+  return (int32_t)exact_sign_diff(u, a, b, d);
+}
+
+extern "C" rmips_status rmips_profile_enable(rmips_index* idx, int32_t enable) {
+  if (!idx) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(idx->mu);
+  idx->prof_on = enable ? 1 : 0;
+  idx->prof = rmips_profile{};
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_profile_read(const rmips_index* idx, rmips_profile* out) {
+  if (!idx || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  rmips_index* m = const_cast<rmips_index*>(idx);
+  std::lock_guard<std::mutex> lk(m->mu);
+  *out = m->prof;
+  return RMIPS_OK;
+}

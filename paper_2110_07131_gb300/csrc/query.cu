@@ -1,0 +1,771 @@
+// Online phase: Algorithm 3 ("Simpfer", Section 4.3) on the GPU.
+//
+// Per query q (with k):
+//   k_qprep    ||q|| (float64, rounded up), finiteness check, error slack;
+//   k_filter   Lemma 3 per block (prune iff ||u_first|| ||q|| < L^k(B)), then
+//              for every user of a surviving block u.q with a rigorous error
+//              bound e:  no  if u.q + e < lo_k(u)              (Lemma 1),
+//                        yes if u.q - e >= hi_k(u)             (full-P index)
+//                        yes if u.q - e >= ||u|| ||p_k||       (Lemma 2, P' index),
+//              anything else goes to the todo list.  User rows are staged
+//              32 at a time into shared memory by the TMA engine
+//              (cp.async.bulk), double-buffered per warp;
+//   k_resolve  todo users: exact count over the user's proven candidate list
+//              (full-P index), else Algorithm 2 -- a norm-ordered scan of P
+//              with Corollary 1 (stop once ||u|| ||p_j|| <= u.q) and
+//              Corollary 2 (stop once k items are strictly above u.q);
+//              comparisons within their rounding bound are decided exactly;
+//   k_emit     sorted positions -> caller ids, optional segment filter,
+//              ascending order, capacity check, CSR offsets.
+#include <climits>
+#include <cmath>
+
+#include "rmips_internal.cuh"
+
+namespace rmips {
+namespace {
+
+constexpr float kInf = __builtin_huge_valf();
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int FW = 4;                      // warps per filter CTA
+constexpr int EMIT_THREADS = 1024;
+constexpr int EMIT_SORT_CAP = 8192;
+
+// Relative error factor of a length-d float32 dot product whose inputs were
+// rounded to a format with unit roundoff u_in (0 for float32 inputs):
+// |fl(sum x_i q_i) - sum u_i q_i| <= (u_in + gamma_d (1 + u_in)) sum |u_i q_i|,
+// gamma_d = d 2^-24 / (1 - d 2^-24); the computed sum |x_i q_i| is itself
+// within (1 + u_in)(1 + gamma_d) of the exact one.  (d + 4) 2^-24 covers
+// gamma_d and its own rounding for d <= 256.
+inline float err_factor(int d, int precision) {
+  double u_in = precision == RMIPS_BF16 ? 0x1p-8 : precision == RMIPS_FP16 ? 0x1p-11 : 0.0;
+  double g = (d + 4) * 0x1p-24;
+  double f = (u_in + g * (1.0 + u_in)) / (1.0 - u_in - g) * (1.0 + 0x1p-20);
+  return (float)f;
+}
+
+struct Common {
+  const float* Qs;
+  const void* Qrows;           // Qs (float32) or the reduced-precision copy
+  const float* Ps;
+  const float2* Lb;
+  const float* LB;
+  const float* hdr;
+  const float* unorm;
+  const float* pnorm;
+  const int32_t* cand;
+  const uint8_t* incomp;
+  const int32_t* permQ;
+  int64_t n, m, nb;
+  int d, bs, k_max, full_p;
+  float cg;                    // relative error factor of the filter dot product
+  float cg32;                  // same for float32 inputs (verification)
+  // query staging
+  const float* dq;
+  const int32_t* dk;
+  float* dqn;
+  float* deps;
+  // workspace
+  int32_t* yes;
+  int32_t* todo;
+  long long* ctr;
+};
+
+// --- query preparation ---------------------------------------------------------------
+__global__ void k_qprep(Common c, int64_t nq, int precision) {
+  const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (j >= nq) return;
+  const float* q = c.dq + j * c.d;
+  double acc = 0.0;
+  float qmax = 0.f;
+  bool fin = true;
+  if (lane == 0) {
+    for (int i = 0; i < c.d; ++i) {
+      float v = q[i];
+      fin = fin && isfinite(v);
+      acc = fma((double)v, (double)v, acc);
+      qmax = fmaxf(qmax, fabsf(v));
+    }
+    int k = c.dk[j];
+    if (!fin) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_NONFINITE);
+    if (k < 1 || k > c.k_max) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_INTERNAL);
+    c.dqn[j] = __double2float_ru(__dmul_ru(sqrt(acc), 1.0 + (c.d + 8) * 0x1p-52));
+    // Absolute slack: float32 products below the normal range lose up to 2^-150
+    // each; FP16 storage rounds values below 2^-14 with absolute error 2^-25.
+    double sub = (precision == RMIPS_FP16) ? 0x1p-25 : (precision == RMIPS_BF16 ? 0x1p-133 : 0.0);
+    c.deps[j] = __double2float_ru((c.d + 2) * (sub * qmax + 0x1p-148));
+  }
+}
+
+// --- filter ------------------------------------------------------------------------
+template <class T, bool FULLP>
+__global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* sq = reinterpret_cast<float*>(smem);                        // [RMIPS_DMAX]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 512);          // [FW][2]
+  unsigned char* bufs = smem + 512 + FW * 2 * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int d = c.d;
+  const int64_t n = c.n;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_skip = (st0 != 0 && st0 != ST_CAPACITY);                    // bad input: nothing to do
+  }
+  __syncthreads();
+  if (s_skip) return;                                               // uniform across the CTA
+  const int k = c.dk[j];
+  const float* q = c.dq + (int64_t)j * d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) sq[i] = q[i];
+  const float qn = c.dqn[j], qeps = c.deps[j];
+  const float pk = (k <= c.m) ? c.pnorm[k - 1] : -kInf;
+  if (lane == 0) {
+    mbar_init(&bars[warp * 2 + 0], 1);
+    mbar_init(&bars[warp * 2 + 1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint32_t chunk_bytes = 32u * d * (uint32_t)sizeof(T);        // multiple of 16
+  unsigned char* mybuf = bufs + (size_t)warp * 2 * chunk_bytes;
+  const int64_t nchunks = (n + 31) / 32;
+  const int64_t W = (int64_t)gridDim.x * FW;
+  const int64_t w0 = (int64_t)blockIdx.x * FW + warp;
+  const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
+  const float2* Lbk = c.Lb + (int64_t)(k - 1) * n;
+
+  int64_t gbase = 0;       // next group of 32 slots of this warp's chunk sequence
+  int64_t gcur = 0;        // base of the group the mask belongs to
+  uint32_t mask = 0;
+  long long pruned = 0, tested = 0, yesfast = 0, todosum = 0;
+  auto next_chunk = [&]() -> int64_t {
+    while (mask == 0) {
+      if (w0 + gbase * W >= nchunks) return -1;
+      const int64_t ch = w0 + (gbase + lane) * W;
+      bool ok = false;
+      if (ch < nchunks) {
+        const int64_t blk = (ch * 32) / c.bs;
+        ok = !(__fmul_ru(c.hdr[blk], qn) < LBk[blk]);   // Lemma 3, strict
+      }
+      mask = __ballot_sync(FULL, ok);
+      pruned += __popc(__ballot_sync(FULL, ch < nchunks && !ok));
+      gcur = gbase;
+      gbase += 32;
+    }
+    const int bit = __ffs(mask) - 1;
+    mask &= mask - 1;
+    return w0 + (gcur + bit) * W;
+  };
+  auto issue = [&](int64_t ch, int s) {
+    if (lane == 0) {
+      const int64_t rows = (n - ch * 32) < 32 ? (n - ch * 32) : 32;
+      const uint32_t bytes = ((uint32_t)(rows * d * sizeof(T)) + 15u) & ~15u;
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bars[warp * 2 + s], bytes);
+      bulk_g2s(mybuf + (size_t)s * chunk_bytes,
+               reinterpret_cast<const unsigned char*>(c.Qrows) + (size_t)ch * chunk_bytes, bytes,
+               &bars[warp * 2 + s]);
+    }
+  };
+
+  uint32_t phase = 0;      // bit s = parity to wait for on buffer s
+  int s = 0;
+  int64_t cur = next_chunk();
+  if (cur >= 0) issue(cur, 0);
+  while (cur >= 0) {
+    const int64_t nxt = next_chunk();
+    if (nxt >= 0) issue(nxt, s ^ 1);
+    const int64_t pos = cur * 32 + lane;
+    const bool valid = pos < n;
+    const float2 L = valid ? Lbk[pos] : make_float2(kInf, kInf);
+    const float un = (!FULLP && valid) ? c.unorm[pos] : 0.f;
+    bool ok = mbar_wait_bounded(&bars[warp * 2 + s], (phase >> s) & 1u);
+    ok = __all_sync(FULL, ok);
+    if (!ok) {
+      set_status(c.ctr, ST_TIMEOUT);
+      if (nxt >= 0) mbar_wait_bounded(&bars[warp * 2 + (s ^ 1)], (phase >> (s ^ 1)) & 1u);
+      return;
+    }
+    phase ^= 1u << s;
+    const T* row = reinterpret_cast<const T*>(mybuf + (size_t)s * chunk_bytes) + (size_t)lane * d;
+    float g = 0.f, A = 0.f;
+    int r = lane % d;                       // rotated start: lanes hit different banks
+    for (int i = 0; i < d; ++i) {
+      const float uv = to_f32<T>(row[r]);
+      const float qv = sq[r];
+      g = fmaf(uv, qv, g);
+      A = fmaf(fabsf(uv), fabsf(qv), A);
+      r = (r + 1 == d) ? 0 : r + 1;
+    }
+    __syncwarp();
+    bool yes = false, todo = false;
+    if (valid) {
+      const float e = __fmaf_ru(A, c.cg, qeps);
+      const float hi = __fadd_ru(g, e), lo = __fsub_rd(g, e);
+      const bool no = hi < L.x;                                   // Lemma 1 (strict)
+      if (!no) {
+        yes = FULLP ? (lo >= L.y) : (lo >= __fmul_ru(un, pk));    // hi_k, or Lemma 2
+        todo = !yes;
+      }
+    }
+    const uint32_t by = __ballot_sync(FULL, yes), bt = __ballot_sync(FULL, todo);
+    const uint32_t lt = (1u << lane) - 1u;
+    if (by) {
+      long long base = 0;
+      if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
+      base = __shfl_sync(FULL, base, 0);
+      if (yes) c.yes[base + __popc(by & lt)] = (int32_t)pos;
+    }
+    if (bt) {
+      long long base = 0;
+      if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_TODO], (unsigned long long)__popc(bt));
+      base = __shfl_sync(FULL, base, 0);
+      if (todo) c.todo[base + __popc(bt & lt)] = (int32_t)pos;
+    }
+    tested += __popc(__ballot_sync(FULL, valid));
+    yesfast += __popc(by);
+    todosum += __popc(bt);
+    cur = nxt;
+    s ^= 1;
+  }
+  if (lane == 0) {
+    if (pruned) atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)pruned);
+    if (tested) atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)tested);
+    if (yesfast) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)yesfast);
+    if (todosum) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)todosum);
+  }
+}
+
+// --- Algorithm 2 for one user, one warp ----------------------------------------------
+__device__ bool verify_scan(const float* __restrict__ u, float un, const Common& c, const float* sq, int k,
+                            float qeps) {
+  const int lane = threadIdx.x & 31;
+  const int d = c.d;
+  float g = 0.f, A = 0.f;
+  for (int i = 0; i < d; ++i) {
+    g = fmaf(u[i], sq[i], g);
+    A = fmaf(fabsf(u[i]), fabsf(sq[i]), A);
+  }
+  const float tiny = (d + 2) * 0x1p-148f;
+  const float e = __fmaf_ru(A, c.cg32, qeps);
+  const float gl = __fsub_rd(g, e), gh = __fadd_ru(g, e);
+  int above = 0;
+  for (int64_t j0 = 0; j0 < c.m; j0 += 32) {
+    if (__fmul_ru(un, c.pnorm[j0]) <= gl) break;                 // Corollary 1
+    const int64_t jj = j0 + lane;
+    bool gt = false;
+    if (jj < c.m && __fmul_ru(un, c.pnorm[jj]) > gl) {
+      const float* p = c.Ps + jj * d;
+      float sp = 0.f, B = 0.f;
+      for (int i = 0; i < d; ++i) {
+        sp = fmaf(u[i], p[i], sp);
+        B = fmaf(fabsf(u[i]), fabsf(p[i]), B);
+      }
+      const float ep = __fmaf_ru(B, c.cg32, tiny);
+      if (__fsub_rd(sp, ep) > gh) gt = true;
+      else if (__fadd_ru(sp, ep) < gl) gt = false;
+      else gt = cmp_dot(u, p, sq, d, c.ctr) > 0;
+    }
+    above += __popc(__ballot_sync(FULL, gt));
+    if (above >= k) return false;                                 // Corollary 2
+  }
+  return true;
+}
+
+// --- resolve the todo list ------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_resolve(Common c, int j) {
+  __shared__ float sq[RMIPS_DMAX];
+  __shared__ int s_skip;
+  __shared__ long long s_cnt;
+  const int d = c.d;
+  for (int i = threadIdx.x; i < d; i += blockDim.x) sq[i] = c.dq[(int64_t)j * d + i];
+  if (threadIdx.x == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_skip = (st0 != 0 && st0 != ST_CAPACITY);
+    s_cnt = c.ctr[C_TODO];
+  }
+  __syncthreads();
+  if (s_skip) return;                                               // uniform across the CTA
+  const long long cnt = s_cnt;
+  const int k = c.dk[j];
+  const float qeps = c.deps[j];
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < cnt; t += nw) {
+    const int32_t pos = c.todo[t];
+    const float* u = c.Qs + (int64_t)pos * d;
+    bool yes;
+    if (c.full_p && !c.incomp[pos]) {
+      // The candidate list holds every item that can reach u's k_max-th place,
+      // so u is a yes iff fewer than k candidates are strictly above u.q.
+      const int32_t it = c.cand[(int64_t)pos * RMIPS_KC + lane];
+      const bool gt = it >= 0 && cmp_dot(u, c.Ps + (int64_t)it * d, sq, d, c.ctr) > 0;
+      yes = __popc(__ballot_sync(FULL, gt)) < k;
+    } else {
+      yes = verify_scan(u, c.unorm[pos], c, sq, k, qeps);
+    }
+    if (lane == 0 && yes) {
+      long long b = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+      c.yes[b] = pos;
+    }
+  }
+}
+
+// --- emit ----------------------------------------------------------------------------
+struct EmitArgs {
+  const uint32_t* segmask;     // optional allowed-id bitmap (nullptr = all)
+  int64_t seg_lo, seg_hi;      // allowed id range
+  uint32_t* bitmap;            // [n/32 + 1] zero on entry and exit
+  long long* out;              // result ids
+  long long capacity;
+  long long* offs;             // offsets (device-visible; entry j+1 written)
+};
+
+__device__ __forceinline__ bool seg_ok(const EmitArgs& e, int32_t id) {
+  if (id < e.seg_lo || id >= e.seg_hi) return false;
+  if (e.segmask && !((e.segmask[id >> 5] >> (id & 31)) & 1u)) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int j) {
+  __shared__ int32_t keys[EMIT_SORT_CAP];
+  __shared__ int s_warp[EMIT_THREADS / 32];
+  __shared__ long long s_total, s_cnt, s_base;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_bad = (st0 != 0 && st0 != ST_CAPACITY);
+    s_cnt = c.ctr[C_YES];
+    s_base = c.ctr[C_CURSOR];
+  }
+  __syncthreads();
+  const long long cnt = s_cnt;
+  const long long base = s_base;
+  const bool bad = s_bad != 0;
+  long long total = 0;
+  if (bad) {
+    total = 0;
+  } else if (cnt <= EMIT_SORT_CAP) {
+    int N2 = 1;
+    while (N2 < cnt) N2 <<= 1;
+    for (int i = tid; i < N2; i += EMIT_THREADS) {
+      int32_t id = INT_MAX;
+      if (i < cnt) {
+        int32_t v = c.permQ[c.yes[i]];
+        if (seg_ok(e, v)) id = v;
+      }
+      keys[i] = id;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= N2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = tid; i < N2; i += EMIT_THREADS) {
+          int p = i ^ jj;
+          if (p > i) {
+            int32_t a = keys[i], b = keys[p];
+            if ((a > b) == ((i & kk) == 0)) { keys[i] = b; keys[p] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (tid == 0) {
+      int lo = 0, hi = N2;                 // first INT_MAX
+      while (lo < hi) { int mid = (lo + hi) >> 1; if (keys[mid] == INT_MAX) hi = mid; else lo = mid + 1; }
+      s_total = lo;
+    }
+    __syncthreads();
+    total = s_total;
+    if (base + total <= e.capacity) {
+      for (int i = tid; i < total; i += EMIT_THREADS) e.out[base + i] = keys[i];
+    }
+  } else {
+    for (long long i = tid; i < cnt; i += EMIT_THREADS) {
+      int32_t v = c.permQ[c.yes[i]];
+      if (seg_ok(e, v)) atomicOr(&e.bitmap[v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    const int64_t nw = (c.n + 31) / 32;
+    const int64_t per = (nw + EMIT_THREADS - 1) / EMIT_THREADS;
+    const int64_t w0 = tid * per, w1 = (w0 + per < nw) ? w0 + per : nw;
+    int local = 0;
+    for (int64_t w = w0; w < w1; ++w) local += __popc(__ldcg(&e.bitmap[w]));
+    // block-wide exclusive scan of `local`
+    int x = local;
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int v = s_warp[lane];
+      for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, v, o); if (lane >= o) v += y; }
+      s_warp[lane] = v;
+    }
+    __syncthreads();
+    const long long excl = (long long)(x - local) + (wid ? s_warp[wid - 1] : 0);
+    total = s_warp[31];
+    if (base + total <= e.capacity) {
+      long long o = base + excl;
+      for (int64_t w = w0; w < w1; ++w) {
+        uint32_t word = __ldcg(&e.bitmap[w]);
+        while (word) {
+          int b = __ffs(word) - 1;
+          word &= word - 1;
+          e.out[o++] = w * 32 + b;
+        }
+      }
+    }
+    for (int64_t w = w0; w < w1; ++w) e.bitmap[w] = 0u;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (!bad && base + total > e.capacity)
+      atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_CAPACITY);
+    e.offs[j + 1] = base + total;
+    c.ctr[C_CURSOR] = base + total;
+    c.ctr[C_YES] = 0;
+    c.ctr[C_TODO] = 0;
+  }
+}
+
+struct Launch {
+  int filter_grid = 0;
+  size_t filter_smem = 0;
+  int resolve_grid = 0;
+};
+
+template <class T, bool FULLP>
+cudaError_t launch_filter(const Common& c, int j, int grid, size_t smem, cudaStream_t st) {
+  static thread_local bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_filter<T, FULLP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_filter<T, FULLP><<<grid, FW * 32, smem, st>>>(c, j);
+  return cudaGetLastError();
+}
+
+cudaError_t filter_dispatch(const rmips_index* idx, const Common& c, int j, int grid, size_t smem, cudaStream_t st) {
+  const bool fp = idx->full_p != 0;
+  switch (idx->precision) {
+    case RMIPS_BF16:
+      return fp ? launch_filter<__nv_bfloat16, true>(c, j, grid, smem, st)
+                : launch_filter<__nv_bfloat16, false>(c, j, grid, smem, st);
+    case RMIPS_FP16:
+      return fp ? launch_filter<__half, true>(c, j, grid, smem, st) : launch_filter<__half, false>(c, j, grid, smem, st);
+    default:
+      return fp ? launch_filter<float, true>(c, j, grid, smem, st) : launch_filter<float, false>(c, j, grid, smem, st);
+  }
+}
+
+int elem_bytes(int precision) { return precision == RMIPS_FP32 ? 4 : 2; }
+
+Common make_common(const rmips_index* idx, Workspace* ws) {
+  Common c{};
+  c.Qs = idx->Qs;
+  c.Qrows = idx->precision == RMIPS_FP32 ? (const void*)idx->Qs : idx->Qh;
+  c.Ps = idx->Ps;
+  c.Lb = idx->Lb;
+  c.LB = idx->LB;
+  c.hdr = idx->hdr;
+  c.unorm = idx->unorm;
+  c.pnorm = idx->pnorm;
+  c.cand = idx->cand;
+  c.incomp = idx->incomp;
+  c.permQ = idx->permQ;
+  c.n = idx->n;
+  c.m = idx->m;
+  c.nb = idx->nb;
+  c.d = idx->d;
+  c.bs = idx->bs;
+  c.k_max = idx->k_max;
+  c.full_p = idx->full_p;
+  c.cg = err_factor(idx->d, idx->precision);
+  c.cg32 = err_factor(idx->d, RMIPS_FP32);
+  c.dq = ws->dq;
+  c.dk = ws->dk;
+  c.dqn = ws->dqn;
+  c.deps = ws->deps;
+  c.yes = ws->yes;
+  c.todo = ws->todo;
+  c.ctr = ws->ctr;
+  return c;
+}
+
+rmips_status ensure_queries(rmips_index* idx, Workspace* ws, int64_t nq) {
+  if (ws->cap_q >= nq) return RMIPS_OK;
+  int64_t cap = nq < 64 ? 64 : nq;
+  cudaFree(ws->dq); cudaFree(ws->dk); cudaFree(ws->dqn); cudaFree(ws->deps); cudaFree(ws->doffs);
+  cudaFreeHost(ws->h_offs);
+  ws->dq = nullptr; ws->dk = nullptr; ws->dqn = nullptr; ws->deps = nullptr; ws->doffs = nullptr; ws->h_offs = nullptr;
+  ws->cap_q = 0;
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dq, cap * idx->d * sizeof(float)));
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dk, cap * sizeof(int32_t)));
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dqn, cap * sizeof(float)));
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->deps, cap * sizeof(float)));
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->doffs, (cap + 1) * sizeof(long long)));
+  RMIPS_TRY_CUDA(cudaHostAlloc((void**)&ws->h_offs, (cap + 1) * sizeof(long long), cudaHostAllocDefault));
+  ws->cap_q = cap;
+  return RMIPS_OK;
+}
+
+rmips_status ensure_dout(Workspace* ws, int64_t cap) {
+  if (ws->cap_out >= cap) return RMIPS_OK;
+  cudaFree(ws->dout);
+  ws->dout = nullptr;
+  ws->cap_out = 0;
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dout, (cap < 1024 ? 1024 : cap) * sizeof(long long)));
+  ws->cap_out = cap < 1024 ? 1024 : cap;
+  return RMIPS_OK;
+}
+
+rmips_status check_segment(const rmips_index* idx, const rmips_segment* seg) {
+  if (!seg) return RMIPS_OK;
+  if (seg->reserved != 0 || seg->kind < 0 || seg->kind > 2) { set_error("bad segment"); return RMIPS_ERR_ARG; }
+  if (seg->kind == 1 && (seg->begin < 0 || seg->end < seg->begin)) { set_error("bad segment range"); return RMIPS_ERR_ARG; }
+  if (seg->kind == 2) {
+    if (seg->n_ids < 0 || (seg->n_ids > 0 && !seg->ids)) { set_error("bad segment list"); return RMIPS_ERR_ARG; }
+    for (int64_t i = 0; i < seg->n_ids; ++i)
+      if (seg->ids[i] < 0 || seg->ids[i] >= idx->n) { set_error("segment id out of range"); return RMIPS_ERR_ARG; }
+  }
+  return RMIPS_OK;
+}
+
+// Runs queries [0, nq) already staged in ws->dq / ws->dk.  Results go to
+// `out` (device-visible), offsets to ws->doffs.
+rmips_status run_queries(rmips_index* idx, Workspace* ws, int64_t nq, const rmips_segment* segs,
+                         long long* out, long long capacity, cudaStream_t st) {
+  Common c = make_common(idx, ws);
+  static thread_local int sm_count = 0;
+  if (!sm_count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (sm_count <= 0) sm_count = 1;
+  }
+  const size_t smem = 512 + FW * 2 * 8 + (size_t)FW * 2 * 32 * idx->d * elem_bytes(idx->precision);
+  const int64_t nchunks = (idx->n + 31) / 32;
+  int64_t want = (nchunks + FW - 1) / FW;
+  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 1024);
+  if (per_sm > 8) per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
+  int64_t cap = (int64_t)sm_count * per_sm;
+  const int fgrid = (int)(want < cap ? want : cap);
+  const int rgrid = sm_count;
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+  k_qprep<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, st>>>(c, nq, idx->precision);
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws->doffs, 0, sizeof(long long), st));
+  uint32_t* segmask = nullptr;
+  std::vector<uint32_t> hmask;
+  for (int64_t j = 0; j < nq; ++j) {
+    EmitArgs e{};
+    e.seg_lo = 0;
+    e.seg_hi = INT64_MAX;
+    e.segmask = nullptr;
+    if (segs) {
+      const rmips_segment& sg = segs[j];
+      if (sg.kind == 1) { e.seg_lo = sg.begin; e.seg_hi = sg.end; }
+      if (sg.kind == 2) {
+        const int64_t nw = idx->n / 32 + 1;
+        if (!segmask) RMIPS_TRY_CUDA(cudaMallocAsync((void**)&segmask, nw * sizeof(uint32_t), st));
+        hmask.assign(nw, 0u);
+        for (int64_t i = 0; i < sg.n_ids; ++i) hmask[sg.ids[i] >> 5] |= 1u << (sg.ids[i] & 31);
+        RMIPS_TRY_CUDA(cudaMemcpyAsync(segmask, hmask.data(), nw * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        RMIPS_TRY_CUDA(cudaStreamSynchronize(st));   // hmask is reused by the next query
+        e.segmask = segmask;
+      }
+    }
+    e.bitmap = ws->bitmap;
+    e.out = out;
+    e.capacity = capacity;
+    e.offs = ws->doffs;
+    const bool prof = idx->prof_on != 0;
+    if (prof) {
+      while ((int64_t)ws->ev.size() < 2 * (ws->ev_used + 1)) {
+        cudaEvent_t ev;
+        RMIPS_TRY_CUDA(cudaEventCreate(&ev));
+        ws->ev.push_back(ev);
+      }
+      RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used], st));
+    }
+    RMIPS_TRY_CUDA(filter_dispatch(idx, c, (int)j, fgrid, smem, st));
+    if (prof) {
+      RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used + 1], st));
+      ws->ev_used++;
+    }
+    k_resolve<<<rgrid, 256, 0, st>>>(c, (int)j);
+    k_emit<<<1, EMIT_THREADS, 0, st>>>(c, e, (int)j);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+  }
+  if (segmask) RMIPS_TRY_CUDA(cudaFreeAsync(segmask, st));
+  return RMIPS_OK;
+}
+
+rmips_status status_from_device(long long s) {
+  switch ((int)s) {
+    case ST_OK: return RMIPS_OK;
+    case ST_NONFINITE: set_error("non-finite value in a query"); return RMIPS_ERR_NONFINITE;
+    case ST_CAPACITY: set_error("output capacity too small"); return RMIPS_ERR_CAPACITY;
+    case ST_TIMEOUT: set_error("a device wait timed out"); return RMIPS_ERR_TIMEOUT;
+    default: set_error("device-side consistency check failed"); return RMIPS_ERR_INTERNAL;
+  }
+}
+
+struct WsGuard {
+  rmips_index* idx;
+  Workspace* ws;
+  ~WsGuard() { if (ws) release_workspace(idx, ws); }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev); else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+// Stage nq queries and ks into the workspace (one copy each).
+rmips_status stage_inputs(rmips_index* idx, Workspace* ws, const float* qs, int64_t nq, const int32_t* ks,
+                          cudaStream_t st) {
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dq, qs, nq * idx->d * sizeof(float),
+                                 is_device_ptr(qs) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dk, ks, nq * sizeof(int32_t),
+                                 is_device_ptr(ks) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  return RMIPS_OK;
+}
+
+void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t nq) {
+  std::lock_guard<std::mutex> lk(idx->mu);
+  if (ws->ev_used > 0) {
+    double ms = 0.0;
+    for (int64_t i = 0; i < ws->ev_used; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ws->ev[2 * i], ws->ev[2 * i + 1]) == cudaSuccess) ms += t;
+    }
+    if (idx->prof_on) {
+      const int es = idx->precision == RMIPS_FP32 ? 4 : 2;
+      const double per_user = (double)idx->d * es + 8.0 + (idx->full_p ? 0.0 : 4.0);
+      idx->prof.filter_launches += ws->ev_used;
+      idx->prof.filter_ms += ms;
+      idx->prof.filter_alg_bytes += 8.0 * idx->nb * ws->ev_used + per_user * h[C_TESTED] +
+                                    4.0 * (double)(h[C_YESFAST] + h[C_TODOSUM]);
+      idx->prof.users_tested += h[C_TESTED];
+      idx->prof.blocks_pruned += h[C_PRUNED] * 32 / idx->bs;
+      idx->prof.blocks_total += idx->nb * nq;
+    }
+    ws->ev_used = 0;
+  }
+  rmips_query_stats s{};
+  s.blocks_total = idx->nb;
+  s.blocks_pruned = h[C_PRUNED] * 32 / idx->bs;
+  s.users_tested = h[C_TESTED];
+  s.yes_fast = h[C_YESFAST];
+  s.todo = h[C_TODOSUM];
+  s.exact_calls = h[C_EXACT];
+  idx->last_stats = s;
+}
+
+}  // namespace
+}  // namespace rmips
+
+using namespace rmips;
+
+extern "C" rmips_status rmips_query(rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg,
+                                    int64_t* out_ids, int64_t capacity, int64_t* out_count, void* stream) {
+  if (!idx || !q || !out_count || (!out_ids && capacity > 0) || capacity < 0) {
+    set_error("null argument or negative capacity");
+    return RMIPS_ERR_ARG;
+  }
+  if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  rmips_status s = check_segment(idx, seg);
+  if (s != RMIPS_OK) return s;
+  DeviceGuard dg(idx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  s = RMIPS_OK;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ensure_queries(idx, ws, 1)) != RMIPS_OK) return s;
+  const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
+  long long* out;
+  if (out_dev) out = (long long*)out_ids;
+  else if (capacity <= ws->cap_hout) out = ws->h_out;            // device-mapped pinned host memory
+  else {
+    if ((s = ensure_dout(ws, capacity)) != RMIPS_OK) return s;
+    out = ws->dout;
+  }
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dq, q, idx->d * sizeof(float),
+                                 is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dk, &k, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if ((s = run_queries(idx, ws, 1, seg, out, capacity, st)) != RMIPS_OK) return s;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, 2 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  const long long count = ws->h_offs[1];
+  *out_count = count;
+  record_stats(idx, ws, ws->h_ctr, 1);
+  {
+    std::lock_guard<std::mutex> lk(idx->mu);
+    idx->last_stats.result = count;
+  }
+  if ((s = status_from_device(ws->h_ctr[C_STATUS])) != RMIPS_OK) return s;
+  if (!out_dev && count > 0) {
+    if (out == ws->h_out) memcpy(out_ids, ws->h_out, count * sizeof(long long));
+    else RMIPS_TRY_CUDA(cudaMemcpy(out_ids, ws->dout, count * sizeof(long long), cudaMemcpyDeviceToHost));
+  }
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int64_t nq, const int32_t* ks,
+                                          const rmips_segment* segs, int64_t* out_ids, int64_t capacity,
+                                          int64_t* out_offsets, void* stream) {
+  if (!idx || nq < 0 || (nq > 0 && (!qs || !ks)) || !out_offsets || capacity < 0 || (!out_ids && capacity > 0)) {
+    set_error("null argument or negative size");
+    return RMIPS_ERR_ARG;
+  }
+  out_offsets[0] = 0;
+  if (nq == 0) return RMIPS_OK;
+  rmips_status s = RMIPS_OK;
+  if (segs)
+    for (int64_t j = 0; j < nq; ++j)
+      if ((s = check_segment(idx, &segs[j])) != RMIPS_OK) return s;
+  if (!is_device_ptr(ks)) {
+    for (int64_t j = 0; j < nq; ++j)
+      if (ks[j] < 1 || ks[j] > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  }
+  DeviceGuard dg(idx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ensure_queries(idx, ws, nq)) != RMIPS_OK) return s;
+  const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
+  long long* out;
+  if (out_dev) out = (long long*)out_ids;
+  else {
+    if ((s = ensure_dout(ws, capacity)) != RMIPS_OK) return s;
+    out = ws->dout;
+  }
+  if ((s = stage_inputs(idx, ws, qs, nq, ks, st)) != RMIPS_OK) return s;
+  if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j <= nq; ++j) out_offsets[j] = ws->h_offs[j];
+  record_stats(idx, ws, ws->h_ctr, nq);
+  {
+    std::lock_guard<std::mutex> lk(idx->mu);
+    idx->last_stats.result = ws->h_offs[nq];
+  }
+  if (ws->h_ctr[C_STATUS] == ST_INTERNAL) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  if ((s = status_from_device(ws->h_ctr[C_STATUS])) != RMIPS_OK) return s;
+  const long long total = ws->h_offs[nq];
+  if (!out_dev && total > 0)
+    RMIPS_TRY_CUDA(cudaMemcpy(out_ids, ws->dout, total * sizeof(long long), cudaMemcpyDeviceToHost));
+  return RMIPS_OK;
+}

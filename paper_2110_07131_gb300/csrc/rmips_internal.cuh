@@ -1,0 +1,294 @@
+// Internal definitions shared by the librmips translation units.
+//
+// Index layout in device memory (n users, m items, d dims, sorted positions):
+//   Qs     float [n][d]        users in descending-norm order (Algorithm 1)
+//   Qh     bf16/fp16 [n][d]    reduced-precision copy for the online filter
+//   Ps     float [m][d]        items in descending-norm order
+//   unorm  float [n]           ||u|| rounded up (an upper bound of the exact norm)
+//   pnorm  float [m]           ||p|| rounded up
+//   permQ  int32 [n]           sorted position -> caller's user id
+//   permP  int32 [m]           sorted position -> caller's item id
+//   Lb     float2 [k_max][n]   (lo, hi): lo <= v_j(u) <= hi, v_j = j-th largest u.p
+//                              over P' (hi = +inf when not proven)
+//   cand   int32 [n][KC]       item positions whose set provably contains u's
+//                              top-k_max (full-P index only)
+//   incomp uint8 [n]           1 when cand could not be proven complete
+//   LB     float [k_max][nb]   block minima of lo (Equation 1)
+//   hdr    float [nb]          upper bound of the first user's norm of each block
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rmips.h"
+
+#define RMIPS_KC 32              // candidate slots per user (>= k_max + slack)
+#define RMIPS_KMAX_LIMIT 28      // largest supported k_max
+#define RMIPS_DMAX 128           // largest supported dimension
+
+#if defined(__CUDACC__)
+#define RMIPS_HD __host__ __device__ __forceinline__
+#else
+#define RMIPS_HD inline
+#endif
+
+namespace rmips {
+
+// ---------------------------------------------------------------------------
+// Error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+
+#define RMIPS_TRY_CUDA(expr)                                                           \
+  do {                                                                                 \
+    cudaError_t e__ = (expr);                                                          \
+    if (e__ != cudaSuccess) {                                                          \
+      ::rmips::set_error(std::string(#expr) + ": " + cudaGetErrorString(e__));         \
+      return (e__ == cudaErrorMemoryAllocation) ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;      \
+    }                                                                                  \
+  } while (0)
+
+// Device status word values (first error wins).
+enum : int { ST_OK = 0, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_INTERNAL = 8 };
+
+// Per-call device counters (int64 slots).
+enum : int {
+  C_YES = 0,        // users appended to the yes list
+  C_TODO = 1,       // users appended to the todo list
+  C_STATUS = 2,     // status word
+  C_EXACT = 3,      // exact integer tie decisions
+  C_PRUNED = 4,     // blocks pruned by Lemma 3
+  C_TESTED = 5,     // users of unpruned blocks
+  C_CURSOR = 6,     // running output offset (batches)
+  C_YESFAST = 7,    // users decided yes by the O(1) tests
+  C_TODOSUM = 8,    // users sent to the todo list (all queries of the call)
+  C_NCOUNTERS = 9
+};
+
+// ---------------------------------------------------------------------------
+// Query workspace: scratch for one in-flight call.
+// ---------------------------------------------------------------------------
+struct Workspace {
+  int32_t* yes = nullptr;       // [n] sorted positions decided yes
+  int32_t* todo = nullptr;      // [n] sorted positions needing recheck / scan
+  uint32_t* bitmap = nullptr;   // [n/32 + 1] all-zero between calls
+  long long* ctr = nullptr;     // [C_NCOUNTERS] device counters
+  long long* h_ctr = nullptr;   // pinned mirror of the counters
+  float* dq = nullptr;          // [cap_q][d] staged queries
+  int32_t* dk = nullptr;        // [cap_q] staged k
+  float* dqn = nullptr;         // [cap_q] query norms rounded up
+  float* deps = nullptr;        // [cap_q] absolute error slack per query
+  long long* doffs = nullptr;   // [cap_q + 1] device offsets
+  long long* h_offs = nullptr;  // [cap_q + 1] pinned offsets
+  int64_t cap_q = 0;
+  long long* dout = nullptr;    // [cap_out] device staging of result ids
+  int64_t cap_out = 0;
+  long long* h_out = nullptr;   // [n] pinned, device-mapped result staging
+  int64_t cap_hout = 0;
+  std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch
+  int64_t ev_used = 0;
+};
+
+}  // namespace rmips
+
+struct rmips_index {
+  int64_t n = 0, m = 0;
+  int d = 0, k_max = 0, bs = 32, precision = RMIPS_FP32;
+  int64_t nb = 0, pp = 0;
+  int full_p = 1;
+  int device = 0;
+  int64_t incomplete = 0;
+  int64_t device_bytes = 0;
+  double build_ms = 0.0;
+  float pn0 = 0.f;              // largest item norm (rounded up)
+
+  float* Qs = nullptr;
+  void* Qh = nullptr;
+  float* Ps = nullptr;
+  float* unorm = nullptr;
+  float* pnorm = nullptr;
+  int32_t* permQ = nullptr;
+  int32_t* permP = nullptr;
+  float2* Lb = nullptr;
+  int32_t* cand = nullptr;
+  uint8_t* incomp = nullptr;
+  float* LB = nullptr;
+  float* hdr = nullptr;
+
+  std::mutex mu;
+  std::vector<rmips::Workspace*> pool;
+  rmips_query_stats last_stats{};
+  int prof_on = 0;
+  rmips_profile prof{};
+};
+
+namespace rmips {
+
+// Allocation helpers (tracked in idx->device_bytes).
+template <class T>
+cudaError_t dalloc(rmips_index* idx, T** p, size_t count) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess && idx) idx->device_bytes += (int64_t)bytes;
+  return e;
+}
+
+bool is_device_ptr(const void* p);
+
+Workspace* acquire_workspace(rmips_index* idx, rmips_status* st);
+void release_workspace(rmips_index* idx, Workspace* ws);
+void destroy_workspace(Workspace* ws);
+
+// ---------------------------------------------------------------------------
+// Exact sign of u.a - u.b on float32 inputs.
+//
+// Every float32 is m * 2^e with an integer |m| < 2^24 and e in [-149, 104], so
+// every product u_i a_i is an integer < 2^48 times 2^(e1 + e2), with
+// e1 + e2 in [-298, 208].  The products are added into a fixed-point integer
+// with its least significant bit at 2^-298, held as nine signed 128-bit limbs
+// of 64-bit weight each; a limb receives at most 2d terms below 2^111, so no
+// limb can overflow for d <= 256.  Carries are propagated once at the end and
+// the sign is read off the top limb.  The result is exact: no rounding occurs.
+// ---------------------------------------------------------------------------
+RMIPS_HD void exact_acc_add(__int128* acc, float x, float y, bool negate) {
+  uint32_t bx, by;
+  memcpy(&bx, &x, 4);
+  memcpy(&by, &y, 4);
+  uint32_t ex = (bx >> 23) & 0xffu, ey = (by >> 23) & 0xffu;
+  uint64_t mx = bx & 0x7fffffu, my = by & 0x7fffffu;
+  if (ex) mx |= 0x800000u; else ex = 1;      // subnormal: m * 2^(1 - 150)
+  if (ey) my |= 0x800000u; else ey = 1;
+  if (mx == 0 || my == 0) return;
+  uint64_t mag = mx * my;                    // < 2^48
+  bool neg = (((bx ^ by) >> 31) != 0) != negate;
+  int pos = (int)(ex + ey) - 2;              // exponent + 298, in [0, 506]
+  int limb = pos >> 6, off = pos & 63;
+  __int128 t = ((__int128)mag) << off;
+  acc[limb] += neg ? -t : t;
+}
+
+RMIPS_HD int exact_acc_sign(__int128* acc) {
+  const __int128 base = ((__int128)1) << 64;
+  for (int i = 0; i < 8; ++i) {
+    __int128 carry = acc[i] >> 64;           // floor division by 2^64
+    acc[i] -= carry * base;                  // now 0 <= acc[i] < 2^64
+    acc[i + 1] += carry;
+  }
+  if (acc[8] > 0) return 1;
+  if (acc[8] < 0) return -1;
+  for (int i = 7; i >= 0; --i)
+    if (acc[i] != 0) return 1;
+  return 0;
+}
+
+RMIPS_HD int exact_sign_diff(const float* u, const float* a, const float* b, int d) {
+  __int128 acc[9];
+  for (int i = 0; i < 9; ++i) acc[i] = 0;
+  for (int i = 0; i < d; ++i) {
+    exact_acc_add(acc, u[i], a[i], false);
+    exact_acc_add(acc, u[i], b[i], true);
+  }
+  return exact_acc_sign(acc);
+}
+
+#if defined(__CUDACC__)
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(long long* ctr, int st) {
+  atomicCAS((unsigned long long*)&ctr[C_STATUS], 0ull, (unsigned long long)st);
+}
+
+// Sign of u.a - u.b: float64 when the difference clears its rounding bound
+// (each float32 product is exact in float64; the sums carry at most
+// gamma_d * sum|u_i x_i| error), else the exact integer accumulator.
+__device__ __forceinline__ int cmp_dot(const float* __restrict__ u, const float* __restrict__ a,
+                                       const float* __restrict__ b, int d, long long* ctr) {
+  double sa = 0.0, sb = 0.0, aa = 0.0, ab = 0.0;
+  for (int i = 0; i < d; ++i) {
+    double ui = (double)u[i], ai = (double)a[i], bi = (double)b[i];
+    sa = fma(ui, ai, sa);
+    sb = fma(ui, bi, sb);
+    aa = fma(fabs(ui), fabs(ai), aa);
+    ab = fma(fabs(ui), fabs(bi), ab);
+  }
+  double diff = sa - sb;
+  double bound = (4.0 * (d + 2) * 0x1p-53) * (aa + ab);
+  if (diff > bound) return 1;
+  if (diff < -bound) return -1;
+  if (ctr) atomicAdd((unsigned long long*)&ctr[C_EXACT], 1ull);
+  return exact_sign_diff(u, a, b, d);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion signalled on `bar`.
+// dst, src 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2^31 SM clocks (about
+// one second) and reports false so the caller can flag a timeout and return.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ float to_f32(T x);
+template <>
+__device__ __forceinline__ float to_f32<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half x) { return __half2float(x); }
+#endif  // __CUDACC__
+
+}  // namespace rmips

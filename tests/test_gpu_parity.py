@@ -1,0 +1,206 @@
+"""CUDA path vs the CPU oracle: exact-set parity, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import rmips_oracle as O
+from paper_2110_07131_gb300 import datagen, rmips
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    cfg = datagen.CONFIGS["tiny"]
+    Q, P = datagen.make_problem(cfg["n"], cfg["m"], cfg["d"], cfg["seed"])
+    qs, qidx = datagen.queries_from_items(P, cfg["nq"], cfg["seed"])
+    rq = datagen.random_queries(10, cfg["d"], cfg["seed"])
+    allq = np.concatenate([qs, rq])
+    counts = O.counts_greater_multi(Q, P, allq)          # [nq, n] exact c(u)
+    return Q, P, allq, counts
+
+
+def _check_all(index, allq, counts, ks):
+    for k in ks:
+        ids, offs = rmips.rmips_query_batch(index, allq, np.full(len(allq), k, np.int32))
+        for j in range(len(allq)):
+            exp = np.nonzero(counts[j] < k)[0]
+            got = ids[offs[j]:offs[j + 1]]
+            assert np.array_equal(got, exp), (k, j, len(got), len(exp))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+@pytest.mark.parametrize("p_prime", [0, 100])
+def test_tiny_config_parity(tiny, precision, p_prime):
+    Q, P, allq, counts = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime, precision=precision)
+    _check_all(index, allq, counts, (1, 5, 10, 25))
+    index.close()
+
+
+@pytest.mark.parametrize("bs", [64, 256])
+def test_block_sizes(tiny, bs):
+    Q, P, allq, counts = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25, block_size=bs)
+    _check_all(index, allq, counts, (3, 10))
+
+
+def test_single_query_api_matches(tiny):
+    Q, P, allq, counts = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    for j in range(0, len(allq), 7):
+        for k in (1, 10, 25):
+            got = rmips.rmips_query(index, allq[j], k)
+            assert np.array_equal(got, np.nonzero(counts[j] < k)[0])
+
+
+def test_index_arrays_match_oracle(tiny):
+    Q, P, _, _ = tiny
+    k_max = 25
+    index = rmips.rmips_build_index(Q, P, k_max=k_max)
+    permQ = rmips.rmips_index_export(index, "permQ")
+    permP = rmips.rmips_index_export(index, "permP")
+    assert np.array_equal(permQ, O.norm_order(Q))
+    assert np.array_equal(permP, O.norm_order(P))
+    v = O.kth_values(Q[permQ], P, k_max)                   # [n, k_max] float64
+    lo = rmips.rmips_index_export(index, "lo").T
+    hi = rmips.rmips_index_export(index, "hi").T
+    scale = np.abs(Q[permQ]).astype(np.float64) @ np.abs(P).astype(np.float64).max(axis=0)
+    tol = 1e-12 * scale[:, None]
+    assert (lo <= v + tol).all() and (hi >= v - tol).all()
+    assert (hi - lo <= 1e-5 * (1 + np.abs(v))).all()      # bounds are tight
+    LB = rmips.rmips_index_export(index, "LB")
+    hdr = rmips.rmips_index_export(index, "hdr")
+    for b in range(LB.shape[1]):
+        assert np.array_equal(LB[:, b], lo[32 * b:32 * b + 32].min(axis=0))
+    nrm = O.norms_fp64(Q[permQ])
+    assert (hdr >= nrm[::32]).all() and (hdr <= nrm[::32] * (1 + 1e-6)).all()
+    assert rmips.rmips_index_get_info(index)["incomplete"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("p_prime", [0, 8])
+def test_integer_ties_exact(precision, p_prime):
+    Q, P = datagen.integer_problem(300, 90, 8, 5, lim=2)
+    qs = np.concatenate([P[:12], Q[:4], np.zeros((1, 8), np.float32)])
+    counts = O.counts_greater_multi(Q, P, qs)
+    index = rmips.rmips_build_index(Q, P, k_max=12, p_prime=p_prime, precision=precision)
+    _check_all(index, qs, counts, (1, 2, 5, 12))
+    info = rmips.rmips_index_get_info(index)
+    if p_prime == 0:
+        assert info["incomplete"] > 0          # ties defeat the completeness proof: scan fallback runs
+
+
+@pytest.mark.parametrize("n,m,d,k_max", [(1, 1, 3, 1), (31, 3, 5, 5), (33, 40, 7, 8), (1007, 31, 50, 25),
+                                         (70, 2, 64, 25), (257, 129, 128, 4)])
+def test_ragged_sizes(n, m, d, k_max):
+    Q, P = datagen.make_problem(n, m, d, 17)
+    qs = np.concatenate([P[:2], datagen.random_queries(2, d, 3)])
+    counts = O.counts_greater_multi(Q, P, qs)
+    for p_prime in (0, 2):
+        index = rmips.rmips_build_index(Q, P, k_max=k_max, p_prime=p_prime)
+        _check_all(index, qs, counts, sorted({1, k_max}))
+
+
+def test_zero_and_scaled_queries(tiny):
+    Q, P, _, _ = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    qs = np.stack([np.zeros(50, np.float32), P[3] * 8.0, P[5] * 0.125, -P[9]]).astype(np.float32)
+    counts = O.counts_greater_multi(Q, P, qs)
+    _check_all(index, qs, counts, (1, 10, 25))
+
+
+def test_errors(tiny):
+    Q, P, allq, _ = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=10)
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query(index, allq[0], 0)
+    assert e.value.status == 2
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query(index, allq[0], 11)
+    assert e.value.status == 2
+    bad = allq[0].copy()
+    bad[3] = np.nan
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query(index, bad, 5)
+    assert e.value.status == 3
+    # the index stays usable after an error
+    full = rmips.rmips_query(index, allq[1], 10)
+    assert len(full) > 1
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query(index, allq[1], 10, capacity=len(full) - 1)
+    assert e.value.status == 5
+    assert np.array_equal(rmips.rmips_query(index, allq[1], 10, capacity=len(full)), full)
+    Qb = Q.copy()
+    Qb[7, 2] = np.inf
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_build_index(Qb, P, k_max=10)
+    assert e.value.status == 3
+
+
+def test_segments(tiny):
+    Q, P, allq, counts = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    rng = np.random.default_rng(0)
+    subset = np.sort(rng.choice(Q.shape[0], 700, replace=False))
+    for j in range(0, 40, 3):
+        exp = np.nonzero(counts[j] < 25)[0]
+        got = rmips.rmips_query(index, allq[j], 25, segment=(500, 1500))
+        assert np.array_equal(got, exp[(exp >= 500) & (exp < 1500)])
+        got = rmips.rmips_query(index, allq[j], 25, segment=subset)
+        assert np.array_equal(got, np.intersect1d(exp, subset))
+    ids, offs = rmips.rmips_query_batch(index, allq[:6], 25, segments=[None, (0, 10), subset, None, (1990, 2000), subset])
+    for j, sg in enumerate([None, (0, 10), subset, None, (1990, 2000), subset]):
+        exp = np.nonzero(counts[j] < 25)[0]
+        if isinstance(sg, tuple):
+            exp = exp[(exp >= sg[0]) & (exp < sg[1])]
+        elif sg is not None:
+            exp = np.intersect1d(exp, sg)
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], exp)
+
+
+def test_device_pointers(tiny):
+    torch = pytest.importorskip("torch")
+    Q, P, allq, counts = tiny
+    dQ, dP = torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda()
+    index = rmips.rmips_build_index(dQ, dP, k_max=25)
+    dq = torch.from_numpy(allq[:20]).cuda()
+    dk = torch.full((20,), 10, dtype=torch.int32, device="cuda")
+    out = torch.empty(20 * 2000, dtype=torch.int64, device="cuda")
+    ids, offs = rmips.rmips_query_batch(index, dq, dk, out=out)
+    ids = ids.cpu().numpy()
+    for j in range(20):
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], np.nonzero(counts[j] < 10)[0])
+    out1 = torch.empty(2000, dtype=torch.int64, device="cuda")
+    got = rmips.rmips_query(index, dq[3], 10, out=out1)
+    assert np.array_equal(got.cpu().numpy(), np.nonzero(counts[3] < 10)[0])
+
+
+def test_large_result_bitmap_path():
+    # a query with a huge norm is in the top-k of most users: > 8192 results
+    Q, P = datagen.make_problem(20000, 500, 16, 2)
+    q = (P[0] * 50.0).astype(np.float32)
+    counts = O.counts_greater(Q, P, q)
+    index = rmips.rmips_build_index(Q, P, k_max=5)
+    got = rmips.rmips_query(index, q, 5)
+    exp = np.nonzero(counts < 5)[0]
+    assert len(exp) > 8192
+    assert np.array_equal(got, exp)
+
+
+def test_plain_config_sum_identity_and_samples():
+    cfg = datagen.CONFIGS["plain"]
+    n, m, d = cfg["n"], cfg["m"], cfg["d"]
+    Q, P = datagen.make_problem(n, m, d, cfg["seed"])
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    # Every item as a query: each user has exactly k items whose top-k holds it.
+    for k in (1, 10):
+        ids, offs = rmips.rmips_query_batch(index, P, np.full(m, k, np.int32))
+        assert offs[-1] == n * k
+    qs, _ = datagen.queries_from_items(P, 6, cfg["seed"])
+    rng = np.random.default_rng(5)
+    for j, q in enumerate(qs):
+        for k in cfg["ks"][::2]:
+            got = rmips.rmips_query(index, q, k)
+            sample = np.unique(np.concatenate([got, rng.choice(n, 150, replace=False)]))
+            truth = O.decide_users(Q, P, q, k, sample)
+            assert np.array_equal(sample[truth], got), (j, k)
