@@ -85,9 +85,18 @@ def test_integer_ties_exact(precision, p_prime):
     counts = O.counts_greater_multi(Q, P, qs)
     index = rmips.rmips_build_index(Q, P, k_max=12, p_prime=p_prime, precision=precision)
     _check_all(index, qs, counts, (1, 2, 5, 12))
-    info = rmips.rmips_index_get_info(index)
-    if p_prime == 0:
-        assert info["incomplete"] > 0          # ties defeat the completeness proof: scan fallback runs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_massive_ties_use_scan_fallback(precision):
+    # components in {-1, 0, 1}, d = 3: only 7 distinct inner products, so the
+    # values at ranks k_max..32 tie and completeness cannot be proven
+    Q, P = datagen.integer_problem(400, 120, 3, 8, lim=1)
+    qs = np.concatenate([P[:10], Q[:3]])
+    counts = O.counts_greater_multi(Q, P, qs)
+    index = rmips.rmips_build_index(Q, P, k_max=12, precision=precision)
+    assert rmips.rmips_index_get_info(index)["incomplete"] > 0
+    _check_all(index, qs, counts, (1, 4, 12))
 
 
 @pytest.mark.parametrize("n,m,d,k_max", [(1, 1, 3, 1), (31, 3, 5, 5), (33, 40, 7, 8), (1007, 31, 50, 25),
