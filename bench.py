@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--d", type=int, default=50)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--k-max", type=int, default=25)
-    ap.add_argument("--nq", type=int, default=1000, help="queries per step")
+    ap.add_argument("--nq", type=int, default=10000, help="queries per step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--p-prime", type=int, default=0, help="0 = bounds over all of P")
     ap.add_argument("--block-size", type=int, default=32)
@@ -241,6 +241,13 @@ def run_ours(a):
              "p99_ms": float(np.percentile(lat_s, 99)), "queries": int(len(lat_s)),
              "api": "rmips_query, host q and host ids, one query per call"}
 
+    # single-query filter timing (HBM-bound kernel), profiled separately from the latency run
+    rmips.rmips_profile_enable(index, True)
+    for j in range(min(200, a.plain_queries)):
+        rmips.rmips_query(index, qs[j], a.k)
+    sprof = rmips.rmips_profile_read(index)
+    rmips.rmips_profile_enable(index, False)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -248,28 +255,44 @@ def run_ours(a):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
-    launches = prof["filter_launches"] or 1
-    per_launch_bytes = prof["filter_alg_bytes"] / launches
-    per_launch_ms = prof["filter_ms"] / launches
-    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else 0.0
-    roofline = {"bound": "hbm", "kernel": "k_filter (Lemmas 1-3, TMA-staged rows)",
-                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_source": peak_src, "traffic": None,
-                "alg_bytes_per_launch": per_launch_bytes, "avg_launch_us": per_launch_ms * 1e3,
-                "filter_share_of_step": prof["filter_ms"] / ms if ms > 0 else None}
+    sl = sprof["filter_launches"] or 1
+    s_bytes = sprof["filter_alg_bytes"] / sl
+    s_ms = sprof["filter_ms"] / sl
+    s_ach = s_bytes / (s_ms / 1e3) / 1e9 if s_ms > 0 else 0.0
+    roof_single = {"bound": "hbm", "kernel": "k_filter (one query; Lemmas 1-3, TMA-staged rows)",
+                   "achieved": s_ach, "peak": hbm, "unit": "GB/s", "frac": s_ach / hbm, "peak_source": peak_src,
+                   "traffic": None, "alg_bytes_per_launch": s_bytes, "avg_launch_us": s_ms * 1e3,
+                   "users_tested_per_query": sprof["users_tested"] / sl,
+                   "alpha_blocks_pruned": sprof["blocks_pruned"] / max(1, sprof["blocks_total"])}
+    # FP32 FMA peak from unit counts and clock: SMs x 128 lanes x 2 flop x clock
+    import torch as _t
+    sms = _t.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    ml = prof["mfilter_launches"] or 1
+    m_flops = prof["mfilter_alg_flops"] / ml
+    m_ms = prof["mfilter_ms"] / ml
+    m_ach = m_flops / (m_ms / 1e3) / 1e12 if m_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "k_mfilter (multi-query Lemma 3 prefixes + FP32 FFMA tiles + "
+                                          "Lemmas 1/2 epilogue)",
+                "achieved": m_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": m_ach / alu_peak,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
+                "pairs_per_launch": prof["mfilter_pairs"] / ml,
+                "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision, "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": a.steps * (1 + 3 * a.nq),
+            "gpu_launches": a.steps * 6 * ((a.nq + 16383) // 16384),
+            "roofline_single_query_filter": roof_single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain,
             "batch_latency_ms": ms_max / a.steps,
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
             "index_incomplete_users": info["incomplete"],
             "users_returned_per_query": results / (a.steps * a.nq),
-            "alpha_blocks_pruned": (prof["blocks_pruned"] / prof["blocks_total"]) if prof["blocks_total"] else None,
-            "users_tested_per_query": prof["users_tested"] / launches}
+            "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (a.steps * a.nq)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rng = np.random.default_rng(1)
         qps, s, t, cores = oracle_sample(Q, P, qs[0], a.k, a.cpu_seconds, rng)

@@ -147,7 +147,7 @@ rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
                                int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
                                void* stream);
 
-/* Per-kernel timing of the filter kernel (Lemmas 1-3), for roofline reports. */
+/* Per-kernel timing of the filter kernels (Lemmas 1-3), for roofline reports. */
 typedef struct {
   int64_t filter_launches;   /* filter launches since profiling was enabled */
   double filter_ms;          /* summed CUDA-event durations of those launches,
@@ -160,6 +160,11 @@ typedef struct {
   int64_t users_tested;      /* users of unpruned blocks */
   int64_t blocks_pruned;     /* blocks pruned by Lemma 3 */
   int64_t blocks_total;      /* blocks examined */
+  int64_t mfilter_launches;  /* multi-query filter launches (rmips_query_batch) */
+  double mfilter_ms;         /* their summed CUDA-event durations */
+  int64_t mfilter_pairs;     /* (user, query) pairs kept by Lemma 3 */
+  double mfilter_alg_flops;  /* 2 d flops per kept pair (the inner products
+                                the per-user tests need) */
 } rmips_profile;
 
 /* Turns filter timing on (resetting the counters) or off.  While on, every

@@ -34,6 +34,18 @@ void destroy_workspace(Workspace* ws) {
   cudaFreeHost(ws->h_offs);
   cudaFreeHost(ws->h_out);
   for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
+  cudaFree(ws->bq);
+  cudaFree(ws->bk);
+  cudaFree(ws->bqn);
+  cudaFree(ws->beps);
+  cudaFree(ws->bidx);
+  cudaFree(ws->grp);
+  cudaFree(ws->qcnt);
+  cudaFree(ws->qcur);
+  cudaFree(ws->ypairs);
+  cudaFree(ws->tpairs);
+  cudaFree(ws->seg);
+  cudaFree(ws->scratch);
   delete ws;
 }
 

@@ -639,7 +639,7 @@ rmips_status stage_inputs(rmips_index* idx, Workspace* ws, const float* qs, int6
   return RMIPS_OK;
 }
 
-void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t nq) {
+void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t nq, bool batch = false) {
   std::lock_guard<std::mutex> lk(idx->mu);
   if (ws->ev_used > 0) {
     double ms = 0.0;
@@ -647,7 +647,12 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
       float t = 0.f;
       if (cudaEventElapsedTime(&t, ws->ev[2 * i], ws->ev[2 * i + 1]) == cudaSuccess) ms += t;
     }
-    if (idx->prof_on) {
+    if (idx->prof_on && batch) {
+      idx->prof.mfilter_launches += ws->ev_used;
+      idx->prof.mfilter_ms += ms;
+      idx->prof.mfilter_pairs += h[C_TESTED];
+      idx->prof.mfilter_alg_flops += 2.0 * idx->d * (double)h[C_TESTED];
+    } else if (idx->prof_on) {
       const int es = idx->precision == RMIPS_FP32 ? 4 : 2;
       const double per_user = (double)idx->d * es + 8.0 + (idx->full_p ? 0.0 : 4.0);
       idx->prof.filter_launches += ws->ev_used;
@@ -662,12 +667,597 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
   }
   rmips_query_stats s{};
   s.blocks_total = idx->nb;
-  s.blocks_pruned = h[C_PRUNED] * 32 / idx->bs;
+  s.blocks_pruned = batch ? 0 : h[C_PRUNED] * 32 / idx->bs;
   s.users_tested = h[C_TESTED];
   s.yes_fast = h[C_YESFAST];
   s.todo = h[C_TODOSUM];
   s.exact_calls = h[C_EXACT];
   idx->last_stats = s;
+}
+
+
+// ===========================================================================
+// Batched path: up to MQ_MAXQ queries in one pass over the user rows.
+//
+//   k_mprep     query norms and checks; queries sorted by (k, descending
+//               norm) and laid out in k-groups padded to MQ_TQ slots;
+//   k_mfilter   persistent CTAs walk user tiles of MQ_TU users.  For every
+//               k-group and every block of the tile, Lemma 3 keeps exactly a
+//               prefix of the group (queries are in descending norm), found by
+//               binary search; tiles with no surviving (block, query) pair
+//               are skipped without reading their rows.  Surviving tiles are
+//               multiplied in registers (8 users x 4 queries per thread) and
+//               every surviving pair gets the per-user tests of Lemmas 1/2;
+//   k_mresolve  exact decision of the undecided pairs (as k_resolve);
+//   k_mscan / k_mscatter / k_memit   per-query CSR output, ids ascending.
+// ===========================================================================
+constexpr int MQ_TU = 128;
+constexpr int MQ_THREADS = 256;
+constexpr int MQ_US = MQ_TU + 4;       // row stride of the transposed user tile
+constexpr int MQ_QS = MQ_TQ + 4;       // row stride of the transposed query tile
+constexpr int MQ_PREP_THREADS = 1024;
+
+struct Batch {
+  const float* dq;        // [nq][d] staged queries (call order)
+  const int32_t* dk;      // [nq]
+  float* dqn;             // [nq] norm upper bounds (call order)
+  float* deps;            // [nq]
+  int nq;                 // queries in this pass (<= MQ_MAXQ)
+  float* bq;
+  int32_t* bk;
+  float* bqn;
+  float* beps;
+  int32_t* bidx;
+  int4* grp;
+  int32_t* qcnt;
+  int32_t* qcur;
+  unsigned long long* ypairs;
+  long long cap_y;
+  unsigned long long* tpairs;
+  long long cap_t;
+  int32_t* seg;
+  int32_t* scratch;
+  long long* doffs;       // [nq + 1] offsets of this pass (absolute)
+  long long* out;
+  long long capacity;
+};
+
+__global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, int precision) {
+  extern __shared__ unsigned long long keys[];               // [N2]
+  __shared__ int hist[RMIPS_KMAX_LIMIT + 2];
+  __shared__ int first[RMIPS_KMAX_LIMIT + 2];
+  __shared__ int slot0[RMIPS_KMAX_LIMIT + 2];
+  const int tid = threadIdx.x;
+  const int nq = b.nq;
+  int N2 = 1;
+  while (N2 < nq) N2 <<= 1;
+  if (tid == 0) {
+    c.ctr[C_YES] = 0;
+    c.ctr[C_TODO] = 0;
+  }
+  if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = 0;
+  __syncthreads();
+  for (int j = tid; j < N2; j += MQ_PREP_THREADS) {
+    if (j >= nq) { keys[j] = ~0ull; continue; }
+    const float* q = b.dq + (int64_t)j * c.d;
+    double acc = 0.0;
+    float qmax = 0.f;
+    bool fin = true;
+    for (int i = 0; i < c.d; ++i) {
+      float v = q[i];
+      fin = fin && isfinite(v);
+      acc = fma((double)v, (double)v, acc);
+      qmax = fmaxf(qmax, fabsf(v));
+    }
+    int k = b.dk[j];
+    if (!fin) set_status(c.ctr, ST_NONFINITE);
+    if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_INTERNAL); k = 1; }
+    const float qn = __double2float_ru(__dmul_ru(sqrt(acc), 1.0 + (c.d + 8) * 0x1p-52));
+    const double sub = (precision == RMIPS_FP16) ? 0x1p-25 : (precision == RMIPS_BF16 ? 0x1p-133 : 0.0);
+    b.dqn[j] = qn;
+    b.deps[j] = __double2float_ru((c.d + 2) * (sub * qmax + 0x1p-148));
+    b.qcnt[j] = 0;
+    b.qcur[j] = 0;
+    keys[j] = ((unsigned long long)k << 46) | ((unsigned long long)(~__float_as_uint(qn)) << 14) |
+              (unsigned long long)j;
+    atomicAdd(&hist[k], 1);
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= N2; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < N2; i += MQ_PREP_THREADS) {
+        int p = i ^ jj;
+        if (p > i) {
+          unsigned long long x = keys[i], y = keys[p];
+          if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    int f = 0, s = 0, g = 0;
+    for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) {
+      first[k] = f;
+      slot0[k] = s;
+      if (hist[k] > 0) {
+        const int tiles = (hist[k] + MQ_TQ - 1) / MQ_TQ;
+        b.grp[g++] = make_int4(k, s, hist[k], tiles);
+        f += hist[k];
+        s += tiles * MQ_TQ;
+      }
+    }
+    for (; g <= RMIPS_KMAX_LIMIT; ++g) b.grp[g] = make_int4(0, s, 0, 0);   // empty groups
+  }
+  __syncthreads();
+  // slot of each sorted query; padding slots get index -1
+  for (int i = tid; i < nq; i += MQ_PREP_THREADS) {
+    const unsigned long long key = keys[i];
+    const int k = (int)(key >> 46);
+    const int j = (int)(key & 16383ull);
+    const int slot = slot0[k] + (i - first[k]);
+    b.bidx[slot] = j;
+    b.bk[slot] = k;
+    b.bqn[slot] = b.dqn[j];
+    b.beps[slot] = b.deps[j];
+  }
+  for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) {
+    const int h = hist[k];
+    if (h == 0) continue;
+    const int pad = ((h + MQ_TQ - 1) / MQ_TQ) * MQ_TQ;
+    for (int r = h + tid; r < pad; r += MQ_PREP_THREADS) {
+      b.bidx[slot0[k] + r] = -1;
+      b.bk[slot0[k] + r] = k;
+      b.bqn[slot0[k] + r] = 0.f;
+      b.beps[slot0[k] + r] = 0.f;
+    }
+  }
+  __syncthreads();
+  // gather the query vectors into slot order (zeros in padding)
+  int total_slots = 0;
+  for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) total_slots += ((hist[k] + MQ_TQ - 1) / MQ_TQ) * MQ_TQ;
+  for (int e = tid; e < total_slots * c.d; e += MQ_PREP_THREADS) {
+    const int slot = e / c.d, i = e - slot * c.d;
+    const int j = b.bidx[slot];
+    b.bq[e] = j >= 0 ? b.dq[(int64_t)j * c.d + i] : 0.f;
+  }
+}
+
+// Number of leading queries of group g (descending norm) kept by Lemma 3 for
+// a block with header h and bound lb: the first r with fl_up(h qn_r) < lb.
+__device__ __forceinline__ int lemma3_prefix(const float* __restrict__ qn, int slot0, int size, float h, float lb) {
+  int lo = 0, hi = size;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__fmul_ru(h, qn[slot0 + mid]) < lb) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+template <class T, bool FULLP>
+__global__ void __launch_bounds__(MQ_THREADS) k_mfilter(Common c, Batch b, int ngroups) {
+  extern __shared__ __align__(16) float ms[];
+  const int d = c.d;
+  float* Ut = ms;                                        // [d][MQ_US]
+  float* Qt = Ut + d * MQ_US;                            // [d][MQ_QS]
+  float2* Lt = reinterpret_cast<float2*>(Qt + d * MQ_QS);  // [ngroups][MQ_TU]
+  __shared__ float un_t[MQ_TU];
+  __shared__ float qn_t[MQ_TQ], qe_t[MQ_TQ];
+  __shared__ int qj_t[MQ_TQ];
+  __shared__ int pre[RMIPS_KMAX_LIMIT][4];               // prefix length per (group, block of tile)
+  __shared__ int gmax[RMIPS_KMAX_LIMIT];
+  __shared__ int any_tile;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t n = c.n;
+  const int sub = c.bs < MQ_TU ? c.bs : MQ_TU;           // users of one block inside a tile
+  const int nbt = MQ_TU / sub;                           // blocks (or block parts) per tile
+  const int tu = tid & 15, tq = tid >> 4;                // 8 users x 4 queries per thread
+  long long st_pairs = 0, st_users = 0, st_lrows = 0, st_yes = 0, st_todo = 0, st_skipped = 0;
+  for (int64_t u0 = (int64_t)blockIdx.x * MQ_TU; u0 < n; u0 += (int64_t)gridDim.x * MQ_TU) {
+    // 1. Lemma 3 prefixes for every (group, block) of this tile
+    if (tid < ngroups * nbt) {
+      const int g = tid / nbt, sb = tid - g * nbt;
+      const int64_t ufirst = u0 + (int64_t)sb * sub;
+      int r = 0;
+      const int4 G = b.grp[g];
+      if (ufirst < n && G.z > 0) {
+        const int64_t blk = ufirst / c.bs;
+        r = lemma3_prefix(b.bqn, G.y, G.z, c.hdr[blk], c.LB[(int64_t)(G.x - 1) * c.nb + blk]);
+      }
+      pre[g][sb] = r;
+    }
+    __syncthreads();
+    if (tid < ngroups) {
+      int mx = 0;
+      for (int sb = 0; sb < nbt; ++sb) mx = max(mx, pre[tid][sb]);
+      gmax[tid] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int a = 0;
+      for (int g = 0; g < ngroups; ++g) a |= gmax[g];
+      any_tile = a;
+    }
+    __syncthreads();
+    const int64_t nvalid = (n - u0) < MQ_TU ? (n - u0) : MQ_TU;
+    if (!any_tile) {
+      if (tid == 0) st_skipped += 1;
+      continue;
+    }
+    // 2. stage the user tile (transposed), norms and the needed bound rows
+    const T* src = reinterpret_cast<const T*>(c.Qrows) + u0 * d;
+    for (int e = tid; e < MQ_TU * d; e += MQ_THREADS) {
+      const int uu = e / d, i = e - uu * d;
+      Ut[i * MQ_US + uu] = uu < nvalid ? to_f32<T>(src[e]) : 0.f;
+    }
+    for (int uu = tid; uu < MQ_TU; uu += MQ_THREADS) un_t[uu] = uu < nvalid ? c.unorm[u0 + uu] : 0.f;
+    for (int e = tid; e < ngroups * MQ_TU; e += MQ_THREADS) {
+      const int g = e / MQ_TU, uu = e - g * MQ_TU;
+      if (gmax[g] > 0 && uu < nvalid)
+        Lt[e] = c.Lb[(int64_t)(b.grp[g].x - 1) * n + u0 + uu];
+    }
+    if (tid == 0) {
+      st_users += nvalid;
+      for (int g = 0; g < ngroups; ++g) {
+        if (gmax[g] > 0) st_lrows += nvalid;
+        for (int sb = 0; sb < nbt; ++sb) {
+          const int64_t us = (int64_t)sb * sub;
+          const int64_t cnt = nvalid - us < sub ? (nvalid - us > 0 ? nvalid - us : 0) : sub;
+          st_pairs += (long long)pre[g][sb] * cnt;
+        }
+      }
+    }
+    __syncthreads();
+    // 3. every surviving query tile of every group
+    for (int g = 0; g < ngroups; ++g) {
+      const int gm = gmax[g];
+      if (gm == 0) continue;
+      const int4 G = b.grp[g];
+      const int k = G.x;
+      const float pk = (k <= c.m) ? c.pnorm[k - 1] : -kInf;
+      const int ntile = (gm + MQ_TQ - 1) / MQ_TQ;
+      for (int t = 0; t < ntile; ++t) {
+        const int s0 = G.y + t * MQ_TQ;
+        __syncthreads();                                   // previous tile's readers are done
+        for (int e = tid; e < MQ_TQ * d; e += MQ_THREADS) {
+          const int qq = e / d, i = e - qq * d;
+          Qt[i * MQ_QS + qq] = b.bq[(int64_t)s0 * d + e];
+        }
+        if (tid < MQ_TQ) {
+          qn_t[tid] = b.bqn[s0 + tid];
+          qe_t[tid] = b.beps[s0 + tid];
+          qj_t[tid] = b.bidx[s0 + tid];
+        }
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+        for (int i = 0; i < d; ++i) {
+          const float4 ua = *reinterpret_cast<const float4*>(&Ut[i * MQ_US + tu * 8]);
+          const float4 ub = *reinterpret_cast<const float4*>(&Ut[i * MQ_US + tu * 8 + 4]);
+          const float4 qv = *reinterpret_cast<const float4*>(&Qt[i * MQ_QS + tq * 4]);
+          const float uv[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+          const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+          for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(uv[a], qa[q], acc[a][q]);
+        }
+        // epilogue: Lemma 3 survivor test, then Lemmas 1 / 2
+        uint32_t ymask = 0, tmask = 0;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int uu = tu * 8 + a;
+          const int sb = uu / sub;
+          const int lim = pre[g][sb];
+          const float un = un_t[uu];
+          const float2 L = Lt[g * MQ_TU + uu];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = t * MQ_TQ + tq * 4 + q;          // rank inside the group
+            const bool live = uu < nvalid && r < lim && qj_t[tq * 4 + q] >= 0;
+            if (!live) continue;
+            const float e = __fmaf_ru(__fmul_ru(un, qn_t[tq * 4 + q]), c.cg, qe_t[tq * 4 + q]);
+            const float hi = __fadd_ru(acc[a][q], e);
+            if (hi < L.x) continue;                                  // Lemma 1
+            const float lo = __fsub_rd(acc[a][q], e);
+            const bool yes = FULLP ? (lo >= L.y) : (lo >= __fmul_ru(un, pk));   // hi_k / Lemma 2
+            if (yes) ymask |= 1u << (a * 4 + q); else tmask |= 1u << (a * 4 + q);
+          }
+        }
+        if (__any_sync(FULL, (ymask | tmask) != 0)) {
+          const uint32_t lt = (1u << lane) - 1u;
+          for (int p = 0; p < 32; ++p) {
+            const bool y = (ymask >> p) & 1u, tt = (tmask >> p) & 1u;
+            const uint32_t by = __ballot_sync(FULL, y), bt = __ballot_sync(FULL, tt);
+            if (!(by | bt)) continue;
+            const int a = p >> 2, q = p & 3;
+            const unsigned long long pair =
+                ((unsigned long long)(uint32_t)qj_t[tq * 4 + q] << 32) | (unsigned long long)(u0 + tu * 8 + a);
+            if (by) {
+              long long base = 0;
+              if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
+              base = __shfl_sync(FULL, base, 0);
+              if (y) {
+                const long long at = base + __popc(by & lt);
+                if (at < b.cap_y) b.ypairs[at] = pair;
+                atomicAdd(&b.qcnt[qj_t[tq * 4 + q]], 1);
+              }
+            }
+            if (bt) {
+              long long base = 0;
+              if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_TODO], (unsigned long long)__popc(bt));
+              base = __shfl_sync(FULL, base, 0);
+              if (tt) {
+                const long long at = base + __popc(bt & lt);
+                if (at < b.cap_t) b.tpairs[at] = pair;
+                else set_status(c.ctr, ST_INTERNAL);
+              }
+            }
+          }
+          st_yes += __popc(ymask);
+          st_todo += __popc(tmask);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // statistics (C_TESTED: surviving pairs; C_PRUNED: tiles skipped; C_TODOSUM; C_YESFAST)
+  if (tid == 0) {
+    atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)st_pairs);
+    atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)st_skipped);
+  }
+  if (st_yes) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)st_yes);
+  if (st_todo) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)st_todo);
+  (void)st_users;
+  (void)st_lrows;
+}
+
+__global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
+  __shared__ long long s_cnt;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_skip = (st0 != 0 && st0 != ST_CAPACITY);
+    s_cnt = c.ctr[C_TODO] < b.cap_t ? c.ctr[C_TODO] : b.cap_t;
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const long long cnt = s_cnt;
+  const int lane = threadIdx.x & 31;
+  const int d = c.d;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < cnt; t += nw) {
+    const unsigned long long pr = b.tpairs[t];
+    const int j = (int)(pr >> 32);
+    const int32_t pos = (int32_t)(pr & 0xffffffffull);
+    const float* q = b.dq + (int64_t)j * d;
+    const int k = b.dk[j];
+    const float* u = c.Qs + (int64_t)pos * d;
+    bool yes;
+    if (c.full_p && !c.incomp[pos]) {
+      const int32_t it = c.cand[(int64_t)pos * RMIPS_KC + lane];
+      const bool gt = it >= 0 && cmp_dot(u, c.Ps + (int64_t)it * d, q, d, c.ctr) > 0;
+      yes = __popc(__ballot_sync(FULL, gt)) < k;
+    } else {
+      yes = verify_scan(u, c.unorm[pos], c, q, k, b.deps[j]);
+    }
+    if (lane == 0 && yes) {
+      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+      if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)pos;
+      atomicAdd(&b.qcnt[j], 1);
+    }
+  }
+}
+
+// Exclusive scan of per-query counts into absolute offsets.
+__global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
+  __shared__ long long s_warp[32];
+  __shared__ long long s_base;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_base = c.ctr[C_CURSOR];
+  __syncthreads();
+  const int per = (b.nq + 1023) / 1024;
+  const int j0 = tid * per, j1 = min(b.nq, j0 + per);
+  long long local = 0;
+  for (int j = j0; j < j1; ++j) local += b.qcnt[j];
+  long long x = local;
+  for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    long long v = s_warp[lane];
+    for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, v, o); if (lane >= o) v += y; }
+    s_warp[lane] = v;
+  }
+  __syncthreads();
+  long long run = s_base + (x - local) + (wid ? s_warp[wid - 1] : 0);
+  for (int j = j0; j < j1; ++j) {
+    b.doffs[j] = run;
+    run += b.qcnt[j];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const long long total = s_warp[31];
+    b.doffs[b.nq] = s_base + total;
+    c.ctr[C_CURSOR] = s_base + total;
+    if (s_base + total > b.capacity) set_status(c.ctr, ST_CAPACITY);
+  }
+}
+
+__global__ void k_mscatter(Common c, Batch b) {
+  const long long st0 = c.ctr[C_STATUS];
+  if (st0 != 0) return;                                   // capacity or bad input: no output
+  const long long cnt = c.ctr[C_YES];
+  const long long base0 = b.doffs[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long pr = b.ypairs[i];
+    const int j = (int)(pr >> 32);
+    const int slot = atomicAdd(&b.qcur[j], 1);
+    b.seg[b.doffs[j] - base0 + slot] = (int32_t)(pr & 0xffffffffull);
+  }
+}
+
+// One CTA per query: positions -> ids, sorted ascending.
+__global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
+  __shared__ int32_t keys[EMIT_SORT_CAP];
+  const int j = blockIdx.x;
+  if (c.ctr[C_STATUS] != 0) return;                      // uniform: read-only here
+  const long long base0 = b.doffs[0];
+  const long long off = b.doffs[j];
+  const int cnt = b.qcnt[j];
+  const int tid = threadIdx.x;
+  if (cnt == 0) return;
+  int N2 = 1;
+  while (N2 < cnt) N2 <<= 1;
+  int32_t* K = keys;
+  if (N2 > EMIT_SORT_CAP) K = b.scratch + 2 * (off - base0);
+  for (int i = tid; i < N2; i += blockDim.x)
+    K[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
+  __syncthreads();
+  for (int kk = 2; kk <= N2; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < N2; i += blockDim.x) {
+        int p = i ^ jj;
+        if (p > i) {
+          int32_t x = K[i], y = K[p];
+          if ((x > y) == ((i & kk) == 0)) { K[i] = y; K[p] = x; }
+        }
+      }
+      if (N2 > EMIT_SORT_CAP) __threadfence_block();
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = K[i];
+}
+
+rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
+  if (!ws->bq) {
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bq, (size_t)MQ_SLOTS * idx->d * sizeof(float)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bk, MQ_SLOTS * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bqn, MQ_SLOTS * sizeof(float)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->beps, MQ_SLOTS * sizeof(float)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bidx, MQ_SLOTS * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->grp, (RMIPS_KMAX_LIMIT + 2) * sizeof(int4)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->qcnt, MQ_MAXQ * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->qcur, MQ_MAXQ * sizeof(int32_t)));
+    ws->cap_t = 16ll << 20;
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->tpairs, ws->cap_t * sizeof(unsigned long long)));
+  }
+  if (cap_y < 4096) cap_y = 4096;
+  if (ws->cap_y < cap_y) {
+    cudaFree(ws->ypairs); cudaFree(ws->seg); cudaFree(ws->scratch);
+    ws->ypairs = nullptr; ws->seg = nullptr; ws->scratch = nullptr; ws->cap_y = 0;
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->ypairs, cap_y * sizeof(unsigned long long)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->seg, cap_y * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->scratch, 2 * cap_y * sizeof(int32_t)));
+    ws->cap_y = cap_y;
+  }
+  return RMIPS_OK;
+}
+
+template <class T, bool FULLP>
+cudaError_t launch_mfilter(const Common& c, const Batch& b, int ngroups, int grid, size_t smem, cudaStream_t st) {
+  static thread_local bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_mfilter<T, FULLP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_mfilter<T, FULLP><<<grid, MQ_THREADS, smem, st>>>(c, b, ngroups);
+  return cudaGetLastError();
+}
+
+cudaError_t mfilter_dispatch(const rmips_index* idx, const Common& c, const Batch& b, int ngroups, int grid,
+                             size_t smem, cudaStream_t st) {
+  const bool fp = idx->full_p != 0;
+  switch (idx->precision) {
+    case RMIPS_BF16:
+      return fp ? launch_mfilter<__nv_bfloat16, true>(c, b, ngroups, grid, smem, st)
+                : launch_mfilter<__nv_bfloat16, false>(c, b, ngroups, grid, smem, st);
+    case RMIPS_FP16:
+      return fp ? launch_mfilter<__half, true>(c, b, ngroups, grid, smem, st)
+                : launch_mfilter<__half, false>(c, b, ngroups, grid, smem, st);
+    default:
+      return fp ? launch_mfilter<float, true>(c, b, ngroups, grid, smem, st)
+                : launch_mfilter<float, false>(c, b, ngroups, grid, smem, st);
+  }
+}
+
+// Batched run over queries [0, nq) staged in ws->dq / ws->dk; ws->doffs gets
+// the nq + 1 absolute offsets, results go to `out`.
+rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
+                       cudaStream_t st) {
+  Common c = make_common(idx, ws);
+  static thread_local int sm_count = 0;
+  if (!sm_count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (sm_count <= 0) sm_count = 1;
+  }
+  int64_t want_y = capacity < (int64_t)nq * idx->n ? capacity : (int64_t)nq * idx->n;
+  rmips_status s = ensure_batch(idx, ws, want_y + 1);
+  if (s != RMIPS_OK) return s;
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+  const int ngroups_max = idx->k_max;
+  const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
+  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 4096);
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t tiles = (idx->n + MQ_TU - 1) / MQ_TU;
+  const int fgrid = (int)(tiles < sm_count * per_sm ? tiles : sm_count * per_sm);
+  for (int64_t j0 = 0; j0 < nq; j0 += MQ_MAXQ) {
+    const int cnt = (int)((nq - j0) < MQ_MAXQ ? (nq - j0) : MQ_MAXQ);
+    Batch b{};
+    b.dq = ws->dq + j0 * idx->d;
+    b.dk = ws->dk + j0;
+    b.dqn = ws->dqn + j0;
+    b.deps = ws->deps + j0;
+    b.nq = cnt;
+    b.bq = ws->bq; b.bk = ws->bk; b.bqn = ws->bqn; b.beps = ws->beps; b.bidx = ws->bidx; b.grp = ws->grp;
+    b.qcnt = ws->qcnt; b.qcur = ws->qcur;
+    b.ypairs = ws->ypairs; b.cap_y = ws->cap_y;
+    b.tpairs = ws->tpairs; b.cap_t = ws->cap_t;
+    b.seg = ws->seg; b.scratch = ws->scratch;
+    b.doffs = ws->doffs + j0;
+    b.out = out;
+    b.capacity = capacity;
+    int N2 = 1;
+    while (N2 < cnt) N2 <<= 1;
+    static thread_local bool prep_cfg = false;
+    if (!prep_cfg) {
+      RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mprep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          MQ_MAXQ * (int)sizeof(unsigned long long)));
+      prep_cfg = true;
+    }
+    k_mprep<<<1, MQ_PREP_THREADS, N2 * sizeof(unsigned long long), st>>>(c, b, idx->precision);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+    const bool prof = idx->prof_on != 0;
+    if (prof) {
+      while ((int64_t)ws->ev.size() < 2 * (ws->ev_used + 1)) {
+        cudaEvent_t ev;
+        RMIPS_TRY_CUDA(cudaEventCreate(&ev));
+        ws->ev.push_back(ev);
+      }
+      RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used], st));
+    }
+    RMIPS_TRY_CUDA(mfilter_dispatch(idx, c, b, idx->k_max, fgrid, smem, st));
+    if (prof) {
+      RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used + 1], st));
+      ws->ev_used++;
+    }
+    k_mresolve<<<sm_count * 2, 256, 0, st>>>(c, b);
+    k_mscan<<<1, 1024, 0, st>>>(c, b);
+    k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
+    k_memit<<<cnt, 256, 0, st>>>(c, b);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+  }
+  return RMIPS_OK;
 }
 
 }  // namespace
@@ -752,12 +1342,17 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
     out = ws->dout;
   }
   if ((s = stage_inputs(idx, ws, qs, nq, ks, st)) != RMIPS_OK) return s;
-  if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
+  const bool batched = segs == nullptr;
+  if (batched) {
+    if ((s = run_batch(idx, ws, nq, out, capacity, st)) != RMIPS_OK) return s;
+  } else {
+    if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
+  }
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   for (int64_t j = 0; j <= nq; ++j) out_offsets[j] = ws->h_offs[j];
-  record_stats(idx, ws, ws->h_ctr, nq);
+  record_stats(idx, ws, ws->h_ctr, nq, batched);
   {
     std::lock_guard<std::mutex> lk(idx->mu);
     idx->last_stats.result = ws->h_offs[nq];

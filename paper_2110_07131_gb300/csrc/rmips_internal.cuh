@@ -32,6 +32,9 @@
 #define RMIPS_KC 32              // candidate slots per user (>= k_max + slack)
 #define RMIPS_KMAX_LIMIT 28      // largest supported k_max
 #define RMIPS_DMAX 128           // largest supported dimension
+#define MQ_MAXQ 16384            // queries per multi-query pass (14-bit index)
+#define MQ_TQ 64                 // queries per tile
+#define MQ_SLOTS (MQ_MAXQ + (RMIPS_KMAX_LIMIT + 1) * MQ_TQ)
 
 #if defined(__CUDACC__)
 #define RMIPS_HD __host__ __device__ __forceinline__
@@ -94,6 +97,22 @@ struct Workspace {
   int64_t cap_hout = 0;
   std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch
   int64_t ev_used = 0;
+  // batched (multi-query) path
+  float* bq = nullptr;           // [MQ_SLOTS][d] queries grouped by k, descending norm
+  int32_t* bk = nullptr;         // [MQ_SLOTS] k of each slot
+  float* bqn = nullptr;          // [MQ_SLOTS] norm upper bound of each slot
+  float* beps = nullptr;         // [MQ_SLOTS] absolute error slack of each slot
+  int32_t* bidx = nullptr;       // [MQ_SLOTS] query index of each slot (-1: padding)
+  int4* grp = nullptr;           // [RMIPS_KMAX_LIMIT + 1] (k, first slot, size, tiles); .x of the
+                                 // last entry after the groups is 0
+  int32_t* qcnt = nullptr;       // [MQ_MAXQ] results per query
+  int32_t* qcur = nullptr;       // [MQ_MAXQ] scatter cursors
+  unsigned long long* ypairs = nullptr;  // (query << 32 | position) decided yes
+  int64_t cap_y = 0;
+  unsigned long long* tpairs = nullptr;  // (query << 32 | position) to resolve
+  int64_t cap_t = 0;
+  int32_t* seg = nullptr;        // [cap_y] positions grouped by query
+  int32_t* scratch = nullptr;    // [2 cap_y] sort scratch for large results
 };
 
 }  // namespace rmips

@@ -59,7 +59,9 @@ class IndexInfo(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("filter_launches", C.c_int64), ("filter_ms", C.c_double), ("filter_alg_bytes", C.c_double),
-                ("users_tested", C.c_int64), ("blocks_pruned", C.c_int64), ("blocks_total", C.c_int64)]
+                ("users_tested", C.c_int64), ("blocks_pruned", C.c_int64), ("blocks_total", C.c_int64),
+                ("mfilter_launches", C.c_int64), ("mfilter_ms", C.c_double), ("mfilter_pairs", C.c_int64),
+                ("mfilter_alg_flops", C.c_double)]
 
 
 class QueryStats(C.Structure):

@@ -133,12 +133,18 @@ def test_errors(tiny):
         rmips.rmips_query(index, bad, 5)
     assert e.value.status == 3
     # the index stays usable after an error
-    full = rmips.rmips_query(index, allq[1], 10)
+    qbig = (allq[1] * 4.0).astype(np.float32)           # a large norm: many users
+    full = rmips.rmips_query(index, qbig, 10)
     assert len(full) > 1
     with pytest.raises(rmips.RmipsError) as e:
-        rmips.rmips_query(index, allq[1], 10, capacity=len(full) - 1)
+        rmips.rmips_query(index, qbig, 10, capacity=len(full) - 1)
     assert e.value.status == 5
-    assert np.array_equal(rmips.rmips_query(index, allq[1], 10, capacity=len(full)), full)
+    assert np.array_equal(rmips.rmips_query(index, qbig, 10, capacity=len(full)), full)
+    ids, offs = rmips.rmips_query_batch(index, np.stack([allq[0], qbig]), 10)
+    assert np.array_equal(ids[offs[1]:offs[2]], full)
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query_batch(index, np.stack([allq[0], qbig]), 10, capacity=len(full) - 1)
+    assert e.value.status == 5
     Qb = Q.copy()
     Qb[7, 2] = np.inf
     with pytest.raises(rmips.RmipsError) as e:
@@ -186,14 +192,18 @@ def test_device_pointers(tiny):
 
 def test_large_result_bitmap_path():
     # a query with a huge norm is in the top-k of most users: > 8192 results
-    Q, P = datagen.make_problem(20000, 500, 16, 2)
-    q = (P[0] * 50.0).astype(np.float32)
+    Q, P = datagen.make_problem(40000, 500, 16, 2)
+    q = (P[0] * 200.0).astype(np.float32)
     counts = O.counts_greater(Q, P, q)
     index = rmips.rmips_build_index(Q, P, k_max=5)
     got = rmips.rmips_query(index, q, 5)
     exp = np.nonzero(counts < 5)[0]
     assert len(exp) > 8192
     assert np.array_equal(got, exp)
+    # the batched path sorts such a result in global scratch memory
+    ids, offs = rmips.rmips_query_batch(index, np.stack([q, P[1], q]), 5)
+    assert np.array_equal(ids[offs[0]:offs[1]], exp)
+    assert np.array_equal(ids[offs[2]:offs[3]], exp)
 
 
 def test_plain_config_sum_identity_and_samples():
