@@ -181,7 +181,7 @@ def run_ours(a):
     ks = np.full(a.nq, a.k, np.int32)
     dqs = torch.from_numpy(qs).to(dev)
     dks = torch.from_numpy(ks).to(dev)
-    cap = 64 << 20
+    cap = max(1 << 20, a.nq * 2048)
     dout = torch.empty(cap, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
