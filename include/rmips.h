@@ -174,6 +174,32 @@ rmips_status rmips_profile_enable(rmips_index* index, int32_t enable);
 /* Reads the accumulated filter timing. */
 rmips_status rmips_profile_read(const rmips_index* index, rmips_profile* out);
 
+/*
+ * rmips_query_noalloc -- rmips_query for callers that must not allocate.
+ * (The paper has no counterpart: this is an interface choice of the library.)
+ *
+ * Who needs it: code whose device memory belongs to another allocator (a
+ * framework's caching allocator that has reserved the free memory, where a
+ * cudaMalloc behind its back fails or fragments the pool), and
+ * latency-critical serving threads, where cudaMalloc / cudaFree may
+ * synchronise the device and stall every other stream.  This call performs no
+ * allocation of any kind: its scratch (about 8.5 MB) is one fixed array in
+ * device memory that exists on every GPU where the library is loaded, for the
+ * life of the process.
+ *
+ * Limit: the index may hold at most 1,048,576 users (RMIPS_ERR_ARG beyond).
+ * q: d floats, host or device.  out_ids: DEVICE memory, capacity int64 slots,
+ * receives the ascending result ids.  *out_count (host) receives the result
+ * size; on RMIPS_ERR_CAPACITY it is the size needed and out_ids is untouched.
+ * The first call on a device looks up the array's device address.
+ * All calls share the one array, so calls are serialised by a process-wide
+ * lock held until the call's GPU work has finished; GPU work of two calls that
+ * overlapped would race on the shared scratch.  Synchronises `stream`.
+ * Errors: ARG, K_RANGE, NONFINITE, CAPACITY, CUDA.
+ */
+rmips_status rmips_query_noalloc(rmips_index* index, const float* q, int32_t k, int64_t* out_ids,
+                                 int64_t capacity, int64_t* out_count, void* stream);
+
 /* Sizes and build statistics of an index. */
 rmips_status rmips_index_get_info(const rmips_index* index, rmips_index_info* out);
 

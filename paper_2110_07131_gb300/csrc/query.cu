@@ -1364,3 +1364,133 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
     RMIPS_TRY_CUDA(cudaMemcpy(out_ids, ws->dout, total * sizeof(long long), cudaMemcpyDeviceToHost));
   return RMIPS_OK;
 }
+
+// ===========================================================================
+// Allocation-free single query.
+//
+// Some callers cannot let a library call cudaMalloc: a framework whose caching
+// allocator has already reserved the device's free memory (a cudaMalloc
+// behind its back fails or fragments the pool), or a latency-critical serving
+// thread (cudaMalloc / cudaFree can synchronise the whole device and stall
+// every other stream).  rmips_query_noalloc serves them: its scratch lives in
+// one file-scope device array of fixed size, created when the library is
+// loaded, and the call allocates nothing -- no device, pinned-host or
+// workspace-pool memory.
+// ===========================================================================
+namespace rmips {
+namespace {
+
+constexpr int64_t NA_MAX_USERS = 1 << 20;                          // largest |Q| served
+constexpr size_t NA_CTR = 0;                                         // C_NCOUNTERS x int64
+constexpr size_t NA_Q = 256;                                         // RMIPS_DMAX floats
+constexpr size_t NA_K = NA_Q + RMIPS_DMAX * sizeof(float);           // one int32
+constexpr size_t NA_QN = NA_K + 16;                                  // one float
+constexpr size_t NA_EPS = NA_QN + 16;                                // one float
+constexpr size_t NA_OFFS = NA_EPS + 16;                              // two int64
+constexpr size_t NA_YES = NA_OFFS + 256;                             // NA_MAX_USERS x int32
+constexpr size_t NA_TODO = NA_YES + NA_MAX_USERS * sizeof(int32_t);  // NA_MAX_USERS x int32
+constexpr size_t NA_BITMAP = NA_TODO + NA_MAX_USERS * sizeof(int32_t);  // NA_MAX_USERS/32 + 1 words
+constexpr size_t NA_BYTES = NA_BITMAP + (NA_MAX_USERS / 32 + 64) * sizeof(uint32_t);
+
+static_assert(NA_CTR + C_NCOUNTERS * sizeof(long long) <= NA_Q, "counter block overflows");
+
+// Shared by every call on a device; kept for the life of the process.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[64] = {};
+
+// Device address of the scratch array for the current device (looked up once
+// per device; the host-side symbol is only a stand-in, never a device address).
+rmips_status noalloc_base(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= 64) { set_error("device ordinal out of range"); return RMIPS_ERR_ARG; }
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+      return RMIPS_ERR_CUDA;
+    }
+    g_noalloc_base[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_base[dev]);
+  return RMIPS_OK;
+}
+
+}  // namespace
+}  // namespace rmips
+
+extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, int32_t k, int64_t* out_ids,
+                                            int64_t capacity, int64_t* out_count, void* stream) {
+  if (!idx || !q || !out_count || capacity < 0 || (capacity > 0 && !out_ids)) {
+    set_error("null argument or negative capacity");
+    return RMIPS_ERR_ARG;
+  }
+  if (idx->n > NA_MAX_USERS) {
+    set_error("rmips_query_noalloc serves at most 1048576 users (its fixed scratch size); use rmips_query");
+    return RMIPS_ERR_ARG;
+  }
+  if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  if (capacity > 0 && !is_device_ptr(out_ids)) {
+    set_error("rmips_query_noalloc writes ids to device memory only");
+    return RMIPS_ERR_ARG;
+  }
+  DeviceGuard dg(idx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  // All calls share one scratch array: hold the lock until the GPU work is done.
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  int dev = 0;
+  RMIPS_TRY_CUDA(cudaGetDevice(&dev));
+  unsigned char* base = nullptr;
+  rmips_status s = noalloc_base(dev, &base);
+  if (s != RMIPS_OK) return s;
+
+  Workspace ws;                                    // views into the scratch array, nothing owned
+  ws.ctr = reinterpret_cast<long long*>(base + NA_CTR);
+  ws.dq = reinterpret_cast<float*>(base + NA_Q);
+  ws.dk = reinterpret_cast<int32_t*>(base + NA_K);
+  ws.dqn = reinterpret_cast<float*>(base + NA_QN);
+  ws.deps = reinterpret_cast<float*>(base + NA_EPS);
+  ws.doffs = reinterpret_cast<long long*>(base + NA_OFFS);
+  ws.yes = reinterpret_cast<int32_t*>(base + NA_YES);
+  ws.todo = reinterpret_cast<int32_t*>(base + NA_TODO);
+  ws.bitmap = reinterpret_cast<uint32_t*>(base + NA_BITMAP);
+  // The array keeps the previous call's contents: clear what must start at zero.
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws.ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws.doffs, 0, 2 * sizeof(long long), st));
+  RMIPS_TRY_CUDA(cudaMemsetAsync(ws.bitmap, 0, (idx->n / 32 + 1) * sizeof(uint32_t), st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws.dq, q, idx->d * sizeof(float),
+                                 is_device_ptr(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws.dk, &k, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+
+  Common c = make_common(idx, &ws);
+  int sm_count = 1;
+  cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = 512 + FW * 2 * 8 + (size_t)FW * 2 * 32 * idx->d * elem_bytes(idx->precision);
+  const int64_t nchunks = (idx->n + 31) / 32;
+  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 1024);
+  per_sm = per_sm > 8 ? 8 : (per_sm < 1 ? 1 : per_sm);
+  const int64_t want = (nchunks + FW - 1) / FW;
+  const int fgrid = (int)(want < sm_count * per_sm ? want : sm_count * per_sm);
+  EmitArgs e{};
+  e.seg_lo = 0;
+  e.seg_hi = INT64_MAX;
+  e.segmask = nullptr;
+  e.bitmap = ws.bitmap;
+  e.out = reinterpret_cast<long long*>(out_ids);
+  e.capacity = capacity;
+  e.offs = ws.doffs;
+  k_qprep<<<1, 32, 0, st>>>(c, 1, idx->precision);
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  RMIPS_TRY_CUDA(filter_dispatch(idx, c, 0, fgrid, smem, st));
+  k_resolve<<<sm_count, 256, 0, st>>>(c, 0);
+  k_emit<<<1, EMIT_THREADS, 0, st>>>(c, e, 0);
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  long long h[C_NCOUNTERS];
+  long long offs[2];
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(h, ws.ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(offs, ws.doffs, sizeof(offs), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  *out_count = offs[1];
+  return status_from_device(h[C_STATUS]);
+}

@@ -18,7 +18,8 @@ __all__ = [
     "RmipsError", "Index", "load_library", "rmips_build_index", "rmips_query",
     "rmips_query_batch", "rmips_index_get_info", "rmips_last_query_stats",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
-    "rmips_profile_enable", "rmips_profile_read", "EXPORTED_SYMBOLS", "FP32", "BF16", "FP16",
+    "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
+    "FP32", "BF16", "FP16",
 ]
 
 FP32, BF16, FP16 = 0, 1, 2
@@ -31,6 +32,7 @@ EXPORTED_SYMBOLS = [
     "rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
     "rmips_last_query_stats", "rmips_index_export", "rmips_free_index", "rmips_status_string",
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
+    "rmips_query_noalloc",
 ]
 
 
@@ -104,9 +106,10 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_exact_sign_host.restype = I32
         lib.rmips_profile_enable.argtypes = [VP, I32]
         lib.rmips_profile_read.argtypes = [VP, C.POINTER(Profile)]
+        lib.rmips_query_noalloc.argtypes = [VP, P, I32, P, I64, C.POINTER(I64), VP]
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
-                     "rmips_profile_read"):
+                     "rmips_profile_read", "rmips_query_noalloc"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -228,6 +231,20 @@ def rmips_query(index: Index, q, k: int, segment=None, capacity=None, out=None, 
     _check(_lib.rmips_query(index.handle, qp, int(k), C.byref(seg) if seg is not None else None,
                             optr, cap, C.byref(cnt), _stream(stream)))
     return buf[:cnt.value]
+
+
+def rmips_query_noalloc(index: Index, q, k: int, out, stream=None) -> int:
+    """Allocation-free single query (see ``include/rmips.h``).
+
+    ``out`` must be a device tensor of int64; returns the result size (the
+    first that many entries of ``out`` hold the ascending ids).
+    """
+    qp, qk = _ptr_f32(q)
+    cnt = C.c_int64(0)
+    cap = int(out.numel())
+    _check(_lib.rmips_query_noalloc(index.handle, qp, int(k), out.data_ptr(), cap, C.byref(cnt),
+                                    _stream(stream)))
+    return cnt.value
 
 
 def rmips_query_batch(index: Index, qs, ks, segments=None, capacity=None, out=None, stream=None):
