@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--p-prime", type=int, default=0, help="0 = bounds over all of P")
     ap.add_argument("--block-size", type=int, default=32)
+    ap.add_argument("--batch-kernel", default="tc", choices=["tc", "cuda"],
+                    help="batched filter on tensor cores (TF32 tiles) or CUDA cores (FP32 FMA)")
     ap.add_argument("--plain-queries", type=int, default=400)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU baseline time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,6 +59,7 @@ def workload(a):
             "n_users": a.n, "n_items": a.m, "d": a.d, "k": a.k, "k_max": a.k_max,
             "queries_per_step": a.nq, "index": "full-P" if a.p_prime == 0 else f"P'={a.p_prime}",
             "block_size": a.block_size, "filter_precision": a.precision,
+            "batch_filter": "tcgen05 TF32 tiles" if a.batch_kernel == "tc" else "CUDA-core FP32 FMA tiles",
             "l2": "inputs larger than L2 (Q 200 MB fp32 + bounds 200 MB); no flush between steps"}
 
 
@@ -172,7 +175,7 @@ def run_ours(a):
     Q, P = datagen.make_problem(a.n, a.m, a.d, SEED)
     t0 = time.perf_counter()
     index = rmips.rmips_build_index(Q, P, k_max=a.k_max, block_size=a.block_size, p_prime=a.p_prime,
-                                    precision=a.precision)
+                                    precision=a.precision, batch_tensor_cores=(a.batch_kernel == "tc"))
     build_s = time.perf_counter() - t0
     info = index.info()
 
@@ -273,19 +276,33 @@ def run_ours(a):
     m_flops = prof["mfilter_alg_flops"] / ml
     m_ms = prof["mfilter_ms"] / ml
     m_ach = m_flops / (m_ms / 1e3) / 1e12 if m_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "k_mfilter (multi-query Lemma 3 prefixes + FP32 FFMA tiles + "
-                                          "Lemmas 1/2 epilogue)",
-                "achieved": m_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": m_ach / alu_peak,
-                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
-                "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
-                "pairs_per_launch": prof["mfilter_pairs"] / ml,
-                "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
+    tc_path = a.batch_kernel == "tc" and a.d <= 64 and a.precision == "fp32"
+    if tc_path:
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        tf32_peak = bf16 * (1.1 / 2.25)
+        roofline = {"bound": "tensor", "kernel": "k_mfilter_tc (Lemma 3 prefixes + tcgen05 TF32 128x64x64 tiles "
+                                                  "in TMEM + Lemmas 1/2 epilogue)",
+                    "achieved": m_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m_ach / tf32_peak,
+                    "peak_source": f"measured bf16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25",
+                    "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
+                    "pairs_per_launch": prof["mfilter_pairs"] / ml,
+                    "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
+    else:
+        roofline = {"bound": "alu", "kernel": "k_mfilter (multi-query Lemma 3 prefixes + FP32 FFMA tiles + "
+                                              "Lemmas 1/2 epilogue)",
+                    "achieved": m_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": m_ach / alu_peak,
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                    "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
+                    "pairs_per_launch": prof["mfilter_pairs"] / ml,
+                    "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
 
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else a.precision, "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": ("tf32" if tc_path else ("f32" if a.precision == "fp32" else a.precision)) + "+f64 recheck",
+            "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": a.steps * 6 * ((a.nq + 16383) // 16384),
+            "gpu_launches": a.steps * 7 * ((a.nq + 16383) // 16384),
             "roofline_single_query_filter": roof_single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain,
             "batch_latency_ms": ms_max / a.steps,

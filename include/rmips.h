@@ -69,8 +69,12 @@ typedef struct {
                          over all of P ("full-P"); otherwise over the first
                          p_prime items in descending norm, as in the paper */
   int32_t precision;  /* RMIPS_FP32, RMIPS_BF16 or RMIPS_FP16 */
-  int32_t reserved;   /* must be 0 */
+  int32_t flags;      /* RMIPS_FLAG_* bits; 0 for the defaults */
 } rmips_build_opts;
+
+/* rmips_build_opts.flags: run the batched filter on CUDA cores (float32 FMA)
+   instead of tensor cores (TF32 tiles, used for float32 indexes with d <= 64). */
+#define RMIPS_FLAG_BATCH_CUDA_CORES 1
 
 /* Optional restriction of a query to a subset of users. */
 typedef struct {
@@ -236,6 +240,18 @@ const char* rmips_last_error(void);
  * without a GPU.  Ordinary host function; d in 1..256.
  */
 int32_t rmips_exact_sign_host(const float* u, const float* a, const float* b, int32_t d);
+
+/*
+ * rmips_debug_tc_tile -- test hook for the tensor-core tiles of the batched
+ * filter (no counterpart in the paper).  Runs one 128 x 64 x 64 TF32 tile
+ * through the shared-memory layout, UMMA descriptors (with the given leading
+ * and stride byte offsets), tcgen05.mma and TMEM loads the batched filter
+ * uses: D[128][64] = A[128][64] * B[64][64]^T.  A, B, D: device float32,
+ * row-major.  lbo, sbo: multiples of 16 in [16, 4096].  Synchronises
+ * `stream`.  Errors: ARG, TIMEOUT, CUDA.
+ */
+rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t lbo, int32_t sbo,
+                                 void* stream);
 
 #ifdef __cplusplus
 }

@@ -291,7 +291,8 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   }
   int bs = opts->block_size == 0 ? 32 : opts->block_size;
   if (opts->k_max < 1 || opts->k_max > RMIPS_KMAX_LIMIT || !(bs == 32 || bs == 64 || bs == 128 || bs == 256) ||
-      opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 || opts->reserved != 0) {
+      opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 ||
+      (opts->flags & ~RMIPS_FLAG_BATCH_CUDA_CORES) != 0) {
     set_error("invalid build options (k_max 1..28, block_size 32/64/128/256, precision 0..2)");
     return RMIPS_ERR_ARG;
   }
@@ -300,6 +301,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   rmips_index* idx = new rmips_index();
   idx->n = n; idx->m = m; idx->d = d; idx->k_max = opts->k_max; idx->bs = bs;
   idx->precision = opts->precision;
+  idx->batch_tc = (opts->flags & RMIPS_FLAG_BATCH_CUDA_CORES) ? 0 : 1;
   idx->pp = (opts->p_prime == 0 || opts->p_prime >= m) ? m : opts->p_prime;
   idx->full_p = idx->pp == m ? 1 : 0;
   idx->nb = (n + bs - 1) / bs;

@@ -45,7 +45,9 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->ypairs);
   cudaFree(ws->tpairs);
   cudaFree(ws->seg);
-  cudaFree(ws->scratch);
+  cudaFree(ws->bqt);
+  cudaFree(ws->big);
+  cudaFree(ws->bigmaps);
   delete ws;
 }
 

@@ -676,6 +676,136 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
 }
 
 
+
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) helpers: TMEM allocation, UMMA shared
+// memory descriptors, MMA issue/commit and TMEM loads.
+//
+// Operand tiles use the K-major, non-swizzled canonical layout: the tile is cut
+// into core matrices of 8 rows x 16 bytes (8 x 4 TF32 values); row r of a core
+// matrix sits 16*r bytes from its start; core matrices adjacent along K are
+// TC_LBO bytes apart and 8-row groups are TC_SBO bytes apart.
+// ---------------------------------------------------------------------------
+constexpr uint32_t TC_K = 64;                        // padded inner dimension (d <= 64)
+constexpr uint32_t TC_LBO = 128;                     // next 16-byte K chunk
+constexpr uint32_t TC_SBO = (TC_K / 4) * 128;        // next 8-row group (2048 bytes)
+
+__host__ __device__ __forceinline__ uint32_t tc_off(uint32_t row, uint32_t k) {
+  return (row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4;   // bytes
+}
+
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                            // descriptor version of sm_100 family
+  return d;                                          // base offset 0, no swizzle
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(uint32_t M, uint32_t N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// One 128 x 64 x 64 TF32 tile through the layout, descriptors, MMA and TMEM
+// loads used by the batched filter (test hook).  A [128][64], B [64][64]
+// row-major float32 in global memory; D [128][64] = A B^T.
+__global__ void __launch_bounds__(128) k_debug_tc(const float* __restrict__ A, const float* __restrict__ B,
+                                                  float* __restrict__ D, uint32_t lbo, uint32_t sbo,
+                                                  long long* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  float* sA = reinterpret_cast<float*>(dsm);                     // 128 x 64 (32 KB)
+  float* sB = reinterpret_cast<float*>(dsm + 128 * TC_K * 4);    // 64 x 64 (16 KB)
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < 128 * (int)TC_K; e += 128) sA[tc_off(e / TC_K, e % TC_K) / 4] = A[e];
+  for (int e = tid; e < 64 * (int)TC_K; e += 128) sB[tc_off(e / TC_K, e % TC_K) / 4] = B[e];
+  if (warp == 0) {
+    tmem_alloc(&taddr_s, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = taddr_s;
+  if (tid == 0) {
+    const uint32_t idesc = tc_idesc_tf32(128, 64);
+    for (uint32_t s = 0; s < TC_K / 8; ++s) {
+      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, lbo, sbo);
+      const uint64_t bd = tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, lbo, sbo);
+      tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+    }
+    tc_commit(&bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0)) s_fail = 1;
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) set_status(status, ST_TIMEOUT);
+  } else {
+    tc_fence_after();
+    float v[16];
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_ld_wait();
+      for (int i = 0; i < 16; ++i) D[(warp * 32 + lane) * 64 + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, 64);
+}
+
 // ===========================================================================
 // Batched path: up to MQ_MAXQ queries in one pass over the user rows.
 //
@@ -716,7 +846,10 @@ struct Batch {
   unsigned long long* tpairs;
   long long cap_t;
   int32_t* seg;
-  int32_t* scratch;
+  float* bqt;             // query tiles in the UMMA layout (TC path), may be null
+  int32_t* big;           // queries with more than EMIT_SORT_CAP results
+  uint32_t* bigmaps;      // MQ_BIG_SLOTS id bitmaps of nw words each
+  int64_t nw;             // words per id bitmap
   long long* doffs;       // [nq + 1] offsets of this pass (absolute)
   long long* out;
   long long capacity;
@@ -734,6 +867,7 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, in
   if (tid == 0) {
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
+    c.ctr[C_NBIG] = 0;
   }
   if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = 0;
   __syncthreads();
@@ -820,6 +954,14 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, in
     const int slot = e / c.d, i = e - slot * c.d;
     const int j = b.bidx[slot];
     b.bq[e] = j >= 0 ? b.dq[(int64_t)j * c.d + i] : 0.f;
+  }
+  if (b.bqt) {                     // 64-query tiles in the UMMA layout, K padded to 64
+    for (int e = tid; e < total_slots * (int)TC_K; e += MQ_PREP_THREADS) {
+      const int slot = e / (int)TC_K, k = e - slot * (int)TC_K;
+      const int j = b.bidx[slot];
+      const float v = (j >= 0 && k < c.d) ? b.dq[(int64_t)j * c.d + k] : 0.f;
+      b.bqt[(size_t)(slot / MQ_TQ) * (MQ_TQ * TC_K) + tc_off(slot % MQ_TQ, k) / 4] = v;
+    }
   }
 }
 
@@ -1077,6 +1219,10 @@ __global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
   for (int j = j0; j < j1; ++j) {
     b.doffs[j] = run;
     run += b.qcnt[j];
+    if (b.qcnt[j] > EMIT_SORT_CAP) {
+      const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
+      b.big[r] = j;
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -1101,7 +1247,8 @@ __global__ void k_mscatter(Common c, Batch b) {
   }
 }
 
-// One CTA per query: positions -> ids, sorted ascending.
+// One CTA per query with at most EMIT_SORT_CAP results: positions -> ids,
+// bitonic sort in shared memory, ascending.
 __global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
   __shared__ int32_t keys[EMIT_SORT_CAP];
   const int j = blockIdx.x;
@@ -1110,28 +1257,341 @@ __global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
   const long long off = b.doffs[j];
   const int cnt = b.qcnt[j];
   const int tid = threadIdx.x;
-  if (cnt == 0) return;
+  if (cnt == 0 || cnt > EMIT_SORT_CAP) return;           // large results: k_memit_big
   int N2 = 1;
   while (N2 < cnt) N2 <<= 1;
-  int32_t* K = keys;
-  if (N2 > EMIT_SORT_CAP) K = b.scratch + 2 * (off - base0);
   for (int i = tid; i < N2; i += blockDim.x)
-    K[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
+    keys[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
   __syncthreads();
   for (int kk = 2; kk <= N2; kk <<= 1) {
     for (int jj = kk >> 1; jj > 0; jj >>= 1) {
       for (int i = tid; i < N2; i += blockDim.x) {
         int p = i ^ jj;
         if (p > i) {
-          int32_t x = K[i], y = K[p];
-          if ((x > y) == ((i & kk) == 0)) { K[i] = y; K[p] = x; }
+          int32_t x = keys[i], y = keys[p];
+          if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
         }
       }
-      if (N2 > EMIT_SORT_CAP) __threadfence_block();
       __syncthreads();
     }
   }
-  for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = K[i];
+  for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = keys[i];
+}
+
+// Queries with large results: each CTA owns one id bitmap and handles the
+// large queries r = blockIdx.x, blockIdx.x + gridDim.x, ... in turn: set one
+// bit per result id, then read the bitmap back in order (block-wide prefix of
+// per-thread bit counts), clearing it for the next query.
+__global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
+  __shared__ int s_warp[32];
+  __shared__ long long s_nbig;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
+    s_bad = c.ctr[C_STATUS] != 0;
+    s_nbig = c.ctr[C_NBIG];
+  }
+  __syncthreads();
+  if (s_bad) return;
+  uint32_t* bm = b.bigmaps + (int64_t)blockIdx.x * b.nw;
+  const long long base0 = b.doffs[0];
+  const int64_t per = (b.nw + 1023) / 1024;
+  const int64_t w0 = tid * per, w1 = (w0 + per < b.nw) ? w0 + per : b.nw;
+  for (long long r = blockIdx.x; r < s_nbig; r += gridDim.x) {
+    const int j = b.big[r];
+    const long long off = b.doffs[j];
+    const int cnt = b.qcnt[j];
+    for (int i = tid; i < cnt; i += 1024) {
+      const int32_t v = c.permQ[b.seg[off - base0 + i]];
+      atomicOr(&bm[v >> 5], 1u << (v & 31));
+    }
+    __syncthreads();
+    int local = 0;
+    for (int64_t w = w0; w < w1; ++w) local += __popc(__ldcg(&bm[w]));
+    int x = local;
+    for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int v = s_warp[lane];
+      for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, v, o); if (lane >= o) v += y; }
+      s_warp[lane] = v;
+    }
+    __syncthreads();
+    long long o = off + (x - local) + (wid ? s_warp[wid - 1] : 0);
+    for (int64_t w = w0; w < w1; ++w) {
+      uint32_t word = __ldcg(&bm[w]);
+      bm[w] = 0u;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        word &= word - 1;
+        b.out[o++] = w * 32 + bit;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+
+// ===========================================================================
+// Batched filter on tensor cores (TF32, d <= 64).
+//
+// Same work decomposition as k_mfilter: a CTA owns a tile of 128 users, finds
+// the Lemma 3 prefix of every k-group for every block of the tile, and skips
+// the tile when nothing survives.  The users are written once into shared
+// memory in the UMMA layout (K padded to 64 with zeros); the surviving
+// 64-query tiles (laid out the same way by k_mprep) arrive by 1-D TMA, one
+// ahead.  Thread 0 issues the 8 tcgen05.mma (128 x 64 x 8, TF32 in, FP32
+// accumulate in TMEM) of a tile; every thread owns one user row, copies its
+// 64 accumulators from TMEM into registers, after which the next tile's MMA
+// runs while the row is classified (Lemma 1, then hi_k / Lemma 2).
+//
+// Error bound of a TF32 inner product: each operand is within 2^-10 of its
+// float32 value (10 fraction bits, any rounding), each product of two TF32
+// values is exact in float32, and the float32 accumulation over K = 64 terms
+// (8 chained MMAs) is charged 65 * 2^-22 relative to sum |a_i b_i|; with
+// sum |a_i b_i| <= ||u|| ||q|| the bound is TC_ERR ||u|| ||q|| plus the
+// slack of operands below the normal range.
+// ===========================================================================
+constexpr int TCU = 128;                       // users per tile (MMA M)
+constexpr int TCQ = MQ_TQ;                     // queries per tile (MMA N)
+constexpr int TC_THREADS = 128;
+constexpr float TC_ERR = 0.00198f;             // >= 2^-9 + 2^-20 + 65 * 2^-22 * (1 + 2^-9)
+constexpr uint32_t TC_TILE_BYTES = TCQ * TC_K * 4;   // one query tile (16 KB)
+constexpr uint32_t TC_A_BYTES = TCU * TC_K * 4;      // one user tile (32 KB)
+
+__global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, const float* __restrict__ bqt,
+                                                            int ngroups) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  float* sA = reinterpret_cast<float*>(tsm);                                   // 32 KB
+  float* sB = reinterpret_cast<float*>(tsm + TC_A_BYTES);                      // 2 x 16 KB
+  __shared__ __align__(8) uint64_t bar_b[2];     // query tile landed
+  __shared__ __align__(8) uint64_t bar_m;        // MMA done
+  __shared__ uint32_t taddr_s;
+  __shared__ float un_s[TCU];
+  __shared__ float eq_s[2][TCQ], qe_s[2][TCQ];
+  __shared__ int qj_s[2][TCQ];
+  __shared__ int pre[RMIPS_KMAX_LIMIT][4];
+  __shared__ int gmax[RMIPS_KMAX_LIMIT];
+  __shared__ int any_tile, s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int d = c.d;
+  const int64_t n = c.n;
+  const int sub = c.bs < TCU ? c.bs : TCU;
+  const int nbt = TCU / sub;
+  const float un0 = c.unorm[0];                   // largest user norm (users are sorted)
+  const float tiny = (d + 2) * 0x1p-126f;
+
+  if (warp == 0) {
+    tmem_alloc(&taddr_s, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_b[0], 1);
+    mbar_init(&bar_b[1], 1);
+    mbar_init(&bar_m, 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = taddr_s;
+  const uint32_t idesc = tc_idesc_tf32(TCU, TCQ);
+  uint32_t phb = 0, ph_m = 0;                    // parity of the next wait: bit x for bar_b[x] / bar_m
+  long long st_pairs = 0, st_skipped = 0, st_yes = 0, st_todo = 0;
+
+  for (int64_t u0 = (int64_t)blockIdx.x * TCU; u0 < n && !s_fail; u0 += (int64_t)gridDim.x * TCU) {
+    // 1. Lemma 3 prefixes
+    if (tid < ngroups * nbt) {
+      const int g = tid / nbt, sb = tid - g * nbt;
+      const int64_t ufirst = u0 + (int64_t)sb * sub;
+      int r = 0;
+      const int4 G = b.grp[g];
+      if (ufirst < n && G.z > 0) {
+        const int64_t blk = ufirst / c.bs;
+        r = lemma3_prefix(b.bqn, G.y, G.z, c.hdr[blk], c.LB[(int64_t)(G.x - 1) * c.nb + blk]);
+      }
+      pre[g][sb] = r;
+    }
+    __syncthreads();
+    if (tid < ngroups) {
+      int mx = 0;
+      for (int sb = 0; sb < nbt; ++sb) mx = max(mx, pre[tid][sb]);
+      gmax[tid] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int a = 0;
+      for (int g = 0; g < ngroups; ++g) a |= gmax[g];
+      any_tile = a;
+    }
+    __syncthreads();
+    if (!any_tile) {
+      if (tid == 0) st_skipped += 1;
+      continue;
+    }
+    const int64_t nvalid = (n - u0) < TCU ? (n - u0) : TCU;
+    // 2. user tile into the UMMA layout (float32 rows -> K-padded core matrices)
+    {
+      const float* src = c.Qs + u0 * d;
+      for (int e = tid; e < TCU * (int)TC_K; e += TC_THREADS) {
+        const int uu = e / (int)TC_K, k = e - uu * (int)TC_K;
+        const float v = (uu < nvalid && k < d) ? src[(int64_t)uu * d + k] : 0.f;
+        sA[tc_off(uu, k) / 4] = v;
+      }
+      un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
+    }
+    if (tid == 0) {
+      for (int g = 0; g < ngroups; ++g)
+        for (int sb = 0; sb < nbt; ++sb) {
+          const int64_t us = (int64_t)sb * sub;
+          const int64_t cnt = nvalid - us < sub ? (nvalid - us > 0 ? nvalid - us : 0) : sub;
+          st_pairs += (long long)pre[g][sb] * cnt;
+        }
+    }
+    fence_proxy_async();
+    // 3. walk the (group, query tile) items of this user tile
+    int nitems = 0;
+    for (int g = 0; g < ngroups; ++g) nitems += (gmax[g] + TCQ - 1) / TCQ;
+    // item -> (group, tile) by walking the groups
+    int g_ld = 0, t_ld = 0;                       // next item to load
+    auto advance = [&](int& g, int& t) {
+      ++t;
+      while (g < ngroups && t >= (gmax[g] + TCQ - 1) / TCQ) { ++g; t = 0; }
+    };
+    while (g_ld < ngroups && gmax[g_ld] == 0) ++g_ld;
+    auto load_item = [&](int g, int t, int buf) {
+      const int s0 = b.grp[g].y + t * TCQ;
+      if (tid == 0) {
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&bar_b[buf], TC_TILE_BYTES);
+        bulk_g2s(reinterpret_cast<unsigned char*>(sB) + (size_t)buf * TC_TILE_BYTES,
+                 bqt + (size_t)(s0 / TCQ) * (TC_TILE_BYTES / 4), TC_TILE_BYTES, &bar_b[buf]);
+      }
+      if (tid < TCQ) {
+        const float qn = b.bqn[s0 + tid];
+        eq_s[buf][tid] = __fmul_ru(qn, TC_ERR);
+        qe_s[buf][tid] = __fmaf_ru(fmaxf(qn, un0), tiny, b.beps[s0 + tid]);
+        qj_s[buf][tid] = b.bidx[s0 + tid];
+      }
+    };
+    int g_cur = g_ld, t_cur = 0;
+    load_item(g_ld, 0, 0);
+    advance(g_ld, t_ld);
+    __syncthreads();                               // user tile written, constants of item 0 visible
+    // issue MMA(0)
+    if (tid == 0) {
+      bool ok = mbar_wait_bounded(&bar_b[0], phb & 1u);
+      if (ok) {
+        tc_fence_after();
+        for (uint32_t s = 0; s < TC_K / 8; ++s)
+          tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
+                      tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
+        tc_commit(&bar_m);
+      } else {
+        s_fail = 1;
+      }
+    }
+    phb ^= 1u;
+    int g_L = -1;                                  // group whose bound row is in L
+    float2 L = make_float2(kInf, kInf);
+    for (int it = 0; it < nitems; ++it) {
+      const int buf = it & 1;
+      // A. prefetch the next query tile into the other buffer (its last reader,
+      //    MMA(it - 1), has completed)
+      const bool has_next = it + 1 < nitems;
+      if (has_next) load_item(g_ld, t_ld, buf ^ 1);
+      // B. wait for MMA(it); copy this thread's accumulator row to registers
+      bool ok = s_fail ? false : mbar_wait_bounded(&bar_m, ph_m);
+      ph_m ^= 1u;
+      ok = __syncthreads_and(ok && !s_fail);
+      if (!ok) {
+        if (tid == 0) s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      float acc[TCQ];
+#pragma unroll
+      for (int c0 = 0; c0 < TCQ; c0 += 16) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc + c0);
+      tmem_ld_wait();
+      if (g_cur != g_L) {                            // this user's (lo, hi) for the group's k
+        L = tid < nvalid ? c.Lb[(int64_t)(b.grp[g_cur].x - 1) * n + u0 + tid] : make_float2(kInf, kInf);
+        g_L = g_cur;
+      }
+      tc_fence_before();
+      __syncthreads();                               // TMEM row consumed; next constants visible
+      // C. issue MMA(it + 1) on the next query tile; it overlaps the epilogue below
+      if (has_next && tid == 0) {
+        bool okb = mbar_wait_bounded(&bar_b[buf ^ 1], (phb >> (buf ^ 1)) & 1u);
+        if (okb) {
+          tc_fence_after();
+          const uint32_t bbase = smem_u32(sB) + (uint32_t)(buf ^ 1) * TC_TILE_BYTES;
+          for (uint32_t s = 0; s < TC_K / 8; ++s)
+            tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
+                        tc_sdesc(bbase + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
+          tc_commit(&bar_m);
+        } else {
+          s_fail = 1;
+        }
+      }
+      if (has_next) phb ^= 1u << (buf ^ 1);
+      // D. epilogue for (this user, the 64 queries of item it)
+      const int uu = tid;
+      const int sb = uu / sub;
+      int live = pre[g_cur][sb] - t_cur * TCQ;
+      live = live < 0 ? 0 : (live > TCQ ? TCQ : live);
+      if (uu >= nvalid) live = 0;
+      const float un = un_s[uu];
+      const int k = b.grp[g_cur].x;
+      const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
+      uint64_t ym = 0, tm = 0;
+#pragma unroll
+      for (int q = 0; q < TCQ; ++q) {
+        if (q < live) {
+          const float e = __fmaf_ru(un, eq_s[buf][q], qe_s[buf][q]);
+          if (!(__fadd_ru(acc[q], e) < L.x)) {                 // not decided no by Lemma 1
+            const float lo = __fsub_rd(acc[q], e);
+            const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
+            if (yes) ym |= 1ull << q; else tm |= 1ull << q;
+          }
+        }
+      }
+      while (ym) {
+        const int q = __ffsll((long long)ym) - 1;
+        ym &= ym - 1;
+        const int j = qj_s[buf][q];
+        const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+        if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
+        atomicAdd(&b.qcnt[j], 1);
+        ++st_yes;
+      }
+      while (tm) {
+        const int q = __ffsll((long long)tm) - 1;
+        tm &= tm - 1;
+        const int j = qj_s[buf][q];
+        const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
+        if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
+        else set_status(c.ctr, ST_INTERNAL);
+        ++st_todo;
+      }
+      g_cur = g_ld;
+      t_cur = t_ld;
+      if (has_next) advance(g_ld, t_ld);
+      __syncthreads();                               // constants of item it consumed
+    }
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) set_status(c.ctr, ST_TIMEOUT);
+  if (tid == 0) {
+    atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)st_pairs);
+    atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)st_skipped);
+  }
+  if (st_yes) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)st_yes);
+  if (st_todo) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)st_todo);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, 64);
 }
 
 rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
@@ -1147,13 +1607,20 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
     ws->cap_t = 16ll << 20;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->tpairs, ws->cap_t * sizeof(unsigned long long)));
   }
+  if (!ws->bqt && idx->d <= (int)TC_K)
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bqt, (size_t)MQ_SLOTS * TC_K * sizeof(float)));
+  if (!ws->big) {
+    const int64_t nw = idx->n / 32 + 1;
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->big, MQ_MAXQ * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bigmaps, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
+    RMIPS_TRY_CUDA(cudaMemset(ws->bigmaps, 0, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
+  }
   if (cap_y < 4096) cap_y = 4096;
   if (ws->cap_y < cap_y) {
-    cudaFree(ws->ypairs); cudaFree(ws->seg); cudaFree(ws->scratch);
-    ws->ypairs = nullptr; ws->seg = nullptr; ws->scratch = nullptr; ws->cap_y = 0;
+    cudaFree(ws->ypairs); cudaFree(ws->seg);
+    ws->ypairs = nullptr; ws->seg = nullptr; ws->cap_y = 0;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->ypairs, cap_y * sizeof(unsigned long long)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->seg, cap_y * sizeof(int32_t)));
-    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->scratch, 2 * cap_y * sizeof(int32_t)));
     ws->cap_y = cap_y;
   }
   return RMIPS_OK;
@@ -1205,7 +1672,11 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   if (s != RMIPS_OK) return s;
   RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
   const int ngroups_max = idx->k_max;
+  const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K && idx->precision == RMIPS_FP32;
   const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
+  const size_t smem_tc = TC_A_BYTES + 2 * TC_TILE_BYTES;
+  const int64_t tc_tiles = (idx->n + TCU - 1) / TCU;
+  const int tc_grid = (int)(tc_tiles < sm_count * 3 ? tc_tiles : sm_count * 3);
   int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 4096);
   if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) per_sm = 1;
@@ -1223,7 +1694,11 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.qcnt = ws->qcnt; b.qcur = ws->qcur;
     b.ypairs = ws->ypairs; b.cap_y = ws->cap_y;
     b.tpairs = ws->tpairs; b.cap_t = ws->cap_t;
-    b.seg = ws->seg; b.scratch = ws->scratch;
+    b.seg = ws->seg;
+    b.bqt = use_tc ? ws->bqt : nullptr;
+    b.big = ws->big;
+    b.bigmaps = ws->bigmaps;
+    b.nw = idx->n / 32 + 1;
     b.doffs = ws->doffs + j0;
     b.out = out;
     b.capacity = capacity;
@@ -1246,7 +1721,17 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       }
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used], st));
     }
-    RMIPS_TRY_CUDA(mfilter_dispatch(idx, c, b, idx->k_max, fgrid, smem, st));
+    if (use_tc) {
+      static thread_local bool tc_cfg = false;
+      if (!tc_cfg) {
+        RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mfilter_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc));
+        tc_cfg = true;
+      }
+      k_mfilter_tc<<<tc_grid, TC_THREADS, smem_tc, st>>>(c, b, ws->bqt, idx->k_max);
+      RMIPS_TRY_CUDA(cudaGetLastError());
+    } else {
+      RMIPS_TRY_CUDA(mfilter_dispatch(idx, c, b, idx->k_max, fgrid, smem, st));
+    }
     if (prof) {
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used + 1], st));
       ws->ev_used++;
@@ -1255,6 +1740,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     k_mscan<<<1, 1024, 0, st>>>(c, b);
     k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
     k_memit<<<cnt, 256, 0, st>>>(c, b);
+    k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, st>>>(c, b);
     RMIPS_TRY_CUDA(cudaGetLastError());
   }
   return RMIPS_OK;
@@ -1493,4 +1979,29 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   *out_count = offs[1];
   return status_from_device(h[C_STATUS]);
+}
+
+extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t lbo, int32_t sbo,
+                                           void* stream) {
+  if (!A || !B || !D || lbo <= 0 || sbo <= 0 || lbo > 4096 || sbo > 4096 || (lbo & 15) || (sbo & 15)) {
+    set_error("bad argument");
+    return RMIPS_ERR_ARG;
+  }
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(D)) {
+    set_error("A, B and D must be device memory");
+    return RMIPS_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  long long* status = nullptr;
+  RMIPS_TRY_CUDA(cudaMallocAsync((void**)&status, sizeof(long long), st));
+  RMIPS_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(long long), st));
+  const int dsmem = (int)(192 * TC_K * 4);
+  RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
+  k_debug_tc<<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  long long h = 0;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaFreeAsync(status, st));
+  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  return status_from_device(h);
 }

@@ -34,6 +34,7 @@
 #define RMIPS_DMAX 128           // largest supported dimension
 #define MQ_MAXQ 16384            // queries per multi-query pass (14-bit index)
 #define MQ_TQ 64                 // queries per tile
+#define MQ_BIG_SLOTS 64          // concurrent large-result emitters (one id bitmap each)
 #define MQ_SLOTS (MQ_MAXQ + (RMIPS_KMAX_LIMIT + 1) * MQ_TQ)
 
 #if defined(__CUDACC__)
@@ -72,7 +73,8 @@ enum : int {
   C_CURSOR = 6,     // running output offset (batches)
   C_YESFAST = 7,    // users decided yes by the O(1) tests
   C_TODOSUM = 8,    // users sent to the todo list (all queries of the call)
-  C_NCOUNTERS = 9
+  C_NBIG = 9,       // queries of a batch pass with more than EMIT_SORT_CAP results
+  C_NCOUNTERS = 10
 };
 
 // ---------------------------------------------------------------------------
@@ -112,7 +114,9 @@ struct Workspace {
   unsigned long long* tpairs = nullptr;  // (query << 32 | position) to resolve
   int64_t cap_t = 0;
   int32_t* seg = nullptr;        // [cap_y] positions grouped by query
-  int32_t* scratch = nullptr;    // [2 cap_y] sort scratch for large results
+  float* bqt = nullptr;          // [MQ_SLOTS / MQ_TQ][MQ_TQ * 64] query tiles, UMMA layout
+  int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
+  uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
 
 }  // namespace rmips
@@ -122,6 +126,7 @@ struct rmips_index {
   int d = 0, k_max = 0, bs = 32, precision = RMIPS_FP32;
   int64_t nb = 0, pp = 0;
   int full_p = 1;
+  int batch_tc = 1;             // batched filter on tensor cores (TF32) when eligible
   int device = 0;
   int64_t incomplete = 0;
   int64_t device_bytes = 0;

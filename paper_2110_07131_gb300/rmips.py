@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
     "rmips_last_query_stats", "rmips_index_export", "rmips_free_index", "rmips_status_string",
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
-    "rmips_query_noalloc",
+    "rmips_query_noalloc", "rmips_debug_tc_tile",
 ]
 
 
@@ -44,7 +44,7 @@ class RmipsError(RuntimeError):
 
 class BuildOpts(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("block_size", C.c_int32), ("p_prime", C.c_int64),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("flags", C.c_int32)]
 
 
 class Segment(C.Structure):
@@ -107,9 +107,10 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_profile_enable.argtypes = [VP, I32]
         lib.rmips_profile_read.argtypes = [VP, C.POINTER(Profile)]
         lib.rmips_query_noalloc.argtypes = [VP, P, I32, P, I64, C.POINTER(I64), VP]
+        lib.rmips_debug_tc_tile.argtypes = [P, P, P, I32, I32, VP]
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
-                     "rmips_profile_read", "rmips_query_noalloc"):
+                     "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -199,8 +200,10 @@ class Index:
 
 
 def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
-                      precision="fp32", stream=None) -> Index:
-    """Build the index of Algorithm 1 from users Q [n, d] and items P [m, d]."""
+                      precision="fp32", batch_tensor_cores: bool = True, stream=None) -> Index:
+    """Build the index of Algorithm 1 from users Q [n, d] and items P [m, d].
+
+    ``batch_tensor_cores=False`` keeps the batched filter on CUDA cores."""
     load_library()
     qp, qk = _ptr_f32(Q)
     pp, pk = _ptr_f32(P)
@@ -208,7 +211,8 @@ def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
     m = int(pk.shape[0])
     if int(pk.shape[1]) != d:
         raise RmipsError(1, "Q and P differ in dimension")
-    opts = BuildOpts(int(k_max), int(block_size), int(p_prime), _PREC[precision], 0)
+    opts = BuildOpts(int(k_max), int(block_size), int(p_prime), _PREC[precision],
+                     0 if batch_tensor_cores else 1)
     out = C.c_void_p()
     _check(_lib.rmips_build_index(qp, n, pp, m, d, C.byref(opts), _stream(stream), C.byref(out)))
     return Index(out.value, n, m, d, int(k_max))
@@ -245,6 +249,13 @@ def rmips_query_noalloc(index: Index, q, k: int, out, stream=None) -> int:
     _check(_lib.rmips_query_noalloc(index.handle, qp, int(k), out.data_ptr(), cap, C.byref(cnt),
                                     _stream(stream)))
     return cnt.value
+
+
+def rmips_debug_tc_tile(A, B, D, lbo: int = 128, sbo: int = 2048, stream=None):
+    """One 128x64x64 TF32 tensor-core tile (device tensors): D = A @ B.T."""
+    load_library()
+    _check(_lib.rmips_debug_tc_tile(A.data_ptr(), B.data_ptr(), D.data_ptr(), int(lbo), int(sbo),
+                                    _stream(stream)))
 
 
 def rmips_query_batch(index: Index, qs, ks, segments=None, capacity=None, out=None, stream=None):

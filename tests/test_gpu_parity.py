@@ -37,6 +37,23 @@ def test_tiny_config_parity(tiny, precision, p_prime):
     index.close()
 
 
+def test_tiny_config_parity_cuda_core_batches(tiny):
+    Q, P, allq, counts = tiny
+    for p_prime in (0, 100):
+        index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime, batch_tensor_cores=False)
+        _check_all(index, allq, counts, (1, 10, 25))
+
+
+def test_mixed_k_batch_tensor_and_cuda_cores_agree(tiny):
+    Q, P, allq, counts = tiny
+    ks = datagen.random_ks(len(allq), 1, 25, 0)
+    for tc in (True, False):
+        index = rmips.rmips_build_index(Q, P, k_max=25, batch_tensor_cores=tc)
+        ids, offs = rmips.rmips_query_batch(index, allq, ks)
+        for j in range(len(allq)):
+            assert np.array_equal(ids[offs[j]:offs[j + 1]], np.nonzero(counts[j] < ks[j])[0])
+
+
 @pytest.mark.parametrize("bs", [64, 256])
 def test_block_sizes(tiny, bs):
     Q, P, allq, counts = tiny
@@ -223,3 +240,18 @@ def test_plain_config_sum_identity_and_samples():
             sample = np.unique(np.concatenate([got, rng.choice(n, 150, replace=False)]))
             truth = O.decide_users(Q, P, q, k, sample)
             assert np.array_equal(sample[truth], got), (j, k)
+
+
+def test_batch_with_many_large_results():
+    # more large-result queries than the batched emitter's 64 bitmaps: several rounds
+    Q, P = datagen.make_problem(20000, 400, 8, 4)
+    qs = np.concatenate([(P[:70] * 500.0).astype(np.float32), P[70:90]])
+    counts = O.counts_greater_multi(Q, P, qs)
+    index = rmips.rmips_build_index(Q, P, k_max=5)
+    ids, offs = rmips.rmips_query_batch(index, qs, np.full(len(qs), 5, np.int32))
+    big = 0
+    for j in range(len(qs)):
+        exp = np.nonzero(counts[j] < 5)[0]
+        big += len(exp) > 8192
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], exp), j
+    assert big > 64
