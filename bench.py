@@ -211,6 +211,7 @@ def run_ours(a):
     torch.cuda.synchronize(dev)
     prof = rmips.rmips_profile_read(index)
     rmips.rmips_profile_enable(index, False)
+    qstats = rmips.rmips_last_query_stats(index)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -309,7 +310,9 @@ def run_ours(a):
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
             "index_incomplete_users": info["incomplete"],
             "users_returned_per_query": results / (a.steps * a.nq),
-            "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (a.steps * a.nq)}
+            "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (a.steps * a.nq),
+            "last_step": {"pairs_decided_yes_in_o1": qstats["yes_fast"], "pairs_rechecked": qstats["todo"],
+                          "exact_integer_decisions": qstats["exact_calls"], "results": qstats["result"]}}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rng = np.random.default_rng(1)
         qps, s, t, cores = oracle_sample(Q, P, qs[0], a.k, a.cpu_seconds, rng)
