@@ -303,7 +303,7 @@ def run_ours(a):
             "dtype": ("tf32" if tc_path else ("f32" if a.precision == "fp32" else a.precision)) + "+f64 recheck",
             "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": a.steps * 7 * ((a.nq + 16383) // 16384),
+            "gpu_launches": a.steps * 9 * ((a.nq + 16383) // 16384),
             "roofline_single_query_filter": roof_single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain,
             "batch_latency_ms": ms_max / a.steps,

@@ -46,6 +46,8 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->tpairs);
   cudaFree(ws->seg);
   cudaFree(ws->bqt);
+  cudaFree(ws->keys);
+  cudaFree(ws->hist);
   cudaFree(ws->big);
   cudaFree(ws->bigmaps);
   delete ws;

@@ -71,30 +71,39 @@ struct Common {
   long long* ctr;
 };
 
+// Upper bound of ||q|| (float32, every step rounded up, so no float64 chain)
+// and the absolute slack of the filter's error bound: float32 products below
+// the normal range lose up to 2^-150 each, FP16 storage rounds values below
+// 2^-14 with absolute error up to 2^-25 (BF16 below 2^-126: 2^-134).
+__device__ __forceinline__ bool query_bounds(const float* q, int d, int precision, float* qn, float* eps) {
+  float acc = 0.f, qmax = 0.f;
+  bool fin = true;
+  for (int i = 0; i < d; ++i) {
+    const float v = q[i];
+    fin = fin && isfinite(v);
+    acc = __fmaf_ru(v, v, acc);
+    qmax = fmaxf(qmax, fabsf(v));
+  }
+  *qn = __fsqrt_ru(acc);
+  const float sub = (precision == RMIPS_FP16) ? 0x1p-25f : (precision == RMIPS_BF16 ? 0x1p-133f : 0.f);
+  *eps = __fmul_ru((float)(d + 2), __fmaf_ru(sub, qmax, 0x1p-148f));
+  return fin;
+}
+
 // --- query preparation ---------------------------------------------------------------
 __global__ void k_qprep(Common c, int64_t nq, int precision) {
   const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (j >= nq) return;
   const float* q = c.dq + j * c.d;
-  double acc = 0.0;
-  float qmax = 0.f;
-  bool fin = true;
   if (lane == 0) {
-    for (int i = 0; i < c.d; ++i) {
-      float v = q[i];
-      fin = fin && isfinite(v);
-      acc = fma((double)v, (double)v, acc);
-      qmax = fmaxf(qmax, fabsf(v));
-    }
-    int k = c.dk[j];
+    float qn, eps;
+    const bool fin = query_bounds(q, c.d, precision, &qn, &eps);
+    const int k = c.dk[j];
     if (!fin) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_NONFINITE);
     if (k < 1 || k > c.k_max) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_INTERNAL);
-    c.dqn[j] = __double2float_ru(__dmul_ru(sqrt(acc), 1.0 + (c.d + 8) * 0x1p-52));
-    // Absolute slack: float32 products below the normal range lose up to 2^-150
-    // each; FP16 storage rounds values below 2^-14 with absolute error 2^-25.
-    double sub = (precision == RMIPS_FP16) ? 0x1p-25 : (precision == RMIPS_BF16 ? 0x1p-133 : 0.0);
-    c.deps[j] = __double2float_ru((c.d + 2) * (sub * qmax + 0x1p-148));
+    c.dqn[j] = qn;
+    c.deps[j] = eps;
   }
 }
 
@@ -272,6 +281,69 @@ __device__ bool verify_scan(const float* __restrict__ u, float un, const Common&
   return true;
 }
 
+
+// Exact recheck of one user against its proven candidate list (one warp, one
+// candidate per lane): u is a yes iff fewer than k candidates p have
+// u.p > u.q.  Each comparison is taken at the cheapest level that decides it:
+// float32 with its rounding bound, then "p is bit-identical to q" (an exact
+// tie, q's own copy in P), then float64 with its bound, then the exact
+// integer accumulator.  u.q is formed once per user, split across lanes.
+__device__ bool recheck_candidates(const float* __restrict__ u, const float* q, const int32_t* __restrict__ crow,
+                                   const float* __restrict__ Ps, int d, int k, float cg32, long long* ctr) {
+  const int lane = threadIdx.x & 31;
+  float g32 = 0.f, a32 = 0.f;
+  double g64 = 0.0, a64 = 0.0;
+  for (int i = lane; i < d; i += 32) {
+    const float x = u[i], y = q[i];
+    g32 = fmaf(x, y, g32);
+    a32 = fmaf(fabsf(x), fabsf(y), a32);
+    g64 = fma((double)x, (double)y, g64);
+    a64 = fma(fabs((double)x), fabs((double)y), a64);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    g32 += __shfl_xor_sync(FULL, g32, o);
+    a32 += __shfl_xor_sync(FULL, a32, o);
+    g64 += __shfl_xor_sync(FULL, g64, o);
+    a64 += __shfl_xor_sync(FULL, a64, o);
+  }
+  const float tiny = (d + 2) * 0x1p-148f;
+  const float eg = __fmaf_ru(a32, cg32, tiny);
+  const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
+  const int32_t it = crow[lane];
+  bool gt = false;
+  if (it >= 0) {
+    const float* p = Ps + (int64_t)it * d;
+    float sp = 0.f, B = 0.f;
+    for (int i = 0; i < d; ++i) {
+      sp = fmaf(u[i], p[i], sp);
+      B = fmaf(fabsf(u[i]), fabsf(p[i]), B);
+    }
+    const float ep = __fmaf_ru(B, cg32, tiny);
+    if (__fsub_rd(sp, ep) > gh) {
+      gt = true;
+    } else if (!(__fadd_ru(sp, ep) < gl)) {
+      bool same = true;
+      for (int i = 0; i < d; ++i) same = same && (__float_as_uint(p[i]) == __float_as_uint(q[i]));
+      if (!same) {
+        double s64 = 0.0, b64 = 0.0;
+        for (int i = 0; i < d; ++i) {
+          s64 = fma((double)u[i], (double)p[i], s64);
+          b64 = fma(fabs((double)u[i]), fabs((double)p[i]), b64);
+        }
+        const double diff = s64 - g64;
+        const double bound = (4.0 * (d + 2) * 0x1p-53) * (b64 + a64);
+        if (diff > bound) gt = true;
+        else if (!(diff < -bound)) {
+          if (ctr) atomicAdd((unsigned long long*)&ctr[C_EXACT], 1ull);
+          gt = exact_sign_diff(u, p, q, d) > 0;
+        }
+      }
+    }
+  }
+  return __popc(__ballot_sync(FULL, gt)) < k;
+}
+
 // --- resolve the todo list ------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_resolve(Common c, int j) {
   __shared__ float sq[RMIPS_DMAX];
@@ -298,9 +370,7 @@ __global__ void __launch_bounds__(256) k_resolve(Common c, int j) {
     if (c.full_p && !c.incomp[pos]) {
       // The candidate list holds every item that can reach u's k_max-th place,
       // so u is a yes iff fewer than k candidates are strictly above u.q.
-      const int32_t it = c.cand[(int64_t)pos * RMIPS_KC + lane];
-      const bool gt = it >= 0 && cmp_dot(u, c.Ps + (int64_t)it * d, sq, d, c.ctr) > 0;
-      yes = __popc(__ballot_sync(FULL, gt)) < k;
+      yes = recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr);
     } else {
       yes = verify_scan(u, c.unorm[pos], c, sq, k, qeps);
     }
@@ -847,6 +917,8 @@ struct Batch {
   long long cap_t;
   int32_t* seg;
   float* bqt;             // query tiles in the UMMA layout (TC path), may be null
+  unsigned long long* keys;  // [nq] sort keys
+  int* hist;              // [RMIPS_KMAX_LIMIT + 2] queries per k
   int32_t* big;           // queries with more than EMIT_SORT_CAP results
   uint32_t* bigmaps;      // MQ_BIG_SLOTS id bitmaps of nw words each
   int64_t nw;             // words per id bitmap
@@ -855,11 +927,31 @@ struct Batch {
   long long capacity;
 };
 
-__global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, int precision) {
+// (a) per query: norm bound, slack, checks, sort key, k histogram.
+__global__ void k_mprep_a(Common c, Batch b, int precision) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.nq) return;
+  float qn, eps;
+  const bool fin = query_bounds(b.dq + (int64_t)j * c.d, c.d, precision, &qn, &eps);
+  int k = b.dk[j];
+  if (!fin) set_status(c.ctr, ST_NONFINITE);
+  if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_INTERNAL); k = 1; }
+  b.dqn[j] = qn;
+  b.deps[j] = eps;
+  b.qcnt[j] = 0;
+  b.qcur[j] = 0;
+  b.keys[j] = ((unsigned long long)k << 46) | ((unsigned long long)(~__float_as_uint(qn)) << 14) |
+              (unsigned long long)j;
+  atomicAdd(&b.hist[k], 1);
+}
+
+// (b) one CTA: sort the keys (k ascending, norm descending), lay the queries
+// out in k-groups padded to MQ_TQ slots.
+__global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep_b(Common c, Batch b) {
   extern __shared__ unsigned long long keys[];               // [N2]
-  __shared__ int hist[RMIPS_KMAX_LIMIT + 2];
   __shared__ int first[RMIPS_KMAX_LIMIT + 2];
   __shared__ int slot0[RMIPS_KMAX_LIMIT + 2];
+  __shared__ int hist[RMIPS_KMAX_LIMIT + 2];
   const int tid = threadIdx.x;
   const int nq = b.nq;
   int N2 = 1;
@@ -869,33 +961,8 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, in
     c.ctr[C_TODO] = 0;
     c.ctr[C_NBIG] = 0;
   }
-  if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = 0;
-  __syncthreads();
-  for (int j = tid; j < N2; j += MQ_PREP_THREADS) {
-    if (j >= nq) { keys[j] = ~0ull; continue; }
-    const float* q = b.dq + (int64_t)j * c.d;
-    double acc = 0.0;
-    float qmax = 0.f;
-    bool fin = true;
-    for (int i = 0; i < c.d; ++i) {
-      float v = q[i];
-      fin = fin && isfinite(v);
-      acc = fma((double)v, (double)v, acc);
-      qmax = fmaxf(qmax, fabsf(v));
-    }
-    int k = b.dk[j];
-    if (!fin) set_status(c.ctr, ST_NONFINITE);
-    if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_INTERNAL); k = 1; }
-    const float qn = __double2float_ru(__dmul_ru(sqrt(acc), 1.0 + (c.d + 8) * 0x1p-52));
-    const double sub = (precision == RMIPS_FP16) ? 0x1p-25 : (precision == RMIPS_BF16 ? 0x1p-133 : 0.0);
-    b.dqn[j] = qn;
-    b.deps[j] = __double2float_ru((c.d + 2) * (sub * qmax + 0x1p-148));
-    b.qcnt[j] = 0;
-    b.qcur[j] = 0;
-    keys[j] = ((unsigned long long)k << 46) | ((unsigned long long)(~__float_as_uint(qn)) << 14) |
-              (unsigned long long)j;
-    atomicAdd(&hist[k], 1);
-  }
+  if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = b.hist[tid];
+  for (int j = tid; j < N2; j += MQ_PREP_THREADS) keys[j] = j < nq ? b.keys[j] : ~0ull;
   __syncthreads();
   for (int kk = 2; kk <= N2; kk <<= 1) {
     for (int jj = kk >> 1; jj > 0; jj >>= 1) {
@@ -921,10 +988,9 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, in
         s += tiles * MQ_TQ;
       }
     }
-    for (; g <= RMIPS_KMAX_LIMIT; ++g) b.grp[g] = make_int4(0, s, 0, 0);   // empty groups
+    for (; g <= RMIPS_KMAX_LIMIT; ++g) b.grp[g] = make_int4(0, s, 0, 0);   // empty groups; .y = total slots
   }
   __syncthreads();
-  // slot of each sorted query; padding slots get index -1
   for (int i = tid; i < nq; i += MQ_PREP_THREADS) {
     const unsigned long long key = keys[i];
     const int k = (int)(key >> 46);
@@ -946,18 +1012,21 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep(Common c, Batch b, in
       b.beps[slot0[k] + r] = 0.f;
     }
   }
-  __syncthreads();
-  // gather the query vectors into slot order (zeros in padding)
-  int total_slots = 0;
-  for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) total_slots += ((hist[k] + MQ_TQ - 1) / MQ_TQ) * MQ_TQ;
-  for (int e = tid; e < total_slots * c.d; e += MQ_PREP_THREADS) {
-    const int slot = e / c.d, i = e - slot * c.d;
+}
+
+// (c) grid: gather the query vectors into slot order (zeros in padding), row
+// major for the CUDA-core path and in 64-query UMMA tiles for tensor cores.
+__global__ void k_mprep_c(Common c, Batch b) {
+  const int total_slots = b.grp[RMIPS_KMAX_LIMIT].y;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)total_slots * c.d; e += stride) {
+    const int slot = (int)(e / c.d), i = (int)(e - (int64_t)slot * c.d);
     const int j = b.bidx[slot];
     b.bq[e] = j >= 0 ? b.dq[(int64_t)j * c.d + i] : 0.f;
   }
-  if (b.bqt) {                     // 64-query tiles in the UMMA layout, K padded to 64
-    for (int e = tid; e < total_slots * (int)TC_K; e += MQ_PREP_THREADS) {
-      const int slot = e / (int)TC_K, k = e - slot * (int)TC_K;
+  if (b.bqt) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)total_slots * TC_K; e += stride) {
+      const int slot = (int)(e / TC_K), k = (int)(e - (int64_t)slot * TC_K);
       const int j = b.bidx[slot];
       const float v = (j >= 0 && k < c.d) ? b.dq[(int64_t)j * c.d + k] : 0.f;
       b.bqt[(size_t)(slot / MQ_TQ) * (MQ_TQ * TC_K) + tc_off(slot % MQ_TQ, k) / 4] = v;
@@ -1180,9 +1249,7 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
     const float* u = c.Qs + (int64_t)pos * d;
     bool yes;
     if (c.full_p && !c.incomp[pos]) {
-      const int32_t it = c.cand[(int64_t)pos * RMIPS_KC + lane];
-      const bool gt = it >= 0 && cmp_dot(u, c.Ps + (int64_t)it * d, q, d, c.ctr) > 0;
-      yes = __popc(__ballot_sync(FULL, gt)) < k;
+      yes = recheck_candidates(u, q, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr);
     } else {
       yes = verify_scan(u, c.unorm[pos], c, q, k, b.deps[j]);
     }
@@ -1355,13 +1422,14 @@ __global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
 // ===========================================================================
 constexpr int TCU = 128;                       // users per tile (MMA M)
 constexpr int TCQ = MQ_TQ;                     // queries per tile (MMA N)
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;                // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4) ...
+constexpr int TC_HALF = TCQ / 2;               // ... and split the 64 query columns in halves
 constexpr float TC_ERR = 0.00198f;             // >= 2^-9 + 2^-20 + 65 * 2^-22 * (1 + 2^-9)
 constexpr uint32_t TC_TILE_BYTES = TCQ * TC_K * 4;   // one query tile (16 KB)
 constexpr uint32_t TC_A_BYTES = TCU * TC_K * 4;      // one user tile (32 KB)
 
-__global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, const float* __restrict__ bqt,
-                                                            int ngroups) {
+__global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b, const float* __restrict__ bqt,
+                                                               int ngroups) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   float* sA = reinterpret_cast<float*>(tsm);                                   // 32 KB
   float* sB = reinterpret_cast<float*>(tsm + TC_A_BYTES);                      // 2 x 16 KB
@@ -1369,17 +1437,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
   __shared__ __align__(8) uint64_t bar_m;        // MMA done
   __shared__ uint32_t taddr_s;
   __shared__ float un_s[TCU];
-  __shared__ float eq_s[2][TCQ], qe_s[2][TCQ];
+  __shared__ float2 cq_s[2][TCQ];                // (error scale, absolute slack) per query of a tile
   __shared__ int qj_s[2][TCQ];
   __shared__ int pre[RMIPS_KMAX_LIMIT][4];
   __shared__ int gmax[RMIPS_KMAX_LIMIT];
   __shared__ int any_tile, s_fail;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int uu = tid & (TCU - 1);                // this thread's user row (TMEM lane)
+  const int half = tid >> 7;                     // which 32 query columns
   const int d = c.d;
   const int64_t n = c.n;
   const int sub = c.bs < TCU ? c.bs : TCU;
   const int nbt = TCU / sub;
-  const float un0 = c.unorm[0];                   // largest user norm (users are sorted)
+  const float un0 = c.unorm[0];                  // largest user norm (users are sorted)
   const float tiny = (d + 2) * 0x1p-126f;
 
   if (warp == 0) {
@@ -1397,6 +1467,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = taddr_s;
+  const uint32_t tlane = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * TC_HALF);
   const uint32_t idesc = tc_idesc_tf32(TCU, TCQ);
   uint32_t phb = 0, ph_m = 0;                    // parity of the next wait: bit x for bar_b[x] / bar_m
   long long st_pairs = 0, st_skipped = 0, st_yes = 0, st_todo = 0;
@@ -1432,15 +1503,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
       continue;
     }
     const int64_t nvalid = (n - u0) < TCU ? (n - u0) : TCU;
-    // 2. user tile into the UMMA layout (float32 rows -> K-padded core matrices)
+    // 2. user tile into the UMMA layout: one 16-byte chunk (4 consecutive k of
+    //    one row) per store, consecutive threads on consecutive rows
     {
       const float* src = c.Qs + u0 * d;
-      for (int e = tid; e < TCU * (int)TC_K; e += TC_THREADS) {
-        const int uu = e / (int)TC_K, k = e - uu * (int)TC_K;
-        const float v = (uu < nvalid && k < d) ? src[(int64_t)uu * d + k] : 0.f;
-        sA[tc_off(uu, k) / 4] = v;
+      for (int e = tid; e < TCU * (int)(TC_K / 4); e += TC_THREADS) {
+        const int r = e & (TCU - 1), k0 = (e >> 7) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < nvalid) {
+          const float* row = src + (int64_t)r * d;
+          if (k0 + 0 < d) v.x = row[k0 + 0];
+          if (k0 + 1 < d) v.y = row[k0 + 1];
+          if (k0 + 2 < d) v.z = row[k0 + 2];
+          if (k0 + 3 < d) v.w = row[k0 + 3];
+        }
+        *reinterpret_cast<float4*>(&sA[tc_off(r, k0) / 4]) = v;
       }
-      un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
+      if (tid < TCU) un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
     }
     if (tid == 0) {
       for (int g = 0; g < ngroups; ++g)
@@ -1454,7 +1533,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
     // 3. walk the (group, query tile) items of this user tile
     int nitems = 0;
     for (int g = 0; g < ngroups; ++g) nitems += (gmax[g] + TCQ - 1) / TCQ;
-    // item -> (group, tile) by walking the groups
     int g_ld = 0, t_ld = 0;                       // next item to load
     auto advance = [&](int& g, int& t) {
       ++t;
@@ -1471,8 +1549,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
       }
       if (tid < TCQ) {
         const float qn = b.bqn[s0 + tid];
-        eq_s[buf][tid] = __fmul_ru(qn, TC_ERR);
-        qe_s[buf][tid] = __fmaf_ru(fmaxf(qn, un0), tiny, b.beps[s0 + tid]);
+        cq_s[buf][tid] = make_float2(__fmul_ru(qn, TC_ERR), __fmaf_ru(fmaxf(qn, un0), tiny, b.beps[s0 + tid]));
         qj_s[buf][tid] = b.bidx[s0 + tid];
       }
     };
@@ -1480,10 +1557,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
     load_item(g_ld, 0, 0);
     advance(g_ld, t_ld);
     __syncthreads();                               // user tile written, constants of item 0 visible
-    // issue MMA(0)
-    if (tid == 0) {
-      bool ok = mbar_wait_bounded(&bar_b[0], phb & 1u);
-      if (ok) {
+    if (tid == 0) {                                // MMA(0)
+      if (mbar_wait_bounded(&bar_b[0], phb & 1u)) {
         tc_fence_after();
         for (uint32_t s = 0; s < TC_K / 8; ++s)
           tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
@@ -1494,15 +1569,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
       }
     }
     phb ^= 1u;
-    int g_L = -1;                                  // group whose bound row is in L
+    int g_L = -1;                                  // group whose bounds are in L
     float2 L = make_float2(kInf, kInf);
     for (int it = 0; it < nitems; ++it) {
       const int buf = it & 1;
-      // A. prefetch the next query tile into the other buffer (its last reader,
-      //    MMA(it - 1), has completed)
+      // A. prefetch the next query tile (its buffer's last reader, MMA(it-1), is done)
       const bool has_next = it + 1 < nitems;
       if (has_next) load_item(g_ld, t_ld, buf ^ 1);
-      // B. wait for MMA(it); copy this thread's accumulator row to registers
+      // B. wait for MMA(it); copy this thread's 32 accumulators out of TMEM
       bool ok = s_fail ? false : mbar_wait_bounded(&bar_m, ph_m);
       ph_m ^= 1u;
       ok = __syncthreads_and(ok && !s_fail);
@@ -1511,20 +1585,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
         break;
       }
       tc_fence_after();
-      float acc[TCQ];
-#pragma unroll
-      for (int c0 = 0; c0 < TCQ; c0 += 16) tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc + c0);
+      float acc[TC_HALF];
+      tmem_ld16(tlane, acc);
+      tmem_ld16(tlane + 16, acc + 16);
       tmem_ld_wait();
-      if (g_cur != g_L) {                            // this user's (lo, hi) for the group's k
-        L = tid < nvalid ? c.Lb[(int64_t)(b.grp[g_cur].x - 1) * n + u0 + tid] : make_float2(kInf, kInf);
+      if (g_cur != g_L) {                          // this user's (lo, hi) for the group's k
+        L = uu < nvalid ? c.Lb[(int64_t)(b.grp[g_cur].x - 1) * n + u0 + uu] : make_float2(kInf, kInf);
         g_L = g_cur;
       }
       tc_fence_before();
-      __syncthreads();                               // TMEM row consumed; next constants visible
-      // C. issue MMA(it + 1) on the next query tile; it overlaps the epilogue below
+      __syncthreads();                             // TMEM consumed; next constants visible
+      // C. MMA(it + 1) overlaps the epilogue below
       if (has_next && tid == 0) {
-        bool okb = mbar_wait_bounded(&bar_b[buf ^ 1], (phb >> (buf ^ 1)) & 1u);
-        if (okb) {
+        if (mbar_wait_bounded(&bar_b[buf ^ 1], (phb >> (buf ^ 1)) & 1u)) {
           tc_fence_after();
           const uint32_t bbase = smem_u32(sB) + (uint32_t)(buf ^ 1) * TC_TILE_BYTES;
           for (uint32_t s = 0; s < TC_K / 8; ++s)
@@ -1536,40 +1609,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
         }
       }
       if (has_next) phb ^= 1u << (buf ^ 1);
-      // D. epilogue for (this user, the 64 queries of item it)
-      const int uu = tid;
-      const int sb = uu / sub;
-      int live = pre[g_cur][sb] - t_cur * TCQ;
-      live = live < 0 ? 0 : (live > TCQ ? TCQ : live);
+      // D. epilogue: (this user, 32 queries of item it)
+      int live = pre[g_cur][uu / sub] - t_cur * TCQ - half * TC_HALF;
+      live = live < 0 ? 0 : (live > TC_HALF ? TC_HALF : live);
       if (uu >= nvalid) live = 0;
       const float un = un_s[uu];
       const int k = b.grp[g_cur].x;
       const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
-      uint64_t ym = 0, tm = 0;
+      uint32_t ym = 0, tm = 0;
 #pragma unroll
-      for (int q = 0; q < TCQ; ++q) {
+      for (int q = 0; q < TC_HALF; ++q) {
         if (q < live) {
-          const float e = __fmaf_ru(un, eq_s[buf][q], qe_s[buf][q]);
-          if (!(__fadd_ru(acc[q], e) < L.x)) {                 // not decided no by Lemma 1
+          const float2 cq = cq_s[buf][half * TC_HALF + q];
+          const float e = __fmaf_ru(un, cq.x, cq.y);
+          if (!(__fadd_ru(acc[q], e) < L.x)) {                  // not decided no by Lemma 1
             const float lo = __fsub_rd(acc[q], e);
             const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
-            if (yes) ym |= 1ull << q; else tm |= 1ull << q;
+            if (yes) ym |= 1u << q; else tm |= 1u << q;
           }
         }
       }
       while (ym) {
-        const int q = __ffsll((long long)ym) - 1;
+        const int q = __ffs(ym) - 1;
         ym &= ym - 1;
-        const int j = qj_s[buf][q];
+        const int j = qj_s[buf][half * TC_HALF + q];
         const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
         if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
         atomicAdd(&b.qcnt[j], 1);
         ++st_yes;
       }
       while (tm) {
-        const int q = __ffsll((long long)tm) - 1;
+        const int q = __ffs(tm) - 1;
         tm &= tm - 1;
-        const int j = qj_s[buf][q];
+        const int j = qj_s[buf][half * TC_HALF + q];
         const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
         if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
         else set_status(c.ctr, ST_INTERNAL);
@@ -1578,7 +1650,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_mfilter_tc(Common c, Batch b, co
       g_cur = g_ld;
       t_cur = t_ld;
       if (has_next) advance(g_ld, t_ld);
-      __syncthreads();                               // constants of item it consumed
+      __syncthreads();                             // constants of item it consumed
     }
     __syncthreads();
   }
@@ -1609,6 +1681,10 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
   }
   if (!ws->bqt && idx->d <= (int)TC_K)
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bqt, (size_t)MQ_SLOTS * TC_K * sizeof(float)));
+  if (!ws->keys) {
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->keys, MQ_MAXQ * sizeof(unsigned long long)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->hist, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
+  }
   if (!ws->big) {
     const int64_t nw = idx->n / 32 + 1;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->big, MQ_MAXQ * sizeof(int32_t)));
@@ -1696,6 +1772,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.tpairs = ws->tpairs; b.cap_t = ws->cap_t;
     b.seg = ws->seg;
     b.bqt = use_tc ? ws->bqt : nullptr;
+    b.keys = ws->keys;
+    b.hist = ws->hist;
     b.big = ws->big;
     b.bigmaps = ws->bigmaps;
     b.nw = idx->n / 32 + 1;
@@ -1706,11 +1784,14 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     while (N2 < cnt) N2 <<= 1;
     static thread_local bool prep_cfg = false;
     if (!prep_cfg) {
-      RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mprep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mprep_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           MQ_MAXQ * (int)sizeof(unsigned long long)));
       prep_cfg = true;
     }
-    k_mprep<<<1, MQ_PREP_THREADS, N2 * sizeof(unsigned long long), st>>>(c, b, idx->precision);
+    RMIPS_TRY_CUDA(cudaMemsetAsync(b.hist, 0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int), st));
+    k_mprep_a<<<(cnt + 255) / 256, 256, 0, st>>>(c, b, idx->precision);
+    k_mprep_b<<<1, MQ_PREP_THREADS, N2 * sizeof(unsigned long long), st>>>(c, b);
+    k_mprep_c<<<sm_count * 4, 256, 0, st>>>(c, b);
     RMIPS_TRY_CUDA(cudaGetLastError());
     const bool prof = idx->prof_on != 0;
     if (prof) {

@@ -115,6 +115,8 @@ struct Workspace {
   int64_t cap_t = 0;
   int32_t* seg = nullptr;        // [cap_y] positions grouped by query
   float* bqt = nullptr;          // [MQ_SLOTS / MQ_TQ][MQ_TQ * 64] query tiles, UMMA layout
+  unsigned long long* keys = nullptr;  // [MQ_MAXQ] query sort keys
+  int* hist = nullptr;           // [RMIPS_KMAX_LIMIT + 2] queries per k
   int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
   uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
@@ -248,6 +250,9 @@ __device__ __forceinline__ int cmp_dot(const float* __restrict__ u, const float*
   double bound = (4.0 * (d + 2) * 0x1p-53) * (aa + ab);
   if (diff > bound) return 1;
   if (diff < -bound) return -1;
+  bool same = true;                                  // bit-identical vectors tie exactly
+  for (int i = 0; i < d; ++i) same = same && (__float_as_uint(a[i]) == __float_as_uint(b[i]));
+  if (same) return 0;
   if (ctr) atomicAdd((unsigned long long*)&ctr[C_EXACT], 1ull);
   return exact_sign_diff(u, a, b, d);
 }
