@@ -430,12 +430,10 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     __syncthreads();
     for (int kk = 2; kk <= N2; kk <<= 1) {
       for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int i = tid; i < N2; i += EMIT_THREADS) {
-          int p = i ^ jj;
-          if (p > i) {
-            int32_t a = keys[i], b = keys[p];
-            if ((a > b) == ((i & kk) == 0)) { keys[i] = b; keys[p] = a; }
-          }
+        for (int t = tid; t < (N2 >> 1); t += EMIT_THREADS) {
+          const int i = 2 * t - (t & (jj - 1)), p = i + jj;
+          const int32_t a = keys[i], b = keys[p];
+          if ((a > b) == ((i & kk) == 0)) { keys[i] = b; keys[p] = a; }
         }
         __syncthreads();
       }
@@ -966,12 +964,10 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep_b(Common c, Batch b) 
   __syncthreads();
   for (int kk = 2; kk <= N2; kk <<= 1) {
     for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int i = tid; i < N2; i += MQ_PREP_THREADS) {
-        int p = i ^ jj;
-        if (p > i) {
-          unsigned long long x = keys[i], y = keys[p];
-          if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
-        }
+      for (int t = tid; t < (N2 >> 1); t += MQ_PREP_THREADS) {
+        const int i = 2 * t - (t & (jj - 1)), p = i + jj;      // the pair (i, i + jj)
+        const unsigned long long x = keys[i], y = keys[p];
+        if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
       }
       __syncthreads();
     }
@@ -1314,35 +1310,67 @@ __global__ void k_mscatter(Common c, Batch b) {
   }
 }
 
-// One CTA per query with at most EMIT_SORT_CAP results: positions -> ids,
-// bitonic sort in shared memory, ascending.
-__global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
-  __shared__ int32_t keys[EMIT_SORT_CAP];
-  const int j = blockIdx.x;
-  if (c.ctr[C_STATUS] != 0) return;                      // uniform: read-only here
-  const long long base0 = b.doffs[0];
-  const long long off = b.doffs[j];
-  const int cnt = b.qcnt[j];
-  const int tid = threadIdx.x;
-  if (cnt == 0 || cnt > EMIT_SORT_CAP) return;           // large results: k_memit_big
-  int N2 = 1;
-  while (N2 < cnt) N2 <<= 1;
-  for (int i = tid; i < N2; i += blockDim.x)
-    keys[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
-  __syncthreads();
-  for (int kk = 2; kk <= N2; kk <<= 1) {
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int i = tid; i < N2; i += blockDim.x) {
-        int p = i ^ jj;
-        if (p > i) {
-          int32_t x = keys[i], y = keys[p];
-          if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
-        }
-      }
-      __syncthreads();
+// Ascending sort of one int per lane across a warp (bitonic network).
+__device__ __forceinline__ int32_t warp_sort_asc(int32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int32_t y = __shfl_xor_sync(FULL, x, j);
+      const bool keep_min = (((lane & j) == 0) == ((lane & k) == 0));
+      x = keep_min ? min(x, y) : max(x, y);
     }
   }
-  for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = keys[i];
+  return x;
+}
+
+// Positions -> ids, ascending, for queries with at most EMIT_SORT_CAP results.
+// A CTA serves 8 consecutive queries: a result of at most 32 ids is sorted by
+// one warp in registers; a larger one by the whole CTA in shared memory.
+constexpr int MEMIT_Q = 8;
+__global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
+  __shared__ int32_t keys[EMIT_SORT_CAP];
+  if (c.ctr[C_STATUS] != 0) return;                      // uniform: read-only here
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long base0 = b.doffs[0];
+  const int j0 = blockIdx.x * MEMIT_Q;
+  {
+    const int j = j0 + warp;
+    if (j < b.nq) {
+      const int cnt = b.qcnt[j];
+      if (cnt > 0 && cnt <= 32) {
+        const long long off = b.doffs[j];
+        int32_t v = lane < cnt ? c.permQ[b.seg[off - base0 + lane]] : INT_MAX;
+        v = warp_sort_asc(v);
+        if (lane < cnt) b.out[off + lane] = v;
+      }
+    }
+  }
+  for (int w = 0; w < MEMIT_Q; ++w) {
+    const int j = j0 + w;
+    if (j >= b.nq) break;
+    const int cnt = b.qcnt[j];
+    if (cnt <= 32 || cnt > EMIT_SORT_CAP) continue;      // small: done above; large: k_memit_big
+    const long long off = b.doffs[j];
+    int N2 = 64;
+    while (N2 < cnt) N2 <<= 1;
+    __syncthreads();                                     // keys of the previous query consumed
+    for (int i = tid; i < N2; i += blockDim.x)
+      keys[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
+    __syncthreads();
+    for (int kk = 2; kk <= N2; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int t = tid; t < (N2 >> 1); t += blockDim.x) {
+          const int i = 2 * t - (t & (jj - 1)), p = i + jj;
+          const int32_t x = keys[i], y = keys[p];
+          if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = keys[i];
+  }
 }
 
 // Queries with large results: each CTA owns one id bitmap and handles the
@@ -1614,18 +1642,29 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
       live = live < 0 ? 0 : (live > TC_HALF ? TC_HALF : live);
       if (uu >= nvalid) live = 0;
       const float un = un_s[uu];
-      const int k = b.grp[g_cur].x;
-      const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
-      uint32_t ym = 0, tm = 0;
+      // Fast Lemma 1: slots are in descending norm, so the tile's first query
+      // carries the largest error scale and slack; with e_u >= e(u, q) for
+      // every q of the tile, acc < lo_k - e_u (rounded down) proves "no".
+      const float2 c0 = cq_s[buf][0];
+      const float thr = __fsub_rd(L.x, __fmaf_ru(un, c0.x, c0.y));
+      uint32_t hit = 0;
 #pragma unroll
-      for (int q = 0; q < TC_HALF; ++q) {
-        if (q < live) {
-          const float2 cq = cq_s[buf][half * TC_HALF + q];
-          const float e = __fmaf_ru(un, cq.x, cq.y);
-          if (!(__fadd_ru(acc[q], e) < L.x)) {                  // not decided no by Lemma 1
-            const float lo = __fsub_rd(acc[q], e);
-            const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
-            if (yes) ym |= 1u << q; else tm |= 1u << q;
+      for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
+      hit &= live >= TC_HALF ? 0xffffffffu : ((1u << live) - 1u);
+      uint32_t ym = 0, tm = 0;
+      if (hit) {
+        const int k = b.grp[g_cur].x;
+        const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
+#pragma unroll
+        for (int q = 0; q < TC_HALF; ++q) {
+          if ((hit >> q) & 1u) {
+            const float2 cq = cq_s[buf][half * TC_HALF + q];
+            const float e = __fmaf_ru(un, cq.x, cq.y);
+            if (!(__fadd_ru(acc[q], e) < L.x)) {                  // not decided no by Lemma 1
+              const float lo = __fsub_rd(acc[q], e);
+              const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
+              if (yes) ym |= 1u << q; else tm |= 1u << q;
+            }
           }
         }
       }
@@ -1820,7 +1859,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     k_mresolve<<<sm_count * 2, 256, 0, st>>>(c, b);
     k_mscan<<<1, 1024, 0, st>>>(c, b);
     k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_memit<<<cnt, 256, 0, st>>>(c, b);
+    k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, st>>>(c, b);
     k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, st>>>(c, b);
     RMIPS_TRY_CUDA(cudaGetLastError());
   }
