@@ -54,7 +54,8 @@ typedef enum {
                                is reported, nothing is written */
   RMIPS_ERR_TIMEOUT = 6,    /* a bounded device wait gave up */
   RMIPS_ERR_CUDA = 7,       /* a CUDA runtime call failed */
-  RMIPS_ERR_INTERNAL = 8    /* a device-side consistency check failed */
+  RMIPS_ERR_INTERNAL = 8,   /* a device-side consistency check failed */
+  RMIPS_ERR_BUSY = 9        /* serving: admission refused, too many pending */
 } rmips_status;
 
 /* Arithmetic of the online filter (the index always keeps float32 copies). */
@@ -203,6 +204,67 @@ rmips_status rmips_profile_read(const rmips_index* index, rmips_profile* out);
  */
 rmips_status rmips_query_noalloc(rmips_index* index, const float* q, int32_t k, int64_t* out_ids,
                                  int64_t capacity, int64_t* out_count, void* stream);
+
+/*
+ * Serving loop: continuous batching of reverse k-MIPS requests on one index
+ * (no counterpart in the paper, whose queries arrive one at a time).
+ *
+ * A dispatcher thread closes a batch when it holds max_batch requests or when
+ * its oldest request has waited max_wait_us, and launches it through the
+ * batched filter on one of `streams` CUDA streams; requests arriving while
+ * batches run join the next batch, and up to `streams` batches overlap on the
+ * device.  Results are exactly those of rmips_query for the same request.
+ * Admission: at most max_pending requests queued or in flight
+ * (RMIPS_ERR_BUSY beyond), and max_result_ids device-visible result slots per
+ * batch (a batch that needs more is re-run one request at a time).
+ * Requests with an id-list segment are answered through the single-query
+ * path.  The index must outlive the server; no other server call may be in
+ * progress when rmips_server_destroy is called.
+ */
+typedef struct rmips_server rmips_server;
+
+typedef struct {
+  int32_t max_batch;        /* requests per batch, 1..16384 (default 4096) */
+  int32_t max_wait_us;      /* batch closing deadline in microseconds (default 200) */
+  int32_t streams;          /* batches in flight, 1..16 (default 2) */
+  int32_t reserved;         /* must be 0 */
+  int64_t max_pending;      /* admission bound on queued + running requests */
+  int64_t max_result_ids;   /* result slots per batch; 0 = 256 per request */
+} rmips_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, rejected, pending;
+  int64_t batches;
+  double mean_batch;        /* requests per launched batch */
+  double p50_ms, p99_ms, max_ms;   /* request latency, submit to completion */
+} rmips_server_stats;
+
+/* opts may be NULL for the defaults.  Spawns two host threads. */
+rmips_status rmips_server_create(rmips_index* index, const rmips_server_opts* opts, rmips_server** out);
+
+/* Queues one request (q: d floats in HOST memory, copied).  Validates k,
+   finiteness and the segment immediately.  *ticket identifies the request. */
+rmips_status rmips_server_submit(rmips_server* server, const float* q, int32_t k, const rmips_segment* seg,
+                                 int64_t* ticket);
+
+/* Queues nq requests at once (all or none are admitted). */
+rmips_status rmips_server_submit_many(rmips_server* server, const float* qs, int64_t nq, const int32_t* ks,
+                                      const rmips_segment* segs, int64_t* tickets);
+
+/* Waits up to timeout_ms (negative: forever, 0: poll) for a request; copies
+   its ascending ids to out_ids (host or device, capacity slots), its size to
+   *out_count and its latency to *latency_ms (may be NULL), then forgets the
+   ticket.  RMIPS_ERR_TIMEOUT: not finished (ticket kept).
+   RMIPS_ERR_CAPACITY: *out_count is the size needed (ticket kept). */
+rmips_status rmips_server_wait(rmips_server* server, int64_t ticket, int64_t* out_ids, int64_t capacity,
+                               int64_t* out_count, double* latency_ms, int32_t timeout_ms);
+
+/* Counters and latency percentiles of the requests completed so far. */
+rmips_status rmips_server_get_stats(rmips_server* server, rmips_server_stats* out);
+
+/* Stops the threads (queued requests fail), waits for running batches and
+   releases everything. */
+void rmips_server_destroy(rmips_server* server);
 
 /* Sizes and build statistics of an index. */
 rmips_status rmips_index_get_info(const rmips_index* index, rmips_index_info* out);

@@ -47,6 +47,8 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->seg);
   cudaFree(ws->bqt);
   cudaFree(ws->keys);
+  cudaFree(ws->dseglo);
+  cudaFree(ws->dseghi);
   cudaFree(ws->hist);
   cudaFree(ws->big);
   cudaFree(ws->bigmaps);
@@ -107,6 +109,7 @@ extern "C" const char* rmips_status_string(rmips_status s) {
     case RMIPS_ERR_TIMEOUT: return "device wait timed out";
     case RMIPS_ERR_CUDA: return "CUDA runtime error";
     case RMIPS_ERR_INTERNAL: return "internal consistency check failed";
+    case RMIPS_ERR_BUSY: return "admission refused: too many requests pending";
   }
   return "unknown status";
 }

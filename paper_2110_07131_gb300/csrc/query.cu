@@ -915,6 +915,8 @@ struct Batch {
   long long cap_t;
   int32_t* seg;
   float* bqt;             // query tiles in the UMMA layout (TC path), may be null
+  const long long* seglo;   // [nq] allowed id range per query (null: all users)
+  const long long* seghi;
   unsigned long long* keys;  // [nq] sort keys
   int* hist;              // [RMIPS_KMAX_LIMIT + 2] queries per k
   int32_t* big;           // queries with more than EMIT_SORT_CAP results
@@ -1028,6 +1030,13 @@ __global__ void k_mprep_c(Common c, Batch b) {
       b.bqt[(size_t)(slot / MQ_TQ) * (MQ_TQ * TC_K) + tc_off(slot % MQ_TQ, k) / 4] = v;
     }
   }
+}
+
+// True when the user at sorted position pos lies in query j's id range.
+__device__ __forceinline__ bool in_segment(const Common& c, const Batch& b, int j, int64_t pos) {
+  if (!b.seglo) return true;
+  const long long id = c.permQ[pos];
+  return id >= b.seglo[j] && id < b.seghi[j];
 }
 
 // Number of leading queries of group g (descending norm) kept by Lemma 3 for
@@ -1177,12 +1186,13 @@ __global__ void __launch_bounds__(MQ_THREADS) k_mfilter(Common c, Batch b, int n
         if (__any_sync(FULL, (ymask | tmask) != 0)) {
           const uint32_t lt = (1u << lane) - 1u;
           for (int p = 0; p < 32; ++p) {
-            const bool y = (ymask >> p) & 1u, tt = (tmask >> p) & 1u;
-            const uint32_t by = __ballot_sync(FULL, y), bt = __ballot_sync(FULL, tt);
-            if (!(by | bt)) continue;
+            bool y = (ymask >> p) & 1u, tt = (tmask >> p) & 1u;
+            if (!__any_sync(FULL, y || tt)) continue;
             const int a = p >> 2, q = p & 3;
             const unsigned long long pair =
                 ((unsigned long long)(uint32_t)qj_t[tq * 4 + q] << 32) | (unsigned long long)(u0 + tu * 8 + a);
+            if ((y || tt) && !in_segment(c, b, qj_t[tq * 4 + q], u0 + tu * 8 + a)) { y = false; tt = false; }
+            const uint32_t by = __ballot_sync(FULL, y), bt = __ballot_sync(FULL, tt);
             if (by) {
               long long base = 0;
               if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
@@ -1672,6 +1682,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
         const int q = __ffs(ym) - 1;
         ym &= ym - 1;
         const int j = qj_s[buf][half * TC_HALF + q];
+        if (!in_segment(c, b, j, u0 + uu)) continue;
         const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
         if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
         atomicAdd(&b.qcnt[j], 1);
@@ -1681,6 +1692,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
         const int q = __ffs(tm) - 1;
         tm &= tm - 1;
         const int j = qj_s[buf][half * TC_HALF + q];
+        if (!in_segment(c, b, j, u0 + uu)) continue;
         const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
         if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
         else set_status(c.ctr, ST_INTERNAL);
@@ -1772,8 +1784,21 @@ cudaError_t mfilter_dispatch(const rmips_index* idx, const Common& c, const Batc
 
 // Batched run over queries [0, nq) staged in ws->dq / ws->dk; ws->doffs gets
 // the nq + 1 absolute offsets, results go to `out`.
+rmips_status ensure_segments(Workspace* ws, int64_t nq) {
+  if (ws->cap_seg >= nq) return RMIPS_OK;
+  cudaFree(ws->dseglo);
+  cudaFree(ws->dseghi);
+  ws->dseglo = ws->dseghi = nullptr;
+  ws->cap_seg = 0;
+  const int64_t cap = nq < 1024 ? 1024 : nq;
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dseglo, cap * sizeof(long long)));
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dseghi, cap * sizeof(long long)));
+  ws->cap_seg = cap;
+  return RMIPS_OK;
+}
+
 rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
-                       cudaStream_t st) {
+                       cudaStream_t st, const long long* dseglo, const long long* dseghi) {
   Common c = make_common(idx, ws);
   static thread_local int sm_count = 0;
   if (!sm_count) {
@@ -1813,6 +1838,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.bqt = use_tc ? ws->bqt : nullptr;
     b.keys = ws->keys;
     b.hist = ws->hist;
+    b.seglo = dseglo ? dseglo + j0 : nullptr;
+    b.seghi = dseghi ? dseghi + j0 : nullptr;
     b.big = ws->big;
     b.bigmaps = ws->bigmaps;
     b.nw = idx->n / 32 + 1;
@@ -1948,9 +1975,26 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
     out = ws->dout;
   }
   if ((s = stage_inputs(idx, ws, qs, nq, ks, st)) != RMIPS_OK) return s;
-  const bool batched = segs == nullptr;
+  bool ranges_only = true;
+  if (segs)
+    for (int64_t j = 0; j < nq; ++j) ranges_only = ranges_only && segs[j].kind != 2;
+  const bool batched = ranges_only;
   if (batched) {
-    if ((s = run_batch(idx, ws, nq, out, capacity, st)) != RMIPS_OK) return s;
+    const long long* dlo = nullptr;
+    const long long* dhi = nullptr;
+    if (segs) {
+      if ((s = ensure_segments(ws, nq)) != RMIPS_OK) return s;
+      std::vector<long long> lo(nq), hi(nq);
+      for (int64_t j = 0; j < nq; ++j) {
+        lo[j] = segs[j].kind == 1 ? segs[j].begin : 0;
+        hi[j] = segs[j].kind == 1 ? segs[j].end : INT64_MAX;
+      }
+      RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, lo.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+      RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, hi.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+      dlo = ws->dseglo;
+      dhi = ws->dseghi;
+    }
+    if ((s = run_batch(idx, ws, nq, out, capacity, st, dlo, dhi)) != RMIPS_OK) return s;
   } else {
     if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
   }
@@ -2125,3 +2169,18 @@ extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, floa
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   return status_from_device(h);
 }
+
+namespace rmips {
+// Entry points for the serving loop (same translation-unit-local machinery).
+rmips_status batch_reserve(rmips_index* idx, Workspace* ws, int64_t nq) {
+  rmips_status s = ensure_queries(idx, ws, nq);
+  if (s != RMIPS_OK) return s;
+  return ensure_segments(ws, nq);
+}
+rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
+                          cudaStream_t st, bool with_segments) {
+  return run_batch(idx, ws, nq, out, capacity, st, with_segments ? ws->dseglo : nullptr,
+                   with_segments ? ws->dseghi : nullptr);
+}
+rmips_status device_status(long long s) { return status_from_device(s); }
+}  // namespace rmips

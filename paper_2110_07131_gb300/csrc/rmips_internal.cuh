@@ -117,6 +117,9 @@ struct Workspace {
   float* bqt = nullptr;          // [MQ_SLOTS / MQ_TQ][MQ_TQ * 64] query tiles, UMMA layout
   unsigned long long* keys = nullptr;  // [MQ_MAXQ] query sort keys
   int* hist = nullptr;           // [RMIPS_KMAX_LIMIT + 2] queries per k
+  long long* dseglo = nullptr;   // [cap_seg] per-query id ranges of a batch
+  long long* dseghi = nullptr;
+  int64_t cap_seg = 0;
   int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
   uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
@@ -170,6 +173,13 @@ cudaError_t dalloc(rmips_index* idx, T** p, size_t count) {
 bool is_device_ptr(const void* p);
 
 Workspace* acquire_workspace(rmips_index* idx, rmips_status* st);
+// Batched run on a workspace whose ws->dq / ws->dk (and ws->dseglo/dseghi)
+// already hold nq staged queries; results to `out` (device-visible),
+// offsets to ws->doffs.  Asynchronous on `st`.
+rmips_status batch_reserve(rmips_index* idx, Workspace* ws, int64_t nq);
+rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
+                          cudaStream_t st, bool with_segments);
+rmips_status device_status(long long s);
 void release_workspace(rmips_index* idx, Workspace* ws);
 void destroy_workspace(Workspace* ws);
 

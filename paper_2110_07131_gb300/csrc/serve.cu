@@ -1,0 +1,468 @@
+// Serving loop: continuous batching of reverse k-MIPS requests.
+//
+// Requests (q, k, optional id range or id list) are queued by
+// rmips_server_submit.  A dispatcher thread closes a batch when it holds
+// max_batch requests or when its oldest request has waited max_wait_us, and
+// launches it on a free stream slot (each slot owns a workspace, pinned
+// staging buffers and device-mapped result memory); requests that arrive in
+// the meantime wait for the next batch, so up to `streams` batches overlap on
+// the GPU.  A completer thread finishes slots in launch order, copies each
+// request's ids out of the mapped buffer and records its latency (submit to
+// completion).  Admission: at most max_pending requests queued or in flight,
+// and at most max_result_ids result ids per batch (a batch that needs more is
+// re-run one request at a time).
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "rmips_internal.cuh"
+
+using Clock = std::chrono::steady_clock;
+
+namespace rmips {
+namespace {
+
+struct Request {
+  std::vector<float> q;
+  int32_t k = 1;
+  int kind = 0;                 // 0 all users, 1 id range, 2 id list
+  int64_t lo = 0, hi = INT64_MAX;
+  std::vector<int64_t> list;
+  Clock::time_point t0;
+  int state = 0;                // 0 queued, 1 running, 2 done
+  rmips_status st = RMIPS_OK;
+  std::vector<int64_t> ids;
+  double ms = 0.0;
+};
+
+struct Slot {
+  Workspace* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  float* h_q = nullptr;         // pinned staging
+  int32_t* h_k = nullptr;
+  long long* h_lo = nullptr;
+  long long* h_hi = nullptr;
+  long long* h_offs = nullptr;
+  long long* h_ctr = nullptr;
+  long long* h_out = nullptr;   // device-mapped pinned result ids
+  int64_t cap_out = 0;
+  std::vector<int64_t> tickets;
+  bool segments = false;
+  rmips_status launch = RMIPS_OK;
+  bool busy = false;
+};
+
+constexpr size_t LAT_CAP = 1 << 20;
+
+}  // namespace
+}  // namespace rmips
+
+struct rmips_server {
+  rmips_index* idx = nullptr;
+  rmips_server_opts o{};
+  std::mutex mu;
+  std::condition_variable cv_in, cv_slot, cv_fly, cv_done;
+  std::unordered_map<int64_t, rmips::Request*> reqs;
+  std::deque<int64_t> queue;
+  std::vector<rmips::Slot> slots;
+  std::deque<int> inflight;
+  int64_t next = 1, pending = 0;
+  bool stop = false;
+  std::thread disp, comp;
+  int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched = 0;
+  std::vector<double> lat;
+  size_t lat_n = 0;
+};
+
+using namespace rmips;
+
+namespace {
+
+void record_latency(rmips_server* S, double ms) {
+  if (S->lat.size() < LAT_CAP) S->lat.push_back(ms);
+  else S->lat[S->lat_n % LAT_CAP] = ms;
+  ++S->lat_n;
+}
+
+// One request through the single-query path (list segments, capacity retries).
+void run_single(rmips_server* S, Request* r, std::vector<int64_t>& ids, rmips_status& st) {
+  rmips_segment seg{};
+  seg.kind = r->kind;
+  seg.begin = r->lo;
+  seg.end = r->hi;
+  seg.ids = r->list.data();
+  seg.n_ids = (int64_t)r->list.size();
+  ids.resize((size_t)S->idx->n);
+  int64_t cnt = 0;
+  st = rmips_query(S->idx, r->q.data(), r->k, r->kind ? &seg : nullptr, ids.data(), S->idx->n, &cnt, nullptr);
+  ids.resize(st == RMIPS_OK ? (size_t)cnt : 0);
+}
+
+void finish(rmips_server* S, Request* r, std::vector<int64_t>&& ids, rmips_status st, Clock::time_point now) {
+  r->ids = std::move(ids);
+  r->st = st;
+  r->ms = std::chrono::duration<double, std::milli>(now - r->t0).count();
+  r->state = 2;
+  record_latency(S, r->ms);
+  ++S->completed;
+  --S->pending;
+}
+
+rmips_status launch_slot(rmips_server* S, Slot& sl, int64_t nq) {
+  rmips_index* idx = S->idx;
+  Workspace* ws = sl.ws;
+  cudaStream_t st = sl.stream;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dq, sl.h_q, nq * idx->d * sizeof(float), cudaMemcpyHostToDevice, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dk, sl.h_k, nq * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (sl.segments) {
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, sl.h_lo, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, sl.h_hi, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+  }
+  rmips_status s = batch_launch(idx, ws, nq, sl.h_out, sl.cap_out, st, sl.segments);
+  if (s != RMIPS_OK) return s;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(sl.h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(sl.h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RMIPS_TRY_CUDA(cudaEventRecord(sl.done, st));
+  return RMIPS_OK;
+}
+
+void dispatcher(rmips_server* S) {
+  cudaSetDevice(S->idx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    S->cv_in.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+    if (S->stop) break;
+    const auto deadline = S->reqs[S->queue.front()]->t0 + std::chrono::microseconds(S->o.max_wait_us);
+    while (!S->stop && (int64_t)S->queue.size() < S->o.max_batch && Clock::now() < deadline)
+      S->cv_in.wait_until(lk, deadline);
+    if (S->stop) break;
+    int si = -1;
+    S->cv_slot.wait(lk, [&] {
+      if (S->stop) return true;
+      for (int i = 0; i < (int)S->slots.size(); ++i)
+        if (!S->slots[i].busy) { si = i; return true; }
+      return false;
+    });
+    if (S->stop) break;
+    Slot& sl = S->slots[si];
+    sl.busy = true;
+    sl.tickets.clear();
+    sl.segments = false;
+    std::vector<Request*> batch, singles;
+    std::vector<int64_t> single_t;
+    while (!S->queue.empty() && (int64_t)batch.size() < S->o.max_batch) {
+      const int64_t t = S->queue.front();
+      S->queue.pop_front();
+      Request* r = S->reqs[t];
+      r->state = 1;
+      if (r->kind == 2) { singles.push_back(r); single_t.push_back(t); continue; }
+      sl.tickets.push_back(t);
+      batch.push_back(r);
+      sl.segments = sl.segments || r->kind == 1;
+    }
+    lk.unlock();
+    // id-list segments: one request at a time through the single-query path
+    for (Request* r : singles) {
+      std::vector<int64_t> ids;
+      rmips_status st;
+      run_single(S, r, ids, st);
+      std::lock_guard<std::mutex> g(S->mu);
+      finish(S, r, std::move(ids), st, Clock::now());
+      S->cv_done.notify_all();
+    }
+    const int64_t nq = (int64_t)batch.size();
+    if (nq > 0) {
+      const int d = S->idx->d;
+      for (int64_t i = 0; i < nq; ++i) {
+        memcpy(sl.h_q + i * d, batch[i]->q.data(), d * sizeof(float));
+        sl.h_k[i] = batch[i]->k;
+        sl.h_lo[i] = batch[i]->kind == 1 ? batch[i]->lo : 0;
+        sl.h_hi[i] = batch[i]->kind == 1 ? batch[i]->hi : INT64_MAX;
+      }
+      sl.launch = launch_slot(S, sl, nq);
+    }
+    lk.lock();
+    if (nq > 0) {
+      S->inflight.push_back(si);
+      ++S->batches;
+      S->batched += nq;
+      S->cv_fly.notify_one();
+    } else {
+      sl.busy = false;
+      S->cv_slot.notify_all();
+    }
+  }
+  // stopped: fail whatever is still queued
+  const auto now = Clock::now();
+  while (!S->queue.empty()) {
+    Request* r = S->reqs[S->queue.front()];
+    S->queue.pop_front();
+    finish(S, r, {}, RMIPS_ERR_ARG, now);
+  }
+  S->cv_done.notify_all();
+}
+
+void completer(rmips_server* S) {
+  cudaSetDevice(S->idx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    S->cv_fly.wait(lk, [&] { return S->stop || !S->inflight.empty(); });
+    if (S->inflight.empty()) {
+      if (S->stop) break;
+      continue;
+    }
+    const int si = S->inflight.front();
+    S->inflight.pop_front();
+    Slot& sl = S->slots[si];
+    std::vector<Request*> rs;
+    for (int64_t t : sl.tickets) rs.push_back(S->reqs[t]);
+    lk.unlock();
+    const int64_t nq = (int64_t)rs.size();
+    rmips_status st = sl.launch;
+    if (st == RMIPS_OK) {
+      if (cudaEventSynchronize(sl.done) != cudaSuccess) {
+        set_error("batch failed on the device");
+        st = RMIPS_ERR_CUDA;
+      } else {
+        st = device_status(sl.h_ctr[C_STATUS]);
+      }
+    }
+    std::vector<std::vector<int64_t>> res(nq);
+    std::vector<rmips_status> sts(nq, st);
+    if (st == RMIPS_OK) {
+      for (int64_t i = 0; i < nq; ++i)
+        res[i].assign(sl.h_out + sl.h_offs[i], sl.h_out + sl.h_offs[i + 1]);
+    } else if (st == RMIPS_ERR_CAPACITY) {
+      for (int64_t i = 0; i < nq; ++i) run_single(S, rs[i], res[i], sts[i]);
+    }
+    const auto now = Clock::now();
+    lk.lock();
+    for (int64_t i = 0; i < nq; ++i) finish(S, rs[i], std::move(res[i]), sts[i], now);
+    sl.busy = false;
+    S->cv_slot.notify_all();
+    S->cv_done.notify_all();
+  }
+}
+
+rmips_status check_request(const rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg) {
+  if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  for (int i = 0; i < idx->d; ++i)
+    if (!std::isfinite(q[i])) { set_error("non-finite value in a query"); return RMIPS_ERR_NONFINITE; }
+  if (seg) {
+    if (seg->reserved != 0 || seg->kind < 0 || seg->kind > 2) { set_error("bad segment"); return RMIPS_ERR_ARG; }
+    if (seg->kind == 1 && (seg->begin < 0 || seg->end < seg->begin)) { set_error("bad segment range"); return RMIPS_ERR_ARG; }
+    if (seg->kind == 2) {
+      if (seg->n_ids < 0 || (seg->n_ids > 0 && !seg->ids)) { set_error("bad segment list"); return RMIPS_ERR_ARG; }
+      for (int64_t i = 0; i < seg->n_ids; ++i)
+        if (seg->ids[i] < 0 || seg->ids[i] >= idx->n) { set_error("segment id out of range"); return RMIPS_ERR_ARG; }
+    }
+  }
+  return RMIPS_OK;
+}
+
+Request* make_request(const rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg) {
+  Request* r = new Request();
+  r->q.assign(q, q + idx->d);
+  r->k = k;
+  if (seg) {
+    r->kind = seg->kind;
+    r->lo = seg->begin;
+    r->hi = seg->end;
+    if (seg->kind == 2) r->list.assign(seg->ids, seg->ids + seg->n_ids);
+  }
+  r->t0 = Clock::now();
+  return r;
+}
+
+}  // namespace
+
+extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server_opts* opts, rmips_server** out) {
+  if (!idx || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  *out = nullptr;
+  rmips_server_opts o{};
+  o.max_batch = 4096;
+  o.max_wait_us = 200;
+  o.streams = 2;
+  o.max_pending = 1 << 20;
+  o.max_result_ids = 0;
+  if (opts) o = *opts;
+  if (o.max_batch < 1 || o.max_batch > MQ_MAXQ || o.max_wait_us < 0 || o.streams < 1 || o.streams > 16 ||
+      o.max_pending < 1 || o.max_result_ids < 0 || o.reserved != 0) {
+    set_error("bad server options (max_batch 1..16384, streams 1..16)");
+    return RMIPS_ERR_ARG;
+  }
+  if (o.max_result_ids == 0) o.max_result_ids = (int64_t)o.max_batch * 256;
+  rmips_server* S = new rmips_server();
+  S->idx = idx;
+  S->o = o;
+  S->slots.resize(o.streams);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(idx->device);
+  rmips_status st = RMIPS_OK;
+  for (Slot& sl : S->slots) {
+    sl.ws = acquire_workspace(idx, &st);
+    if (!sl.ws) break;
+    if ((st = batch_reserve(idx, sl.ws, o.max_batch)) != RMIPS_OK) break;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_q, (size_t)o.max_batch * idx->d * sizeof(float), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_k, o.max_batch * sizeof(int32_t), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_lo, o.max_batch * sizeof(long long), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_hi, o.max_batch * sizeof(long long), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_offs, (o.max_batch + 1) * sizeof(long long), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_ctr, C_NCOUNTERS * sizeof(long long), 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_out, o.max_result_ids * sizeof(long long), cudaHostAllocMapped);
+    sl.cap_out = o.max_result_ids;
+    if (e != cudaSuccess) {
+      set_error(std::string("server allocation: ") + cudaGetErrorString(e));
+      st = e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
+      break;
+    }
+  }
+  if (prev >= 0) cudaSetDevice(prev);
+  if (st != RMIPS_OK) {
+    rmips_server_destroy(S);
+    return st;
+  }
+  S->disp = std::thread(dispatcher, S);
+  S->comp = std::thread(completer, S);
+  *out = S;
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* qs, int64_t nq, const int32_t* ks,
+                                                 const rmips_segment* segs, int64_t* tickets) {
+  if (!S || nq < 0 || (nq > 0 && (!qs || !ks || !tickets))) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  const int d = S->idx->d;
+  for (int64_t j = 0; j < nq; ++j) {
+    rmips_status st = check_request(S->idx, qs + j * d, ks[j], segs ? &segs[j] : nullptr);
+    if (st != RMIPS_OK) return st;
+  }
+  std::vector<Request*> rs(nq);
+  for (int64_t j = 0; j < nq; ++j) rs[j] = make_request(S->idx, qs + j * d, ks[j], segs ? &segs[j] : nullptr);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      for (Request* r : rs) delete r;
+      set_error("server is stopping");
+      return RMIPS_ERR_ARG;
+    }
+    if (S->pending + nq > S->o.max_pending) {
+      for (Request* r : rs) delete r;
+      S->rejected += nq;
+      set_error("admission refused: too many requests pending");
+      return RMIPS_ERR_BUSY;
+    }
+    for (int64_t j = 0; j < nq; ++j) {
+      const int64_t t = S->next++;
+      S->reqs[t] = rs[j];
+      S->queue.push_back(t);
+      tickets[j] = t;
+    }
+    S->pending += nq;
+    S->submitted += nq;
+  }
+  S->cv_in.notify_one();
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_server_submit(rmips_server* S, const float* q, int32_t k, const rmips_segment* seg,
+                                            int64_t* ticket) {
+  if (!q || !ticket) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  return rmips_server_submit_many(S, q, 1, &k, seg, ticket);
+}
+
+extern "C" rmips_status rmips_server_wait(rmips_server* S, int64_t ticket, int64_t* out_ids, int64_t capacity,
+                                          int64_t* out_count, double* latency_ms, int32_t timeout_ms) {
+  if (!S || !out_count || capacity < 0 || (capacity > 0 && !out_ids)) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) { set_error("unknown ticket"); return RMIPS_ERR_ARG; }
+  Request* r = it->second;
+  auto done = [&] { return r->state == 2; };
+  if (timeout_ms < 0) S->cv_done.wait(lk, done);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+    set_error("request not finished yet");
+    return RMIPS_ERR_TIMEOUT;
+  }
+  *out_count = (int64_t)r->ids.size();
+  if (latency_ms) *latency_ms = r->ms;
+  const rmips_status st = r->st;
+  if (st == RMIPS_OK && (int64_t)r->ids.size() > capacity) {
+    set_error("output capacity too small");
+    return RMIPS_ERR_CAPACITY;                   // the request is kept: wait again with more room
+  }
+  if (st == RMIPS_OK && !r->ids.empty()) {
+    if (is_device_ptr(out_ids)) {
+      lk.unlock();
+      cudaError_t e = cudaMemcpy(out_ids, r->ids.data(), r->ids.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+      lk.lock();
+      if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return RMIPS_ERR_CUDA; }
+    } else {
+      memcpy(out_ids, r->ids.data(), r->ids.size() * sizeof(int64_t));
+    }
+  }
+  S->reqs.erase(ticket);
+  delete r;
+  return st;
+}
+
+extern "C" rmips_status rmips_server_get_stats(rmips_server* S, rmips_server_stats* out) {
+  if (!S || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  std::vector<double> v;
+  rmips_server_stats s{};
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    v = S->lat;
+    s.submitted = S->submitted;
+    s.completed = S->completed;
+    s.rejected = S->rejected;
+    s.batches = S->batches;
+    s.mean_batch = S->batches ? (double)S->batched / S->batches : 0.0;
+    s.pending = S->pending;
+  }
+  if (!v.empty()) {
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)std::floor(p * (v.size() - 1) + 0.5))]; };
+    s.p50_ms = pct(0.50);
+    s.p99_ms = pct(0.99);
+    s.max_ms = v.back();
+  }
+  *out = s;
+  return RMIPS_OK;
+}
+
+extern "C" void rmips_server_destroy(rmips_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_in.notify_all();
+  S->cv_slot.notify_all();
+  S->cv_fly.notify_all();
+  if (S->disp.joinable()) S->disp.join();
+  if (S->comp.joinable()) S->comp.join();
+  for (Slot& sl : S->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.ws) release_workspace(S->idx, sl.ws);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.done) cudaEventDestroy(sl.done);
+    cudaFreeHost(sl.h_q);
+    cudaFreeHost(sl.h_k);
+    cudaFreeHost(sl.h_lo);
+    cudaFreeHost(sl.h_hi);
+    cudaFreeHost(sl.h_offs);
+    cudaFreeHost(sl.h_ctr);
+    cudaFreeHost(sl.h_out);
+  }
+  for (auto& kv : S->reqs) delete kv.second;
+  delete S;
+}

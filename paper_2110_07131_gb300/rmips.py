@@ -19,20 +19,21 @@ __all__ = [
     "rmips_query_batch", "rmips_index_get_info", "rmips_last_query_stats",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
     "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
-    "FP32", "BF16", "FP16",
+    "FP32", "BF16", "FP16", "Server",
 ]
 
 FP32, BF16, FP16 = 0, 1, 2
 _PREC = {"fp32": FP32, "bf16": BF16, "fp16": FP16, FP32: FP32, BF16: BF16, FP16: FP16}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_K_RANGE", 3: "ERR_NONFINITE", 4: "ERR_OOM",
-          5: "ERR_CAPACITY", 6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_INTERNAL"}
+          5: "ERR_CAPACITY", 6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_INTERNAL", 9: "ERR_BUSY"}
 
 EXPORTED_SYMBOLS = [
     "rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
     "rmips_last_query_stats", "rmips_index_export", "rmips_free_index", "rmips_status_string",
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
-    "rmips_query_noalloc", "rmips_debug_tc_tile",
+    "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
+    "rmips_server_submit_many", "rmips_server_wait", "rmips_server_get_stats", "rmips_server_destroy",
 ]
 
 
@@ -64,6 +65,17 @@ class Profile(C.Structure):
                 ("users_tested", C.c_int64), ("blocks_pruned", C.c_int64), ("blocks_total", C.c_int64),
                 ("mfilter_launches", C.c_int64), ("mfilter_ms", C.c_double), ("mfilter_pairs", C.c_int64),
                 ("mfilter_alg_flops", C.c_double)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("streams", C.c_int32),
+                ("reserved", C.c_int32), ("max_pending", C.c_int64), ("max_result_ids", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
+                ("pending", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double)]
 
 
 class QueryStats(C.Structure):
@@ -108,9 +120,18 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_profile_read.argtypes = [VP, C.POINTER(Profile)]
         lib.rmips_query_noalloc.argtypes = [VP, P, I32, P, I64, C.POINTER(I64), VP]
         lib.rmips_debug_tc_tile.argtypes = [P, P, P, I32, I32, VP]
+        lib.rmips_server_create.argtypes = [VP, C.POINTER(ServerOpts), C.POINTER(VP)]
+        lib.rmips_server_submit.argtypes = [VP, P, I32, C.POINTER(Segment), C.POINTER(I64)]
+        lib.rmips_server_submit_many.argtypes = [VP, P, I64, P, C.POINTER(Segment), P]
+        lib.rmips_server_wait.argtypes = [VP, I64, P, I64, C.POINTER(I64), C.POINTER(C.c_double), I32]
+        lib.rmips_server_get_stats.argtypes = [VP, C.POINTER(ServerStats)]
+        lib.rmips_server_destroy.argtypes = [VP]
+        lib.rmips_server_destroy.restype = None
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
-                     "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile"):
+                     "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
+                     "rmips_server_create", "rmips_server_submit", "rmips_server_submit_many",
+                     "rmips_server_wait", "rmips_server_get_stats"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -348,3 +369,68 @@ def rmips_exact_sign_host(u, a, b) -> int:
     a = np.ascontiguousarray(a, np.float32)
     b = np.ascontiguousarray(b, np.float32)
     return int(_lib.rmips_exact_sign_host(u.ctypes.data, a.ctypes.data, b.ctypes.data, u.shape[0]))
+
+
+class Server:
+    """Continuous-batching request loop over an index (see ``include/rmips.h``)."""
+
+    def __init__(self, index: Index, max_batch: int = 4096, max_wait_us: int = 200, streams: int = 2,
+                 max_pending: int = 1 << 20, max_result_ids: int = 0):
+        load_library()
+        self.index = index                       # keeps the index alive
+        opts = ServerOpts(int(max_batch), int(max_wait_us), int(streams), 0, int(max_pending),
+                          int(max_result_ids))
+        h = C.c_void_p()
+        _check(_lib.rmips_server_create(index.handle, C.byref(opts), C.byref(h)))
+        self.handle = h
+
+    def submit(self, q, k: int, segment=None) -> int:
+        keep = []
+        qa = np.ascontiguousarray(q, np.float32)
+        seg = _segment(segment, keep)
+        t = C.c_int64(0)
+        _check(_lib.rmips_server_submit(self.handle, qa.ctypes.data, int(k),
+                                        C.byref(seg) if seg is not None else None, C.byref(t)))
+        return t.value
+
+    def submit_many(self, qs, ks, segments=None) -> np.ndarray:
+        keep = []
+        qa = np.ascontiguousarray(qs, np.float32)
+        nq = qa.shape[0]
+        ka = np.ascontiguousarray(np.broadcast_to(np.asarray(ks), (nq,)), np.int32)
+        segs = None
+        if segments is not None:
+            segs = (Segment * nq)()
+            for j, sg in enumerate(segments):
+                s = _segment(sg, keep)
+                segs[j] = s if s is not None else Segment()
+        tickets = np.empty(nq, np.int64)
+        _check(_lib.rmips_server_submit_many(self.handle, qa.ctypes.data, nq, ka.ctypes.data, segs,
+                                             tickets.ctypes.data))
+        return tickets
+
+    def wait(self, ticket: int, timeout_ms: int = -1, capacity: int | None = None):
+        """Returns ``(ids, latency_ms)``."""
+        cap = self.index.n if capacity is None else int(capacity)
+        buf = np.empty(max(cap, 1), np.int64)
+        cnt = C.c_int64(0)
+        lat = C.c_double(0.0)
+        _check(_lib.rmips_server_wait(self.handle, int(ticket), buf.ctypes.data, cap, C.byref(cnt),
+                                      C.byref(lat), int(timeout_ms)))
+        return buf[:cnt.value], lat.value
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.rmips_server_get_stats(self.handle, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib.rmips_server_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,117 @@
+"""Serving loop: each request's result is the same alone and in the mix."""
+import threading
+
+import numpy as np
+import pytest
+
+from oracle import rmips_oracle as O
+from paper_2110_07131_gb300 import datagen, rmips
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    Q, P = datagen.make_problem(3000, 1500, 50, 9)
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    yield Q, P, index
+    index.close()
+
+
+def _requests(P, n_req, seed):
+    rng = np.random.default_rng(seed)
+    qs, _ = datagen.queries_from_items(P, n_req, seed)
+    ks = rng.integers(1, 26, n_req)
+    segs = []
+    for j in range(n_req):
+        r = j % 4
+        if r == 1:
+            a = int(rng.integers(0, 3000))
+            segs.append((a, a + int(rng.integers(1, 3000))))      # uneven id ranges
+        elif r == 2:
+            segs.append(np.sort(rng.choice(3000, int(rng.integers(1, 2000)), replace=False)))
+        else:
+            segs.append(None)
+    return qs, ks, segs
+
+
+def test_results_identical_alone_and_in_the_mix(setup):
+    Q, P, index = setup
+    qs, ks, segs = _requests(P, 600, 1)
+    alone = [rmips.rmips_query(index, qs[j], int(ks[j]), segment=segs[j]) for j in range(len(qs))]
+    srv = rmips.Server(index, max_batch=64, max_wait_us=300, streams=3)
+    got = [None] * len(qs)
+    errs = []
+
+    def client(lo, hi):
+        try:
+            tickets = [(j, srv.submit(qs[j], int(ks[j]), segs[j])) for j in range(lo, hi)]
+            for j, t in tickets:
+                got[j], lat = srv.wait(t)
+                assert lat >= 0.0
+        except Exception as e:                # surfaced below
+            errs.append(e)
+
+    threads = [threading.Thread(target=client, args=(i * 150, (i + 1) * 150)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errs, errs
+    for j in range(len(qs)):
+        assert np.array_equal(got[j], alone[j]), j
+    st = srv.stats()
+    assert st["completed"] == len(qs) and st["pending"] == 0
+    assert st["batches"] >= 1 and st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    srv.close()
+
+
+def test_batched_requests_match_oracle(setup):
+    Q, P, index = setup
+    qs, ks, _ = _requests(P, 200, 2)
+    srv = rmips.Server(index, max_batch=128, max_wait_us=1000, streams=2)
+    tickets = srv.submit_many(qs, ks.astype(np.int32))
+    counts = O.counts_greater_multi(Q, P, qs)
+    for j, t in enumerate(tickets):
+        ids, _ = srv.wait(int(t))
+        assert np.array_equal(ids, np.nonzero(counts[j] < ks[j])[0])
+    srv.close()
+
+
+def test_admission_and_bad_requests_do_not_stop_the_loop(setup):
+    Q, P, index = setup
+    srv = rmips.Server(index, max_batch=32, max_wait_us=100000, streams=1, max_pending=8)
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit_many(P[:20], 5)
+    assert e.value.status == 9                    # admission refused, nothing queued
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit(P[0], 0)
+    assert e.value.status == 2
+    bad = P[1].copy()
+    bad[4] = np.inf
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit(bad, 3)
+    assert e.value.status == 3
+    t = srv.submit(P[2], 7)
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.wait(t, timeout_ms=0)                 # the batch is still open (long deadline)
+    assert e.value.status == 6
+    ids, _ = srv.wait(t)
+    assert np.array_equal(ids, rmips.rmips_query(index, P[2], 7))
+    st = srv.stats()
+    assert st["rejected"] == 20 and st["completed"] == 1
+    srv.close()
+
+
+def test_small_result_budget_falls_back_per_request(setup):
+    Q, P, index = setup
+    qs, ks, _ = _requests(P, 40, 3)
+    srv = rmips.Server(index, max_batch=40, max_wait_us=2000, streams=1, max_result_ids=8)
+    tickets = srv.submit_many(qs, ks.astype(np.int32))
+    for j, t in enumerate(tickets):
+        ids, _ = srv.wait(int(t))
+        assert np.array_equal(ids, rmips.rmips_query(index, qs[j], int(ks[j])))
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.wait(12345678)
+    assert e.value.status == 1
+    srv.close()
