@@ -80,7 +80,14 @@ def exact_dot(u, x) -> Fraction:
 
 
 def exact_sign_diff(u, a, b) -> int:
-    """Sign of ``u.a - u.b`` in exact arithmetic: -1, 0 or +1."""
+    """Sign of ``u.a - u.b`` in exact arithmetic: -1, 0 or +1.
+
+    When a and b hold the same values, ``u.a - u.b`` is exactly zero (this is
+    the tie between a query and its own copy in P), so no rational arithmetic
+    is needed.
+    """
+    if np.array_equal(np.asarray(a, dtype=np.float32), np.asarray(b, dtype=np.float32)):
+        return 0
     diff = exact_dot(u, a) - exact_dot(u, b)
     return (diff > 0) - (diff < 0)
 
