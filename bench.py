@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--plain-queries", type=int, default=400)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU baseline time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=60000, help="requests per serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=1.0e6, help="offered load of the paced serving run (q/s)")
     return ap.parse_args()
 
 
@@ -157,6 +159,56 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- serving
+def run_serving(rmips, index, qs, a):
+    """Continuous batching through rmips_server_*: a saturating burst and a
+    paced open-loop run.  Latencies are measured inside the library from
+    submit to completion; a separate warm-up server runs first (its slots'
+    workspaces return to the index and are reused)."""
+    import threading
+    n_req = min(a.serve_requests, len(qs))
+    opts = dict(max_batch=4096, max_wait_us=200, streams=2, max_pending=1 << 21)
+    warm = rmips.Server(index, **opts)
+    for t in warm.submit_many(qs[:4096], a.k):
+        warm.wait(int(t))
+    warm.close()
+    out = {}
+    for mode in ("saturated", "paced"):
+        srv = rmips.Server(index, **opts)
+        chunks = []
+        n_chunks = (n_req + 1023) // 1024
+
+        def collect():
+            i = 0
+            while i < n_chunks:
+                if i < len(chunks):
+                    for t in chunks[i]:
+                        srv.wait(int(t))
+                    i += 1
+                else:
+                    time.sleep(0.0002)
+
+        th = threading.Thread(target=collect)
+        th.start()
+        t0 = time.perf_counter()
+        for c0 in range(0, n_req, 1024):
+            if mode == "paced":
+                due = t0 + c0 / a.serve_rate
+                while time.perf_counter() < due:
+                    pass
+            chunks.append(srv.submit_many(qs[c0:c0 + 1024], a.k))
+        th.join()
+        el = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        out[mode] = {"qps": n_req / el, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                     "max_ms": st["max_ms"], "mean_batch": st["mean_batch"], "batches": st["batches"],
+                     "requests": n_req, "offered_qps": None if mode == "saturated" else a.serve_rate}
+    out["config"] = ("rmips_server: max_batch 4096, max_wait 200 us, 2 streams; k = 10; queries = random items "
+                     "of P submitted in chunks of 1024 from the host")
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_ours(a):
     import torch
@@ -245,6 +297,8 @@ def run_ours(a):
              "p99_ms": float(np.percentile(lat_s, 99)), "queries": int(len(lat_s)),
              "api": "rmips_query, host q and host ids, one query per call"}
 
+    serving = run_serving(rmips, index, qs, a) if a.serve_requests > 0 else None
+
     # single-query filter timing (HBM-bound kernel), profiled separately from the latency run
     rmips.rmips_profile_enable(index, True)
     for j in range(min(200, a.plain_queries)):
@@ -305,7 +359,7 @@ def run_ours(a):
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
             "gpu_launches": a.steps * 9 * ((a.nq + 16383) // 16384),
             "roofline_single_query_filter": roof_single,
-            "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain,
+            "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain, "serving": serving,
             "batch_latency_ms": ms_max / a.steps,
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
             "index_incomplete_users": info["incomplete"],

@@ -33,6 +33,8 @@ void destroy_workspace(Workspace* ws) {
   cudaFreeHost(ws->h_ctr);
   cudaFreeHost(ws->h_offs);
   cudaFreeHost(ws->h_out);
+  cudaFreeHost(ws->h_q);
+  cudaFreeHost(ws->h_res);
   for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
   cudaFree(ws->bq);
   cudaFree(ws->bk);
@@ -77,6 +79,8 @@ Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_ctr, C_NCOUNTERS * sizeof(long long), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_out, n * sizeof(long long), cudaHostAllocMapped);
   if (e == cudaSuccess) ws->cap_hout = n;
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_q, RMIPS_DMAX * sizeof(float), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&ws->h_res, (2 + C_NCOUNTERS) * sizeof(long long), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));

@@ -108,38 +108,24 @@ __global__ void k_qprep(Common c, int64_t nq, int precision) {
 }
 
 // --- filter ------------------------------------------------------------------------
+// Lemmas 1-3 for one query over this CTA's share of 32-user chunks.  Warp w
+// of the grid owns chunks w, w + W, w + 2W, ... (W = warps in the grid); it
+// tests Lemma 3 for 32 of its chunks at once (one lane each), then streams
+// the surviving chunks' rows into shared memory with 1-D TMA bulk copies,
+// double-buffered, and tests every user.  Returns false if a TMA wait gave up.
 template <class T, bool FULLP>
-__global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  float* sq = reinterpret_cast<float*>(smem);                        // [RMIPS_DMAX]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 512);          // [FW][2]
-  unsigned char* bufs = smem + 512 + FW * 2 * 8;
+__device__ bool filter_chunks(const Common& c, const float* sq, int k, float qn, float qeps, uint64_t* bars,
+                              unsigned char* bufs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int d = c.d;
   const int64_t n = c.n;
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) {
-    const long long st0 = c.ctr[C_STATUS];
-    s_skip = (st0 != 0 && st0 != ST_CAPACITY);                    // bad input: nothing to do
-  }
-  __syncthreads();
-  if (s_skip) return;                                               // uniform across the CTA
-  const int k = c.dk[j];
-  const float* q = c.dq + (int64_t)j * d;
-  for (int i = threadIdx.x; i < d; i += blockDim.x) sq[i] = q[i];
-  const float qn = c.dqn[j], qeps = c.deps[j];
   const float pk = (k <= c.m) ? c.pnorm[k - 1] : -kInf;
-  if (lane == 0) {
-    mbar_init(&bars[warp * 2 + 0], 1);
-    mbar_init(&bars[warp * 2 + 1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   const uint32_t chunk_bytes = 32u * d * (uint32_t)sizeof(T);        // multiple of 16
   unsigned char* mybuf = bufs + (size_t)warp * 2 * chunk_bytes;
   const int64_t nchunks = (n + 31) / 32;
-  const int64_t W = (int64_t)gridDim.x * FW;
-  const int64_t w0 = (int64_t)blockIdx.x * FW + warp;
+  const int nwarp = blockDim.x >> 5;
+  const int64_t W = (int64_t)gridDim.x * nwarp;
+  const int64_t w0 = (int64_t)blockIdx.x * nwarp + warp;
   const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
   const float2* Lbk = c.Lb + (int64_t)(k - 1) * n;
 
@@ -179,6 +165,7 @@ __global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
 
   uint32_t phase = 0;      // bit s = parity to wait for on buffer s
   int s = 0;
+  bool good = true;
   int64_t cur = next_chunk();
   if (cur >= 0) issue(cur, 0);
   while (cur >= 0) {
@@ -193,7 +180,8 @@ __global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
     if (!ok) {
       set_status(c.ctr, ST_TIMEOUT);
       if (nxt >= 0) mbar_wait_bounded(&bars[warp * 2 + (s ^ 1)], (phase >> (s ^ 1)) & 1u);
-      return;
+      good = false;
+      break;
     }
     phase ^= 1u << s;
     const T* row = reinterpret_cast<const T*>(mybuf + (size_t)s * chunk_bytes) + (size_t)lane * d;
@@ -243,6 +231,37 @@ __global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
     if (yesfast) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)yesfast);
     if (todosum) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)todosum);
   }
+  return good;
+}
+
+__device__ __forceinline__ void init_filter_barriers(uint64_t* bars) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    mbar_init(&bars[warp * 2 + 0], 1);
+    mbar_init(&bars[warp * 2 + 1], 1);
+    fence_mbar_init();
+  }
+}
+
+template <class T, bool FULLP>
+__global__ void __launch_bounds__(FW * 32) k_filter(Common c, int j) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* sq = reinterpret_cast<float*>(smem);                        // [RMIPS_DMAX]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 512);          // [FW][2]
+  unsigned char* bufs = smem + 512 + FW * 2 * 8;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_skip = (st0 != 0 && st0 != ST_CAPACITY);                    // bad input: nothing to do
+  }
+  __syncthreads();
+  if (s_skip) return;                                               // uniform across the CTA
+  const int k = c.dk[j];
+  const float* q = c.dq + (int64_t)j * c.d;
+  for (int i = threadIdx.x; i < c.d; i += blockDim.x) sq[i] = q[i];
+  init_filter_barriers(bars);
+  __syncthreads();
+  filter_chunks<T, FULLP>(c, sq, k, c.dqn[j], c.deps[j], bars, bufs);
 }
 
 // --- Algorithm 2 for one user, one warp ----------------------------------------------
@@ -397,32 +416,21 @@ __device__ __forceinline__ bool seg_ok(const EmitArgs& e, int32_t id) {
   return true;
 }
 
-__global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int j) {
-  __shared__ int32_t keys[EMIT_SORT_CAP];
-  __shared__ int s_warp[EMIT_THREADS / 32];
-  __shared__ long long s_total, s_cnt, s_base;
-  __shared__ int s_bad;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    const long long st0 = c.ctr[C_STATUS];
-    s_bad = (st0 != 0 && st0 != ST_CAPACITY);
-    s_cnt = c.ctr[C_YES];
-    s_base = c.ctr[C_CURSOR];
-  }
-  __syncthreads();
-  const long long cnt = s_cnt;
-  const long long base = s_base;
-  const bool bad = s_bad != 0;
+// Block-wide emit (any block size that is a multiple of 32): the cnt listed
+// positions -> caller ids, segment filter, ascending order, written at
+// e.out[base ..] when they fit in e.capacity.  keys: EMIT_SORT_CAP ints of
+// shared memory; s_warp: 32 ints.  Returns the number of ids.
+__device__ long long emit_block(const Common& c, const EmitArgs& e, long long cnt, long long base,
+                                int32_t* keys, int* s_warp, long long* s_total) {
+  const int tid = threadIdx.x, nt = blockDim.x, nwarp = nt >> 5;
   long long total = 0;
-  if (bad) {
-    total = 0;
-  } else if (cnt <= EMIT_SORT_CAP) {
+  if (cnt <= EMIT_SORT_CAP) {
     int N2 = 1;
     while (N2 < cnt) N2 <<= 1;
-    for (int i = tid; i < N2; i += EMIT_THREADS) {
+    for (int i = tid; i < N2; i += nt) {
       int32_t id = INT_MAX;
       if (i < cnt) {
-        int32_t v = c.permQ[c.yes[i]];
+        int32_t v = c.permQ[__ldcg(&c.yes[i])];
         if (seg_ok(e, v)) id = v;
       }
       keys[i] = id;
@@ -430,7 +438,7 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     __syncthreads();
     for (int kk = 2; kk <= N2; kk <<= 1) {
       for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int t = tid; t < (N2 >> 1); t += EMIT_THREADS) {
+        for (int t = tid; t < (N2 >> 1); t += nt) {
           const int i = 2 * t - (t & (jj - 1)), p = i + jj;
           const int32_t a = keys[i], b = keys[p];
           if ((a > b) == ((i & kk) == 0)) { keys[i] = b; keys[p] = a; }
@@ -441,21 +449,21 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     if (tid == 0) {
       int lo = 0, hi = N2;                 // first INT_MAX
       while (lo < hi) { int mid = (lo + hi) >> 1; if (keys[mid] == INT_MAX) hi = mid; else lo = mid + 1; }
-      s_total = lo;
+      *s_total = lo;
     }
     __syncthreads();
-    total = s_total;
+    total = *s_total;
     if (base + total <= e.capacity) {
-      for (int i = tid; i < total; i += EMIT_THREADS) e.out[base + i] = keys[i];
+      for (int i = tid; i < total; i += nt) e.out[base + i] = keys[i];
     }
   } else {
-    for (long long i = tid; i < cnt; i += EMIT_THREADS) {
-      int32_t v = c.permQ[c.yes[i]];
+    for (long long i = tid; i < cnt; i += nt) {
+      int32_t v = c.permQ[__ldcg(&c.yes[i])];
       if (seg_ok(e, v)) atomicOr(&e.bitmap[v >> 5], 1u << (v & 31));
     }
     __syncthreads();
     const int64_t nw = (c.n + 31) / 32;
-    const int64_t per = (nw + EMIT_THREADS - 1) / EMIT_THREADS;
+    const int64_t per = (nw + nt - 1) / nt;
     const int64_t w0 = tid * per, w1 = (w0 + per < nw) ? w0 + per : nw;
     int local = 0;
     for (int64_t w = w0; w < w1; ++w) local += __popc(__ldcg(&e.bitmap[w]));
@@ -466,13 +474,13 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-      int v = s_warp[lane];
+      int v = lane < nwarp ? s_warp[lane] : 0;
       for (int o = 1; o < 32; o <<= 1) { int y = __shfl_up_sync(FULL, v, o); if (lane >= o) v += y; }
-      s_warp[lane] = v;
+      if (lane < nwarp) s_warp[lane] = v;
     }
     __syncthreads();
     const long long excl = (long long)(x - local) + (wid ? s_warp[wid - 1] : 0);
-    total = s_warp[31];
+    total = s_warp[nwarp - 1];
     if (base + total <= e.capacity) {
       long long o = base + excl;
       for (int64_t w = w0; w < w1; ++w) {
@@ -486,6 +494,25 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     }
     for (int64_t w = w0; w < w1; ++w) e.bitmap[w] = 0u;
   }
+  return total;
+}
+
+__global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int j) {
+  __shared__ int32_t keys[EMIT_SORT_CAP];
+  __shared__ int s_warp[EMIT_THREADS / 32];
+  __shared__ long long s_total, s_cnt, s_base;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const long long st0 = c.ctr[C_STATUS];
+    s_bad = (st0 != 0 && st0 != ST_CAPACITY);
+    s_cnt = c.ctr[C_YES];
+    s_base = c.ctr[C_CURSOR];
+  }
+  __syncthreads();
+  const long long base = s_base;
+  const bool bad = s_bad != 0;
+  const long long total = bad ? 0 : emit_block(c, e, s_cnt, base, keys, s_warp, &s_total);
   __syncthreads();
   if (tid == 0) {
     if (!bad && base + total > e.capacity)
@@ -494,6 +521,73 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
     c.ctr[C_CURSOR] = base + total;
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
+  }
+}
+
+// --- one launch per query (full-P index) ---------------------------------------------
+// Every CTA forms ||q|| itself and runs the filter on its chunks; the last CTA
+// to finish (a device-wide counter taken after a memory fence, nothing waits)
+// rechecks the undecided users, sorts and writes the ids, copies the status,
+// count and counters to `res` (device-visible host memory) and clears the
+// counters for the next call.
+constexpr int RES_STATUS = 0, RES_COUNT = 1, RES_CTR = 2;     // res layout: [2 + C_NCOUNTERS]
+
+template <class T>
+__global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const float* q_src, int k, int precision,
+                                                     long long* res) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* sq = reinterpret_cast<float*>(smem);                        // [RMIPS_DMAX]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 512);          // [FW][2]
+  unsigned char* bufs = smem + 512 + FW * 2 * 8;                     // TMA buffers, later sort keys
+  __shared__ float s_qn, s_eps;
+  __shared__ int s_fin, s_last;
+  __shared__ int s_warp[32];
+  __shared__ long long s_total;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d = c.d;
+  for (int i = tid; i < d; i += blockDim.x) sq[i] = q_src[i];
+  init_filter_barriers(bars);
+  __syncthreads();
+  if (tid == 0) s_fin = query_bounds(sq, d, precision, &s_qn, &s_eps) ? 1 : 0;
+  __syncthreads();
+  if (s_fin) filter_chunks<T, true>(c, sq, k, s_qn, s_eps, bars, bufs);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd((unsigned long long*)&c.ctr[C_DONE], 1ull) == (unsigned long long)(gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  long long status = s_fin ? __ldcg(&c.ctr[C_STATUS]) : ST_NONFINITE;
+  long long total = 0;
+  if (status == 0) {
+    // exact recheck of the undecided users: one warp per user
+    const long long ntodo = __ldcg(&c.ctr[C_TODO]);
+    for (long long t = warp; t < ntodo; t += FW) {
+      const int32_t pos = __ldcg(&c.todo[t]);
+      const float* u = c.Qs + (int64_t)pos * d;
+      const bool yes = !c.incomp[pos]
+                           ? recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr)
+                           : verify_scan(u, c.unorm[pos], c, sq, k, s_eps);
+      if (lane == 0 && yes) {
+        const long long b = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+        c.yes[b] = pos;
+      }
+    }
+    __threadfence_block();
+    __syncthreads();
+    total = emit_block(c, e, __ldcg(&c.ctr[C_YES]), 0, reinterpret_cast<int32_t*>(bufs), s_warp, &s_total);
+    if (total > e.capacity) status = ST_CAPACITY;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    res[RES_STATUS] = status;
+    res[RES_COUNT] = total;
+    for (int i = 0; i < C_NCOUNTERS; ++i) {
+      res[RES_CTR + i] = c.ctr[i];
+      c.ctr[i] = 0;
+    }
+    c.ctr[C_DONE] = 0;
+    __threadfence_system();
   }
 }
 
@@ -605,6 +699,7 @@ rmips_status check_segment(const rmips_index* idx, const rmips_segment* seg) {
 // `out` (device-visible), offsets to ws->doffs.
 rmips_status run_queries(rmips_index* idx, Workspace* ws, int64_t nq, const rmips_segment* segs,
                          long long* out, long long capacity, cudaStream_t st) {
+  ws->ctr_dirty = true;
   Common c = make_common(idx, ws);
   static thread_local int sm_count = 0;
   if (!sm_count) {
@@ -680,6 +775,87 @@ rmips_status status_from_device(long long s) {
     case ST_TIMEOUT: set_error("a device wait timed out"); return RMIPS_ERR_TIMEOUT;
     default: set_error("device-side consistency check failed"); return RMIPS_ERR_INTERNAL;
   }
+}
+
+template <class T>
+cudaError_t launch_query1(const Common& c, const EmitArgs& e, const float* q, int k, int precision, long long* res,
+                          int grid, size_t smem, cudaStream_t st) {
+  static thread_local bool configured = false;
+  if (!configured) {
+    cudaError_t err = cudaFuncSetAttribute(k_query1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (err != cudaSuccess) return err;
+    configured = true;
+  }
+  k_query1<T><<<grid, FW * 32, smem, st>>>(c, e, q, k, precision, res);
+  return cudaGetLastError();
+}
+
+// Single query in one launch; results land in device-mapped host memory.
+rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_t k, const rmips_segment* seg,
+                         int64_t* out_ids, int64_t capacity, int64_t* out_count, cudaStream_t st) {
+  const int d = idx->d;
+  const float* q_src = q;
+  if (!is_device_ptr(q)) {                      // stage q in device-mapped pinned memory
+    memcpy(ws->h_q, q, d * sizeof(float));
+    q_src = ws->h_q;
+  }
+  Common c = make_common(idx, ws);
+  static thread_local int sm_count = 0;
+  if (!sm_count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (sm_count <= 0) sm_count = 1;
+  }
+  size_t smem = 512 + FW * 2 * 8 + (size_t)FW * 2 * 32 * d * elem_bytes(idx->precision);
+  const size_t smem_keys = 512 + FW * 2 * 8 + EMIT_SORT_CAP * sizeof(int32_t);
+  if (smem < smem_keys) smem = smem_keys;
+  const int64_t nchunks = (idx->n + 31) / 32;
+  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 1024);
+  per_sm = per_sm > 8 ? 8 : (per_sm < 1 ? 1 : per_sm);
+  const int64_t want = (nchunks + FW - 1) / FW;
+  const int grid = (int)(want < sm_count * per_sm ? want : sm_count * per_sm);
+  const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
+  if (ws->ctr_dirty) {                           // the one-launch kernel needs zero counters
+    RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+    ws->ctr_dirty = false;
+  }
+  EmitArgs e{};
+  e.seg_lo = (seg && seg->kind == 1) ? seg->begin : 0;
+  e.seg_hi = (seg && seg->kind == 1) ? seg->end : INT64_MAX;
+  e.segmask = nullptr;
+  e.bitmap = ws->bitmap;
+  e.out = out_dev ? (long long*)out_ids : ws->h_out;
+  e.capacity = out_dev ? capacity : (capacity < ws->cap_hout ? capacity : ws->cap_hout);
+  e.offs = nullptr;
+  cudaError_t err;
+  switch (idx->precision) {
+    case RMIPS_BF16: err = launch_query1<__nv_bfloat16>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
+    case RMIPS_FP16: err = launch_query1<__half>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
+    default: err = launch_query1<float>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
+  }
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  const long long status = ws->h_res[RES_STATUS];
+  const long long count = ws->h_res[RES_COUNT];
+  *out_count = count;
+  {
+    std::lock_guard<std::mutex> lk(idx->mu);
+    rmips_query_stats s{};
+    s.blocks_total = idx->nb;
+    s.blocks_pruned = ws->h_res[RES_CTR + C_PRUNED] * 32 / idx->bs;
+    s.users_tested = ws->h_res[RES_CTR + C_TESTED];
+    s.yes_fast = ws->h_res[RES_CTR + C_YESFAST];
+    s.todo = ws->h_res[RES_CTR + C_TODOSUM];
+    s.exact_calls = ws->h_res[RES_CTR + C_EXACT];
+    s.result = count;
+    idx->last_stats = s;
+  }
+  if (status == ST_TIMEOUT || status == ST_INTERNAL) ws->ctr_dirty = true;
+  rmips_status s = status_from_device(status);
+  if (s != RMIPS_OK) return s;
+  if (!out_dev && count > 0) memcpy(out_ids, ws->h_out, count * sizeof(long long));
+  return RMIPS_OK;
 }
 
 struct WsGuard {
@@ -1799,6 +1975,7 @@ rmips_status ensure_segments(Workspace* ws, int64_t nq) {
 
 rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
                        cudaStream_t st, const long long* dseglo, const long long* dseghi) {
+  ws->ctr_dirty = true;
   Common c = make_common(idx, ws);
   static thread_local int sm_count = 0;
   if (!sm_count) {
@@ -1914,6 +2091,10 @@ extern "C" rmips_status rmips_query(rmips_index* idx, const float* q, int32_t k,
   if (!ws) return s;
   WsGuard g{idx, ws};
   if ((s = ensure_queries(idx, ws, 1)) != RMIPS_OK) return s;
+  if (idx->full_p && (!seg || seg->kind != 2)) {
+    s = query_fused(idx, ws, q, k, seg, out_ids, capacity, out_count, st);
+    if (s != RMIPS_ERR_INTERNAL) return s;      // internal: fall through to the multi-kernel path
+  }
   const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
   long long* out;
   if (out_dev) out = (long long*)out_ids;

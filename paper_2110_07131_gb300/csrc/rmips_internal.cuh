@@ -74,7 +74,8 @@ enum : int {
   C_YESFAST = 7,    // users decided yes by the O(1) tests
   C_TODOSUM = 8,    // users sent to the todo list (all queries of the call)
   C_NBIG = 9,       // queries of a batch pass with more than EMIT_SORT_CAP results
-  C_NCOUNTERS = 10
+  C_DONE = 10,      // CTAs finished (one-launch query)
+  C_NCOUNTERS = 11
 };
 
 // ---------------------------------------------------------------------------
@@ -97,6 +98,9 @@ struct Workspace {
   int64_t cap_out = 0;
   long long* h_out = nullptr;   // [n] pinned, device-mapped result staging
   int64_t cap_hout = 0;
+  float* h_q = nullptr;          // [RMIPS_DMAX] pinned, device-mapped query staging
+  long long* h_res = nullptr;    // [2 + C_NCOUNTERS] pinned, device-mapped status / count / counters
+  bool ctr_dirty = false;        // counters may be non-zero (multi-kernel paths leave them so)
   std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch
   int64_t ev_used = 0;
   // batched (multi-query) path

@@ -61,13 +61,17 @@ def test_block_sizes(tiny, bs):
     _check_all(index, allq, counts, (3, 10))
 
 
-def test_single_query_api_matches(tiny):
+@pytest.mark.parametrize("p_prime", [0, 100])
+def test_single_query_api_matches(tiny, p_prime):
     Q, P, allq, counts = tiny
-    index = rmips.rmips_build_index(Q, P, k_max=25)
+    index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime)
     for j in range(0, len(allq), 7):
         for k in (1, 10, 25):
             got = rmips.rmips_query(index, allq[j], k)
             assert np.array_equal(got, np.nonzero(counts[j] < k)[0])
+            # alternate with batches on the same index: shared workspaces stay consistent
+            ids, offs = rmips.rmips_query_batch(index, allq[j:j + 2], k)
+            assert np.array_equal(ids[offs[0]:offs[1]], got)
 
 
 def test_index_arrays_match_oracle(tiny):
