@@ -76,6 +76,9 @@ typedef struct {
 /* rmips_build_opts.flags: run the batched filter on CUDA cores (float32 FMA)
    instead of tensor cores (TF32 tiles, used for float32 indexes with d <= 64). */
 #define RMIPS_FLAG_BATCH_CUDA_CORES 1
+/* rmips_build_index: select each user's candidate items on CUDA cores (float32
+   FMA) instead of tensor cores (TF32 tiles, used when d <= 64). */
+#define RMIPS_FLAG_BUILD_CUDA_CORES 2
 
 /* Optional restriction of a query to a subset of users. */
 typedef struct {
@@ -258,6 +261,16 @@ rmips_status rmips_server_submit_many(rmips_server* server, const float* qs, int
    RMIPS_ERR_CAPACITY: *out_count is the size needed (ticket kept). */
 rmips_status rmips_server_wait(rmips_server* server, int64_t ticket, int64_t* out_ids, int64_t capacity,
                                int64_t* out_count, double* latency_ms, int32_t timeout_ms);
+
+/* Waits for a set of requests and returns their results in CSR form:
+   request i's ids are out_ids[out_offsets[i] .. out_offsets[i+1]) (out_offsets
+   has nt + 1 entries, host); latency_ms (NULL or nt entries) receives each
+   latency.  On success every ticket is forgotten; the first failing request's
+   status is returned (its slice is empty).  RMIPS_ERR_TIMEOUT and
+   RMIPS_ERR_CAPACITY (offsets filled) keep all tickets. */
+rmips_status rmips_server_wait_many(rmips_server* server, const int64_t* tickets, int64_t nt, int64_t* out_ids,
+                                    int64_t capacity, int64_t* out_offsets, double* latency_ms,
+                                    int32_t timeout_ms);
 
 /* Counters and latency percentiles of the requests completed so far. */
 rmips_status rmips_server_get_stats(rmips_server* server, rmips_server_stats* out);

@@ -15,6 +15,7 @@
 #include <cmath>
 
 #include "rmips_internal.cuh"
+#include "tc_common.cuh"
 
 namespace rmips {
 namespace {
@@ -101,17 +102,18 @@ constexpr int TOPK_THREADS = 128;
 template <int DP>
 __global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__ Qs, const float* __restrict__ Ps,
                                                        int64_t n, int64_t pp, int d, float* __restrict__ cval,
-                                                       int32_t* __restrict__ cid) {
+                                                       int32_t* __restrict__ cid, const int32_t* __restrict__ ulist) {
   extern __shared__ __align__(16) float topk_smem[];
   float* tile = topk_smem;                                                   // [DP][TS]
   float (*lv)[TOPK_THREADS] = reinterpret_cast<float (*)[TOPK_THREADS]>(topk_smem + DP * TS);
   int32_t (*li)[TOPK_THREADS] =
       reinterpret_cast<int32_t (*)[TOPK_THREADS]>(topk_smem + DP * TS + RMIPS_KC * TOPK_THREADS);
   const int t = threadIdx.x;
-  const int64_t u = blockIdx.x * (int64_t)TOPK_THREADS + t;
+  const int64_t slot = blockIdx.x * (int64_t)TOPK_THREADS + t;   // n = users to do (list length if ulist)
+  const int64_t u = slot < n ? (ulist ? (int64_t)ulist[slot] : slot) : n;
   float ur[DP];
 #pragma unroll
-  for (int i = 0; i < DP; ++i) ur[i] = (u < n && i < d) ? Qs[u * d + i] : 0.f;
+  for (int i = 0; i < DP; ++i) ur[i] = (slot < n && i < d) ? Qs[u * d + i] : 0.f;
 #pragma unroll
   for (int s = 0; s < RMIPS_KC; ++s) {
     lv[s][t] = -kInf;
@@ -154,12 +156,194 @@ __global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__
       }
     }
   }
-  if (u < n) {
+  if (slot < n) {
     for (int s = 0; s < RMIPS_KC; ++s) {
       cval[u * RMIPS_KC + s] = lv[s][t];
       cid[u * RMIPS_KC + s] = li[s][t];
     }
   }
+}
+
+// Positions of the users whose candidate list is not proven complete.
+__global__ void k_list_incomplete(const uint8_t* __restrict__ incomp, int64_t n, int32_t* __restrict__ list,
+                                  unsigned long long* __restrict__ count) {
+  const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (u < n && incomp[u]) list[atomicAdd(count, 1ull)] = (int32_t)u;
+}
+
+// --- 3'. top-KC candidates per user on tensor cores (TF32, d <= 64) ------------------
+// A CTA keeps 128 users (one per thread, TMEM lane = user) and streams every
+// 64-item tile of P' through one 128 x 64 x 64 TF32 MMA; items arrive by 1-D
+// TMA in the UMMA layout prepared by k_item_tiles.  Each thread keeps its
+// user's KC best (value, position) in shared memory and `uex`, an upper bound
+// on the exact inner product of every item it did not keep: a rejected item
+// adds its TF32 value plus ||u|| * TC_TF32_ERR * ||p|| (for a whole tile, the
+// tile's first item has the largest norm), an evicted item the same.
+constexpr int TB_THREADS = 128;
+constexpr int TB_TILE = 64;
+
+__global__ void k_item_tiles(const float* __restrict__ Ps, const float* __restrict__ pnorm, int64_t pp, int d,
+                             int64_t ntiles, float* __restrict__ Pt, float* __restrict__ cp) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < ntiles * TB_TILE * (int64_t)TC_K) {
+    const int64_t tile = e / (TB_TILE * TC_K);
+    const int r = (int)((e / TC_K) % TB_TILE), k = (int)(e % TC_K);
+    const int64_t p = tile * TB_TILE + r;
+    Pt[tile * (TB_TILE * TC_K) + tc_off(r, k) / 4] = (p < pp && k < d) ? Ps[p * d + k] : 0.f;
+  }
+  if (e < ntiles * TB_TILE) cp[e] = e < pp ? __fmul_ru(pnorm[e], TC_TF32_ERR) : 0.f;
+}
+
+__global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict__ Qs, const float* __restrict__ Pt,
+                                                        const float* __restrict__ cp, const float* __restrict__ unorm,
+                                                        int64_t n, int64_t pp, int d, float* __restrict__ cval,
+                                                        int32_t* __restrict__ cid, float* __restrict__ uex_out,
+                                                        int* __restrict__ fail) {
+  extern __shared__ __align__(1024) unsigned char tb[];
+  float* sA = reinterpret_cast<float*>(tb);                                        // 128 x 64 (32 KB)
+  float* sB = reinterpret_cast<float*>(tb + 32768);                                // 2 x (64 x 64)
+  float (*lv)[TB_THREADS] = reinterpret_cast<float (*)[TB_THREADS]>(tb + 65536);   // [KC][128]
+  int32_t (*li)[TB_THREADS] = reinterpret_cast<int32_t (*)[TB_THREADS]>(tb + 65536 + RMIPS_KC * TB_THREADS * 4);
+  __shared__ float cps[2][TB_TILE];
+  __shared__ __align__(8) uint64_t bar_b[2];
+  __shared__ __align__(8) uint64_t bar_m;
+  __shared__ uint32_t taddr_s;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t TILE_BYTES = TB_TILE * TC_K * 4;
+  if (warp == 0) {
+    tmem_alloc(&taddr_s, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar_b[0], 1);
+    mbar_init(&bar_b[1], 1);
+    mbar_init(&bar_m, 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = taddr_s;
+  const uint32_t tlane = taddr + ((uint32_t)(warp * 32) << 16);
+  const uint32_t idesc = tc_idesc_tf32(128, TB_TILE);
+  const int64_t ntiles = (pp + TB_TILE - 1) / TB_TILE;
+  uint32_t phb = 0, ph_m = 0;
+  auto load_tile = [&](int64_t t, int buf) {
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar_b[buf], TILE_BYTES);
+      bulk_g2s(reinterpret_cast<unsigned char*>(sB) + (size_t)buf * TILE_BYTES, Pt + t * (TB_TILE * TC_K),
+               TILE_BYTES, &bar_b[buf]);
+    }
+    if (tid < TB_TILE) cps[buf][tid] = cp[t * TB_TILE + tid];
+  };
+  auto issue_mma = [&](int buf) -> bool {        // thread 0 only
+    if (!mbar_wait_bounded(&bar_b[buf], (phb >> buf) & 1u)) return false;
+    tc_fence_after();
+    const uint32_t bb = smem_u32(sB) + (uint32_t)buf * TILE_BYTES;
+    for (uint32_t s = 0; s < TC_K / 8; ++s)
+      tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
+                  tc_sdesc(bb + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
+    tc_commit(&bar_m);
+    return true;
+  };
+  for (int64_t u0 = (int64_t)blockIdx.x * TB_THREADS; u0 < n && !s_fail; u0 += (int64_t)gridDim.x * TB_THREADS) {
+    const int64_t nvalid = (n - u0) < TB_THREADS ? (n - u0) : TB_THREADS;
+    const float* src = Qs + u0 * d;
+    for (int e = tid; e < TB_THREADS * (int)(TC_K / 4); e += TB_THREADS) {
+      const int r = e & (TB_THREADS - 1), k0 = (e >> 7) * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < nvalid) {
+        const float* row = src + (int64_t)r * d;
+        if (k0 + 0 < d) v.x = row[k0 + 0];
+        if (k0 + 1 < d) v.y = row[k0 + 1];
+        if (k0 + 2 < d) v.z = row[k0 + 2];
+        if (k0 + 3 < d) v.w = row[k0 + 3];
+      }
+      *reinterpret_cast<float4*>(&sA[tc_off(r, k0) / 4]) = v;
+    }
+    const float un = tid < nvalid ? unorm[u0 + tid] : 0.f;
+    for (int s = 0; s < RMIPS_KC; ++s) {
+      lv[s][tid] = -kInf;
+      li[s][tid] = -1;
+    }
+    float thr = -kInf, uex = -kInf;
+    int minslot = 0;
+    fence_proxy_async();
+    load_tile(0, 0);
+    __syncthreads();
+    if (tid == 0 && !issue_mma(0)) s_fail = 1;
+    phb ^= 1u;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const int buf = (int)(t & 1);
+      const bool has_next = t + 1 < ntiles;
+      if (has_next) load_tile(t + 1, buf ^ 1);
+      bool ok = s_fail ? false : mbar_wait_bounded(&bar_m, ph_m);
+      ph_m ^= 1u;
+      ok = __syncthreads_and(ok && !s_fail);
+      if (!ok) {
+        if (tid == 0) s_fail = 1;
+        break;
+      }
+      tc_fence_after();
+      float acc[TB_TILE];
+#pragma unroll
+      for (int c0 = 0; c0 < TB_TILE; c0 += 16) tmem_ld16(tlane + (uint32_t)c0, acc + c0);
+      tmem_ld_wait();
+      tc_fence_before();
+      __syncthreads();
+      if (has_next && tid == 0 && !issue_mma(buf ^ 1)) s_fail = 1;
+      if (has_next) phb ^= 1u << (buf ^ 1);
+      // epilogue: reject against the current KC-th value, insert the rest
+      const int live = (int)((pp - t * TB_TILE) < TB_TILE ? (pp - t * TB_TILE) : TB_TILE);
+      uint64_t cand = 0;
+      float vrej = -kInf;
+#pragma unroll
+      for (int q = 0; q < TB_TILE; ++q) {
+        const bool in = q < live && acc[q] > thr;
+        cand |= (uint64_t)in << q;
+        vrej = (q < live && !in) ? fmaxf(vrej, acc[q]) : vrej;
+      }
+      if (vrej > -kInf) uex = fmaxf(uex, __fmaf_ru(un, cps[buf][0], vrej));
+      while (cand) {
+        const int q = __ffsll((long long)cand) - 1;
+        cand &= cand - 1;
+        float v = acc[0];
+#pragma unroll
+        for (int i = 1; i < TB_TILE; ++i) v = (i == q) ? acc[i] : v;
+        if (v > thr) {
+          const int32_t old = li[minslot][tid];
+          if (old >= 0) uex = fmaxf(uex, __fmaf_ru(un, cp[old], lv[minslot][tid]));
+          lv[minslot][tid] = v;
+          li[minslot][tid] = (int32_t)(t * TB_TILE + q);
+          thr = lv[0][tid];
+          minslot = 0;
+          for (int s = 1; s < RMIPS_KC; ++s) {
+            const float w = lv[s][tid];
+            if (w < thr) { thr = w; minslot = s; }
+          }
+        } else {
+          uex = fmaxf(uex, __fmaf_ru(un, cps[buf][q], v));
+        }
+      }
+      __syncthreads();                              // cps[buf] consumed before it is reloaded
+    }
+    if (tid < nvalid) {
+      const int64_t u = u0 + tid;
+      for (int s = 0; s < RMIPS_KC; ++s) {
+        cval[u * RMIPS_KC + s] = lv[s][tid];
+        cid[u * RMIPS_KC + s] = li[s][tid];
+      }
+      uex_out[u] = uex;
+    }
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) atomicOr(fail, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, 64);
 }
 
 // Bitonic sort of one value per lane, descending across the warp.
@@ -180,13 +364,15 @@ __device__ __forceinline__ double warp_sort_desc(double x) {
 // --- 4. float64 re-dot, bounds, completeness proof (one warp per user) ------------
 __global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict__ Ps,
                            const float* __restrict__ cval, const int32_t* __restrict__ cid,
-                           const float* __restrict__ unorm, float pn0, int64_t n, int64_t pp, int d,
-                           int dp, int k_max, int full_p, float2* __restrict__ Lb,
+                           const float* __restrict__ unorm, const float* __restrict__ uex_in, float pn0, int64_t n,
+                           int64_t pp, int d, int dp, int k_max, int full_p, float2* __restrict__ Lb,
                            int32_t* __restrict__ cand, uint8_t* __restrict__ incomp,
-                           unsigned long long* __restrict__ n_incomplete) {
-  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+                           unsigned long long* __restrict__ n_incomplete, const int32_t* __restrict__ ulist,
+                           int64_t nlist) {
+  const int64_t slot = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n) return;
+  if (slot >= (ulist ? nlist : n)) return;
+  const int64_t w = ulist ? (int64_t)ulist[slot] : slot;
   const float v = cval[w * RMIPS_KC + lane];
   const int32_t id = cid[w * RMIPS_KC + lane];
   double lo = -INFINITY, hi = -INFINITY;
@@ -210,12 +396,24 @@ __global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict
   // value is within E = (dp + 2) 2^-24 ||u|| max||p|| of the exact one, so if
   // t_K + E <= t_kmax - E, no item outside the list can exceed the k_max-th
   // largest exact value among the kept ones.
+  // Every item left out has an exact inner product <= uex (an upper bound
+  // from the selection: float32 selection, the KC-th kept value plus the
+  // float32 error bound with the largest item norm; tensor-core selection,
+  // tracked per rejected / evicted item).  If uex <= the float64 lower bound
+  // of the k_max-th largest kept value, at least k_max kept items reach every
+  // excluded one, so the list holds the top-k_max.
   bool complete = pp <= RMIPS_KC;
   if (!complete) {
-    double tk = __shfl_sync(0xffffffffu, v_s, k_max - 1);
-    double tK = __shfl_sync(0xffffffffu, v_s, RMIPS_KC - 1);
-    double E = __dmul_ru(__dmul_ru((double)(dp + 2) * 0x1p-24, (double)unorm[w]), (double)pn0);
-    complete = __dadd_ru(tK, E) <= __dsub_rd(tk, E);
+    double ub;
+    if (uex_in) {
+      ub = (double)uex_in[w];
+    } else {
+      double tK = __shfl_sync(0xffffffffu, v_s, RMIPS_KC - 1);
+      double E = __dmul_ru(__dmul_ru((double)(dp + 2) * 0x1p-24, (double)unorm[w]), (double)pn0);
+      ub = __dadd_ru(tK, E);
+    }
+    const double lo_k = __shfl_sync(0xffffffffu, lo_s, k_max - 1);
+    complete = ub <= lo_k;
   }
   if (lane < k_max) {
     float flo = __double2float_rd(lo_s);
@@ -268,12 +466,24 @@ rmips_status sort_by_norm(const float* X, int64_t rows, int d, cudaStream_t st, 
 
 template <int DP>
 cudaError_t launch_topk(const float* Qs, const float* Ps, int64_t n, int64_t pp, int d, float* cval,
-                        int32_t* cid, cudaStream_t st) {
+                        int32_t* cid, cudaStream_t st, const int32_t* ulist = nullptr) {
   const size_t smem = (size_t)(DP * TS + 2 * RMIPS_KC * TOPK_THREADS) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_topk<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_topk<DP><<<grid_for(n, TOPK_THREADS), TOPK_THREADS, smem, st>>>(Qs, Ps, n, pp, d, cval, cid);
+  if (n <= 0) return cudaSuccess;
+  k_topk<DP><<<grid_for(n, TOPK_THREADS), TOPK_THREADS, smem, st>>>(Qs, Ps, n, pp, d, cval, cid, ulist);
   return cudaGetLastError();
+}
+
+// Float32 selection for the listed users only (d <= 64): repairs users whose
+// tensor-core selection could not be proven complete.
+cudaError_t launch_topk_list(const float* Qs, const float* Ps, int64_t nlist, int64_t pp, int d, float* cval,
+                             int32_t* cid, const int32_t* ulist, cudaStream_t st, int* dp) {
+  if (d <= 16) { *dp = 16; return launch_topk<16>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
+  if (d <= 32) { *dp = 32; return launch_topk<32>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
+  if (d <= 52) { *dp = 52; return launch_topk<52>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
+  *dp = 64;
+  return launch_topk<64>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist);
 }
 
 }  // namespace
@@ -292,7 +502,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   int bs = opts->block_size == 0 ? 32 : opts->block_size;
   if (opts->k_max < 1 || opts->k_max > RMIPS_KMAX_LIMIT || !(bs == 32 || bs == 64 || bs == 128 || bs == 256) ||
       opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 ||
-      (opts->flags & ~RMIPS_FLAG_BATCH_CUDA_CORES) != 0) {
+      (opts->flags & ~(RMIPS_FLAG_BATCH_CUDA_CORES | RMIPS_FLAG_BUILD_CUDA_CORES)) != 0) {
     set_error("invalid build options (k_max 1..28, block_size 32/64/128/256, precision 0..2)");
     return RMIPS_ERR_ARG;
   }
@@ -310,6 +520,8 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   auto fail = [&](rmips_status s) { rmips_free_index(idx); return s; };
   const bool q_dev = is_device_ptr(Q), p_dev = is_device_ptr(P);
   float *Qin = nullptr, *Pin = nullptr, *qn = nullptr, *pn = nullptr, *cval = nullptr;
+  float *Pt = nullptr, *cpn = nullptr, *uex = nullptr;
+  int32_t* ulist = nullptr;
   int32_t* cid = nullptr;
   int *d_bad = nullptr;
   unsigned long long* d_incomp = nullptr;
@@ -382,16 +594,57 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     // 3: candidates
     TRY(cudaMallocAsync((void**)&cval, (size_t)n * RMIPS_KC * sizeof(float), st));
     TRY(cudaMallocAsync((void**)&cid, (size_t)n * RMIPS_KC * sizeof(int32_t), st));
-    int dp;
-    if (d <= 16) { dp = 16; TRY(launch_topk<16>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
+    int dp = 0;
+    const bool tc_build = d <= (int)TC_K && idx->pp > RMIPS_KC && !(opts->flags & RMIPS_FLAG_BUILD_CUDA_CORES);
+    if (tc_build) {
+      int dev = 0, sms = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t ntiles = (idx->pp + TB_TILE - 1) / TB_TILE;
+      TRY(cudaMallocAsync((void**)&Pt, (size_t)ntiles * TB_TILE * TC_K * sizeof(float), st));
+      TRY(cudaMallocAsync((void**)&cpn, (size_t)ntiles * TB_TILE * sizeof(float), st));
+      TRY(cudaMallocAsync((void**)&uex, (size_t)n * sizeof(float), st));
+      TRY(cudaMemsetAsync(d_bad, 0, 16, st));
+      k_item_tiles<<<grid_for(ntiles * TB_TILE * TC_K, 256), 256, 0, st>>>(idx->Ps, idx->pnorm, idx->pp, d, ntiles,
+                                                                           Pt, cpn);
+      const int smem_tc = 65536 + 2 * RMIPS_KC * TB_THREADS * 4;
+      TRY(cudaFuncSetAttribute(k_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc));
+      const int64_t utiles = (n + TB_THREADS - 1) / TB_THREADS;
+      const int grid = (int)(utiles < 2 * sms ? utiles : 2 * sms);
+      k_topk_tc<<<grid, TB_THREADS, smem_tc, st>>>(idx->Qs, Pt, cpn, idx->unorm, n, idx->pp, d, cval, cid, uex, d_bad);
+      TRY(cudaGetLastError());
+      int h_fail = 0;
+      TRY(cudaMemcpyAsync(&h_fail, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TRY(cudaStreamSynchronize(st));
+      if (h_fail) { set_error("tensor-core selection: a device wait timed out"); s = RMIPS_ERR_TIMEOUT; goto cleanup; }
+    }
+    else if (d <= 16) { dp = 16; TRY(launch_topk<16>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
     else if (d <= 32) { dp = 32; TRY(launch_topk<32>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
     else if (d <= 52) { dp = 52; TRY(launch_topk<52>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
     else if (d <= 64) { dp = 64; TRY(launch_topk<64>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
     else { dp = 128; TRY(launch_topk<128>(idx->Qs, idx->Ps, n, idx->pp, d, cval, cid, st)); }
     // 4: bounds
-    k_finalize<<<grid_for(n * 32, 256), 256, 0, st>>>(idx->Qs, idx->Ps, cval, cid, idx->unorm, idx->pn0, n,
-                                                      idx->pp, d, dp, idx->k_max, idx->full_p, idx->Lb,
-                                                      idx->cand, idx->incomp, d_incomp);
+    k_finalize<<<grid_for(n * 32, 256), 256, 0, st>>>(idx->Qs, idx->Ps, cval, cid, idx->unorm, uex, idx->pn0,
+                                                      n, idx->pp, d, dp, idx->k_max, idx->full_p, idx->Lb,
+                                                      idx->cand, idx->incomp, d_incomp, nullptr, 0);
+    if (tc_build && idx->full_p) {
+      // users the TF32 selection could not prove complete: redo them in float32
+      unsigned long long h_inc = 0;
+      TRY(cudaMemcpyAsync(&h_inc, d_incomp, sizeof(h_inc), cudaMemcpyDeviceToHost, st));
+      TRY(cudaStreamSynchronize(st));
+      if (h_inc > 0) {
+        TRY(cudaMallocAsync((void**)&ulist, (size_t)h_inc * sizeof(int32_t), st));
+        TRY(cudaMemsetAsync(d_incomp, 0, 16, st));
+        k_list_incomplete<<<grid_for(n, 256), 256, 0, st>>>(idx->incomp, n, ulist, d_incomp);
+        TRY(cudaMemsetAsync(d_incomp, 0, 16, st));
+        int dp2 = 64;
+        TRY(launch_topk_list(idx->Qs, idx->Ps, (int64_t)h_inc, idx->pp, d, cval, cid, ulist, st, &dp2));
+        k_finalize<<<grid_for((int64_t)h_inc * 32, 256), 256, 0, st>>>(
+            idx->Qs, idx->Ps, cval, cid, idx->unorm, nullptr, idx->pn0, n, idx->pp, d, dp2, idx->k_max,
+            idx->full_p, idx->Lb, idx->cand, idx->incomp, d_incomp, ulist, (int64_t)h_inc);
+        TRY(cudaGetLastError());
+      }
+    }
     // 5: blocks
     k_blocks<<<grid_for(idx->nb * idx->k_max, 256), 256, 0, st>>>(idx->Lb, idx->unorm, n, bs, idx->nb,
                                                                    idx->k_max, idx->LB, idx->hdr);
@@ -407,6 +660,10 @@ cleanup:
   if (qn) cudaFreeAsync(qn, st);
   if (pn) cudaFreeAsync(pn, st);
   if (cval) cudaFreeAsync(cval, st);
+  if (Pt) cudaFreeAsync(Pt, st);
+  if (cpn) cudaFreeAsync(cpn, st);
+  if (uex) cudaFreeAsync(uex, st);
+  if (ulist) cudaFreeAsync(ulist, st);
   if (cid) cudaFreeAsync(cid, st);
   if (d_bad) cudaFreeAsync(d_bad, st);
   if (d_incomp) cudaFreeAsync(d_incomp, st);

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "rmips_internal.cuh"
+#include "tc_common.cuh"
 
 namespace rmips {
 namespace {
@@ -107,13 +108,18 @@ __global__ void k_qprep(Common c, int64_t nq, int precision) {
   }
 }
 
+__device__ bool verify_scan(const float* __restrict__ u, float un, const Common& c, const float* sq, int k,
+                            float qeps);
+__device__ bool recheck_candidates(const float* __restrict__ u, const float* q, const int32_t* __restrict__ crow,
+                                   const float* __restrict__ Ps, int d, int k, float cg32, long long* ctr);
+
 // --- filter ------------------------------------------------------------------------
 // Lemmas 1-3 for one query over this CTA's share of 32-user chunks.  Warp w
 // of the grid owns chunks w, w + W, w + 2W, ... (W = warps in the grid); it
 // tests Lemma 3 for 32 of its chunks at once (one lane each), then streams
 // the surviving chunks' rows into shared memory with 1-D TMA bulk copies,
 // double-buffered, and tests every user.  Returns false if a TMA wait gave up.
-template <class T, bool FULLP>
+template <class T, bool FULLP, bool INLINE = false>
 __device__ bool filter_chunks(const Common& c, const float* sq, int k, float qn, float qeps, uint64_t* bars,
                               unsigned char* bufs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,8 +211,23 @@ __device__ bool filter_chunks(const Common& c, const float* sq, int k, float qn,
         todo = !yes;
       }
     }
-    const uint32_t by = __ballot_sync(FULL, yes), bt = __ballot_sync(FULL, todo);
+    uint32_t by = __ballot_sync(FULL, yes), bt = __ballot_sync(FULL, todo);
     const uint32_t lt = (1u << lane) - 1u;
+    if (INLINE && bt) {
+      // exact recheck right here, one user at a time, the warp's lanes on its candidates
+      todosum += __popc(bt);
+      for (uint32_t m = bt; m; m &= m - 1) {
+        const int l = __ffs(m) - 1;
+        const int64_t p = cur * 32 + l;
+        const float* u = c.Qs + p * c.d;
+        const bool ok_yes = !c.incomp[p]
+                                ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.Ps, c.d, k, c.cg32, c.ctr)
+                                : verify_scan(u, c.unorm[p], c, sq, k, qeps);
+        if (ok_yes && lane == l) yes = true;
+      }
+      by = __ballot_sync(FULL, yes);
+      bt = 0;
+    }
     if (by) {
       long long base = 0;
       if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
@@ -220,7 +241,7 @@ __device__ bool filter_chunks(const Common& c, const float* sq, int k, float qn,
       if (todo) c.todo[base + __popc(bt & lt)] = (int32_t)pos;
     }
     tested += __popc(__ballot_sync(FULL, valid));
-    yesfast += __popc(by);
+    yesfast += INLINE ? 0 : __popc(by);
     todosum += __popc(bt);
     cur = nxt;
     s ^= 1;
@@ -550,7 +571,7 @@ __global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const 
   __syncthreads();
   if (tid == 0) s_fin = query_bounds(sq, d, precision, &s_qn, &s_eps) ? 1 : 0;
   __syncthreads();
-  if (s_fin) filter_chunks<T, true>(c, sq, k, s_qn, s_eps, bars, bufs);
+  if (s_fin) filter_chunks<T, true, true>(c, sq, k, s_qn, s_eps, bars, bufs);
   __threadfence();
   __syncthreads();
   if (tid == 0) s_last = atomicAdd((unsigned long long*)&c.ctr[C_DONE], 1ull) == (unsigned long long)(gridDim.x - 1);
@@ -828,6 +849,15 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
   e.out = out_dev ? (long long*)out_ids : ws->h_out;
   e.capacity = out_dev ? capacity : (capacity < ws->cap_hout ? capacity : ws->cap_hout);
   e.offs = nullptr;
+  const bool prof = idx->prof_on != 0;
+  if (prof) {
+    while (ws->ev.size() < 2) {
+      cudaEvent_t ev;
+      RMIPS_TRY_CUDA(cudaEventCreate(&ev));
+      ws->ev.push_back(ev);
+    }
+    RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[0], st));
+  }
   cudaError_t err;
   switch (idx->precision) {
     case RMIPS_BF16: err = launch_query1<__nv_bfloat16>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
@@ -835,8 +865,23 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
     default: err = launch_query1<float>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
   }
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  if (prof) RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[1], st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   const long long status = ws->h_res[RES_STATUS];
+  if (prof) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]);
+    const long long* h = ws->h_res + RES_CTR;
+    const int es = idx->precision == RMIPS_FP32 ? 4 : 2;
+    std::lock_guard<std::mutex> lk(idx->mu);
+    idx->prof.filter_launches += 1;
+    idx->prof.filter_ms += ms;
+    idx->prof.filter_alg_bytes += 8.0 * idx->nb + ((double)idx->d * es + 8.0) * h[C_TESTED] +
+                                  4.0 * (double)(h[C_YESFAST] + h[C_TODOSUM]);
+    idx->prof.users_tested += h[C_TESTED];
+    idx->prof.blocks_pruned += h[C_PRUNED] * 32 / idx->bs;
+    idx->prof.blocks_total += idx->nb;
+  }
   const long long count = ws->h_res[RES_COUNT];
   *out_count = count;
   {
@@ -920,79 +965,6 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
 }
 
 
-
-// ---------------------------------------------------------------------------
-// tcgen05 (5th-generation tensor core) helpers: TMEM allocation, UMMA shared
-// memory descriptors, MMA issue/commit and TMEM loads.
-//
-// Operand tiles use the K-major, non-swizzled canonical layout: the tile is cut
-// into core matrices of 8 rows x 16 bytes (8 x 4 TF32 values); row r of a core
-// matrix sits 16*r bytes from its start; core matrices adjacent along K are
-// TC_LBO bytes apart and 8-row groups are TC_SBO bytes apart.
-// ---------------------------------------------------------------------------
-constexpr uint32_t TC_K = 64;                        // padded inner dimension (d <= 64)
-constexpr uint32_t TC_LBO = 128;                     // next 16-byte K chunk
-constexpr uint32_t TC_SBO = (TC_K / 4) * 128;        // next 8-row group (2048 bytes)
-
-__host__ __device__ __forceinline__ uint32_t tc_off(uint32_t row, uint32_t k) {
-  return (row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4;   // bytes
-}
-
-__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;                            // descriptor version of sm_100 family
-  return d;                                          // base offset 0, no swizzle
-}
-
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
-__host__ __device__ constexpr uint32_t tc_idesc_tf32(uint32_t M, uint32_t N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 16 consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // One 128 x 64 x 64 TF32 tile through the layout, descriptors, MMA and TMEM
 // loads used by the batched filter (test hook).  A [128][64], B [64][64]
@@ -1638,7 +1610,7 @@ constexpr int TCU = 128;                       // users per tile (MMA M)
 constexpr int TCQ = MQ_TQ;                     // queries per tile (MMA N)
 constexpr int TC_THREADS = 256;                // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4) ...
 constexpr int TC_HALF = TCQ / 2;               // ... and split the 64 query columns in halves
-constexpr float TC_ERR = 0.00198f;             // >= 2^-9 + 2^-20 + 65 * 2^-22 * (1 + 2^-9)
+constexpr float TC_ERR = TC_TF32_ERR;
 constexpr uint32_t TC_TILE_BYTES = TCQ * TC_K * 4;   // one query tile (16 KB)
 constexpr uint32_t TC_A_BYTES = TCU * TC_K * 4;      // one user tile (32 KB)
 

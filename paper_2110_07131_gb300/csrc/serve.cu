@@ -414,6 +414,63 @@ extern "C" rmips_status rmips_server_wait(rmips_server* S, int64_t ticket, int64
   return st;
 }
 
+extern "C" rmips_status rmips_server_wait_many(rmips_server* S, const int64_t* tickets, int64_t nt,
+                                               int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
+                                               double* latency_ms, int32_t timeout_ms) {
+  if (!S || nt < 0 || (nt > 0 && !tickets) || !out_offsets || capacity < 0 || (capacity > 0 && !out_ids)) {
+    set_error("null argument");
+    return RMIPS_ERR_ARG;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  std::vector<Request*> rs(nt);
+  for (int64_t i = 0; i < nt; ++i) {
+    auto it = S->reqs.find(tickets[i]);
+    if (it == S->reqs.end()) { set_error("unknown ticket"); return RMIPS_ERR_ARG; }
+    rs[i] = it->second;
+  }
+  auto all_done = [&] {
+    for (Request* r : rs)
+      if (r->state != 2) return false;
+    return true;
+  };
+  if (timeout_ms < 0) S->cv_done.wait(lk, all_done);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), all_done)) {
+    set_error("requests not finished yet");
+    return RMIPS_ERR_TIMEOUT;
+  }
+  out_offsets[0] = 0;
+  rmips_status first = RMIPS_OK;
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t c = rs[i]->st == RMIPS_OK ? (int64_t)rs[i]->ids.size() : 0;
+    out_offsets[i + 1] = out_offsets[i] + c;
+    if (first == RMIPS_OK && rs[i]->st != RMIPS_OK) first = rs[i]->st;
+    if (latency_ms) latency_ms[i] = rs[i]->ms;
+  }
+  if (out_offsets[nt] > capacity) {
+    set_error("output capacity too small");
+    return RMIPS_ERR_CAPACITY;                   // tickets kept: wait again with more room
+  }
+  const bool dev = out_offsets[nt] > 0 && is_device_ptr(out_ids);
+  for (int64_t i = 0; i < nt; ++i) {
+    Request* r = rs[i];
+    if (r->st == RMIPS_OK && !r->ids.empty()) {
+      if (dev) {
+        cudaError_t e = cudaMemcpy(out_ids + out_offsets[i], r->ids.data(), r->ids.size() * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return RMIPS_ERR_CUDA; }
+      } else {
+        memcpy(out_ids + out_offsets[i], r->ids.data(), r->ids.size() * sizeof(int64_t));
+      }
+    }
+  }
+  for (int64_t i = 0; i < nt; ++i) {
+    S->reqs.erase(tickets[i]);
+    delete rs[i];
+  }
+  if (first != RMIPS_OK) set_error("a request of the set failed");
+  return first;
+}
+
 extern "C" rmips_status rmips_server_get_stats(rmips_server* S, rmips_server_stats* out) {
   if (!S || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
   std::vector<double> v;

@@ -1,0 +1,89 @@
+// tcgen05 helpers shared by the batched filter (query.cu) and the index build
+// (build_index.cu).  Device code only; include after rmips_internal.cuh.
+#pragma once
+
+#include "rmips_internal.cuh"
+
+namespace rmips {
+
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) helpers: TMEM allocation, UMMA shared
+// memory descriptors, MMA issue/commit and TMEM loads.
+//
+// Operand tiles use the K-major, non-swizzled canonical layout: the tile is cut
+// into core matrices of 8 rows x 16 bytes (8 x 4 TF32 values); row r of a core
+// matrix sits 16*r bytes from its start; core matrices adjacent along K are
+// TC_LBO bytes apart and 8-row groups are TC_SBO bytes apart.
+// ---------------------------------------------------------------------------
+constexpr uint32_t TC_K = 64;                        // padded inner dimension (d <= 64)
+// Relative error bound of a TF32 tensor-core inner product of float32 data,
+// as a multiple of ||a|| ||b||: each operand is within 2^-10 of its float32
+// value (10 fraction bits, any rounding), products of TF32 values are exact in
+// float32, and the float32 accumulation over K = 64 terms (8 chained MMAs) is
+// charged 65 * 2^-22 of sum |a_i b_i| <= ||a|| ||b||.
+constexpr float TC_TF32_ERR = 0.00198f;              // >= 2^-9 + 2^-20 + 65 * 2^-22 * (1 + 2^-9)
+constexpr uint32_t TC_LBO = 128;                     // next 16-byte K chunk
+constexpr uint32_t TC_SBO = (TC_K / 4) * 128;        // next 8-row group (2048 bytes)
+
+__host__ __device__ __forceinline__ uint32_t tc_off(uint32_t row, uint32_t k) {
+  return (row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4;   // bytes
+}
+
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                            // descriptor version of sm_100 family
+  return d;                                          // base offset 0, no swizzle
+}
+
+// Instruction descriptor: D = F32, A = B = TF32, both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(uint32_t M, uint32_t N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+
+}  // namespace rmips

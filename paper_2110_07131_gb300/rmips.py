@@ -33,7 +33,8 @@ EXPORTED_SYMBOLS = [
     "rmips_last_query_stats", "rmips_index_export", "rmips_free_index", "rmips_status_string",
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
-    "rmips_server_submit_many", "rmips_server_wait", "rmips_server_get_stats", "rmips_server_destroy",
+    "rmips_server_submit_many", "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
+    "rmips_server_destroy",
 ]
 
 
@@ -125,13 +126,14 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_server_submit_many.argtypes = [VP, P, I64, P, C.POINTER(Segment), P]
         lib.rmips_server_wait.argtypes = [VP, I64, P, I64, C.POINTER(I64), C.POINTER(C.c_double), I32]
         lib.rmips_server_get_stats.argtypes = [VP, C.POINTER(ServerStats)]
+        lib.rmips_server_wait_many.argtypes = [VP, P, I64, P, I64, P, P, I32]
         lib.rmips_server_destroy.argtypes = [VP]
         lib.rmips_server_destroy.restype = None
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
                      "rmips_server_create", "rmips_server_submit", "rmips_server_submit_many",
-                     "rmips_server_wait", "rmips_server_get_stats"):
+                     "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -221,10 +223,12 @@ class Index:
 
 
 def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
-                      precision="fp32", batch_tensor_cores: bool = True, stream=None) -> Index:
+                      precision="fp32", batch_tensor_cores: bool = True, build_tensor_cores: bool = True,
+                      stream=None) -> Index:
     """Build the index of Algorithm 1 from users Q [n, d] and items P [m, d].
 
-    ``batch_tensor_cores=False`` keeps the batched filter on CUDA cores."""
+    ``batch_tensor_cores=False`` keeps the batched filter on CUDA cores;
+    ``build_tensor_cores=False`` selects candidates on CUDA cores."""
     load_library()
     qp, qk = _ptr_f32(Q)
     pp, pk = _ptr_f32(P)
@@ -233,7 +237,7 @@ def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
     if int(pk.shape[1]) != d:
         raise RmipsError(1, "Q and P differ in dimension")
     opts = BuildOpts(int(k_max), int(block_size), int(p_prime), _PREC[precision],
-                     0 if batch_tensor_cores else 1)
+                     (0 if batch_tensor_cores else 1) | (0 if build_tensor_cores else 2))
     out = C.c_void_p()
     _check(_lib.rmips_build_index(qp, n, pp, m, d, C.byref(opts), _stream(stream), C.byref(out)))
     return Index(out.value, n, m, d, int(k_max))
@@ -418,6 +422,23 @@ class Server:
         _check(_lib.rmips_server_wait(self.handle, int(ticket), buf.ctypes.data, cap, C.byref(cnt),
                                       C.byref(lat), int(timeout_ms)))
         return buf[:cnt.value], lat.value
+
+    def wait_many(self, tickets, timeout_ms: int = -1, capacity: int | None = None):
+        """Results of many requests: ``(ids, offsets, latencies_ms)`` in CSR form."""
+        t = np.ascontiguousarray(tickets, np.int64)
+        nt = t.shape[0]
+        cap = max(1024, nt * 64) if capacity is None else int(capacity)
+        offs = np.zeros(nt + 1, np.int64)
+        lat = np.zeros(max(nt, 1), np.float64)
+        while True:
+            buf = np.empty(max(cap, 1), np.int64)
+            st = _lib.rmips_server_wait_many(self.handle, t.ctypes.data, nt, buf.ctypes.data, cap,
+                                             offs.ctypes.data, lat.ctypes.data, int(timeout_ms))
+            if st == 5 and capacity is None:
+                cap = int(offs[-1])
+                continue
+            _check(st)
+            return buf[:offs[-1]], offs, lat[:nt]
 
     def stats(self) -> dict:
         st = ServerStats()

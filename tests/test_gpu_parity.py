@@ -40,7 +40,8 @@ def test_tiny_config_parity(tiny, precision, p_prime):
 def test_tiny_config_parity_cuda_core_batches(tiny):
     Q, P, allq, counts = tiny
     for p_prime in (0, 100):
-        index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime, batch_tensor_cores=False)
+        index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime, batch_tensor_cores=False,
+                                        build_tensor_cores=False)
         _check_all(index, allq, counts, (1, 10, 25))
 
 
@@ -74,10 +75,11 @@ def test_single_query_api_matches(tiny, p_prime):
             assert np.array_equal(ids[offs[0]:offs[1]], got)
 
 
-def test_index_arrays_match_oracle(tiny):
+@pytest.mark.parametrize("build_tc", [True, False])
+def test_index_arrays_match_oracle(tiny, build_tc):
     Q, P, _, _ = tiny
     k_max = 25
-    index = rmips.rmips_build_index(Q, P, k_max=k_max)
+    index = rmips.rmips_build_index(Q, P, k_max=k_max, build_tensor_cores=build_tc)
     permQ = rmips.rmips_index_export(index, "permQ")
     permP = rmips.rmips_index_export(index, "permP")
     assert np.array_equal(permQ, O.norm_order(Q))

@@ -72,9 +72,13 @@ def test_batched_requests_match_oracle(setup):
     srv = rmips.Server(index, max_batch=128, max_wait_us=1000, streams=2)
     tickets = srv.submit_many(qs, ks.astype(np.int32))
     counts = O.counts_greater_multi(Q, P, qs)
-    for j, t in enumerate(tickets):
+    for j, t in enumerate(tickets[:100]):
         ids, _ = srv.wait(int(t))
         assert np.array_equal(ids, np.nonzero(counts[j] < ks[j])[0])
+    ids, offs, lat = srv.wait_many(tickets[100:])
+    for j in range(100, 200):
+        assert np.array_equal(ids[offs[j - 100]:offs[j - 99]], np.nonzero(counts[j] < ks[j])[0])
+    assert (lat >= 0).all()
     srv.close()
 
 
