@@ -102,7 +102,13 @@ constexpr int TOPK_THREADS = 128;
 template <int DP>
 __global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__ Qs, const float* __restrict__ Ps,
                                                        int64_t n, int64_t pp, int d, float* __restrict__ cval,
-                                                       int32_t* __restrict__ cid, const int32_t* __restrict__ ulist) {
+                                                       int32_t* __restrict__ cid, const int32_t* __restrict__ ulist,
+                                                       int nseg) {
+  // Item range of this CTA: segment blockIdx.y of nseg equal parts of P'.
+  // The output row is the user (nseg = 1, no list) or (slot * nseg + segment).
+  const int64_t segsize = (pp + nseg - 1) / nseg;
+  const int64_t pa = (int64_t)blockIdx.y * segsize;
+  const int64_t pb = pa + segsize < pp ? pa + segsize : pp;
   extern __shared__ __align__(16) float topk_smem[];
   float* tile = topk_smem;                                                   // [DP][TS]
   float (*lv)[TOPK_THREADS] = reinterpret_cast<float (*)[TOPK_THREADS]>(topk_smem + DP * TS);
@@ -121,15 +127,15 @@ __global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__
   }
   float thr = -kInf;
   int minslot = 0;
-  for (int64_t p0 = 0; p0 < pp; p0 += TP) {
+  for (int64_t p0 = pa; p0 < pb; p0 += TP) {
     __syncthreads();
     for (int e = t; e < DP * TP; e += TOPK_THREADS) {
       int i = e / TP, j = e % TP;
       int64_t p = p0 + j;
-      tile[i * TS + j] = (i < d && p < pp) ? Ps[p * d + i] : 0.f;
+      tile[i * TS + j] = (i < d && p < pb) ? Ps[p * d + i] : 0.f;
     }
     __syncthreads();
-    const int jmax = (int)((pp - p0) < TP ? (pp - p0) : TP);
+    const int jmax = (int)((pb - p0) < TP ? (pb - p0) : TP);
     for (int j = 0; j < jmax; j += 4) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
@@ -157,11 +163,66 @@ __global__ void __launch_bounds__(TOPK_THREADS) k_topk(const float* __restrict__
     }
   }
   if (slot < n) {
+    const int64_t row = ulist ? slot * nseg + blockIdx.y : u;
     for (int s = 0; s < RMIPS_KC; ++s) {
-      cval[u * RMIPS_KC + s] = lv[s][t];
-      cid[u * RMIPS_KC + s] = li[s][t];
+      cval[row * RMIPS_KC + s] = lv[s][t];
+      cid[row * RMIPS_KC + s] = li[s][t];
     }
   }
+}
+
+// Descending sort of one 64-bit key per lane across a warp (bitonic network).
+__device__ __forceinline__ unsigned long long warp_sort_desc_u64(unsigned long long x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool keep_max = (((lane & j) == 0) == ((lane & k) == 0));
+      x = keep_max ? (x > y ? x : y) : (x < y ? x : y);
+    }
+  }
+  return x;
+}
+
+// (value, item) as one key ordered by value: larger float -> larger key.
+__device__ __forceinline__ unsigned long long vkey(float v, int32_t id) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t k = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return ((unsigned long long)k << 32) | (uint32_t)(id + 1);
+}
+__device__ __forceinline__ float vkey_value(unsigned long long key) {
+  const uint32_t k = (uint32_t)(key >> 32);
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Merges the nseg per-segment top-KC lists of each listed user into its
+// top-KC (one warp per user): each list is sorted, reversed and combined
+// with the running top-KC by element-wise maximum, which leaves a bitonic
+// sequence holding the KC largest of both; a half-cleaner network sorts it.
+__global__ void k_merge_segments(const float* __restrict__ sval, const int32_t* __restrict__ sid,
+                                 const int32_t* __restrict__ ulist, int64_t nlist, int nseg,
+                                 float* __restrict__ cval, int32_t* __restrict__ cid) {
+  const int64_t slot = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slot >= nlist) return;
+  unsigned long long cur = 0;
+  for (int g = 0; g < nseg; ++g) {
+    const int64_t r = (slot * nseg + g) * RMIPS_KC + lane;
+    unsigned long long x = warp_sort_desc_u64(vkey(sval[r], sid[r]));
+    if (g == 0) { cur = x; continue; }
+    x = __shfl_sync(0xffffffffu, x, 31 - lane);              // ascending
+    cur = cur > x ? cur : x;                                   // bitonic, the KC largest of both
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, cur, j);
+      cur = ((lane & j) == 0) ? (cur > y ? cur : y) : (cur < y ? cur : y);
+    }
+  }
+  const int64_t u = ulist[slot];
+  cval[u * RMIPS_KC + lane] = vkey_value(cur);
+  cid[u * RMIPS_KC + lane] = (int32_t)(cur & 0xffffffffull) - 1;
 }
 
 // Positions of the users whose candidate list is not proven complete.
@@ -298,6 +359,23 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
       if (has_next) phb ^= 1u << (buf ^ 1);
       // epilogue: reject against the current KC-th value, insert the rest
       const int live = (int)((pp - t * TB_TILE) < TB_TILE ? (pp - t * TB_TILE) : TB_TILE);
+      bool done_fast = false;
+      if (live == TB_TILE) {                       // fast path: the tile's maximum decides alone
+        float m0 = acc[0], m1 = acc[1], m2 = acc[2], m3 = acc[3];
+#pragma unroll
+        for (int q = 4; q < TB_TILE; q += 4) {
+          m0 = fmaxf(m0, acc[q]);
+          m1 = fmaxf(m1, acc[q + 1]);
+          m2 = fmaxf(m2, acc[q + 2]);
+          m3 = fmaxf(m3, acc[q + 3]);
+        }
+        const float vmax = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+        if (!(vmax > thr)) {                       // every item of the tile is rejected
+          uex = fmaxf(uex, __fmaf_ru(un, cps[buf][0], vmax));
+          done_fast = true;
+        }
+      }
+      if (!done_fast) {
       uint64_t cand = 0;
       float vrej = -kInf;
 #pragma unroll
@@ -327,6 +405,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
         } else {
           uex = fmaxf(uex, __fmaf_ru(un, cps[buf][q], v));
         }
+      }
       }
       __syncthreads();                              // cps[buf] consumed before it is reloaded
     }
@@ -466,24 +545,25 @@ rmips_status sort_by_norm(const float* X, int64_t rows, int d, cudaStream_t st, 
 
 template <int DP>
 cudaError_t launch_topk(const float* Qs, const float* Ps, int64_t n, int64_t pp, int d, float* cval,
-                        int32_t* cid, cudaStream_t st, const int32_t* ulist = nullptr) {
+                        int32_t* cid, cudaStream_t st, const int32_t* ulist = nullptr, int nseg = 1) {
   const size_t smem = (size_t)(DP * TS + 2 * RMIPS_KC * TOPK_THREADS) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(k_topk<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (n <= 0) return cudaSuccess;
-  k_topk<DP><<<grid_for(n, TOPK_THREADS), TOPK_THREADS, smem, st>>>(Qs, Ps, n, pp, d, cval, cid, ulist);
+  dim3 grid(grid_for(n, TOPK_THREADS), nseg);
+  k_topk<DP><<<grid, TOPK_THREADS, smem, st>>>(Qs, Ps, n, pp, d, cval, cid, ulist, nseg);
   return cudaGetLastError();
 }
 
 // Float32 selection for the listed users only (d <= 64): repairs users whose
 // tensor-core selection could not be proven complete.
-cudaError_t launch_topk_list(const float* Qs, const float* Ps, int64_t nlist, int64_t pp, int d, float* cval,
-                             int32_t* cid, const int32_t* ulist, cudaStream_t st, int* dp) {
-  if (d <= 16) { *dp = 16; return launch_topk<16>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
-  if (d <= 32) { *dp = 32; return launch_topk<32>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
-  if (d <= 52) { *dp = 52; return launch_topk<52>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist); }
+cudaError_t launch_topk_list(const float* Qs, const float* Ps, int64_t nlist, int64_t pp, int d, float* sval,
+                             int32_t* sid, const int32_t* ulist, int nseg, cudaStream_t st, int* dp) {
+  if (d <= 16) { *dp = 16; return launch_topk<16>(Qs, Ps, nlist, pp, d, sval, sid, st, ulist, nseg); }
+  if (d <= 32) { *dp = 32; return launch_topk<32>(Qs, Ps, nlist, pp, d, sval, sid, st, ulist, nseg); }
+  if (d <= 52) { *dp = 52; return launch_topk<52>(Qs, Ps, nlist, pp, d, sval, sid, st, ulist, nseg); }
   *dp = 64;
-  return launch_topk<64>(Qs, Ps, nlist, pp, d, cval, cid, st, ulist);
+  return launch_topk<64>(Qs, Ps, nlist, pp, d, sval, sid, st, ulist, nseg);
 }
 
 }  // namespace
@@ -522,6 +602,8 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   float *Qin = nullptr, *Pin = nullptr, *qn = nullptr, *pn = nullptr, *cval = nullptr;
   float *Pt = nullptr, *cpn = nullptr, *uex = nullptr;
   int32_t* ulist = nullptr;
+  float* sval = nullptr;
+  int32_t* sid = nullptr;
   int32_t* cid = nullptr;
   int *d_bad = nullptr;
   unsigned long long* d_incomp = nullptr;
@@ -637,8 +719,22 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
         TRY(cudaMemsetAsync(d_incomp, 0, 16, st));
         k_list_incomplete<<<grid_for(n, 256), 256, 0, st>>>(idx->incomp, n, ulist, d_incomp);
         TRY(cudaMemsetAsync(d_incomp, 0, 16, st));
+        // split P' into segments so that even a handful of users fill the GPU, then merge
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t rows = ((int64_t)h_inc + TOPK_THREADS - 1) / TOPK_THREADS;
+        int64_t nseg = (4 * (int64_t)sms + rows - 1) / rows;
+        const int64_t seg_cap = idx->pp / (4 * TP) > 1 ? idx->pp / (4 * TP) : 1;
+        if (nseg > seg_cap) nseg = seg_cap;
+        if ((int64_t)h_inc * nseg * RMIPS_KC > (64ll << 20)) nseg = (64ll << 20) / ((int64_t)h_inc * RMIPS_KC);
+        if (nseg < 1) nseg = 1;
+        TRY(cudaMallocAsync((void**)&sval, (size_t)h_inc * nseg * RMIPS_KC * sizeof(float), st));
+        TRY(cudaMallocAsync((void**)&sid, (size_t)h_inc * nseg * RMIPS_KC * sizeof(int32_t), st));
         int dp2 = 64;
-        TRY(launch_topk_list(idx->Qs, idx->Ps, (int64_t)h_inc, idx->pp, d, cval, cid, ulist, st, &dp2));
+        TRY(launch_topk_list(idx->Qs, idx->Ps, (int64_t)h_inc, idx->pp, d, sval, sid, ulist, (int)nseg, st, &dp2));
+        k_merge_segments<<<grid_for((int64_t)h_inc * 32, 256), 256, 0, st>>>(sval, sid, ulist, (int64_t)h_inc,
+                                                                              (int)nseg, cval, cid);
         k_finalize<<<grid_for((int64_t)h_inc * 32, 256), 256, 0, st>>>(
             idx->Qs, idx->Ps, cval, cid, idx->unorm, nullptr, idx->pn0, n, idx->pp, d, dp2, idx->k_max,
             idx->full_p, idx->Lb, idx->cand, idx->incomp, d_incomp, ulist, (int64_t)h_inc);
@@ -664,6 +760,8 @@ cleanup:
   if (cpn) cudaFreeAsync(cpn, st);
   if (uex) cudaFreeAsync(uex, st);
   if (ulist) cudaFreeAsync(ulist, st);
+  if (sval) cudaFreeAsync(sval, st);
+  if (sid) cudaFreeAsync(sid, st);
   if (cid) cudaFreeAsync(cid, st);
   if (d_bad) cudaFreeAsync(d_bad, st);
   if (d_incomp) cudaFreeAsync(d_incomp, st);

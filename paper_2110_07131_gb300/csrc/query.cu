@@ -1806,9 +1806,24 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
       const float2 c0 = cq_s[buf][0];
       const float thr = __fsub_rd(L.x, __fmaf_ru(un, c0.x, c0.y));
       uint32_t hit = 0;
+      if (live == TC_HALF) {                       // fast path: the row maximum decides alone
+        float m0 = acc[0], m1 = acc[1], m2 = acc[2], m3 = acc[3];
 #pragma unroll
-      for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
-      hit &= live >= TC_HALF ? 0xffffffffu : ((1u << live) - 1u);
+        for (int q = 4; q < TC_HALF; q += 4) {
+          m0 = fmaxf(m0, acc[q]);
+          m1 = fmaxf(m1, acc[q + 1]);
+          m2 = fmaxf(m2, acc[q + 2]);
+          m3 = fmaxf(m3, acc[q + 3]);
+        }
+        if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= thr) {
+#pragma unroll
+          for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
+        }
+      } else if (live > 0) {
+#pragma unroll
+        for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
+        hit &= (1u << live) - 1u;
+      }
       uint32_t ym = 0, tm = 0;
       if (hit) {
         const int k = b.grp[g_cur].x;
