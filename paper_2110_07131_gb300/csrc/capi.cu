@@ -49,6 +49,9 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->seg);
   cudaFree(ws->bqt);
   cudaFree(ws->keys);
+  cudaFree(ws->runs);
+  cudaFree(ws->gfirst);
+  cudaFree(ws->gslot0);
   cudaFree(ws->dseglo);
   cudaFree(ws->dseghi);
   cudaFree(ws->hist);

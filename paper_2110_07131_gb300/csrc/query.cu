@@ -332,26 +332,21 @@ __device__ bool recheck_candidates(const float* __restrict__ u, const float* q, 
                                    const float* __restrict__ Ps, int d, int k, float cg32, long long* ctr) {
   const int lane = threadIdx.x & 31;
   float g32 = 0.f, a32 = 0.f;
-  double g64 = 0.0, a64 = 0.0;
   for (int i = lane; i < d; i += 32) {
     const float x = u[i], y = q[i];
     g32 = fmaf(x, y, g32);
     a32 = fmaf(fabsf(x), fabsf(y), a32);
-    g64 = fma((double)x, (double)y, g64);
-    a64 = fma(fabs((double)x), fabs((double)y), a64);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     g32 += __shfl_xor_sync(FULL, g32, o);
     a32 += __shfl_xor_sync(FULL, a32, o);
-    g64 += __shfl_xor_sync(FULL, g64, o);
-    a64 += __shfl_xor_sync(FULL, a64, o);
   }
   const float tiny = (d + 2) * 0x1p-148f;
   const float eg = __fmaf_ru(a32, cg32, tiny);
   const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
   const int32_t it = crow[lane];
-  bool gt = false;
+  bool gt = false, hard = false;
   if (it >= 0) {
     const float* p = Ps + (int64_t)it * d;
     float sp = 0.f, B = 0.f;
@@ -365,19 +360,35 @@ __device__ bool recheck_candidates(const float* __restrict__ u, const float* q, 
     } else if (!(__fadd_ru(sp, ep) < gl)) {
       bool same = true;
       for (int i = 0; i < d; ++i) same = same && (__float_as_uint(p[i]) == __float_as_uint(q[i]));
-      if (!same) {
-        double s64 = 0.0, b64 = 0.0;
-        for (int i = 0; i < d; ++i) {
-          s64 = fma((double)u[i], (double)p[i], s64);
-          b64 = fma(fabs((double)u[i]), fabs((double)p[i]), b64);
-        }
-        const double diff = s64 - g64;
-        const double bound = (4.0 * (d + 2) * 0x1p-53) * (b64 + a64);
-        if (diff > bound) gt = true;
-        else if (!(diff < -bound)) {
-          if (ctr) atomicAdd((unsigned long long*)&ctr[C_EXACT], 1ull);
-          gt = exact_sign_diff(u, p, q, d) > 0;
-        }
+      hard = !same;
+    }
+  }
+  if (__any_sync(FULL, hard)) {
+    // float64 u.q, formed once for the warp, only when some candidate needs it
+    double g64 = 0.0, a64 = 0.0;
+    for (int i = lane; i < d; i += 32) {
+      const double x = (double)u[i], y = (double)q[i];
+      g64 = fma(x, y, g64);
+      a64 = fma(fabs(x), fabs(y), a64);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g64 += __shfl_xor_sync(FULL, g64, o);
+      a64 += __shfl_xor_sync(FULL, a64, o);
+    }
+    if (hard) {
+      const float* p = Ps + (int64_t)it * d;
+      double s64 = 0.0, b64 = 0.0;
+      for (int i = 0; i < d; ++i) {
+        s64 = fma((double)u[i], (double)p[i], s64);
+        b64 = fma(fabs((double)u[i]), fabs((double)p[i]), b64);
+      }
+      const double diff = s64 - g64;
+      const double bound = (4.0 * (d + 2) * 0x1p-53) * (b64 + a64);
+      if (diff > bound) gt = true;
+      else if (!(diff < -bound)) {
+        if (ctr) atomicAdd((unsigned long long*)&ctr[C_EXACT], 1ull);
+        gt = exact_sign_diff(u, p, q, d) > 0;
       }
     }
   }
@@ -1041,7 +1052,6 @@ constexpr int MQ_TU = 128;
 constexpr int MQ_THREADS = 256;
 constexpr int MQ_US = MQ_TU + 4;       // row stride of the transposed user tile
 constexpr int MQ_QS = MQ_TQ + 4;       // row stride of the transposed query tile
-constexpr int MQ_PREP_THREADS = 1024;
 
 struct Batch {
   const float* dq;        // [nq][d] staged queries (call order)
@@ -1066,7 +1076,10 @@ struct Batch {
   const long long* seglo;   // [nq] allowed id range per query (null: all users)
   const long long* seghi;
   unsigned long long* keys;  // [nq] sort keys
+  unsigned long long* runs;  // [nruns * 1024] keys sorted in runs
   int* hist;              // [RMIPS_KMAX_LIMIT + 2] queries per k
+  int* gfirst;            // [RMIPS_KMAX_LIMIT + 2] first sorted position of each k
+  int* gslot0;            // [RMIPS_KMAX_LIMIT + 2] first slot of each k-group
   int32_t* big;           // queries with more than EMIT_SORT_CAP results
   uint32_t* bigmaps;      // MQ_BIG_SLOTS id bitmaps of nw words each
   int64_t nw;             // words per id bitmap
@@ -1093,65 +1106,40 @@ __global__ void k_mprep_a(Common c, Batch b, int precision) {
   atomicAdd(&b.hist[k], 1);
 }
 
-// (b) one CTA: sort the keys (k ascending, norm descending), lay the queries
-// out in k-groups padded to MQ_TQ slots.
-__global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep_b(Common c, Batch b) {
-  extern __shared__ unsigned long long keys[];               // [N2]
+// (b) one CTA: k-group layout from the histogram (first sorted position and
+// first slot of every k, group table, padding slots), counters of the pass.
+__global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
   __shared__ int first[RMIPS_KMAX_LIMIT + 2];
   __shared__ int slot0[RMIPS_KMAX_LIMIT + 2];
-  __shared__ int hist[RMIPS_KMAX_LIMIT + 2];
   const int tid = threadIdx.x;
-  const int nq = b.nq;
-  int N2 = 1;
-  while (N2 < nq) N2 <<= 1;
   if (tid == 0) {
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
     c.ctr[C_NBIG] = 0;
-  }
-  if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = b.hist[tid];
-  for (int j = tid; j < N2; j += MQ_PREP_THREADS) keys[j] = j < nq ? b.keys[j] : ~0ull;
-  __syncthreads();
-  for (int kk = 2; kk <= N2; kk <<= 1) {
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int t = tid; t < (N2 >> 1); t += MQ_PREP_THREADS) {
-        const int i = 2 * t - (t & (jj - 1)), p = i + jj;      // the pair (i, i + jj)
-        const unsigned long long x = keys[i], y = keys[p];
-        if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
-      }
-      __syncthreads();
-    }
-  }
-  if (tid == 0) {
     int f = 0, s = 0, g = 0;
-    for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) {
+    for (int k = 0; k <= RMIPS_KMAX_LIMIT + 1; ++k) {
       first[k] = f;
       slot0[k] = s;
-      if (hist[k] > 0) {
-        const int tiles = (hist[k] + MQ_TQ - 1) / MQ_TQ;
-        b.grp[g++] = make_int4(k, s, hist[k], tiles);
-        f += hist[k];
+      const int h = (k >= 1 && k <= RMIPS_KMAX_LIMIT) ? b.hist[k] : 0;
+      if (h > 0) {
+        const int tiles = (h + MQ_TQ - 1) / MQ_TQ;
+        b.grp[g++] = make_int4(k, s, h, tiles);
+        f += h;
         s += tiles * MQ_TQ;
       }
     }
     for (; g <= RMIPS_KMAX_LIMIT; ++g) b.grp[g] = make_int4(0, s, 0, 0);   // empty groups; .y = total slots
   }
   __syncthreads();
-  for (int i = tid; i < nq; i += MQ_PREP_THREADS) {
-    const unsigned long long key = keys[i];
-    const int k = (int)(key >> 46);
-    const int j = (int)(key & 16383ull);
-    const int slot = slot0[k] + (i - first[k]);
-    b.bidx[slot] = j;
-    b.bk[slot] = k;
-    b.bqn[slot] = b.dqn[j];
-    b.beps[slot] = b.deps[j];
+  if (tid < RMIPS_KMAX_LIMIT + 2) {
+    b.gfirst[tid] = first[tid];
+    b.gslot0[tid] = slot0[tid];
   }
   for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) {
-    const int h = hist[k];
+    const int h = b.hist[k];
     if (h == 0) continue;
     const int pad = ((h + MQ_TQ - 1) / MQ_TQ) * MQ_TQ;
-    for (int r = h + tid; r < pad; r += MQ_PREP_THREADS) {
+    for (int r = h + tid; r < pad; r += blockDim.x) {
       b.bidx[slot0[k] + r] = -1;
       b.bk[slot0[k] + r] = k;
       b.bqn[slot0[k] + r] = 0.f;
@@ -1160,7 +1148,58 @@ __global__ void __launch_bounds__(MQ_PREP_THREADS) k_mprep_b(Common c, Batch b) 
   }
 }
 
-// (c) grid: gather the query vectors into slot order (zeros in padding), row
+// (c) grid: every CTA sorts 1024 keys (k ascending, norm descending, query
+// index) in shared memory; padding keys sort last.
+constexpr int RUN = 1024;
+__global__ void __launch_bounds__(RUN) k_mprep_runs(Batch b) {
+  __shared__ unsigned long long keys[RUN];
+  const int tid = threadIdx.x;
+  const int64_t g = (int64_t)blockIdx.x * RUN + tid;
+  keys[tid] = g < b.nq ? b.keys[g] : ~0ull;
+  __syncthreads();
+  for (int kk = 2; kk <= RUN; kk <<= 1) {
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      if (tid < RUN / 2) {
+        const int i = 2 * tid - (tid & (jj - 1)), p = i + jj;
+        const unsigned long long x = keys[i], y = keys[p];
+        if ((x > y) == ((i & kk) == 0)) { keys[i] = y; keys[p] = x; }
+      }
+      __syncthreads();
+    }
+  }
+  b.runs[g] = keys[tid];
+}
+
+// (d) grid: the final sorted position of each key is its position in its run
+// plus, for every other run, the number of keys below it (keys are distinct),
+// found by binary search; the position gives the query's slot in its k-group.
+__global__ void k_mprep_place(Batch b, int nruns) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= (int64_t)nruns * RUN) return;
+  const unsigned long long key = b.runs[g];
+  if (key == ~0ull) return;                        // padding
+  const int r = (int)(g / RUN);
+  int64_t rank = g - (int64_t)r * RUN;
+  for (int o = 0; o < nruns; ++o) {
+    if (o == r) continue;
+    const unsigned long long* run = b.runs + (int64_t)o * RUN;
+    int lo = 0, hi = RUN;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (run[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    rank += lo;
+  }
+  const int k = (int)(key >> 46);
+  const int j = (int)(key & 16383ull);
+  const int slot = b.gslot0[k] + (int)(rank - b.gfirst[k]);
+  b.bidx[slot] = j;
+  b.bk[slot] = k;
+  b.bqn[slot] = b.dqn[j];
+  b.beps[slot] = b.deps[j];
+}
+
+// (e) grid: gather the query vectors into slot order (zeros in padding), row
 // major for the CUDA-core path and in 64-query UMMA tiles for tensor cores.
 __global__ void k_mprep_c(Common c, Batch b) {
   const int total_slots = b.grp[RMIPS_KMAX_LIMIT].y;
@@ -1897,7 +1936,10 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bqt, (size_t)MQ_SLOTS * TC_K * sizeof(float)));
   if (!ws->keys) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->keys, MQ_MAXQ * sizeof(unsigned long long)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->runs, MQ_MAXQ * sizeof(unsigned long long)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->hist, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->gfirst, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->gslot0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
   }
   if (!ws->big) {
     const int64_t nw = idx->n / 32 + 1;
@@ -2001,7 +2043,10 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.seg = ws->seg;
     b.bqt = use_tc ? ws->bqt : nullptr;
     b.keys = ws->keys;
+    b.runs = ws->runs;
     b.hist = ws->hist;
+    b.gfirst = ws->gfirst;
+    b.gslot0 = ws->gslot0;
     b.seglo = dseglo ? dseglo + j0 : nullptr;
     b.seghi = dseghi ? dseghi + j0 : nullptr;
     b.big = ws->big;
@@ -2010,17 +2055,12 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.doffs = ws->doffs + j0;
     b.out = out;
     b.capacity = capacity;
-    int N2 = 1;
-    while (N2 < cnt) N2 <<= 1;
-    static thread_local bool prep_cfg = false;
-    if (!prep_cfg) {
-      RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mprep_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          MQ_MAXQ * (int)sizeof(unsigned long long)));
-      prep_cfg = true;
-    }
+    const int nruns = (cnt + RUN - 1) / RUN;
     RMIPS_TRY_CUDA(cudaMemsetAsync(b.hist, 0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int), st));
     k_mprep_a<<<(cnt + 255) / 256, 256, 0, st>>>(c, b, idx->precision);
-    k_mprep_b<<<1, MQ_PREP_THREADS, N2 * sizeof(unsigned long long), st>>>(c, b);
+    k_mprep_groups<<<1, 256, 0, st>>>(c, b);
+    k_mprep_runs<<<nruns, RUN, 0, st>>>(b);
+    k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, st>>>(b, nruns);
     k_mprep_c<<<sm_count * 4, 256, 0, st>>>(c, b);
     RMIPS_TRY_CUDA(cudaGetLastError());
     const bool prof = idx->prof_on != 0;

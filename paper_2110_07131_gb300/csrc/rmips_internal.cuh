@@ -34,7 +34,7 @@
 #define RMIPS_DMAX 128           // largest supported dimension
 #define MQ_MAXQ 16384            // queries per multi-query pass (14-bit index)
 #define MQ_TQ 64                 // queries per tile
-#define MQ_BIG_SLOTS 64          // concurrent large-result emitters (one id bitmap each)
+#define MQ_BIG_SLOTS 256         // concurrent large-result emitters (one id bitmap each)
 #define MQ_SLOTS (MQ_MAXQ + (RMIPS_KMAX_LIMIT + 1) * MQ_TQ)
 
 #if defined(__CUDACC__)
@@ -120,6 +120,9 @@ struct Workspace {
   int32_t* seg = nullptr;        // [cap_y] positions grouped by query
   float* bqt = nullptr;          // [MQ_SLOTS / MQ_TQ][MQ_TQ * 64] query tiles, UMMA layout
   unsigned long long* keys = nullptr;  // [MQ_MAXQ] query sort keys
+  unsigned long long* runs = nullptr;  // [MQ_MAXQ] keys sorted in runs of 1024
+  int* gfirst = nullptr;         // [RMIPS_KMAX_LIMIT + 2] first sorted position of each k
+  int* gslot0 = nullptr;         // [RMIPS_KMAX_LIMIT + 2] first slot of each k-group
   int* hist = nullptr;           // [RMIPS_KMAX_LIMIT + 2] queries per k
   long long* dseglo = nullptr;   // [cap_seg] per-query id ranges of a batch
   long long* dseghi = nullptr;
