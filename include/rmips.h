@@ -318,14 +318,15 @@ int32_t rmips_exact_sign_host(const float* u, const float* a, const float* b, in
 
 /*
  * rmips_debug_tc_tile -- test hook for the tensor-core tiles of the batched
- * filter (no counterpart in the paper).  Runs one 128 x 64 x 64 TF32 tile
- * through the shared-memory layout, UMMA descriptors (with the given leading
- * and stride byte offsets), tcgen05.mma and TMEM loads the batched filter
- * uses: D[128][64] = A[128][64] * B[64][64]^T.  A, B, D: device float32,
- * row-major.  lbo, sbo: multiples of 16 in [16, 4096].  Synchronises
- * `stream`.  Errors: ARG, TIMEOUT, CUDA.
+ * filter (no counterpart in the paper).  Runs one 128 x 64 x 64 tile through
+ * the shared-memory layout, UMMA descriptors (with the given leading and
+ * stride byte offsets; 0 selects the filter's own), tcgen05.mma and TMEM
+ * loads the batched filter uses: D[128][64] = A[128][64] * B[64][64]^T.
+ * kind: 0 TF32, 1 BF16, 2 FP16 (A and B rounded to nearest into that format).
+ * A, B, D: device float32, row-major.  lbo, sbo: 0 or multiples of 16 in
+ * [16, 4096].  Synchronises `stream`.  Errors: ARG, TIMEOUT, CUDA.
  */
-rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t lbo, int32_t sbo,
+rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, int32_t lbo, int32_t sbo,
                                  void* stream);
 
 #ifdef __cplusplus

@@ -977,21 +977,32 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
 
 
 
-// One 128 x 64 x 64 TF32 tile through the layout, descriptors, MMA and TMEM
-// loads used by the batched filter (test hook).  A [128][64], B [64][64]
-// row-major float32 in global memory; D [128][64] = A B^T.
+// One 128 x 64 x 64 tile through the layout, descriptors, MMA and TMEM loads
+// used by the batched filter (test hook).  A [128][64], B [64][64] row-major
+// float32 in global memory (rounded to nearest into BF16 / FP16 for those
+// kinds); D [128][64] = A B^T.
+template <int KIND>
 __global__ void __launch_bounds__(128) k_debug_tc(const float* __restrict__ A, const float* __restrict__ B,
                                                   float* __restrict__ D, uint32_t lbo, uint32_t sbo,
                                                   long long* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  float* sA = reinterpret_cast<float*>(dsm);                     // 128 x 64 (32 KB)
-  float* sB = reinterpret_cast<float*>(dsm + 128 * TC_K * 4);    // 64 x 64 (16 KB)
+  constexpr uint32_t E = KIND == TCK_TF32 ? 4 : 2;
+  unsigned char* sA = dsm;                          // 128 x 64
+  unsigned char* sB = dsm + 128 * TC_K * E;         // 64 x 64
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t taddr_s;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < 128 * (int)TC_K; e += 128) sA[tc_off(e / TC_K, e % TC_K) / 4] = A[e];
-  for (int e = tid; e < 64 * (int)TC_K; e += 128) sB[tc_off(e / TC_K, e % TC_K) / 4] = B[e];
+  for (int e = tid; e < 192 * (int)TC_K; e += 128) {
+    const bool isA = e < 128 * (int)TC_K;
+    const int ee = isA ? e : e - 128 * (int)TC_K;
+    const int r = ee / (int)TC_K, k = ee % (int)TC_K;
+    const float v = isA ? A[ee] : B[ee];
+    unsigned char* base = isA ? sA : sB;
+    if (KIND == TCK_TF32) *reinterpret_cast<float*>(base + tc_off(r, k)) = v;
+    else if (KIND == TCK_BF16) *reinterpret_cast<__nv_bfloat16*>(base + tc_off16(r, k)) = __float2bfloat16_rn(v);
+    else *reinterpret_cast<__half*>(base + tc_off16(r, k)) = __float2half_rn(v);
+  }
   if (warp == 0) {
     tmem_alloc(&taddr_s, 64);
     tmem_relinquish();
@@ -1007,11 +1018,12 @@ __global__ void __launch_bounds__(128) k_debug_tc(const float* __restrict__ A, c
   tc_fence_after();
   const uint32_t taddr = taddr_s;
   if (tid == 0) {
-    const uint32_t idesc = tc_idesc_tf32(128, 64);
-    for (uint32_t s = 0; s < TC_K / 8; ++s) {
+    const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(128, 64) : tc_idesc_f16(128, 64, KIND == TCK_BF16);
+    for (uint32_t s = 0; s < TC_K * E / 32; ++s) {
       const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, lbo, sbo);
       const uint64_t bd = tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, lbo, sbo);
-      tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+      if (KIND == TCK_TF32) tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+      else tc_mma_f16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
     }
     tc_commit(&bar);
   }
@@ -1072,7 +1084,8 @@ struct Batch {
   unsigned long long* tpairs;
   long long cap_t;
   int32_t* seg;
-  float* bqt;             // query tiles in the UMMA layout (TC path), may be null
+  unsigned char* bqt;     // query tiles in the UMMA layout (TC path), may be null
+  int bqt_kind;           // TCK_* of the tiles
   const long long* seglo;   // [nq] allowed id range per query (null: all users)
   const long long* seghi;
   unsigned long long* keys;  // [nq] sort keys
@@ -1214,7 +1227,14 @@ __global__ void k_mprep_c(Common c, Batch b) {
       const int slot = (int)(e / TC_K), k = (int)(e - (int64_t)slot * TC_K);
       const int j = b.bidx[slot];
       const float v = (j >= 0 && k < c.d) ? b.dq[(int64_t)j * c.d + k] : 0.f;
-      b.bqt[(size_t)(slot / MQ_TQ) * (MQ_TQ * TC_K) + tc_off(slot % MQ_TQ, k) / 4] = v;
+      const size_t tile = (size_t)(slot / MQ_TQ);
+      if (b.bqt_kind == TCK_TF32) {
+        reinterpret_cast<float*>(b.bqt + tile * (MQ_TQ * TC_K * 4) + tc_off(slot % MQ_TQ, k))[0] = v;
+      } else {
+        unsigned char* dst = b.bqt + tile * (MQ_TQ * TC_K * 2) + tc_off16(slot % MQ_TQ, k);
+        if (b.bqt_kind == TCK_BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+        else *reinterpret_cast<__half*>(dst) = __float2half_rn(v);
+      }
     }
   }
 }
@@ -1649,15 +1669,21 @@ constexpr int TCU = 128;                       // users per tile (MMA M)
 constexpr int TCQ = MQ_TQ;                     // queries per tile (MMA N)
 constexpr int TC_THREADS = 256;                // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4) ...
 constexpr int TC_HALF = TCQ / 2;               // ... and split the 64 query columns in halves
-constexpr float TC_ERR = TC_TF32_ERR;
-constexpr uint32_t TC_TILE_BYTES = TCQ * TC_K * 4;   // one query tile (16 KB)
-constexpr uint32_t TC_A_BYTES = TCU * TC_K * 4;      // one user tile (32 KB)
+__host__ __device__ constexpr uint32_t tc_esize(int kind) { return kind == TCK_TF32 ? 4u : 2u; }
+__host__ __device__ constexpr uint32_t tc_tile_bytes(int kind) { return TCQ * TC_K * tc_esize(kind); }
+__host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K * tc_esize(kind); }
 
-__global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b, const float* __restrict__ bqt,
+template <int KIND>
+__global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b, const unsigned char* __restrict__ bqt,
                                                                int ngroups) {
+  constexpr uint32_t TC_TILE_BYTES = tc_tile_bytes(KIND);   // one query tile
+  constexpr uint32_t TC_A_BYTES = tc_a_bytes(KIND);         // one user tile
+  constexpr uint32_t SBO = KIND == TCK_TF32 ? TC_SBO : TC_SBO16;
+  constexpr uint32_t NSTEP = TC_K * tc_esize(KIND) / 32;    // MMAs per tile (32 bytes of K each)
+  constexpr float TC_ERR = tc_rel_err(KIND);
   extern __shared__ __align__(1024) unsigned char tsm[];
-  float* sA = reinterpret_cast<float*>(tsm);                                   // 32 KB
-  float* sB = reinterpret_cast<float*>(tsm + TC_A_BYTES);                      // 2 x 16 KB
+  unsigned char* sA = tsm;
+  unsigned char* sB = tsm + TC_A_BYTES;                      // 2 query tiles
   __shared__ __align__(8) uint64_t bar_b[2];     // query tile landed
   __shared__ __align__(8) uint64_t bar_m;        // MMA done
   __shared__ uint32_t taddr_s;
@@ -1675,7 +1701,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
   const int sub = c.bs < TCU ? c.bs : TCU;
   const int nbt = TCU / sub;
   const float un0 = c.unorm[0];                  // largest user norm (users are sorted)
-  const float tiny = (d + 2) * 0x1p-126f;
+  const float tiny = (d + 2) * tc_abs_unit(KIND);            // operands below the normal range
 
   if (warp == 0) {
     tmem_alloc(&taddr_s, 64);
@@ -1693,7 +1719,16 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
   tc_fence_after();
   const uint32_t taddr = taddr_s;
   const uint32_t tlane = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * TC_HALF);
-  const uint32_t idesc = tc_idesc_tf32(TCU, TCQ);
+  const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, TCQ) : tc_idesc_f16(TCU, TCQ, KIND == TCK_BF16);
+  auto mma = [&](uint32_t bbase) {                 // one 128 x 64 x 64 tile, thread 0
+    for (uint32_t s = 0; s < NSTEP; ++s) {
+      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, SBO);
+      const uint64_t bd = tc_sdesc(bbase + s * 2 * TC_LBO, TC_LBO, SBO);
+      if (KIND == TCK_TF32) tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+      else tc_mma_f16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+    }
+    tc_commit(&bar_m);
+  };
   uint32_t phb = 0, ph_m = 0;                    // parity of the next wait: bit x for bar_b[x] / bar_m
   long long st_pairs = 0, st_skipped = 0, st_yes = 0, st_todo = 0;
 
@@ -1730,7 +1765,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
     const int64_t nvalid = (n - u0) < TCU ? (n - u0) : TCU;
     // 2. user tile into the UMMA layout: one 16-byte chunk (4 consecutive k of
     //    one row) per store, consecutive threads on consecutive rows
-    {
+    if (KIND == TCK_TF32) {
       const float* src = c.Qs + u0 * d;
       for (int e = tid; e < TCU * (int)(TC_K / 4); e += TC_THREADS) {
         const int r = e & (TCU - 1), k0 = (e >> 7) * 4;
@@ -1742,10 +1777,24 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
           if (k0 + 2 < d) v.z = row[k0 + 2];
           if (k0 + 3 < d) v.w = row[k0 + 3];
         }
-        *reinterpret_cast<float4*>(&sA[tc_off(r, k0) / 4]) = v;
+        *reinterpret_cast<float4*>(sA + tc_off(r, k0)) = v;
       }
-      if (tid < TCU) un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
+    } else {                                       // the index's 16-bit copy, 8 values per chunk
+      const uint16_t* src = reinterpret_cast<const uint16_t*>(c.Qrows) + u0 * d;
+      for (int e = tid; e < TCU * (int)(TC_K / 8); e += TC_THREADS) {
+        const int r = e & (TCU - 1), k0 = (e >> 7) * 8;
+        uint16_t h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = (r < nvalid && k0 + i < d) ? src[(int64_t)r * d + k0 + i] : (uint16_t)0;
+        uint4 v;
+        v.x = h[0] | ((uint32_t)h[1] << 16);
+        v.y = h[2] | ((uint32_t)h[3] << 16);
+        v.z = h[4] | ((uint32_t)h[5] << 16);
+        v.w = h[6] | ((uint32_t)h[7] << 16);
+        *reinterpret_cast<uint4*>(sA + tc_off16(r, k0)) = v;
+      }
     }
+    if (tid < TCU) un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
     if (tid == 0) {
       for (int g = 0; g < ngroups; ++g)
         for (int sb = 0; sb < nbt; ++sb) {
@@ -1769,12 +1818,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
       if (tid == 0) {
         fence_proxy_async();
         mbar_arrive_expect_tx(&bar_b[buf], TC_TILE_BYTES);
-        bulk_g2s(reinterpret_cast<unsigned char*>(sB) + (size_t)buf * TC_TILE_BYTES,
-                 bqt + (size_t)(s0 / TCQ) * (TC_TILE_BYTES / 4), TC_TILE_BYTES, &bar_b[buf]);
+        bulk_g2s(sB + (size_t)buf * TC_TILE_BYTES, bqt + (size_t)(s0 / TCQ) * TC_TILE_BYTES, TC_TILE_BYTES,
+                 &bar_b[buf]);
       }
       if (tid < TCQ) {
         const float qn = b.bqn[s0 + tid];
-        cq_s[buf][tid] = make_float2(__fmul_ru(qn, TC_ERR), __fmaf_ru(fmaxf(qn, un0), tiny, b.beps[s0 + tid]));
+        cq_s[buf][tid] = make_float2(__fmul_ru(qn, TC_ERR), __fmaf_ru(__fadd_ru(qn, un0), tiny, b.beps[s0 + tid]));
         qj_s[buf][tid] = b.bidx[s0 + tid];
       }
     };
@@ -1785,10 +1834,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
     if (tid == 0) {                                // MMA(0)
       if (mbar_wait_bounded(&bar_b[0], phb & 1u)) {
         tc_fence_after();
-        for (uint32_t s = 0; s < TC_K / 8; ++s)
-          tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
-                      tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
-        tc_commit(&bar_m);
+        mma(smem_u32(sB));
       } else {
         s_fail = 1;
       }
@@ -1824,11 +1870,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
       if (has_next && tid == 0) {
         if (mbar_wait_bounded(&bar_b[buf ^ 1], (phb >> (buf ^ 1)) & 1u)) {
           tc_fence_after();
-          const uint32_t bbase = smem_u32(sB) + (uint32_t)(buf ^ 1) * TC_TILE_BYTES;
-          for (uint32_t s = 0; s < TC_K / 8; ++s)
-            tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
-                        tc_sdesc(bbase + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
-          tc_commit(&bar_m);
+          mma(smem_u32(sB) + (uint32_t)(buf ^ 1) * TC_TILE_BYTES);
         } else {
           s_fail = 1;
         }
@@ -1917,6 +1959,23 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(taddr, 64);
+}
+
+cudaError_t launch_mfilter_tc(int kind, const Common& c, const Batch& b, int ngroups, int grid, size_t smem,
+                              cudaStream_t st) {
+  static thread_local bool cfg[3] = {false, false, false};
+  cudaError_t e = cudaSuccess;
+  if (!cfg[kind]) {
+    if (kind == TCK_TF32) e = cudaFuncSetAttribute(k_mfilter_tc<TCK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (kind == TCK_BF16) e = cudaFuncSetAttribute(k_mfilter_tc<TCK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else e = cudaFuncSetAttribute(k_mfilter_tc<TCK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cfg[kind] = true;
+  }
+  if (kind == TCK_TF32) k_mfilter_tc<TCK_TF32><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
+  else if (kind == TCK_BF16) k_mfilter_tc<TCK_BF16><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
+  else k_mfilter_tc<TCK_FP16><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
+  return cudaGetLastError();
 }
 
 rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
@@ -2018,9 +2077,10 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   if (s != RMIPS_OK) return s;
   RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
   const int ngroups_max = idx->k_max;
-  const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K && idx->precision == RMIPS_FP32;
+  const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K;
+  const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
   const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
-  const size_t smem_tc = TC_A_BYTES + 2 * TC_TILE_BYTES;
+  const size_t smem_tc = tc_a_bytes(tck) + 2 * tc_tile_bytes(tck);
   const int64_t tc_tiles = (idx->n + TCU - 1) / TCU;
   const int tc_grid = (int)(tc_tiles < sm_count * 3 ? tc_tiles : sm_count * 3);
   int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 4096);
@@ -2041,7 +2101,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.ypairs = ws->ypairs; b.cap_y = ws->cap_y;
     b.tpairs = ws->tpairs; b.cap_t = ws->cap_t;
     b.seg = ws->seg;
-    b.bqt = use_tc ? ws->bqt : nullptr;
+    b.bqt = use_tc ? reinterpret_cast<unsigned char*>(ws->bqt) : nullptr;
+    b.bqt_kind = tck;
     b.keys = ws->keys;
     b.runs = ws->runs;
     b.hist = ws->hist;
@@ -2073,13 +2134,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used], st));
     }
     if (use_tc) {
-      static thread_local bool tc_cfg = false;
-      if (!tc_cfg) {
-        RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_mfilter_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc));
-        tc_cfg = true;
-      }
-      k_mfilter_tc<<<tc_grid, TC_THREADS, smem_tc, st>>>(c, b, ws->bqt, idx->k_max);
-      RMIPS_TRY_CUDA(cudaGetLastError());
+      RMIPS_TRY_CUDA(launch_mfilter_tc(tck, c, b, idx->k_max, tc_grid, smem_tc, st));
     } else {
       RMIPS_TRY_CUDA(mfilter_dispatch(idx, c, b, idx->k_max, fgrid, smem, st));
     }
@@ -2353,8 +2408,11 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
   return status_from_device(h[C_STATUS]);
 }
 
-extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t lbo, int32_t sbo,
-                                           void* stream) {
+extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, int32_t lbo,
+                                           int32_t sbo, void* stream) {
+  if (kind < TCK_TF32 || kind > TCK_FP16) { set_error("bad kind"); return RMIPS_ERR_ARG; }
+  if (lbo == 0) lbo = (int32_t)TC_LBO;
+  if (sbo == 0) sbo = (int32_t)(kind == TCK_TF32 ? TC_SBO : TC_SBO16);
   if (!A || !B || !D || lbo <= 0 || sbo <= 0 || lbo > 4096 || sbo > 4096 || (lbo & 15) || (sbo & 15)) {
     set_error("bad argument");
     return RMIPS_ERR_ARG;
@@ -2368,8 +2426,16 @@ extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, floa
   RMIPS_TRY_CUDA(cudaMallocAsync((void**)&status, sizeof(long long), st));
   RMIPS_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(long long), st));
   const int dsmem = (int)(192 * TC_K * 4);
-  RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
-  k_debug_tc<<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+  if (kind == TCK_TF32) {
+    RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
+    k_debug_tc<TCK_TF32><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+  } else if (kind == TCK_BF16) {
+    RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
+    k_debug_tc<TCK_BF16><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+  } else {
+    RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
+    k_debug_tc<TCK_FP16><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+  }
   RMIPS_TRY_CUDA(cudaGetLastError());
   long long h = 0;
   RMIPS_TRY_CUDA(cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st));

@@ -67,6 +67,44 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uin
       : "memory");
 }
 
+// kind::f16 (A = B = BF16 or FP16): 16-bit elements, a core matrix row holds
+// 8 of them; the K = 64 tile is 8 chunks of 16 bytes, so 8-row groups are
+// 1024 bytes apart, and one MMA consumes K = 16 (two chunks, 256 bytes).
+constexpr uint32_t TC_SBO16 = (TC_K / 8) * 128;      // 1024 bytes
+
+__host__ __device__ __forceinline__ uint32_t tc_off16(uint32_t row, uint32_t k) {
+  return (row >> 3) * TC_SBO16 + (k >> 3) * TC_LBO + (row & 7) * 16 + (k & 7) * 2;   // bytes
+}
+
+// Instruction descriptor: D = F32, A = B = BF16 (bf16 = true) or FP16, K-major, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_f16(uint32_t M, uint32_t N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Operand kinds of the tensor-core filter: TF32 from float32 rows, or the
+// index's BF16 / FP16 copy.  Relative error bound of one inner product as a
+// multiple of ||a|| ||b|| (operands rounded to nearest with unit roundoff
+// u_in -- TF32 charged 2^-10 for any rounding --, products exact in float32,
+// accumulation over K = 64 charged 65 * 2^-22) and the absolute error unit of
+// operands below the format's normal range.
+enum : int { TCK_TF32 = 0, TCK_BF16 = 1, TCK_FP16 = 2 };
+__host__ __device__ constexpr float tc_rel_err(int kind) {
+  return kind == TCK_TF32 ? 0.00198f : (kind == TCK_BF16 ? 0.00788f : 0.000995f);
+}
+__host__ __device__ constexpr float tc_abs_unit(int kind) {
+  return kind == TCK_FP16 ? 0x1p-25f : 0x1p-125f;
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");

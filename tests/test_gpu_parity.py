@@ -261,3 +261,31 @@ def test_batch_with_many_large_results():
         big += len(exp) > 8192
         assert np.array_equal(ids[offs[j]:offs[j + 1]], exp), j
     assert big > 64
+
+
+def test_precision_modes_return_identical_sets():
+    # d = 64 with queries from P and random N(0, I/d) queries, as in the
+    # precision workload: BF16 / FP16 tensor-core filtering must not change
+    # any result, only how many pairs need the exact recheck
+    n, m, d = 40000, 20000, 64
+    Q, P = datagen.make_problem(n, m, d, 2)
+    qs = np.concatenate([datagen.queries_from_items(P, 300, 2)[0], datagen.random_queries(300, d, 2)])
+    ks = datagen.random_ks(len(qs), 1, 25, 2)
+    res = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        index = rmips.rmips_build_index(Q, P, k_max=25, precision=prec)
+        ids, offs = rmips.rmips_query_batch(index, qs, ks)
+        res[prec] = [ids[offs[j]:offs[j + 1]] for j in range(len(qs))]
+        st = rmips.rmips_last_query_stats(index)
+        res[prec + "_todo"] = st["todo"]
+        index.close()
+    for j in range(len(qs)):
+        assert np.array_equal(res["bf16"][j], res["fp32"][j]), j
+        assert np.array_equal(res["fp16"][j], res["fp32"][j]), j
+    assert res["bf16_todo"] >= res["fp16_todo"]          # coarser format, more rechecks
+    rng = np.random.default_rng(3)
+    for j in rng.choice(len(qs), 4, replace=False):
+        got = res["fp32"][j]
+        sample = np.unique(np.concatenate([got[:100], rng.choice(n, 100, replace=False)]))
+        truth = O.decide_users(Q, P, qs[j], int(ks[j]), sample)
+        assert np.array_equal(np.intersect1d(sample, got), sample[truth])
