@@ -159,6 +159,23 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- ranks
+def reduce_over_ranks(ms: float, units: float, dist=None, device=None):
+    """Max of the timed milliseconds and sum of the processed units over ranks.
+
+    Every rank runs an independent replica (the path shards by users with no
+    exchange step), so whole-job throughput is total units / slowest rank."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_u, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), float(t_u.item())
+
+
 # --------------------------------------------------------------------------- serving
 def run_serving(rmips, index, qs, a):
     """Continuous batching through rmips_server_*: a saturating burst and a
@@ -264,12 +281,8 @@ def run_ours(a):
     qstats = rmips.rmips_last_query_stats(index)
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.barrier()
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = a.steps * a.nq * world / (ms_max / 1e3)
+    ms_max, units = reduce_over_ranks(ms, a.steps * a.nq, dist, dev)
+    value = units / (ms_max / 1e3)
 
     # end to end through the public API with host buffers (copies inside the timed region)
     hq = np.ascontiguousarray(qs[:a.nq])
