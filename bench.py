@@ -280,6 +280,13 @@ def run_ours(a):
     rmips.rmips_profile_enable(index, False)
     qstats = rmips.rmips_last_query_stats(index)
     clocks = sampler.stop()
+    # pipeline counters of the tensor-core filter: one more step with the
+    # instrumented kernel, outside the timed region
+    rmips.rmips_profile_enable(index, 2)
+    step(a.warmup)
+    torch.cuda.synchronize(dev)
+    pprof = rmips.rmips_profile_read(index)
+    rmips.rmips_profile_enable(index, False)
     ms = ev0.elapsed_time(ev1)
     ms_max, units = reduce_over_ranks(ms, a.steps * a.nq, dist, dev)
     value = units / (ms_max / 1e3)
@@ -352,13 +359,23 @@ def run_ours(a):
     if tc_path:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         tf32_peak = bf16 * (1.1 / 2.25)
-        roofline = {"bound": "tensor", "kernel": "k_mfilter_tc (Lemma 3 prefixes + tcgen05 TF32 128x64x64 tiles "
-                                                  "in TMEM + Lemmas 1/2 epilogue)",
+        roofline = {"bound": "tensor", "kernel": "k_mfilter_ws (warp-specialized: TMA-fed tcgen05 TF32 "
+                                                  "128x64xK tiles into 4 TMEM stages + Lemmas 1/2 epilogue)",
                     "achieved": m_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m_ach / tf32_peak,
                     "peak_source": f"measured bf16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25",
                     "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
                     "pairs_per_launch": prof["mfilter_pairs"] / ml,
+                    "tiles_per_launch": pprof["mfilter_tiles"] / max(1, pprof["mfilter_launches"]),
                     "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
+        cyc = pprof["mfilter_cycles"]
+        waits = pprof["mfilter_wait"]
+        names = ["loader_waits_free_slot", "feeder_waits_free_stage", "mma_waits_query_tile",
+                 "mma_waits_free_accumulator", "epilogue_waits_accumulator", "mma_waits_user_tile",
+                 "epilogue_reads_tmem", "mma_issues_mmas"]
+        owner = [0, 1, 2, 2, 3, 2, 3, 2]
+        roofline["active_tiles_per_launch"] = pprof["mfilter_active_tiles"] / max(1, pprof["mfilter_launches"])
+        roofline["pipeline_wait_share"] = {n: (waits[i] / cyc[owner[i]] if cyc[owner[i]] > 0 else None)
+                                           for i, n in enumerate(names)}
     else:
         roofline = {"bound": "alu", "kernel": "k_mfilter (multi-query Lemma 3 prefixes + FP32 FFMA tiles + "
                                               "Lemmas 1/2 epilogue)",
@@ -374,7 +391,7 @@ def run_ours(a):
             "dtype": ("tf32" if tc_path else ("f32" if a.precision == "fp32" else a.precision)) + "+f64 recheck",
             "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": a.steps * 9 * ((a.nq + 16383) // 16384),
+            "gpu_launches": a.steps * (12 if a.batch_kernel == "tc" and a.d <= 64 else 11) * ((a.nq + 16383) // 16384),
             "roofline_single_query_filter": roof_single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain, "serving": serving,
             "batch_latency_ms": ms_max / a.steps,

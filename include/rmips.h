@@ -173,10 +173,26 @@ typedef struct {
   int64_t mfilter_pairs;     /* (user, query) pairs kept by Lemma 3 */
   double mfilter_alg_flops;  /* 2 d flops per kept pair (the inner products
                                 the per-user tests need) */
+  int64_t mfilter_tiles;     /* 128 x 64 tensor-core tiles multiplied (the
+                                padded work behind the kept pairs) */
+  double mfilter_wait[8];    /* SM clock cycles the tensor-core filter's roles
+                                spent waiting, summed over CTAs: loader (free
+                                tile slot), feeder (free query stage), MMA
+                                (query tile landed), MMA (free accumulator),
+                                epilogue warp 0 (accumulator ready), MMA (user
+                                tile landed), epilogue warp 0 reading TMEM,
+                                MMA thread issuing an item's MMAs */
+  double mfilter_cycles[4];  /* cycles of each role from start to finish,
+                                summed over CTAs: loader, feeder, MMA,
+                                epilogue warp 0 */
+  int64_t mfilter_active_tiles;  /* user tiles with at least one item */
 } rmips_profile;
 
 /* Turns filter timing on (resetting the counters) or off.  While on, every
-   query records a CUDA event pair around each filter launch. */
+   query records a CUDA event pair around each filter launch.  enable = 2 also
+   fills the pipeline counters of the tensor-core batched filter
+   (mfilter_tiles, mfilter_wait, mfilter_cycles, mfilter_active_tiles); that
+   runs an instrumented copy of the kernel, so time with enable = 1. */
 rmips_status rmips_profile_enable(rmips_index* index, int32_t enable);
 
 /* Reads the accumulated filter timing. */

@@ -89,6 +89,39 @@ __global__ void k_to_half(const float* __restrict__ src, int64_t count, H* __res
   store_rn(dst + e, src[e]);
 }
 
+// Users in 128-row tiles of the tensor-core operand layout (K-major core
+// matrices, K padded to 64 with zeros): 16-byte chunks, 4 float32 (TF32 kind)
+// or 8 16-bit values; consecutive threads fill consecutive rows of a chunk
+// column.  Rows past n are zero.
+__global__ void k_user_tiles(const float* __restrict__ Qs, const uint16_t* __restrict__ Qh, int64_t n, int d,
+                             unsigned char* __restrict__ out) {
+  const int per = Qh ? 8 : 4;                      // values per chunk
+  const int64_t chunks = 128 * (int64_t)(TC_K / per);
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tiles = (n + 127) / 128;
+  if (e >= tiles * chunks) return;
+  const int64_t t = e / chunks;
+  const int rem = (int)(e - t * chunks);
+  const int r = rem & 127, k0 = (rem >> 7) * per;
+  const int64_t u = t * 128 + r;
+  if (!Qh) {
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (u < n && k0 + i < d) ? Qs[u * d + k0 + i] : 0.f;
+    *reinterpret_cast<float4*>(out + t * (128 * TC_K * 4) + tc_off(r, k0)) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    uint16_t h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = (u < n && k0 + i < d) ? Qh[u * d + k0 + i] : (uint16_t)0;
+    uint4 w;
+    w.x = h[0] | ((uint32_t)h[1] << 16);
+    w.y = h[2] | ((uint32_t)h[3] << 16);
+    w.z = h[4] | ((uint32_t)h[5] << 16);
+    w.w = h[6] | ((uint32_t)h[7] << 16);
+    *reinterpret_cast<uint4*>(out + t * (128 * TC_K * 2) + tc_off16(r, k0)) = w;
+  }
+}
+
 // --- 3. top-KC candidates per user (float32, one user per thread) -----------------
 // Items stream through shared memory in tiles of TP, stored transposed so that
 // every thread reads the same float4 (a broadcast) holding component i of four
@@ -672,6 +705,15 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
         k_to_half<__nv_bfloat16><<<grid_for(n * d, 256), 256, 0, st>>>(idx->Qs, n * d, (__nv_bfloat16*)idx->Qh);
       else
         k_to_half<__half><<<grid_for(n * d, 256), 256, 0, st>>>(idx->Qs, n * d, (__half*)idx->Qh);
+    }
+    if (idx->batch_tc && d <= (int)TC_K) {         // operand tiles of the batched tensor-core filter
+      const int64_t tiles = (n + 127) / 128;
+      const int64_t tile_bytes = 128 * (int64_t)TC_K * (idx->precision == RMIPS_FP32 ? 4 : 2);
+      TRY(dalloc(idx, &idx->Qtc, (size_t)(tiles * tile_bytes)));
+      const int64_t chunks = tiles * 128 * (TC_K / (idx->precision == RMIPS_FP32 ? 4 : 8));
+      k_user_tiles<<<grid_for(chunks, 256), 256, 0, st>>>(
+          idx->Qs, idx->precision == RMIPS_FP32 ? nullptr : (const uint16_t*)idx->Qh, n, d, idx->Qtc);
+      TRY(cudaGetLastError());
     }
     // 3: candidates
     TRY(cudaMallocAsync((void**)&cval, (size_t)n * RMIPS_KC * sizeof(float), st));

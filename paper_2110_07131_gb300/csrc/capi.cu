@@ -47,7 +47,6 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->ypairs);
   cudaFree(ws->tpairs);
   cudaFree(ws->seg);
-  cudaFree(ws->bqt);
   cudaFree(ws->keys);
   cudaFree(ws->runs);
   cudaFree(ws->gfirst);
@@ -57,6 +56,12 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->hist);
   cudaFree(ws->big);
   cudaFree(ws->bigmaps);
+  cudaFree(ws->bcq);
+  cudaFree(ws->bitems);
+  cudaFree(ws->gitem);
+  cudaFree(ws->itemg);
+  cudaFree(ws->gpre);
+  cudaFree(ws->wst);
   delete ws;
 }
 
@@ -203,6 +208,7 @@ extern "C" void rmips_free_index(rmips_index* idx) {
   cudaFree(idx->incomp);
   cudaFree(idx->LB);
   cudaFree(idx->hdr);
+  cudaFree(idx->Qtc);
   if (prev != idx->device) cudaSetDevice(prev);
   delete idx;
 }
@@ -215,7 +221,7 @@ extern "C" int32_t rmips_exact_sign_host(const float* u, const float* a, const f
 extern "C" rmips_status rmips_profile_enable(rmips_index* idx, int32_t enable) {
   if (!idx) { set_error("null argument"); return RMIPS_ERR_ARG; }
   std::lock_guard<std::mutex> lk(idx->mu);
-  idx->prof_on = enable ? 1 : 0;
+  idx->prof_on = enable == 2 ? 2 : (enable ? 1 : 0);
   idx->prof = rmips_profile{};
   return RMIPS_OK;
 }

@@ -952,6 +952,16 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
       idx->prof.mfilter_ms += ms;
       idx->prof.mfilter_pairs += h[C_TESTED];
       idx->prof.mfilter_alg_flops += 2.0 * idx->d * (double)h[C_TESTED];
+      unsigned long long w[WST_N] = {};
+      if (idx->prof_on == 2 && ws->wst && cudaMemcpy(w, ws->wst, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        idx->prof.mfilter_tiles += (int64_t)w[WST_TILES];
+        for (int i = 0; i < 5; ++i) idx->prof.mfilter_wait[i] += (double)w[WST_LOADER_WAIT + i];
+        idx->prof.mfilter_wait[5] += (double)w[WST_MMA_WAIT_A];
+        idx->prof.mfilter_wait[6] += (double)w[WST_EPI_TMEM];
+        idx->prof.mfilter_wait[7] += (double)w[WST_MMA_ISSUE];
+        for (int i = 0; i < 4; ++i) idx->prof.mfilter_cycles[i] += (double)w[WST_LOADER + i];
+        idx->prof.mfilter_active_tiles += (int64_t)w[WST_ACTIVE];
+      }
     } else if (idx->prof_on) {
       const int es = idx->precision == RMIPS_FP32 ? 4 : 2;
       const double per_user = (double)idx->d * es + 8.0 + (idx->full_p ? 0.0 : 4.0);
@@ -1084,8 +1094,13 @@ struct Batch {
   unsigned long long* tpairs;
   long long cap_t;
   int32_t* seg;
-  unsigned char* bqt;     // query tiles in the UMMA layout (TC path), may be null
-  int bqt_kind;           // TCK_* of the tiles
+  int tc_kind;            // TCK_* operand kind of the tensor-core filter
+  float2* bcq;            // [slots] (error scale, absolute slack) of the TC filter
+  unsigned char* bitems;  // [MQ_ITEMS] packed items of the TC filter (null: CUDA-core path)
+  int* gitem;             // [RMIPS_KMAX_LIMIT + 2] first item of each group; [RMIPS_KMAX_LIMIT + 1] = items
+  int2* itemg;            // [MQ_ITEMS] (group, chunk) of each item
+  int32_t* gpre;          // [nb][ngroups] Lemma 3 prefix of each (block, group)
+  unsigned long long* wst;  // [WST_N] role cycle counters of the TC filter (null: off)
   const long long* seglo;   // [nq] allowed id range per query (null: all users)
   const long long* seghi;
   unsigned long long* keys;  // [nq] sort keys
@@ -1129,18 +1144,23 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
     c.ctr[C_NBIG] = 0;
-    int f = 0, s = 0, g = 0;
+    int f = 0, s = 0, g = 0, nit = 0;
     for (int k = 0; k <= RMIPS_KMAX_LIMIT + 1; ++k) {
       first[k] = f;
       slot0[k] = s;
       const int h = (k >= 1 && k <= RMIPS_KMAX_LIMIT) ? b.hist[k] : 0;
       if (h > 0) {
         const int tiles = (h + MQ_TQ - 1) / MQ_TQ;
+        if (b.gitem) {                               // tensor-core items: chunks of 128 queries
+          b.gitem[g] = nit;
+          for (int t = 0; t * 128 < h; ++t) b.itemg[nit++] = make_int2(g, t);
+        }
         b.grp[g++] = make_int4(k, s, h, tiles);
         f += h;
         s += tiles * MQ_TQ;
       }
     }
+    if (b.gitem) b.gitem[RMIPS_KMAX_LIMIT + 1] = nit;
     for (; g <= RMIPS_KMAX_LIMIT; ++g) b.grp[g] = make_int4(0, s, 0, 0);   // empty groups; .y = total slots
   }
   __syncthreads();
@@ -1157,6 +1177,7 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
       b.bk[slot0[k] + r] = k;
       b.bqn[slot0[k] + r] = 0.f;
       b.beps[slot0[k] + r] = 0.f;
+      if (b.bcq) b.bcq[slot0[k] + r] = make_float2(0.f, 0.f);
     }
   }
 }
@@ -1186,7 +1207,7 @@ __global__ void __launch_bounds__(RUN) k_mprep_runs(Batch b) {
 // (d) grid: the final sorted position of each key is its position in its run
 // plus, for every other run, the number of keys below it (keys are distinct),
 // found by binary search; the position gives the query's slot in its k-group.
-__global__ void k_mprep_place(Batch b, int nruns) {
+__global__ void k_mprep_place(Common c, Batch b, int nruns) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= (int64_t)nruns * RUN) return;
   const unsigned long long key = b.runs[g];
@@ -1208,12 +1229,19 @@ __global__ void k_mprep_place(Batch b, int nruns) {
   const int slot = b.gslot0[k] + (int)(rank - b.gfirst[k]);
   b.bidx[slot] = j;
   b.bk[slot] = k;
-  b.bqn[slot] = b.dqn[j];
-  b.beps[slot] = b.deps[j];
+  const float qn = b.dqn[j], eps = b.deps[j];
+  b.bqn[slot] = qn;
+  b.beps[slot] = eps;
+  if (b.bcq) {        // tensor-core error bound of (u, this query): ||u|| x + y, x = err ||q||,
+                      // y covers operands below the normal range (||u|| <= ||u_0||)
+    const float err = tc_rel_err(b.tc_kind);
+    const float tiny = (c.d + 2) * tc_abs_unit(b.tc_kind);
+    b.bcq[slot] = make_float2(__fmul_ru(qn, err), __fmaf_ru(__fadd_ru(qn, c.unorm[0]), tiny, eps));
+  }
 }
 
-// (e) grid: gather the query vectors into slot order (zeros in padding), row
-// major for the CUDA-core path and in 64-query UMMA tiles for tensor cores.
+// (e) grid, CUDA-core path: gather the query vectors into slot order, row
+// major (zeros in padding).
 __global__ void k_mprep_c(Common c, Batch b) {
   const int total_slots = b.grp[RMIPS_KMAX_LIMIT].y;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1222,20 +1250,55 @@ __global__ void k_mprep_c(Common c, Batch b) {
     const int j = b.bidx[slot];
     b.bq[e] = j >= 0 ? b.dq[(int64_t)j * c.d + i] : 0.f;
   }
-  if (b.bqt) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)total_slots * TC_K; e += stride) {
-      const int slot = (int)(e / TC_K), k = (int)(e - (int64_t)slot * TC_K);
-      const int j = b.bidx[slot];
-      const float v = (j >= 0 && k < c.d) ? b.dq[(int64_t)j * c.d + k] : 0.f;
-      const size_t tile = (size_t)(slot / MQ_TQ);
-      if (b.bqt_kind == TCK_TF32) {
-        reinterpret_cast<float*>(b.bqt + tile * (MQ_TQ * TC_K * 4) + tc_off(slot % MQ_TQ, k))[0] = v;
-      } else {
-        unsigned char* dst = b.bqt + tile * (MQ_TQ * TC_K * 2) + tc_off16(slot % MQ_TQ, k);
-        if (b.bqt_kind == TCK_BF16) *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
-        else *reinterpret_cast<__half*>(dst) = __float2half_rn(v);
+}
+
+// (f) one CTA per tensor-core item: the item's 128 query rows in the UMMA
+// operand layout (K padded to 64 with zeros; rows past the group are zero),
+// then their 128 (error scale, slack) pairs and 128 query indices (-1 past the
+// group), contiguous so that one bulk copy moves the whole item.
+__host__ __device__ constexpr uint32_t ws_pack_bytes(int kind) {
+  return 128u * TC_K * (kind == TCK_TF32 ? 4u : 2u) + 128u * 12u;
+}
+__global__ void __launch_bounds__(256) k_mprep_items(Common c, Batch b) {
+  const int p = blockIdx.x;
+  if (p >= b.gitem[RMIPS_KMAX_LIMIT + 1]) return;
+  const int2 it = b.itemg[p];
+  const int4 G = b.grp[it.x];
+  const int r0 = it.y * 128;                       // first query of the item within its group
+  const uint32_t esz = b.tc_kind == TCK_TF32 ? 4u : 2u;
+  unsigned char* dst = b.bitems + (size_t)p * ws_pack_bytes(b.tc_kind);
+  const int per = 16 / (int)esz;                   // values per 16-byte chunk
+  for (int e = threadIdx.x; e < 128 * (int)(TC_K / per); e += blockDim.x) {
+    const int r = e & 127, k0 = (e >> 7) * per;
+    const bool live = r0 + r < G.z;
+    const int j = live ? b.bidx[G.y + r0 + r] : -1;
+    const float* q = b.dq + (int64_t)(j < 0 ? 0 : j) * c.d;
+    if (esz == 4) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = (j >= 0 && k0 + i < c.d) ? q[k0 + i] : 0.f;
+      *reinterpret_cast<float4*>(dst + tc_off(r, k0)) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+      uint16_t h[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float v = (j >= 0 && k0 + i < c.d) ? q[k0 + i] : 0.f;
+        h[i] = b.tc_kind == TCK_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
       }
+      uint4 w;
+      w.x = h[0] | ((uint32_t)h[1] << 16);
+      w.y = h[2] | ((uint32_t)h[3] << 16);
+      w.z = h[4] | ((uint32_t)h[5] << 16);
+      w.w = h[6] | ((uint32_t)h[7] << 16);
+      *reinterpret_cast<uint4*>(dst + tc_off16(r, k0)) = w;
     }
+  }
+  float2* cq = reinterpret_cast<float2*>(dst + 128u * TC_K * esz);
+  int* qj = reinterpret_cast<int*>(cq + 128);
+  for (int r = threadIdx.x; r < 128; r += blockDim.x) {
+    const bool live = r0 + r < G.z;
+    cq[r] = live ? b.bcq[G.y + r0 + r] : make_float2(0.f, 0.f);
+    qj[r] = live ? b.bidx[G.y + r0 + r] : -1;
   }
 }
 
@@ -1645,72 +1708,177 @@ __global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
 }
 
 
-// ===========================================================================
-// Batched filter on tensor cores (TF32, d <= 64).
-//
-// Same work decomposition as k_mfilter: a CTA owns a tile of 128 users, finds
-// the Lemma 3 prefix of every k-group for every block of the tile, and skips
-// the tile when nothing survives.  The users are written once into shared
-// memory in the UMMA layout (K padded to 64 with zeros); the surviving
-// 64-query tiles (laid out the same way by k_mprep) arrive by 1-D TMA, one
-// ahead.  Thread 0 issues the 8 tcgen05.mma (128 x 64 x 8, TF32 in, FP32
-// accumulate in TMEM) of a tile; every thread owns one user row, copies its
-// 64 accumulators from TMEM into registers, after which the next tile's MMA
-// runs while the row is classified (Lemma 1, then hi_k / Lemma 2).
-//
-// Error bound of a TF32 inner product: each operand is within 2^-10 of its
-// float32 value (10 fraction bits, any rounding), each product of two TF32
-// values is exact in float32, and the float32 accumulation over K = 64 terms
-// (8 chained MMAs) is charged 65 * 2^-22 relative to sum |a_i b_i|; with
-// sum |a_i b_i| <= ||u|| ||q|| the bound is TC_ERR ||u|| ||q|| plus the
-// slack of operands below the normal range.
-// ===========================================================================
+// Tile shapes of the batched tensor-core filter: user tiles of 128 rows (MMA
+// M); query tiles of 64 slots as k_mprep lays them out, multiplied two at a
+// time (MMA N up to 128); an epilogue warp owns 32 users x 64 queries.
 constexpr int TCU = 128;                       // users per tile (MMA M)
-constexpr int TCQ = MQ_TQ;                     // queries per tile (MMA N)
-constexpr int TC_THREADS = 256;                // 8 warps: warp w and w + 4 share TMEM lanes 32 (w % 4) ...
-constexpr int TC_HALF = TCQ / 2;               // ... and split the 64 query columns in halves
+constexpr int TCQ = MQ_TQ;                     // queries per laid-out tile
+constexpr int WS_N = 2 * TCQ;                  // queries per item (largest MMA N)
 __host__ __device__ constexpr uint32_t tc_esize(int kind) { return kind == TCK_TF32 ? 4u : 2u; }
 __host__ __device__ constexpr uint32_t tc_tile_bytes(int kind) { return TCQ * TC_K * tc_esize(kind); }
 __host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K * tc_esize(kind); }
 
-template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b, const unsigned char* __restrict__ bqt,
-                                                               int ngroups) {
-  constexpr uint32_t TC_TILE_BYTES = tc_tile_bytes(KIND);   // one query tile
-  constexpr uint32_t TC_A_BYTES = tc_a_bytes(KIND);         // one user tile
+// ===========================================================================
+// Batched filter on tensor cores, warp-specialized.
+//
+// One persistent CTA per SM walks user tiles of 128 rows (round robin over the
+// tiles).  The work of a tile is a list of items, one per (k-group, chunk of
+// up to 128 queries) that Lemma 3 keeps for at least one block of the tile;
+// the MMA's N is the chunk's query count rounded up to 16.  Four roles run as
+// a pipeline joined by mbarriers only:
+//   loader   (warp 8)   reads the tile's Lemma 3 prefixes (k_mprefix), skips a
+//                       tile with no item, copies the users' norms and (lo, hi)
+//                       bounds into one of two tile slots and starts the bulk
+//                       copy of the pre-tiled user rows;
+//   feeder   (warp 9)   bulk-copies each item's query rows, error constants
+//                       and query indices into a ring of stages;
+//   mma      (warp 10)  one thread issues the 128 x N x K MMAs of an item into
+//                       one of WS_NACC TMEM accumulator stages and commits;
+//   epilogue (warps 0-7) warp w reads TMEM lanes 32 (w % 4) .. +31 and
+//                       columns 64 (w / 4) .. +63 of a stage, frees the stage
+//                       and classifies its 32 users x 64 queries (Lemma 1, then
+//                       hi_k or Lemma 2), as k_mfilter does.
+// K is rounded up to the MMA's K step (8 for TF32, 16 for BF16 / FP16), not to
+// 64: the zero padding past d contributes nothing.  Every wait is bounded: on
+// a timeout the CTA raises a flag, each role leaves its loop, waits for its
+// copies in flight, and TMEM is freed.
+// ===========================================================================
+constexpr int WS_EPI = 8;                              // epilogue warps
+constexpr int WS_LOADER = 8, WS_FEEDER = 9, WS_MMA = 10;   // MMA warps 10 and 11 take even / odd items
+constexpr int WS_THREADS = 12 * 32;
+constexpr int WS_NACC = 4;                             // TMEM accumulator stages of WS_N columns
+constexpr int WS_MAXNS = 6;                            // query stages at most
+constexpr int WS_LG = 4;                               // groups per tile whose bounds are staged
+constexpr int WS_ECOLS = 64;                           // query columns per epilogue warp
+enum : int { WI_LAST = 1, WI_END = 2, WI_NEWGROUP = 4 };
+
+struct WsTile {                                        // one tile slot, written by the loader
+  long long u0;
+  int nvalid, ngact, end, seq;
+  int k[RMIPS_KMAX_LIMIT];                             // k of each active group
+  int item0[RMIPS_KMAX_LIMIT];                         // first packed item of each active group
+  int gmax[RMIPS_KMAX_LIMIT];                          // largest prefix over the tile's blocks
+  int pre[RMIPS_KMAX_LIMIT][4];                        // prefix of each block of the tile
+};
+struct WsItem {                                        // one accumulator stage, written by the mma warp
+  int ab, ga, t, stage, flags;
+};
+
+size_t ws_smem_bytes(int kind, int ns) {
+  return 2 * (size_t)tc_a_bytes(kind) + (size_t)ns * ws_pack_bytes(kind) + 2 * (size_t)WS_LG * TCU * 8 +
+         2 * (size_t)TCU * 4;
+}
+
+// Lemma 3 prefix of every (block, k-group): the leading queries of the group
+// (descending norm) whose bound fl_up(h qn) is not below the block's LB.
+__global__ void k_mprefix(Common c, Batch b, int ngroups) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= c.nb * ngroups) return;
+  const int64_t blk = e / ngroups;
+  const int g = (int)(e - blk * ngroups);
+  const int4 G = b.grp[g];
+  int r = 0;
+  if (G.z > 0) r = lemma3_prefix(b.bqn, G.y, G.z, c.hdr[blk], c.LB[(int64_t)(G.x - 1) * c.nb + blk]);
+  b.gpre[e] = r;
+}
+
+// Queries of item t of a group whose tile prefix is gmax, rounded up to the
+// MMA's N granularity (16).
+__device__ __forceinline__ int ws_item_n(int gmax, int t) {
+  const int q = min(WS_N, gmax - t * WS_N);
+  return (q + 15) & ~15;
+}
+
+// Lemma 1 / hi_k / Lemma 2 classification of up to 32 accumulators v of one
+// user against the queries of cq / qj (live leading ones); yes and undecided
+// pairs are appended to the pair lists.
+__device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, const float* v, int live, float thr,
+                                            float un, float2 L, int k, const float2* cq, const int* qj, int64_t pos,
+                                            long long& st_yes, long long& st_todo) {
+  uint32_t hit = 0;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) hit |= (v[q] >= thr ? 1u : 0u) << q;
+  if (live < 32) hit &= (1u << live) - 1u;
+  if (!hit) return;
+  const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
+  uint32_t ym = 0, tm = 0;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    if ((hit >> q) & 1u) {
+      const float2 e2 = cq[q];
+      const float e = __fmaf_ru(un, e2.x, e2.y);
+      if (!(__fadd_ru(v[q], e) < L.x)) {                              // not decided no by Lemma 1
+        const float lo = __fsub_rd(v[q], e);
+        const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
+        if (yes) ym |= 1u << q; else tm |= 1u << q;
+      }
+    }
+  }
+  while (ym) {
+    const int q = __ffs(ym) - 1;
+    ym &= ym - 1;
+    const int j = qj[q];
+    if (!in_segment(c, b, j, pos)) continue;
+    const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+    if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
+    atomicAdd(&b.qcnt[j], 1);
+    ++st_yes;
+  }
+  while (tm) {
+    const int q = __ffs(tm) - 1;
+    tm &= tm - 1;
+    const int j = qj[q];
+    if (!in_segment(c, b, j, pos)) continue;
+    const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
+    if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
+    else set_status(c.ctr, ST_INTERNAL);
+    ++st_todo;
+  }
+}
+
+template <int KIND, int NSTEP, bool PROF>
+__global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b, const unsigned char* __restrict__ qtc,
+                                                               int ngroups, int ns) {
+  constexpr uint32_t TILE = tc_tile_bytes(KIND);
+  constexpr uint32_t ABYTES = tc_a_bytes(KIND);
   constexpr uint32_t SBO = KIND == TCK_TF32 ? TC_SBO : TC_SBO16;
-  constexpr uint32_t NSTEP = TC_K * tc_esize(KIND) / 32;    // MMAs per tile (32 bytes of K each)
-  constexpr float TC_ERR = tc_rel_err(KIND);
-  extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* sA = tsm;
-  unsigned char* sB = tsm + TC_A_BYTES;                      // 2 query tiles
-  __shared__ __align__(8) uint64_t bar_b[2];     // query tile landed
-  __shared__ __align__(8) uint64_t bar_m;        // MMA done
+  constexpr int KSTEP = 32 / (int)tc_esize(KIND);     // K of one MMA
+  static_assert(NSTEP * KSTEP <= (int)TC_K, "K steps beyond the padded tile");
+  constexpr uint32_t PACK = ws_pack_bytes(KIND);      // one stage: an item as k_mprep_items packs it
+  constexpr uint32_t BROWS = 2 * TILE;                 // its query rows; then WS_N (scale, slack), WS_N indices
+  static_assert(PACK % 16 == 0 && BROWS == (uint32_t)WS_N * TC_K * tc_esize(KIND), "item layout");
+  extern __shared__ __align__(1024) unsigned char wsm[];
+  unsigned char* sA = wsm;                             // 2 user tiles
+  unsigned char* sB = sA + 2 * ABYTES;                 // ns packed items
+  float2* sL = reinterpret_cast<float2*>(sB + (size_t)ns * PACK);
+  float* sUN = reinterpret_cast<float*>(sL + 2 * WS_LG * TCU);
+  __shared__ WsTile tinfo[2];
+  __shared__ WsItem items[WS_NACC];
+  __shared__ int4 sgrp[RMIPS_KMAX_LIMIT];
+  __shared__ int sgi[RMIPS_KMAX_LIMIT];
+  __shared__ int lpre[RMIPS_KMAX_LIMIT][4];
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[WS_MAXNS], bempty[WS_MAXNS];
+  __shared__ __align__(8) uint64_t tfull[WS_NACC], tempty[WS_NACC], mdone[2];
   __shared__ uint32_t taddr_s;
-  __shared__ float un_s[TCU];
-  __shared__ float2 cq_s[2][TCQ];                // (error scale, absolute slack) per query of a tile
-  __shared__ int qj_s[2][TCQ];
-  __shared__ int pre[RMIPS_KMAX_LIMIT][4];
-  __shared__ int gmax[RMIPS_KMAX_LIMIT];
-  __shared__ int any_tile, s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int uu = tid & (TCU - 1);                // this thread's user row (TMEM lane)
-  const int half = tid >> 7;                     // which 32 query columns
-  const int d = c.d;
-  const int64_t n = c.n;
-  const int sub = c.bs < TCU ? c.bs : TCU;
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sub = c.bs < TCU ? c.bs : TCU;             // users per block inside a tile
   const int nbt = TCU / sub;
-  const float un0 = c.unorm[0];                  // largest user norm (users are sorted)
-  const float tiny = (d + 2) * tc_abs_unit(KIND);            // operands below the normal range
 
   if (warp == 0) {
-    tmem_alloc(&taddr_s, 64);
+    tmem_alloc(&taddr_s, WS_NACC * WS_N);
     tmem_relinquish();
   }
+  if (tid < ngroups) {
+    sgrp[tid] = b.grp[tid];
+    sgi[tid] = b.gitem[tid];
+  }
   if (tid == 0) {
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
-    mbar_init(&bar_m, 1);
+    for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], WS_EPI); }
+    for (int i = 0; i < ns; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], WS_EPI); }
+    for (int i = 0; i < WS_NACC; ++i) { mbar_init(&tfull[i], 2); mbar_init(&tempty[i], WS_EPI); }
+    mbar_init(&mdone[0], 1);
+    mbar_init(&mdone[1], 1);
     fence_mbar_init();
     s_fail = 0;
   }
@@ -1718,264 +1886,364 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_mfilter_tc(Common c, Batch b,
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = taddr_s;
-  const uint32_t tlane = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * TC_HALF);
-  const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, TCQ) : tc_idesc_f16(TCU, TCQ, KIND == TCK_BF16);
-  auto mma = [&](uint32_t bbase) {                 // one 128 x 64 x 64 tile, thread 0
-    for (uint32_t s = 0; s < NSTEP; ++s) {
-      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, SBO);
-      const uint64_t bd = tc_sdesc(bbase + s * 2 * TC_LBO, TC_LBO, SBO);
-      if (KIND == TCK_TF32) tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
-      else tc_mma_f16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+  // Warp-uniform bounded wait: one probe first; on a miss, a loop that gives
+  // up after ~2^31 clocks or as soon as another role has failed.  False for
+  // the whole warp on failure.  With PROF the cycles spent go to *spent.
+  auto wwait = [&](uint64_t* bar, uint32_t parity, long long* spent) -> bool {
+    long long t0 = 0;
+    if (PROF) t0 = clock64();
+    bool ok = __all_sync(FULL, mbar_try_wait(bar, parity));
+    if (!ok) {
+      const long long t1 = clock64();
+      bool mine = false;
+      while (!(mine = mbar_try_wait(bar, parity)))
+        if (s_fail || clock64() - t1 > (1ll << 31)) break;
+      ok = __all_sync(FULL, mine);
+      if (!ok) s_fail = 1;
     }
-    tc_commit(&bar_m);
+    if (PROF) *spent += clock64() - t0;
+    return ok;
   };
-  uint32_t phb = 0, ph_m = 0;                    // parity of the next wait: bit x for bar_b[x] / bar_m
-  long long st_pairs = 0, st_skipped = 0, st_yes = 0, st_todo = 0;
+  long long t_start = 0;
+  if (PROF) t_start = clock64();
+  long long w_a = 0, w_b = 0;                          // this role's wait cycles (PROF)
+  auto report = [&](int wait_a, int wait_b, int total) {
+    if (!PROF || lane != 0) return;
+    atomicAdd(&b.wst[wait_a], (unsigned long long)w_a);
+    if (wait_b >= 0) atomicAdd(&b.wst[wait_b], (unsigned long long)w_b);
+    atomicAdd(&b.wst[total], (unsigned long long)(clock64() - t_start));
+  };
 
-  for (int64_t u0 = (int64_t)blockIdx.x * TCU; u0 < n && !s_fail; u0 += (int64_t)gridDim.x * TCU) {
-    // 1. Lemma 3 prefixes
-    if (tid < ngroups * nbt) {
-      const int g = tid / nbt, sb = tid - g * nbt;
-      const int64_t ufirst = u0 + (int64_t)sb * sub;
-      int r = 0;
-      const int4 G = b.grp[g];
-      if (ufirst < n && G.z > 0) {
-        const int64_t blk = ufirst / c.bs;
-        r = lemma3_prefix(b.bqn, G.y, G.z, c.hdr[blk], c.LB[(int64_t)(G.x - 1) * c.nb + blk]);
+  if (warp == WS_LOADER) {
+    // ---------------------------------------------------------------- loader
+    const int64_t ntiles = (c.n + TCU - 1) / TCU;
+    long long st_pairs = 0, st_skipped = 0, st_active = 0;
+    uint32_t fpar = 0, fused = 0;           // per slot: parity of its fill count, filled at least once
+    int ab = 0, seq = 0;
+    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+      if (s_fail) break;
+      const int64_t u0 = tt * TCU;
+      const int nvalid = (int)((c.n - u0) < TCU ? (c.n - u0) : TCU);
+      for (int e = lane; e < ngroups * nbt; e += 32) {
+        const int g = e / nbt, sb = e - g * nbt;
+        const int64_t uf = u0 + (int64_t)sb * sub;
+        lpre[g][sb] = (uf < c.n && sgrp[g].z > 0) ? b.gpre[(uf / c.bs) * ngroups + g] : 0;
       }
-      pre[g][sb] = r;
-    }
-    __syncthreads();
-    if (tid < ngroups) {
-      int mx = 0;
-      for (int sb = 0; sb < nbt; ++sb) mx = max(mx, pre[tid][sb]);
-      gmax[tid] = mx;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      int a = 0;
-      for (int g = 0; g < ngroups; ++g) a |= gmax[g];
-      any_tile = a;
-    }
-    __syncthreads();
-    if (!any_tile) {
-      if (tid == 0) st_skipped += 1;
-      continue;
-    }
-    const int64_t nvalid = (n - u0) < TCU ? (n - u0) : TCU;
-    // 2. user tile into the UMMA layout: one 16-byte chunk (4 consecutive k of
-    //    one row) per store, consecutive threads on consecutive rows
-    if (KIND == TCK_TF32) {
-      const float* src = c.Qs + u0 * d;
-      for (int e = tid; e < TCU * (int)(TC_K / 4); e += TC_THREADS) {
-        const int r = e & (TCU - 1), k0 = (e >> 7) * 4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < nvalid) {
-          const float* row = src + (int64_t)r * d;
-          if (k0 + 0 < d) v.x = row[k0 + 0];
-          if (k0 + 1 < d) v.y = row[k0 + 1];
-          if (k0 + 2 < d) v.z = row[k0 + 2];
-          if (k0 + 3 < d) v.w = row[k0 + 3];
-        }
-        *reinterpret_cast<float4*>(sA + tc_off(r, k0)) = v;
-      }
-    } else {                                       // the index's 16-bit copy, 8 values per chunk
-      const uint16_t* src = reinterpret_cast<const uint16_t*>(c.Qrows) + u0 * d;
-      for (int e = tid; e < TCU * (int)(TC_K / 8); e += TC_THREADS) {
-        const int r = e & (TCU - 1), k0 = (e >> 7) * 8;
-        uint16_t h[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) h[i] = (r < nvalid && k0 + i < d) ? src[(int64_t)r * d + k0 + i] : (uint16_t)0;
-        uint4 v;
-        v.x = h[0] | ((uint32_t)h[1] << 16);
-        v.y = h[2] | ((uint32_t)h[3] << 16);
-        v.z = h[4] | ((uint32_t)h[5] << 16);
-        v.w = h[6] | ((uint32_t)h[7] << 16);
-        *reinterpret_cast<uint4*>(sA + tc_off16(r, k0)) = v;
-      }
-    }
-    if (tid < TCU) un_s[tid] = tid < nvalid ? c.unorm[u0 + tid] : 0.f;
-    if (tid == 0) {
-      for (int g = 0; g < ngroups; ++g)
+      __syncwarp();
+      int gm = 0;
+      if (lane < ngroups) {
         for (int sb = 0; sb < nbt; ++sb) {
-          const int64_t us = (int64_t)sb * sub;
-          const int64_t cnt = nvalid - us < sub ? (nvalid - us > 0 ? nvalid - us : 0) : sub;
-          st_pairs += (long long)pre[g][sb] * cnt;
+          const int p = lpre[lane][sb];
+          gm = max(gm, p);
+          const int cnt = min(sub, max(0, nvalid - sb * sub));
+          st_pairs += (long long)p * cnt;
         }
+      }
+      const unsigned act = __ballot_sync(FULL, gm > 0);
+      if (!act) {
+        ++st_skipped;
+        __syncwarp();
+        continue;
+      }
+      if (!wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a)) break;
+      WsTile& T = tinfo[ab];
+      if (gm > 0) {
+        const int ga = __popc(act & ((1u << lane) - 1u));
+        T.k[ga] = sgrp[lane].x;
+        T.item0[ga] = sgi[lane];
+        T.gmax[ga] = gm;
+        for (int sb = 0; sb < 4; ++sb) T.pre[ga][sb] = sb < nbt ? lpre[lane][sb] : 0;
+      }
+      if (lane == 0) {
+        T.u0 = u0;
+        T.nvalid = nvalid;
+        T.ngact = __popc(act);
+        T.end = 0;
+        T.seq = seq;
+      }
+      for (int r = lane; r < TCU; r += 32) sUN[ab * TCU + r] = r < nvalid ? c.unorm[u0 + r] : 0.f;
+      __syncwarp();
+      const int nstage = min(__popc(act), WS_LG);          // further groups' bounds are read from memory
+      for (int ga = 0; ga < nstage; ++ga) {
+        const float2* src = c.Lb + (int64_t)(T.k[ga] - 1) * c.n + u0;
+        float2* dst = sL + ((size_t)ab * WS_LG + ga) * TCU;
+        for (int r = lane; r < TCU; r += 32) dst[r] = r < nvalid ? src[r] : make_float2(kInf, kInf);
+      }
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&afull[ab], ABYTES);
+        bulk_g2s(sA + (size_t)ab * ABYTES, qtc + (size_t)tt * ABYTES, ABYTES, &afull[ab]);
+      }
+      fpar ^= 1u << ab;
+      fused |= 1u << ab;
+      ab ^= 1;
+      ++seq;
+      ++st_active;
     }
-    fence_proxy_async();
-    // 3. walk the (group, query tile) items of this user tile
-    int nitems = 0;
-    for (int g = 0; g < ngroups; ++g) nitems += (gmax[g] + TCQ - 1) / TCQ;
-    int g_ld = 0, t_ld = 0;                       // next item to load
-    auto advance = [&](int& g, int& t) {
-      ++t;
-      while (g < ngroups && t >= (gmax[g] + TCQ - 1) / TCQ) { ++g; t = 0; }
-    };
-    while (g_ld < ngroups && gmax[g_ld] == 0) ++g_ld;
-    auto load_item = [&](int g, int t, int buf) {
-      const int s0 = b.grp[g].y + t * TCQ;
-      if (tid == 0) {
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&bar_b[buf], TC_TILE_BYTES);
-        bulk_g2s(sB + (size_t)buf * TC_TILE_BYTES, bqt + (size_t)(s0 / TCQ) * TC_TILE_BYTES, TC_TILE_BYTES,
-                 &bar_b[buf]);
+    if (!s_fail && wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a)) {  // end marker
+      if (lane == 0) {
+        tinfo[ab].end = 1;
+        __threadfence_block();
+        mbar_arrive(&afull[ab]);
       }
-      if (tid < TCQ) {
-        const float qn = b.bqn[s0 + tid];
-        cq_s[buf][tid] = make_float2(__fmul_ru(qn, TC_ERR), __fmaf_ru(__fadd_ru(qn, un0), tiny, b.beps[s0 + tid]));
-        qj_s[buf][tid] = b.bidx[s0 + tid];
-      }
-    };
-    int g_cur = g_ld, t_cur = 0;
-    load_item(g_ld, 0, 0);
-    advance(g_ld, t_ld);
-    __syncthreads();                               // user tile written, constants of item 0 visible
-    if (tid == 0) {                                // MMA(0)
-      if (mbar_wait_bounded(&bar_b[0], phb & 1u)) {
-        tc_fence_after();
-        mma(smem_u32(sB));
-      } else {
-        s_fail = 1;
-      }
+      fpar ^= 1u << ab;
+      fused |= 1u << ab;
     }
-    phb ^= 1u;
-    int g_L = -1;                                  // group whose bounds are in L
-    float2 L = make_float2(kInf, kInf);
-    for (int it = 0; it < nitems; ++it) {
-      const int buf = it & 1;
-      // A. prefetch the next query tile (its buffer's last reader, MMA(it-1), is done)
-      const bool has_next = it + 1 < nitems;
-      if (has_next) load_item(g_ld, t_ld, buf ^ 1);
-      // B. wait for MMA(it); copy this thread's 32 accumulators out of TMEM
-      bool ok = s_fail ? false : mbar_wait_bounded(&bar_m, ph_m);
-      ph_m ^= 1u;
-      ok = __syncthreads_and(ok && !s_fail);
-      if (!ok) {
-        if (tid == 0) s_fail = 1;
-        break;
-      }
-      tc_fence_after();
-      float acc[TC_HALF];
-      tmem_ld16(tlane, acc);
-      tmem_ld16(tlane + 16, acc + 16);
-      tmem_ld_wait();
-      if (g_cur != g_L) {                          // this user's (lo, hi) for the group's k
-        L = uu < nvalid ? c.Lb[(int64_t)(b.grp[g_cur].x - 1) * n + u0 + uu] : make_float2(kInf, kInf);
-        g_L = g_cur;
-      }
-      tc_fence_before();
-      __syncthreads();                             // TMEM consumed; next constants visible
-      // C. MMA(it + 1) overlaps the epilogue below
-      if (has_next && tid == 0) {
-        if (mbar_wait_bounded(&bar_b[buf ^ 1], (phb >> (buf ^ 1)) & 1u)) {
-          tc_fence_after();
-          mma(smem_u32(sB) + (uint32_t)(buf ^ 1) * TC_TILE_BYTES);
-        } else {
-          s_fail = 1;
-        }
-      }
-      if (has_next) phb ^= 1u << (buf ^ 1);
-      // D. epilogue: (this user, 32 queries of item it)
-      int live = pre[g_cur][uu / sub] - t_cur * TCQ - half * TC_HALF;
-      live = live < 0 ? 0 : (live > TC_HALF ? TC_HALF : live);
-      if (uu >= nvalid) live = 0;
-      const float un = un_s[uu];
-      // Fast Lemma 1: slots are in descending norm, so the tile's first query
-      // carries the largest error scale and slack; with e_u >= e(u, q) for
-      // every q of the tile, acc < lo_k - e_u (rounded down) proves "no".
-      const float2 c0 = cq_s[buf][0];
-      const float thr = __fsub_rd(L.x, __fmaf_ru(un, c0.x, c0.y));
-      uint32_t hit = 0;
-      if (live == TC_HALF) {                       // fast path: the row maximum decides alone
-        float m0 = acc[0], m1 = acc[1], m2 = acc[2], m3 = acc[3];
-#pragma unroll
-        for (int q = 4; q < TC_HALF; q += 4) {
-          m0 = fmaxf(m0, acc[q]);
-          m1 = fmaxf(m1, acc[q + 1]);
-          m2 = fmaxf(m2, acc[q + 2]);
-          m3 = fmaxf(m3, acc[q + 3]);
-        }
-        if (fmaxf(fmaxf(m0, m1), fmaxf(m2, m3)) >= thr) {
-#pragma unroll
-          for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
-        }
-      } else if (live > 0) {
-#pragma unroll
-        for (int q = 0; q < TC_HALF; ++q) hit |= (acc[q] >= thr ? 1u : 0u) << q;
-        hit &= (1u << live) - 1u;
-      }
-      uint32_t ym = 0, tm = 0;
-      if (hit) {
-        const int k = b.grp[g_cur].x;
-        const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
-#pragma unroll
-        for (int q = 0; q < TC_HALF; ++q) {
-          if ((hit >> q) & 1u) {
-            const float2 cq = cq_s[buf][half * TC_HALF + q];
-            const float e = __fmaf_ru(un, cq.x, cq.y);
-            if (!(__fadd_ru(acc[q], e) < L.x)) {                  // not decided no by Lemma 1
-              const float lo = __fsub_rd(acc[q], e);
-              const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
-              if (yes) ym |= 1u << q; else tm |= 1u << q;
-            }
+    for (int x = 0; x < 2; ++x)                                       // copies in flight
+      if ((fused >> x) & 1u) mbar_wait_bounded(&afull[x], ((fpar >> x) & 1u) ^ 1u);
+    for (int o = 16; o > 0; o >>= 1) st_pairs += __shfl_xor_sync(FULL, st_pairs, o);
+    if (lane == 0) {
+      atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)st_pairs);
+      atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)st_skipped);
+    }
+    report(WST_LOADER_WAIT, -1, WST_LOADER);
+    if (PROF && lane == 0) atomicAdd(&b.wst[WST_ACTIVE], (unsigned long long)st_active);
+  } else if (warp == WS_FEEDER) {
+    // ---------------------------------------------------------------- feeder
+    uint32_t wpar = 0;                      // per slot: parity of the next wait
+    uint32_t epar = 0;                      // per stage: uses so far (parity)
+    uint32_t armed = 0;                     // per stage: a copy was started
+    int stg = 0, ab = 0;
+    for (;;) {
+      if (!wwait(&afull[ab], (wpar >> ab) & 1u, &w_b)) break;
+      wpar ^= 1u << ab;
+      const WsTile& T = tinfo[ab];
+      if (T.end) break;
+      bool ok = true;
+      for (int ga = 0; ga < T.ngact && ok; ++ga) {
+        const int gmax = T.gmax[ga], item0 = T.item0[ga];
+        const int nt = (gmax + WS_N - 1) / WS_N;
+        for (int t = 0; t < nt; ++t) {
+          if (!wwait(&bempty[stg], ((epar >> stg) & 1u) ^ 1u, &w_a)) { ok = false; break; }
+          epar ^= 1u << stg;
+          if (lane == 0) {                     // one bulk copy per item: each costs the same up to 64 KB
+            mbar_arrive_expect_tx(&bfull[stg], PACK);
+            bulk_g2s(sB + (size_t)stg * PACK, b.bitems + (size_t)(item0 + t) * PACK, PACK, &bfull[stg]);
           }
+          armed |= 1u << stg;
+          stg = stg + 1 == ns ? 0 : stg + 1;
         }
       }
-      while (ym) {
-        const int q = __ffs(ym) - 1;
-        ym &= ym - 1;
-        const int j = qj_s[buf][half * TC_HALF + q];
-        if (!in_segment(c, b, j, u0 + uu)) continue;
-        const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
-        if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
-        atomicAdd(&b.qcnt[j], 1);
-        ++st_yes;
-      }
-      while (tm) {
-        const int q = __ffs(tm) - 1;
-        tm &= tm - 1;
-        const int j = qj_s[buf][half * TC_HALF + q];
-        if (!in_segment(c, b, j, u0 + uu)) continue;
-        const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
-        if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)(u0 + uu);
-        else set_status(c.ctr, ST_INTERNAL);
-        ++st_todo;
-      }
-      g_cur = g_ld;
-      t_cur = t_ld;
-      if (has_next) advance(g_ld, t_ld);
-      __syncthreads();                             // constants of item it consumed
+      if (!ok) break;
+      ab ^= 1;
     }
-    __syncthreads();
+    for (int x = 0; x < ns; ++x)                                      // copies in flight
+      if ((armed >> x) & 1u) mbar_wait_bounded(&bfull[x], ((epar >> x) & 1u) ^ 1u);
+    report(WST_FEEDER_WAIT, -1, WST_FEEDER);
+  } else if (warp == WS_MMA || warp == WS_MMA + 1) {
+    // ---------------------------------------------------------------- mma
+    // The tensor core queues almost nothing: every cycle the issuing thread
+    // spends between two MMAs (a barrier wait, loop control) leaves it idle.
+    // Two warps therefore issue alternate items -- one waits while the other
+    // issues -- and the K loop has a compile-time trip count.  Items keep the
+    // round-robin stage / accumulator order; with an even ns and WS_NACC each
+    // warp owns fixed stages and accumulators, so parities stay per warp.
+    const int me = warp - WS_MMA;
+    const uint64_t adesc0 = tc_sdesc(smem_u32(sA), TC_LBO, SBO);
+    const uint64_t adesc1 = tc_sdesc(smem_u32(sA + ABYTES), TC_LBO, SBO);
+    const uint64_t bdesc0 = tc_sdesc(smem_u32(sB), TC_LBO, SBO);
+    constexpr uint64_t BSTEP = PACK >> 4;                 // descriptor units per stage
+    uint32_t wpar = 0, fpar = 0, tpar = 0;                // parities: slots, stages, accumulators
+    int stg = 0, acc = 0, ab = 0, it = 0;
+    long long w_c = 0, n_items = 0, w_issue = 0;
+    for (;;) {
+      if (!wwait(&afull[ab], (wpar >> ab) & 1u, &w_c)) break;
+      wpar ^= 1u << ab;
+      const WsTile& T = tinfo[ab];
+      if (T.end) break;
+      const int ngact = T.ngact;
+      bool ok = true;
+      for (int ga = 0; ga < ngact && ok; ++ga) {
+        const int gmax = T.gmax[ga];
+        const int nt = (gmax + WS_N - 1) / WS_N;
+        for (int t = 0; t < nt; ++t, ++it) {
+          if ((it & 1) == me) {
+            if (!wwait(&bfull[stg], (fpar >> stg) & 1u, &w_a)) { ok = false; break; }
+            if (!wwait(&tempty[acc], ((tpar >> acc) & 1u) ^ 1u, &w_b)) { ok = false; break; }
+            fpar ^= 1u << stg;
+            tpar ^= 1u << acc;
+            long long t_is = 0;
+            if (PROF) t_is = clock64();
+            if (lane == 0) {
+              const int nq = ws_item_n(gmax, t);
+              items[acc] = WsItem{ab, ga, t, stg,
+                                  (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0)};
+              const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, (uint32_t)nq)
+                                                      : tc_idesc_f16(TCU, (uint32_t)nq, KIND == TCK_BF16);
+              const uint64_t ad0 = ab ? adesc1 : adesc0, bd0 = bdesc0 + (uint64_t)stg * BSTEP;
+              const uint32_t d = taddr + (uint32_t)(acc * WS_N);
+              tc_fence_after();
+              // one K step is 32 bytes = 2 core-matrix columns = +16 in the
+              // descriptors' 16-byte address field
+#pragma unroll
+              for (int s = 0; s < NSTEP; ++s) {
+                if (KIND == TCK_TF32) tc_mma_tf32(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
+                else tc_mma_f16(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
+              }
+              tc_commit(&tfull[acc]);
+              mbar_arrive(&tfull[acc]);
+              if (PROF) w_issue += clock64() - t_is;
+            }
+            __syncwarp();
+            ++n_items;
+          }
+          stg = stg + 1 == ns ? 0 : stg + 1;
+          acc = acc + 1 == WS_NACC ? 0 : acc + 1;
+        }
+      }
+      if (!ok) break;
+      ab ^= 1;
+    }
+    // end marker: the warp that owns the next item index writes it
+    if ((it & 1) == me && !s_fail && wwait(&tempty[acc], ((tpar >> acc) & 1u) ^ 1u, &w_b)) {
+      if (lane == 0) {
+        items[acc].flags = WI_END;
+        mbar_arrive_cnt(&tfull[acc], 2);
+      }
+    }
+    if (lane == 0) {                                                  // this warp's MMAs in flight
+      tc_commit(&mdone[me]);
+      mbar_wait_bounded(&mdone[me], 0);
+    }
+    __syncwarp();
+    if (me == 0) report(WST_MMA_WAIT_B, WST_MMA_WAIT_T, WST_MMA);
+    if (PROF && lane == 0) {
+      atomicAdd(&b.wst[WST_TILES], (unsigned long long)n_items);
+      if (me == 0) atomicAdd(&b.wst[WST_MMA_WAIT_A], (unsigned long long)w_c);
+      if (me == 0) atomicAdd(&b.wst[WST_MMA_ISSUE], (unsigned long long)w_issue);
+    }
+  } else if (warp < WS_EPI) {
+    // ---------------------------------------------------------------- epilogue
+    const int q4 = warp & 3, col = (warp >> 2) * WS_ECOLS;
+    const int uu = q4 * 32 + lane;                                    // this thread's user row
+    const uint32_t tl = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col;
+    long long st_yes = 0, st_todo = 0;
+    uint32_t tpar = 0;
+    int acc = 0;
+    // constants of the current (tile, group), reloaded on WI_NEWGROUP
+    int pre_w = 0, nvalid = 0, kq = 1;
+    long long u0 = 0;
+    float un = 0.f;
+    float2 L = make_float2(kInf, kInf);
+    for (;;) {
+      if (!wwait(&tfull[acc], (tpar >> acc) & 1u, &w_a)) break;
+      tpar ^= 1u << acc;
+      const WsItem itm = items[acc];
+      if (itm.flags & WI_END) break;
+      if (itm.flags & WI_NEWGROUP) {
+        const WsTile& T = tinfo[itm.ab];
+        pre_w = T.pre[itm.ga][(q4 * 32) / sub];
+        nvalid = T.nvalid;
+        u0 = T.u0;
+        kq = T.k[itm.ga];
+        un = sUN[itm.ab * TCU + uu];
+        L = itm.ga < WS_LG ? sL[((size_t)itm.ab * WS_LG + itm.ga) * TCU + uu]
+                           : (uu < nvalid ? c.Lb[(int64_t)(kq - 1) * c.n + u0 + uu] : make_float2(kInf, kInf));
+      }
+      // live queries of this warp's columns for its block (warp-uniform)
+      int live = pre_w - itm.t * WS_N - col;
+      live = live < 0 ? 0 : (live > WS_ECOLS ? WS_ECOLS : live);
+      float v[WS_ECOLS];
+      long long t_ld = 0;
+      if (PROF) t_ld = clock64();
+      if (live > 0) {
+        tc_fence_after();
+        tmem_ld32(tl + (uint32_t)(acc * WS_N), v);
+        if (live > 32) tmem_ld32(tl + (uint32_t)(acc * WS_N) + 32, v + 32);
+        tmem_ld_wait();
+        tc_fence_before();
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (PROF) w_b += clock64() - t_ld;
+      acc = acc + 1 == WS_NACC ? 0 : acc + 1;
+      if (uu >= nvalid) live = 0;
+      if (live > 0) {
+        const float2* cq0 = reinterpret_cast<const float2*>(sB + (size_t)itm.stage * PACK + BROWS);
+        const float2* cq = cq0 + col;
+        const int* qj = reinterpret_cast<const int*>(cq0 + WS_N) + col;
+        const int64_t pos = u0 + uu;
+        // Fast Lemma 1: the item's first query has the largest error scale
+        // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
+        const float2 c0 = cq0[0];
+        const float thr = __fsub_rd(L.x, __fmaf_ru(un, c0.x, c0.y));
+        bool any = true;
+        if (live == WS_ECOLS) {
+          float m[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) m[i] = v[i];
+#pragma unroll
+          for (int q = 8; q < WS_ECOLS; q += 8)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) m[i] = fmaxf(m[i], v[q + i]);
+          const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
+          any = mx >= thr;
+        }
+        if (any) {
+          ws_classify(c, b, v, min(live, 32), thr, un, L, kq, cq, qj, pos, st_yes, st_todo);
+          if (live > 32) ws_classify(c, b, v + 32, live - 32, thr, un, L, kq, cq + 32, qj + 32, pos, st_yes, st_todo);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&bempty[itm.stage]);
+        if (itm.flags & WI_LAST) mbar_arrive(&aempty[itm.ab]);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      st_yes += __shfl_xor_sync(FULL, st_yes, o);
+      st_todo += __shfl_xor_sync(FULL, st_todo, o);
+    }
+    if (lane == 0 && st_yes) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)st_yes);
+    if (lane == 0 && st_todo) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)st_todo);
+    if (warp == 0) report(WST_EPI_WAIT, WST_EPI_TMEM, WST_EPI);
   }
   if (s_fail && tid == 0) set_status(c.ctr, ST_TIMEOUT);
-  if (tid == 0) {
-    atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)st_pairs);
-    atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)st_skipped);
-  }
-  if (st_yes) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)st_yes);
-  if (st_todo) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)st_todo);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, 64);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, WS_NACC * WS_N);
+  }
 }
 
-cudaError_t launch_mfilter_tc(int kind, const Common& c, const Batch& b, int ngroups, int grid, size_t smem,
-                              cudaStream_t st) {
-  static thread_local bool cfg[3] = {false, false, false};
-  cudaError_t e = cudaSuccess;
-  if (!cfg[kind]) {
-    if (kind == TCK_TF32) e = cudaFuncSetAttribute(k_mfilter_tc<TCK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else if (kind == TCK_BF16) e = cudaFuncSetAttribute(k_mfilter_tc<TCK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else e = cudaFuncSetAttribute(k_mfilter_tc<TCK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int KIND, int NSTEP, bool PROF>
+cudaError_t launch_ws_one(const Common& c, const Batch& b, const unsigned char* qtc, int ngroups, int grid, int ns,
+                          size_t smem, cudaStream_t st) {
+  static thread_local size_t cfg = 0;
+  if (cfg < smem) {
+    const cudaError_t e = cudaFuncSetAttribute(k_mfilter_ws<KIND, NSTEP, PROF>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cfg[kind] = true;
+    cfg = smem;
   }
-  if (kind == TCK_TF32) k_mfilter_tc<TCK_TF32><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
-  else if (kind == TCK_BF16) k_mfilter_tc<TCK_BF16><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
-  else k_mfilter_tc<TCK_FP16><<<grid, TC_THREADS, smem, st>>>(c, b, b.bqt, ngroups);
+  k_mfilter_ws<KIND, NSTEP, PROF><<<grid, WS_THREADS, smem, st>>>(c, b, qtc, ngroups, ns);
   return cudaGetLastError();
+}
+
+// K steps of the MMA loop: the padded dimension in 32-byte steps, compiled for
+// the common cases (d <= 32, d <= 56 for TF32) and for the full 64.
+template <bool PROF>
+cudaError_t launch_ws_prof(int kind, int d, const Common& c, const Batch& b, const unsigned char* qtc, int ngroups,
+                           int grid, int ns, size_t smem, cudaStream_t st) {
+  if (kind == TCK_TF32) {
+    if (d <= 32) return launch_ws_one<TCK_TF32, 4, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+    if (d <= 56) return launch_ws_one<TCK_TF32, 7, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+    return launch_ws_one<TCK_TF32, 8, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+  }
+  if (kind == TCK_BF16) {
+    if (d <= 32) return launch_ws_one<TCK_BF16, 2, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+    return launch_ws_one<TCK_BF16, 4, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+  }
+  if (d <= 32) return launch_ws_one<TCK_FP16, 2, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+  return launch_ws_one<TCK_FP16, 4, PROF>(c, b, qtc, ngroups, grid, ns, smem, st);
+}
+
+cudaError_t launch_mfilter_ws(int kind, const Common& c, const Batch& b, const unsigned char* qtc, int ngroups,
+                              int grid, int ns, size_t smem, cudaStream_t st) {
+  return b.wst ? launch_ws_prof<true>(kind, c.d, c, b, qtc, ngroups, grid, ns, smem, st)
+               : launch_ws_prof<false>(kind, c.d, c, b, qtc, ngroups, grid, ns, smem, st);
 }
 
 rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
@@ -1991,8 +2259,20 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
     ws->cap_t = 16ll << 20;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->tpairs, ws->cap_t * sizeof(unsigned long long)));
   }
-  if (!ws->bqt && idx->d <= (int)TC_K)
-    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bqt, (size_t)MQ_SLOTS * TC_K * sizeof(float)));
+  if (!ws->bitems && idx->d <= (int)TC_K) {
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bcq, (size_t)MQ_SLOTS * sizeof(float2)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bitems, (size_t)MQ_ITEMS * ws_pack_bytes(TCK_TF32)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->gitem, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->itemg, (size_t)MQ_ITEMS * sizeof(int2)));
+  }
+  if (!ws->wst) RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->wst, WST_N * sizeof(unsigned long long)));
+  if (ws->cap_gpre < idx->nb * idx->k_max) {
+    cudaFree(ws->gpre);
+    ws->gpre = nullptr;
+    ws->cap_gpre = 0;
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->gpre, (size_t)idx->nb * idx->k_max * sizeof(int32_t)));
+    ws->cap_gpre = idx->nb * idx->k_max;
+  }
   if (!ws->keys) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->keys, MQ_MAXQ * sizeof(unsigned long long)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->runs, MQ_MAXQ * sizeof(unsigned long long)));
@@ -2076,13 +2356,17 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   rmips_status s = ensure_batch(idx, ws, want_y + 1);
   if (s != RMIPS_OK) return s;
   RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+  if (idx->prof_on == 2) RMIPS_TRY_CUDA(cudaMemsetAsync(ws->wst, 0, WST_N * sizeof(unsigned long long), st));
   const int ngroups_max = idx->k_max;
-  const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K;
+  const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K && idx->Qtc;
   const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
   const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
-  const size_t smem_tc = tc_a_bytes(tck) + 2 * tc_tile_bytes(tck);
+  int ws_ns = WS_MAXNS;                   // query stages that fit beside the user tiles and bounds
+  while (ws_ns > 2 && ws_smem_bytes(tck, ws_ns) > 220 * 1024) --ws_ns;
+  ws_ns &= ~1;                            // even: each MMA warp owns fixed stages
+  const size_t smem_ws = ws_smem_bytes(tck, ws_ns);
   const int64_t tc_tiles = (idx->n + TCU - 1) / TCU;
-  const int tc_grid = (int)(tc_tiles < sm_count * 3 ? tc_tiles : sm_count * 3);
+  const int tc_grid = (int)(tc_tiles < sm_count ? tc_tiles : sm_count);
   int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 4096);
   if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) per_sm = 1;
@@ -2101,8 +2385,13 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.ypairs = ws->ypairs; b.cap_y = ws->cap_y;
     b.tpairs = ws->tpairs; b.cap_t = ws->cap_t;
     b.seg = ws->seg;
-    b.bqt = use_tc ? reinterpret_cast<unsigned char*>(ws->bqt) : nullptr;
-    b.bqt_kind = tck;
+    b.tc_kind = tck;
+    b.bcq = use_tc ? ws->bcq : nullptr;
+    b.bitems = use_tc ? ws->bitems : nullptr;
+    b.gitem = use_tc ? ws->gitem : nullptr;
+    b.itemg = use_tc ? ws->itemg : nullptr;
+    b.gpre = ws->gpre;
+    b.wst = idx->prof_on == 2 ? ws->wst : nullptr;
     b.keys = ws->keys;
     b.runs = ws->runs;
     b.hist = ws->hist;
@@ -2121,8 +2410,10 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     k_mprep_a<<<(cnt + 255) / 256, 256, 0, st>>>(c, b, idx->precision);
     k_mprep_groups<<<1, 256, 0, st>>>(c, b);
     k_mprep_runs<<<nruns, RUN, 0, st>>>(b);
-    k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, st>>>(b, nruns);
-    k_mprep_c<<<sm_count * 4, 256, 0, st>>>(c, b);
+    k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, st>>>(c, b, nruns);
+    if (!use_tc) k_mprep_c<<<sm_count * 4, 256, 0, st>>>(c, b);
+    if (use_tc) k_mprep_items<<<MQ_ITEMS, 256, 0, st>>>(c, b);
+    if (use_tc) k_mprefix<<<(unsigned)((idx->nb * ngroups_max + 255) / 256), 256, 0, st>>>(c, b, ngroups_max);
     RMIPS_TRY_CUDA(cudaGetLastError());
     const bool prof = idx->prof_on != 0;
     if (prof) {
@@ -2134,7 +2425,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used], st));
     }
     if (use_tc) {
-      RMIPS_TRY_CUDA(launch_mfilter_tc(tck, c, b, idx->k_max, tc_grid, smem_tc, st));
+      RMIPS_TRY_CUDA(launch_mfilter_ws(tck, c, b, idx->Qtc, ngroups_max, tc_grid, ws_ns, smem_ws, st));
     } else {
       RMIPS_TRY_CUDA(mfilter_dispatch(idx, c, b, idx->k_max, fgrid, smem, st));
     }

@@ -15,6 +15,9 @@
 //   incomp uint8 [n]           1 when cand could not be proven complete
 //   LB     float [k_max][nb]   block minima of lo (Equation 1)
 //   hdr    float [nb]          upper bound of the first user's norm of each block
+//   Qtc    [ceil(n/128)]       users in 128-row tiles of the tensor-core operand
+//                              layout (K padded to 64 with zeros; TF32 = float32
+//                              bits, or the BF16 / FP16 copy), for the batched filter
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,7 +38,11 @@
 #define MQ_MAXQ 16384            // queries per multi-query pass (14-bit index)
 #define MQ_TQ 64                 // queries per tile
 #define MQ_BIG_SLOTS 256         // concurrent large-result emitters (one id bitmap each)
-#define MQ_SLOTS (MQ_MAXQ + (RMIPS_KMAX_LIMIT + 1) * MQ_TQ)
+// slots of a pass: the queries, each k-group padded to MQ_TQ, and two spare
+// tiles so that a 128-slot read starting in the last tile stays in bounds
+#define MQ_SLOTS (MQ_MAXQ + (RMIPS_KMAX_LIMIT + 3) * MQ_TQ)
+// items of the tensor-core filter: chunks of up to 128 queries of one k-group
+#define MQ_ITEMS (MQ_MAXQ / 128 + RMIPS_KMAX_LIMIT + 1)
 
 #if defined(__CUDACC__)
 #define RMIPS_HD __host__ __device__ __forceinline__
@@ -61,6 +68,13 @@ void set_error(const std::string& msg);
 
 // Device status word values (first error wins).
 enum : int { ST_OK = 0, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_INTERNAL = 8 };
+
+// Cycle counters of the tensor-core filter's roles (profiling only).
+enum : int {
+  WST_LOADER_WAIT = 0, WST_FEEDER_WAIT = 1, WST_MMA_WAIT_B = 2, WST_MMA_WAIT_T = 3, WST_EPI_WAIT = 4,
+  WST_LOADER = 5, WST_FEEDER = 6, WST_MMA = 7, WST_EPI = 8, WST_TILES = 9,
+  WST_MMA_WAIT_A = 10, WST_EPI_TMEM = 11, WST_ACTIVE = 12, WST_MMA_ISSUE = 13, WST_N = 14
+};
 
 // Per-call device counters (int64 slots).
 enum : int {
@@ -118,7 +132,6 @@ struct Workspace {
   unsigned long long* tpairs = nullptr;  // (query << 32 | position) to resolve
   int64_t cap_t = 0;
   int32_t* seg = nullptr;        // [cap_y] positions grouped by query
-  float* bqt = nullptr;          // [MQ_SLOTS / MQ_TQ][MQ_TQ * 64] query tiles, UMMA layout
   unsigned long long* keys = nullptr;  // [MQ_MAXQ] query sort keys
   unsigned long long* runs = nullptr;  // [MQ_MAXQ] keys sorted in runs of 1024
   int* gfirst = nullptr;         // [RMIPS_KMAX_LIMIT + 2] first sorted position of each k
@@ -127,6 +140,13 @@ struct Workspace {
   long long* dseglo = nullptr;   // [cap_seg] per-query id ranges of a batch
   long long* dseghi = nullptr;
   int64_t cap_seg = 0;
+  float2* bcq = nullptr;         // [MQ_SLOTS] (error scale, absolute slack) of each slot
+  unsigned char* bitems = nullptr;  // [MQ_ITEMS] packed items of the tensor-core filter
+  int* gitem = nullptr;          // [RMIPS_KMAX_LIMIT + 2] first item of each k-group; [.. + 1] = items
+  int2* itemg = nullptr;         // [MQ_ITEMS] (group, chunk) of each item
+  int32_t* gpre = nullptr;       // [nb][k_max] Lemma 3 prefix of every (block, k-group)
+  unsigned long long* wst = nullptr;  // [WST_N] role wait / busy cycles of the TC filter (profiling)
+  int64_t cap_gpre = 0;
   int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
   uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
@@ -157,6 +177,7 @@ struct rmips_index {
   uint8_t* incomp = nullptr;
   float* LB = nullptr;
   float* hdr = nullptr;
+  unsigned char* Qtc = nullptr;  // user tiles of the batched tensor-core filter (null: not built)
 
   std::mutex mu;
   std::vector<rmips::Workspace*> pool;
@@ -293,6 +314,14 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
 // 1-D bulk copy global -> shared (TMA engine), completion signalled on `bar`.

@@ -65,7 +65,9 @@ class Profile(C.Structure):
     _fields_ = [("filter_launches", C.c_int64), ("filter_ms", C.c_double), ("filter_alg_bytes", C.c_double),
                 ("users_tested", C.c_int64), ("blocks_pruned", C.c_int64), ("blocks_total", C.c_int64),
                 ("mfilter_launches", C.c_int64), ("mfilter_ms", C.c_double), ("mfilter_pairs", C.c_int64),
-                ("mfilter_alg_flops", C.c_double)]
+                ("mfilter_alg_flops", C.c_double), ("mfilter_tiles", C.c_int64),
+                ("mfilter_wait", C.c_double * 8), ("mfilter_cycles", C.c_double * 4),
+                ("mfilter_active_tiles", C.c_int64)]
 
 
 class ServerOpts(C.Structure):
@@ -348,14 +350,20 @@ def rmips_index_export(index: Index, field: str) -> np.ndarray:
     return arr
 
 
-def rmips_profile_enable(index: Index, enable: bool = True):
-    _check(_lib.rmips_profile_enable(index.handle, 1 if enable else 0))
+def rmips_profile_enable(index: Index, enable=True):
+    """enable: False/0 off, True/1 kernel timing, 2 timing plus pipeline counters."""
+    level = 2 if enable == 2 else (1 if enable else 0)
+    _check(_lib.rmips_profile_enable(index.handle, level))
 
 
 def rmips_profile_read(index: Index) -> dict:
     pr = Profile()
     _check(_lib.rmips_profile_read(index.handle, C.byref(pr)))
-    return {f: getattr(pr, f) for f, _ in Profile._fields_}
+    out = {}
+    for f, _ in Profile._fields_:
+        v = getattr(pr, f)
+        out[f] = list(v) if hasattr(v, "__len__") else v
+    return out
 
 
 def rmips_free_index(index: Index):
