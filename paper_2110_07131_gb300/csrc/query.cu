@@ -1710,7 +1710,7 @@ __global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
 
 // Tile shapes of the batched tensor-core filter: user tiles of 128 rows (MMA
 // M); query tiles of 64 slots as k_mprep lays them out, multiplied two at a
-// time (MMA N up to 128); an epilogue warp owns 32 users x 64 queries.
+// time (MMA N up to 128); an epilogue warp owns 32 users x 32 queries.
 constexpr int TCU = 128;                       // users per tile (MMA M)
 constexpr int TCQ = MQ_TQ;                     // queries per laid-out tile
 constexpr int WS_N = 2 * TCQ;                  // queries per item (largest MMA N)
@@ -1726,30 +1726,33 @@ __host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K 
 // up to 128 queries) that Lemma 3 keeps for at least one block of the tile;
 // the MMA's N is the chunk's query count rounded up to 16.  Four roles run as
 // a pipeline joined by mbarriers only:
-//   loader   (warp 8)   reads the tile's Lemma 3 prefixes (k_mprefix), skips a
+//   loader   (warp 16)  reads the tile's Lemma 3 prefixes (k_mprefix), skips a
 //                       tile with no item, copies the users' norms and (lo, hi)
 //                       bounds into one of two tile slots and starts the bulk
 //                       copy of the pre-tiled user rows;
-//   feeder   (warp 9)   bulk-copies each item's query rows, error constants
-//                       and query indices into a ring of stages;
-//   mma      (warp 10)  one thread issues the 128 x N x K MMAs of an item into
-//                       one of WS_NACC TMEM accumulator stages and commits;
-//   epilogue (warps 0-7) warp w reads TMEM lanes 32 (w % 4) .. +31 and
-//                       columns 64 (w / 4) .. +63 of a stage, frees the stage
-//                       and classifies its 32 users x 64 queries (Lemma 1, then
+//   feeder   (warp 17)  bulk-copies each packed item (query rows, error
+//                       constants, query indices) into a ring of stages, which
+//                       the MMA commit frees;
+//   mma      (warps 18, 19) one thread of each issues the 128 x N x K MMAs
+//                       of alternate items into one of WS_NACC TMEM
+//                       accumulator stages and commits;
+//   epilogue (warps 0-15) warp w reads TMEM lanes 32 (w % 4) .. +31 and
+//                       columns 32 (w / 4) .. +31 of a stage, frees the stage
+//                       and classifies its 32 users x 32 queries (Lemma 1, then
 //                       hi_k or Lemma 2), as k_mfilter does.
 // K is rounded up to the MMA's K step (8 for TF32, 16 for BF16 / FP16), not to
 // 64: the zero padding past d contributes nothing.  Every wait is bounded: on
 // a timeout the CTA raises a flag, each role leaves its loop, waits for its
 // copies in flight, and TMEM is freed.
 // ===========================================================================
-constexpr int WS_EPI = 8;                              // epilogue warps
-constexpr int WS_LOADER = 8, WS_FEEDER = 9, WS_MMA = 10;   // MMA warps 10 and 11 take even / odd items
-constexpr int WS_THREADS = 12 * 32;
+constexpr int WS_EPI = 16;                             // epilogue warps: 4 lane quadrants x 4 column groups
+constexpr int WS_LOADER = WS_EPI, WS_FEEDER = WS_EPI + 1, WS_MMA = WS_EPI + 2;   // MMA warps take even / odd items
+constexpr int WS_THREADS = (WS_EPI + 4) * 32;
 constexpr int WS_NACC = 4;                             // TMEM accumulator stages of WS_N columns
 constexpr int WS_MAXNS = 6;                            // query stages at most
 constexpr int WS_LG = 4;                               // groups per tile whose bounds are staged
-constexpr int WS_ECOLS = 64;                           // query columns per epilogue warp
+constexpr int WS_ECOLS = WS_N / (WS_EPI / 4);          // query columns per epilogue warp
+static_assert(WS_ECOLS == 32, "the epilogue classifies 32 columns per warp (one lane per query)");
 enum : int { WI_LAST = 1, WI_END = 2, WI_NEWGROUP = 4 };
 
 struct WsTile {                                        // one tile slot, written by the loader
@@ -1761,7 +1764,8 @@ struct WsTile {                                        // one tile slot, written
   int pre[RMIPS_KMAX_LIMIT][4];                        // prefix of each block of the tile
 };
 struct WsItem {                                        // one accumulator stage, written by the mma warp
-  int ab, ga, t, stage, flags;
+  int ab, ga, t, item, flags;
+  float2 c0;                                           // (error scale, slack) of the item's first query
 };
 
 size_t ws_smem_bytes(int kind, int ns) {
@@ -1875,7 +1879,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
   }
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], WS_EPI); }
-    for (int i = 0; i < ns; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], WS_EPI); }
+    for (int i = 0; i < ns; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }   // emptied by the MMA commit
     for (int i = 0; i < WS_NACC; ++i) { mbar_init(&tfull[i], 2); mbar_init(&tempty[i], WS_EPI); }
     mbar_init(&mdone[0], 1);
     mbar_init(&mdone[1], 1);
@@ -2067,8 +2071,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
             if (PROF) t_is = clock64();
             if (lane == 0) {
               const int nq = ws_item_n(gmax, t);
-              items[acc] = WsItem{ab, ga, t, stg,
-                                  (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0)};
+              const float2 c0 = *reinterpret_cast<const float2*>(sB + (size_t)stg * PACK + BROWS);
+              items[acc] = WsItem{ab, ga, t, T.item0[ga] + t,
+                                  (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0), c0};
               const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, (uint32_t)nq)
                                                       : tc_idesc_f16(TCU, (uint32_t)nq, KIND == TCK_BF16);
               const uint64_t ad0 = ab ? adesc1 : adesc0, bd0 = bdesc0 + (uint64_t)stg * BSTEP;
@@ -2081,6 +2086,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
                 if (KIND == TCK_TF32) tc_mma_tf32(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
                 else tc_mma_f16(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
               }
+              tc_commit(&bempty[stg]);           // the stage is free once these MMAs have read it
               tc_commit(&tfull[acc]);
               mbar_arrive(&tfull[acc]);
               if (PROF) w_issue += clock64() - t_is;
@@ -2160,14 +2166,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       acc = acc + 1 == WS_NACC ? 0 : acc + 1;
       if (uu >= nvalid) live = 0;
       if (live > 0) {
-        const float2* cq0 = reinterpret_cast<const float2*>(sB + (size_t)itm.stage * PACK + BROWS);
+        // the stage may be refilled already: per-query constants of the
+        // (rare) per-pair tests come from the packed item in global memory
+        const float2* cq0 = reinterpret_cast<const float2*>(b.bitems + (size_t)itm.item * PACK + BROWS);
         const float2* cq = cq0 + col;
         const int* qj = reinterpret_cast<const int*>(cq0 + WS_N) + col;
         const int64_t pos = u0 + uu;
         // Fast Lemma 1: the item's first query has the largest error scale
         // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
-        const float2 c0 = cq0[0];
-        const float thr = __fsub_rd(L.x, __fmaf_ru(un, c0.x, c0.y));
+        const float thr = __fsub_rd(L.x, __fmaf_ru(un, itm.c0.x, itm.c0.y));
         bool any = true;
         if (live == WS_ECOLS) {
           float m[8];
@@ -2180,16 +2187,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
           const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
           any = mx >= thr;
         }
-        if (any) {
-          ws_classify(c, b, v, min(live, 32), thr, un, L, kq, cq, qj, pos, st_yes, st_todo);
-          if (live > 32) ws_classify(c, b, v + 32, live - 32, thr, un, L, kq, cq + 32, qj + 32, pos, st_yes, st_todo);
-        }
+        if (any) ws_classify(c, b, v, live, thr, un, L, kq, cq, qj, pos, st_yes, st_todo);
       }
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&bempty[itm.stage]);
-        if (itm.flags & WI_LAST) mbar_arrive(&aempty[itm.ab]);
-      }
+      if (lane == 0 && (itm.flags & WI_LAST)) mbar_arrive(&aempty[itm.ab]);
     }
     for (int o = 16; o > 0; o >>= 1) {
       st_yes += __shfl_xor_sync(FULL, st_yes, o);
