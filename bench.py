@@ -371,10 +371,12 @@ def run_ours(a):
         waits = pprof["mfilter_wait"]
         names = ["loader_waits_free_slot", "feeder_waits_free_stage", "mma_waits_query_tile",
                  "mma_waits_free_accumulator", "epilogue_waits_accumulator", "mma_waits_user_tile",
-                 "epilogue_reads_tmem", "mma_issues_mmas"]
-        owner = [0, 1, 2, 2, 3, 2, 3, 2]
+                 "epilogue_reads_tmem", "mma_issues_mmas", "epilogue_per_pair_tests",
+                 "epilogue_items_with_per_pair_tests", "epilogue_appends_pairs"]
+        owner = [0, 1, 2, 2, 3, 2, 3, 2, 3, None, 3]
         roofline["active_tiles_per_launch"] = pprof["mfilter_active_tiles"] / max(1, pprof["mfilter_launches"])
-        roofline["pipeline_wait_share"] = {n: (waits[i] / cyc[owner[i]] if cyc[owner[i]] > 0 else None)
+        roofline["pipeline_wait_share"] = {n: (waits[i] if owner[i] is None else
+                                               (waits[i] / cyc[owner[i]] if cyc[owner[i]] > 0 else None))
                                            for i, n in enumerate(names)}
     else:
         roofline = {"bound": "alu", "kernel": "k_mfilter (multi-query Lemma 3 prefixes + FP32 FFMA tiles + "

@@ -175,13 +175,17 @@ typedef struct {
                                 the per-user tests need) */
   int64_t mfilter_tiles;     /* 128 x 64 tensor-core tiles multiplied (the
                                 padded work behind the kept pairs) */
-  double mfilter_wait[8];    /* SM clock cycles the tensor-core filter's roles
+  double mfilter_wait[11];   /* SM clock cycles the tensor-core filter's roles
                                 spent waiting, summed over CTAs: loader (free
                                 tile slot), feeder (free query stage), MMA
                                 (query tile landed), MMA (free accumulator),
                                 epilogue warp 0 (accumulator ready), MMA (user
                                 tile landed), epilogue warp 0 reading TMEM,
-                                MMA thread issuing an item's MMAs */
+                                MMA thread issuing an item's MMAs, epilogue
+                                warp 0 in per-pair tests; [9] is the number of
+                                epilogue warp 0 items that needed them, [10]
+                                the cycles of those tests spent appending
+                                pairs */
   double mfilter_cycles[4];  /* cycles of each role from start to finish,
                                 summed over CTAs: loader, feeder, MMA,
                                 epilogue warp 0 */

@@ -959,6 +959,9 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
         idx->prof.mfilter_wait[5] += (double)w[WST_MMA_WAIT_A];
         idx->prof.mfilter_wait[6] += (double)w[WST_EPI_TMEM];
         idx->prof.mfilter_wait[7] += (double)w[WST_MMA_ISSUE];
+        idx->prof.mfilter_wait[8] += (double)w[WST_EPI_SLOW];
+        idx->prof.mfilter_wait[9] += (double)w[WST_EPI_SLOW_N];
+        idx->prof.mfilter_wait[10] += (double)w[WST_EPI_ATOM];
         for (int i = 0; i < 4; ++i) idx->prof.mfilter_cycles[i] += (double)w[WST_LOADER + i];
         idx->prof.mfilter_active_tiles += (int64_t)w[WST_ACTIVE];
       }
@@ -1793,51 +1796,59 @@ __device__ __forceinline__ int ws_item_n(int gmax, int t) {
   return (q + 15) & ~15;
 }
 
+// v[q] for a run-time q in [0, 32) without local memory: a 5-level select tree.
+__device__ __forceinline__ float ws_pick(const float* v, int q) {
+  float a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = (q & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = (q & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = (q & 4) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a[i] = (q & 8) ? a[2 * i + 1] : a[2 * i];
+  return (q & 16) ? a[1] : a[0];
+}
+
 // Lemma 1 / hi_k / Lemma 2 classification of up to 32 accumulators v of one
-// user against the queries of cq / qj (live leading ones); yes and undecided
-// pairs are appended to the pair lists.
+// user against the queries of cq / qj (live leading ones).  Only columns at or
+// above the fast threshold are tested one by one (a lane has one or two); yes
+// and undecided pairs are appended to the pair lists.
+template <bool PROF>
 __device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, const float* v, int live, float thr,
                                             float un, float2 L, int k, const float2* cq, const int* qj, int64_t pos,
-                                            long long& st_yes, long long& st_todo) {
+                                            long long& st_yes, long long& st_todo, long long& w_atom) {
   uint32_t hit = 0;
 #pragma unroll
   for (int q = 0; q < 32; ++q) hit |= (v[q] >= thr ? 1u : 0u) << q;
   if (live < 32) hit &= (1u << live) - 1u;
   if (!hit) return;
+  long long t_a = 0;
+  if (PROF) t_a = clock64();
   const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
-  uint32_t ym = 0, tm = 0;
-#pragma unroll
-  for (int q = 0; q < 32; ++q) {
-    if ((hit >> q) & 1u) {
-      const float2 e2 = cq[q];
-      const float e = __fmaf_ru(un, e2.x, e2.y);
-      if (!(__fadd_ru(v[q], e) < L.x)) {                              // not decided no by Lemma 1
-        const float lo = __fsub_rd(v[q], e);
-        const bool yes = c.full_p ? (lo >= L.y) : (lo >= pkb);
-        if (yes) ym |= 1u << q; else tm |= 1u << q;
-      }
+  while (hit) {
+    const int q = __ffs(hit) - 1;
+    hit &= hit - 1;
+    const float vq = ws_pick(v, q);
+    const float2 e2 = cq[q];
+    const float e = __fmaf_ru(un, e2.x, e2.y);
+    if (__fadd_ru(vq, e) < L.x) continue;                                  // decided no by Lemma 1
+    const int j = qj[q];
+    if (!in_segment(c, b, j, pos)) continue;
+    const float lo = __fsub_rd(vq, e);
+    if (c.full_p ? (lo >= L.y) : (lo >= pkb)) {
+      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
+      if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
+      atomicAdd(&b.qcnt[j], 1);
+      ++st_yes;
+    } else {
+      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
+      if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
+      else set_status(c.ctr, ST_INTERNAL);
+      ++st_todo;
     }
   }
-  while (ym) {
-    const int q = __ffs(ym) - 1;
-    ym &= ym - 1;
-    const int j = qj[q];
-    if (!in_segment(c, b, j, pos)) continue;
-    const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
-    if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
-    atomicAdd(&b.qcnt[j], 1);
-    ++st_yes;
-  }
-  while (tm) {
-    const int q = __ffs(tm) - 1;
-    tm &= tm - 1;
-    const int j = qj[q];
-    if (!in_segment(c, b, j, pos)) continue;
-    const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
-    if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
-    else set_status(c.ctr, ST_INTERNAL);
-    ++st_todo;
-  }
+  if (PROF) w_atom += clock64() - t_a;
 }
 
 template <int KIND, int NSTEP, bool PROF>
@@ -2124,7 +2135,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     const int q4 = warp & 3, col = (warp >> 2) * WS_ECOLS;
     const int uu = q4 * 32 + lane;                                    // this thread's user row
     const uint32_t tl = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col;
-    long long st_yes = 0, st_todo = 0;
+    long long st_yes = 0, st_todo = 0, w_slow = 0, n_slow = 0, w_atom = 0;
     uint32_t tpar = 0;
     int acc = 0;
     // constants of the current (tile, group), reloaded on WI_NEWGROUP
@@ -2187,7 +2198,13 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
           const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
           any = mx >= thr;
         }
-        if (any) ws_classify(c, b, v, live, thr, un, L, kq, cq, qj, pos, st_yes, st_todo);
+        long long t_sl = 0;
+        if (PROF) t_sl = clock64();
+        if (any) ws_classify<PROF>(c, b, v, live, thr, un, L, kq, cq, qj, pos, st_yes, st_todo, w_atom);
+        if (PROF) {
+          w_slow += clock64() - t_sl;
+          n_slow += __any_sync(__activemask(), any) ? 1 : 0;
+        }
       }
       __syncwarp();
       if (lane == 0 && (itm.flags & WI_LAST)) mbar_arrive(&aempty[itm.ab]);
@@ -2199,6 +2216,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     if (lane == 0 && st_yes) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)st_yes);
     if (lane == 0 && st_todo) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)st_todo);
     if (warp == 0) report(WST_EPI_WAIT, WST_EPI_TMEM, WST_EPI);
+    if (PROF && warp == 0 && lane == 0) {
+      atomicAdd(&b.wst[WST_EPI_SLOW], (unsigned long long)w_slow);
+      atomicAdd(&b.wst[WST_EPI_SLOW_N], (unsigned long long)n_slow);
+      atomicAdd(&b.wst[WST_EPI_ATOM], (unsigned long long)w_atom);
+    }
   }
   if (s_fail && tid == 0) set_status(c.ctr, ST_TIMEOUT);
   tc_fence_before();

@@ -73,7 +73,8 @@ enum : int { ST_OK = 0, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_IN
 enum : int {
   WST_LOADER_WAIT = 0, WST_FEEDER_WAIT = 1, WST_MMA_WAIT_B = 2, WST_MMA_WAIT_T = 3, WST_EPI_WAIT = 4,
   WST_LOADER = 5, WST_FEEDER = 6, WST_MMA = 7, WST_EPI = 8, WST_TILES = 9,
-  WST_MMA_WAIT_A = 10, WST_EPI_TMEM = 11, WST_ACTIVE = 12, WST_MMA_ISSUE = 13, WST_N = 14
+  WST_MMA_WAIT_A = 10, WST_EPI_TMEM = 11, WST_ACTIVE = 12, WST_MMA_ISSUE = 13, WST_EPI_SLOW = 14,
+  WST_EPI_SLOW_N = 15, WST_EPI_ATOM = 16, WST_N = 17
 };
 
 // Per-call device counters (int64 slots).

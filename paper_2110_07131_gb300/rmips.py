@@ -66,7 +66,7 @@ class Profile(C.Structure):
                 ("users_tested", C.c_int64), ("blocks_pruned", C.c_int64), ("blocks_total", C.c_int64),
                 ("mfilter_launches", C.c_int64), ("mfilter_ms", C.c_double), ("mfilter_pairs", C.c_int64),
                 ("mfilter_alg_flops", C.c_double), ("mfilter_tiles", C.c_int64),
-                ("mfilter_wait", C.c_double * 8), ("mfilter_cycles", C.c_double * 4),
+                ("mfilter_wait", C.c_double * 11), ("mfilter_cycles", C.c_double * 4),
                 ("mfilter_active_tiles", C.c_int64)]
 
 
