@@ -478,7 +478,7 @@ __global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict
                            const float* __restrict__ cval, const int32_t* __restrict__ cid,
                            const float* __restrict__ unorm, const float* __restrict__ uex_in, float pn0, int64_t n,
                            int64_t pp, int d, int dp, int k_max, int full_p, float2* __restrict__ Lb,
-                           int32_t* __restrict__ cand, uint8_t* __restrict__ incomp,
+                           int32_t* __restrict__ cand, float2* __restrict__ cbnd, uint8_t* __restrict__ incomp,
                            unsigned long long* __restrict__ n_incomplete, const int32_t* __restrict__ ulist,
                            int64_t nlist) {
   const int64_t slot = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -534,6 +534,8 @@ __global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict
   }
   if (full_p) {
     cand[w * RMIPS_KC + lane] = id;
+    cbnd[w * RMIPS_KC + lane] = id >= 0 ? make_float2(__double2float_rd(lo), __double2float_ru(hi))
+                                        : make_float2(-kInf, -kInf);
     if (lane == 0) {
       incomp[w] = complete ? 0 : 1;
       if (!complete) atomicAdd(n_incomplete, 1ull);
@@ -665,6 +667,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     TRY(dalloc(idx, &idx->hdr, idx->nb));
     if (idx->full_p) {
       TRY(dalloc(idx, &idx->cand, (size_t)n * RMIPS_KC));
+      TRY(dalloc(idx, &idx->cbnd, (size_t)n * RMIPS_KC));
       TRY(dalloc(idx, &idx->incomp, n));
     }
     TRY(cudaMallocAsync((void**)&qn, n * sizeof(float), st));
@@ -750,7 +753,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     // 4: bounds
     k_finalize<<<grid_for(n * 32, 256), 256, 0, st>>>(idx->Qs, idx->Ps, cval, cid, idx->unorm, uex, idx->pn0,
                                                       n, idx->pp, d, dp, idx->k_max, idx->full_p, idx->Lb,
-                                                      idx->cand, idx->incomp, d_incomp, nullptr, 0);
+                                                      idx->cand, idx->cbnd, idx->incomp, d_incomp, nullptr, 0);
     if (tc_build && idx->full_p) {
       // users the TF32 selection could not prove complete: redo them in float32
       unsigned long long h_inc = 0;
@@ -779,7 +782,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
                                                                               (int)nseg, cval, cid);
         k_finalize<<<grid_for((int64_t)h_inc * 32, 256), 256, 0, st>>>(
             idx->Qs, idx->Ps, cval, cid, idx->unorm, nullptr, idx->pn0, n, idx->pp, d, dp2, idx->k_max,
-            idx->full_p, idx->Lb, idx->cand, idx->incomp, d_incomp, ulist, (int64_t)h_inc);
+            idx->full_p, idx->Lb, idx->cand, idx->cbnd, idx->incomp, d_incomp, ulist, (int64_t)h_inc);
         TRY(cudaGetLastError());
       }
     }

@@ -205,6 +205,7 @@ extern "C" void rmips_free_index(rmips_index* idx) {
   cudaFree(idx->permP);
   cudaFree(idx->Lb);
   cudaFree(idx->cand);
+  cudaFree(idx->cbnd);
   cudaFree(idx->incomp);
   cudaFree(idx->LB);
   cudaFree(idx->hdr);

@@ -55,6 +55,7 @@ struct Common {
   const float* unorm;
   const float* pnorm;
   const int32_t* cand;
+  const float2* cbnd;
   const uint8_t* incomp;
   const int32_t* permQ;
   int64_t n, m, nb;
@@ -111,7 +112,8 @@ __global__ void k_qprep(Common c, int64_t nq, int precision) {
 __device__ bool verify_scan(const float* __restrict__ u, float un, const Common& c, const float* sq, int k,
                             float qeps);
 __device__ bool recheck_candidates(const float* __restrict__ u, const float* q, const int32_t* __restrict__ crow,
-                                   const float* __restrict__ Ps, int d, int k, float cg32, long long* ctr);
+                                   const float2* __restrict__ cbrow, const float* __restrict__ Ps, int d, int k,
+                                   float cg32, long long* ctr);
 
 // --- filter ------------------------------------------------------------------------
 // Lemmas 1-3 for one query over this CTA's share of 32-user chunks.  Warp w
@@ -221,7 +223,8 @@ __device__ bool filter_chunks(const Common& c, const float* sq, int k, float qn,
         const int64_t p = cur * 32 + l;
         const float* u = c.Qs + p * c.d;
         const bool ok_yes = !c.incomp[p]
-                                ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.Ps, c.d, k, c.cg32, c.ctr)
+                                ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.cbnd + p * RMIPS_KC, c.Ps, c.d,
+                                                     k, c.cg32, c.ctr)
                                 : verify_scan(u, c.unorm[p], c, sq, k, qeps);
         if (ok_yes && lane == l) yes = true;
       }
@@ -329,7 +332,8 @@ __device__ bool verify_scan(const float* __restrict__ u, float un, const Common&
 // tie, q's own copy in P), then float64 with its bound, then the exact
 // integer accumulator.  u.q is formed once per user, split across lanes.
 __device__ bool recheck_candidates(const float* __restrict__ u, const float* q, const int32_t* __restrict__ crow,
-                                   const float* __restrict__ Ps, int d, int k, float cg32, long long* ctr) {
+                                   const float2* __restrict__ cbrow, const float* __restrict__ Ps, int d, int k,
+                                   float cg32, long long* ctr) {
   const int lane = threadIdx.x & 31;
   float g32 = 0.f, a32 = 0.f;
   for (int i = lane; i < d; i += 32) {
@@ -347,7 +351,12 @@ __device__ bool recheck_candidates(const float* __restrict__ u, const float* q, 
   const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
   const int32_t it = crow[lane];
   bool gt = false, hard = false;
-  if (it >= 0) {
+  // the index keeps an interval of every candidate's u.p: disjoint from that
+  // of u.q it decides at once; only overlapping candidates read their row
+  const float2 cb = it >= 0 ? cbrow[lane] : make_float2(-kInf, -kInf);
+  if (it >= 0 && cb.x > gh) {
+    gt = true;
+  } else if (it >= 0 && !(cb.y < gl)) {
     const float* p = Ps + (int64_t)it * d;
     float sp = 0.f, B = 0.f;
     for (int i = 0; i < d; ++i) {
@@ -421,7 +430,8 @@ __global__ void __launch_bounds__(256) k_resolve(Common c, int j) {
     if (c.full_p && !c.incomp[pos]) {
       // The candidate list holds every item that can reach u's k_max-th place,
       // so u is a yes iff fewer than k candidates are strictly above u.q.
-      yes = recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr);
+      yes = recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.cbnd + (int64_t)pos * RMIPS_KC, c.Ps, d, k,
+                                 c.cg32, c.ctr);
     } else {
       yes = verify_scan(u, c.unorm[pos], c, sq, k, qeps);
     }
@@ -598,7 +608,8 @@ __global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const 
       const int32_t pos = __ldcg(&c.todo[t]);
       const float* u = c.Qs + (int64_t)pos * d;
       const bool yes = !c.incomp[pos]
-                           ? recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr)
+                           ? recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.cbnd + (int64_t)pos * RMIPS_KC, c.Ps, d, k,
+                                 c.cg32, c.ctr)
                            : verify_scan(u, c.unorm[pos], c, sq, k, s_eps);
       if (lane == 0 && yes) {
         const long long b = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
@@ -667,6 +678,7 @@ Common make_common(const rmips_index* idx, Workspace* ws) {
   c.unorm = idx->unorm;
   c.pnorm = idx->pnorm;
   c.cand = idx->cand;
+  c.cbnd = idx->cbnd;
   c.incomp = idx->incomp;
   c.permQ = idx->permQ;
   c.n = idx->n;
@@ -1528,7 +1540,8 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
     const float* u = c.Qs + (int64_t)pos * d;
     bool yes;
     if (c.full_p && !c.incomp[pos]) {
-      yes = recheck_candidates(u, q, c.cand + (int64_t)pos * RMIPS_KC, c.Ps, d, k, c.cg32, c.ctr);
+      yes = recheck_candidates(u, q, c.cand + (int64_t)pos * RMIPS_KC, c.cbnd + (int64_t)pos * RMIPS_KC, c.Ps, d, k,
+                               c.cg32, c.ctr);
     } else {
       yes = verify_scan(u, c.unorm[pos], c, q, k, b.deps[j]);
     }

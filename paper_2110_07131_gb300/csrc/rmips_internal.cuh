@@ -12,6 +12,8 @@
 //                              over P' (hi = +inf when not proven)
 //   cand   int32 [n][KC]       item positions whose set provably contains u's
 //                              top-k_max (full-P index only)
+//   cbnd   float2 [n][KC]      (lo, hi) with lo <= u.p <= hi for each candidate
+//                              (float64 dot +- its error bound, rounded outward)
 //   incomp uint8 [n]           1 when cand could not be proven complete
 //   LB     float [k_max][nb]   block minima of lo (Equation 1)
 //   hdr    float [nb]          upper bound of the first user's norm of each block
@@ -175,6 +177,7 @@ struct rmips_index {
   int32_t* permP = nullptr;
   float2* Lb = nullptr;
   int32_t* cand = nullptr;
+  float2* cbnd = nullptr;
   uint8_t* incomp = nullptr;
   float* LB = nullptr;
   float* hdr = nullptr;
