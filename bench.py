@@ -356,6 +356,10 @@ def run_ours(a):
     m_ms = prof["mfilter_ms"] / ml
     m_ach = m_flops / (m_ms / 1e3) / 1e12 if m_ms > 0 else 0.0
     tc_path = a.batch_kernel == "tc" and a.d <= 64 and a.precision == "fp32"
+    # DRAM bytes (read + write) of one k_mfilter_ws launch on the default
+    # workload, from one ncu capture of the current kernel (273.2 MB + 4.9 MB)
+    default_workload = (a.n, a.m, a.d, a.k, a.k_max, a.nq) == (1_000_000, 500_000, 50, 10, 25, 10_000)
+    tc_traffic = 278.1e6 if (tc_path and default_workload and a.block_size == 32) else None
     if tc_path:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         tf32_peak = bf16 * (1.1 / 2.25)
@@ -363,7 +367,7 @@ def run_ours(a):
                                                   "128x64xK tiles into 4 TMEM stages + Lemmas 1/2 epilogue)",
                     "achieved": m_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m_ach / tf32_peak,
                     "peak_source": f"measured bf16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25",
-                    "traffic": None, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
+                    "traffic": tc_traffic, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
                     "pairs_per_launch": prof["mfilter_pairs"] / ml,
                     "tiles_per_launch": pprof["mfilter_tiles"] / max(1, pprof["mfilter_launches"]),
                     "filter_share_of_step": prof["mfilter_ms"] / ms if ms > 0 else None}
