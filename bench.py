@@ -159,6 +159,22 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def result_sizes(offs):
+    """Distribution of the per-query result sizes of one batch (CSR offsets)."""
+    if offs is None or len(offs) < 2:
+        return None
+    sz = np.diff(np.asarray(offs, dtype=np.int64))
+    out = {"queries": int(len(sz)), "total": int(sz.sum()), "max": int(sz.max())}
+    for p in (50, 90, 99, 99.9):
+        out[f"p{p}"] = float(np.percentile(sz, p))
+    for lo, hi in ((0, 0), (1, 32), (33, 8192), (8193, None)):
+        m = (sz >= lo) if hi is None else ((sz >= lo) & (sz <= hi))
+        key = f"{lo}+" if hi is None else f"{lo}-{hi}"
+        out[f"n_{key}"] = int(m.sum())
+        out[f"ids_{key}"] = int(sz[m].sum())
+    return out
+
+
 # --------------------------------------------------------------------------- ranks
 def reduce_over_ranks(ms: float, units: float, dist=None, device=None):
     """Max of the timed milliseconds and sum of the processed units over ranks.
@@ -255,9 +271,12 @@ def run_ours(a):
     dout = torch.empty(cap, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    last_offs = [None]
+
     def step(i):
         sl = dqs[i * a.nq:(i + 1) * a.nq]
         _, offs = rmips.rmips_query_batch(index, sl, dks, out=dout, stream=stream)
+        last_offs[0] = offs
         return int(offs[-1])
 
     for i in range(a.warmup):
@@ -404,6 +423,7 @@ def run_ours(a):
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
             "index_incomplete_users": info["incomplete"],
             "users_returned_per_query": results / (a.steps * a.nq),
+            "result_sizes_last_step": result_sizes(last_offs[0]),
             "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (a.steps * a.nq),
             "last_step": {"pairs_decided_yes_in_o1": qstats["yes_fast"], "pairs_rechecked": qstats["todo"],
                           "exact_integer_decisions": qstats["exact_calls"], "results": qstats["result"]}}

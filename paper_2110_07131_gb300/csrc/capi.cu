@@ -55,6 +55,8 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->dseghi);
   cudaFree(ws->hist);
   cudaFree(ws->big);
+  cudaFree(ws->mid);
+  cudaFree(ws->bigcnt);
   cudaFree(ws->bigmaps);
   cudaFree(ws->bcq);
   cudaFree(ws->bitems);

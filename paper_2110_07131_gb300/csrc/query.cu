@@ -30,7 +30,8 @@ constexpr float kInf = __builtin_huge_valf();
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int FW = 4;                      // warps per filter CTA
 constexpr int EMIT_THREADS = 1024;
-constexpr int EMIT_SORT_CAP = 8192;
+constexpr int EMIT_SORT_CAP = 8192;       // single query: larger results use the id bitmap
+constexpr int MEMIT_MID_CAP = 2048;       // batch: larger results use id bitmaps spread over the grid
 
 // Relative error factor of a length-d float32 dot product whose inputs were
 // rounded to a format with unit roundoff u_in (0 for float32 inputs):
@@ -1123,9 +1124,12 @@ struct Batch {
   int* hist;              // [RMIPS_KMAX_LIMIT + 2] queries per k
   int* gfirst;            // [RMIPS_KMAX_LIMIT + 2] first sorted position of each k
   int* gslot0;            // [RMIPS_KMAX_LIMIT + 2] first slot of each k-group
-  int32_t* big;           // queries with more than EMIT_SORT_CAP results
+  int32_t* big;           // queries with more than MEMIT_MID_CAP results
+  int32_t* mid;           // queries with 33 .. MEMIT_MID_CAP results
   uint32_t* bigmaps;      // MQ_BIG_SLOTS id bitmaps of nw words each
+  int* bigcnt;            // [MQ_BIG_SLOTS][nwc] ids per 1024-word chunk of each bitmap
   int64_t nw;             // words per id bitmap
+  int64_t nwc;            // 1024-word chunks per id bitmap
   long long* doffs;       // [nq + 1] offsets of this pass (absolute)
   long long* out;
   long long capacity;
@@ -1159,6 +1163,7 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
     c.ctr[C_NBIG] = 0;
+    c.ctr[C_NMID] = 0;
     int f = 0, s = 0, g = 0, nit = 0;
     for (int k = 0; k <= RMIPS_KMAX_LIMIT + 1; ++k) {
       first[k] = f;
@@ -1578,9 +1583,12 @@ __global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
   for (int j = j0; j < j1; ++j) {
     b.doffs[j] = run;
     run += b.qcnt[j];
-    if (b.qcnt[j] > EMIT_SORT_CAP) {
+    if (b.qcnt[j] > MEMIT_MID_CAP) {
       const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
       b.big[r] = j;
+    } else if (b.qcnt[j] > 32) {
+      const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NMID], 1ull);
+      b.mid[r] = j;
     }
   }
   __syncthreads();
@@ -1621,39 +1629,45 @@ __device__ __forceinline__ int32_t warp_sort_asc(int32_t x) {
   return x;
 }
 
-// Positions -> ids, ascending, for queries with at most EMIT_SORT_CAP results.
-// A CTA serves 8 consecutive queries: a result of at most 32 ids is sorted by
-// one warp in registers; a larger one by the whole CTA in shared memory.
+// Positions -> ids, ascending, for queries with at most 32 results: one warp
+// per query sorts in registers (8 queries per CTA).
 constexpr int MEMIT_Q = 8;
 __global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
-  __shared__ int32_t keys[EMIT_SORT_CAP];
   if (c.ctr[C_STATUS] != 0) return;                      // uniform: read-only here
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long base0 = b.doffs[0];
-  const int j0 = blockIdx.x * MEMIT_Q;
-  {
-    const int j = j0 + warp;
-    if (j < b.nq) {
-      const int cnt = b.qcnt[j];
-      if (cnt > 0 && cnt <= 32) {
-        const long long off = b.doffs[j];
-        int32_t v = lane < cnt ? c.permQ[b.seg[off - base0 + lane]] : INT_MAX;
-        v = warp_sort_asc(v);
-        if (lane < cnt) b.out[off + lane] = v;
-      }
-    }
+  const int j = blockIdx.x * MEMIT_Q + warp;
+  if (j >= b.nq) return;
+  const int cnt = b.qcnt[j];
+  if (cnt > 0 && cnt <= 32) {
+    const long long off = b.doffs[j];
+    int32_t v = lane < cnt ? c.permQ[b.seg[off - base0 + lane]] : INT_MAX;
+    v = warp_sort_asc(v);
+    if (lane < cnt) b.out[off + lane] = v;
   }
-  for (int w = 0; w < MEMIT_Q; ++w) {
-    const int j = j0 + w;
-    if (j >= b.nq) break;
+}
+
+// Queries with 33 .. MEMIT_MID_CAP results: one CTA per query, bitonic sort in
+// shared memory.
+__global__ void __launch_bounds__(256) k_memit_mid(Common c, Batch b) {
+  __shared__ int32_t keys[MEMIT_MID_CAP];
+  __shared__ long long s_n;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_bad = c.ctr[C_STATUS] != 0;
+    s_n = c.ctr[C_NMID];
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const long long base0 = b.doffs[0];
+  for (long long r = blockIdx.x; r < s_n; r += gridDim.x) {
+    const int j = b.mid[r];
     const int cnt = b.qcnt[j];
-    if (cnt <= 32 || cnt > EMIT_SORT_CAP) continue;      // small: done above; large: k_memit_big
     const long long off = b.doffs[j];
     int N2 = 64;
     while (N2 < cnt) N2 <<= 1;
-    __syncthreads();                                     // keys of the previous query consumed
-    for (int i = tid; i < N2; i += blockDim.x)
-      keys[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
+    for (int i = tid; i < N2; i += blockDim.x) keys[i] = i < cnt ? c.permQ[b.seg[off - base0 + i]] : INT_MAX;
     __syncthreads();
     for (int kk = 2; kk <= N2; kk <<= 1) {
       for (int jj = kk >> 1; jj > 0; jj >>= 1) {
@@ -1666,13 +1680,111 @@ __global__ void __launch_bounds__(256) k_memit(Common c, Batch b) {
       }
     }
     for (int i = tid; i < cnt; i += blockDim.x) b.out[off + i] = keys[i];
+    __syncthreads();                                     // keys consumed before the next query
   }
 }
 
-// Queries with large results: each CTA owns one id bitmap and handles the
-// large queries r = blockIdx.x, blockIdx.x + gridDim.x, ... in turn: set one
-// bit per result id, then read the bitmap back in order (block-wide prefix of
-// per-thread bit counts), clearing it for the next query.
+// Queries with more than MEMIT_MID_CAP results, the first MQ_BIG_SLOTS of
+// them, each through an id bitmap of its own and spread over the grid:
+//   mark   every result sets its id's bit;
+//   count  ids per 1024-word chunk of every bitmap;
+//   write  each chunk's ids, ascending, at the query's offset plus the ids of
+//          the chunks before it, clearing the words.
+__global__ void __launch_bounds__(256) k_mbig_mark(Common c, Batch b) {
+  if (c.ctr[C_STATUS] != 0) return;
+  const long long nbig = c.ctr[C_NBIG] < MQ_BIG_SLOTS ? c.ctr[C_NBIG] : MQ_BIG_SLOTS;
+  const long long base0 = b.doffs[0];
+  for (long long r = 0; r < nbig; ++r) {
+    const int j = b.big[r];
+    const long long off = b.doffs[j] - base0;
+    const int cnt = b.qcnt[j];
+    uint32_t* bm = b.bigmaps + r * b.nw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x) {
+      const int32_t v = c.permQ[b.seg[off + i]];
+      atomicOr(&bm[v >> 5], 1u << (v & 31));
+    }
+  }
+}
+
+__device__ __forceinline__ int block_sum256(int x, int* s_red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  __syncthreads();
+  if (lane == 0) s_red[wid] = x;
+  __syncthreads();
+  int t = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += s_red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_mbig_count(Common c, Batch b) {
+  __shared__ int s_red[8];
+  if (c.ctr[C_STATUS] != 0) return;
+  const long long nbig = c.ctr[C_NBIG] < MQ_BIG_SLOTS ? c.ctr[C_NBIG] : MQ_BIG_SLOTS;
+  for (long long p = blockIdx.x; p < nbig * b.nwc; p += gridDim.x) {
+    const long long r = p / b.nwc, ch = p - r * b.nwc;
+    const uint32_t* bm = b.bigmaps + r * b.nw;
+    int x = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long w = ch * 1024 + threadIdx.x * 4 + i;
+      if (w < b.nw) x += __popc(__ldcg(&bm[w]));
+    }
+    x = block_sum256(x, s_red);
+    if (threadIdx.x == 0) b.bigcnt[p] = x;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mbig_write(Common c, Batch b) {
+  __shared__ int s_red[8];
+  __shared__ int s_scan[256];
+  if (c.ctr[C_STATUS] != 0) return;
+  const long long nbig = c.ctr[C_NBIG] < MQ_BIG_SLOTS ? c.ctr[C_NBIG] : MQ_BIG_SLOTS;
+  const int tid = threadIdx.x;
+  for (long long p = blockIdx.x; p < nbig * b.nwc; p += gridDim.x) {
+    const long long r = p / b.nwc, ch = p - r * b.nwc;
+    uint32_t* bm = b.bigmaps + r * b.nw;
+    const int j = b.big[r];
+    int before = 0;                                      // ids in the chunks before this one
+    for (long long q = tid; q < ch; q += blockDim.x) before += b.bigcnt[r * b.nwc + q];
+    before = block_sum256(before, s_red);
+    uint32_t w4[4];
+    int x = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long w = ch * 1024 + tid * 4 + i;
+      w4[i] = w < b.nw ? __ldcg(&bm[w]) : 0u;
+      x += __popc(w4[i]);
+    }
+    s_scan[tid] = x;                                     // exclusive scan over the CTA
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      const int y = tid >= o ? s_scan[tid - o] : 0;
+      __syncthreads();
+      s_scan[tid] += y;
+      __syncthreads();
+    }
+    long long o = b.doffs[j] + before + s_scan[tid] - x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long w = ch * 1024 + tid * 4 + i;
+      uint32_t word = w4[i];
+      if (word) bm[w] = 0u;
+      while (word) {
+        const int bit = __ffs(word) - 1;
+        word &= word - 1;
+        b.out[o++] = w * 32 + bit;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Large queries beyond the MQ_BIG_SLOTS handled above: each CTA owns one id
+// bitmap and handles queries r = MQ_BIG_SLOTS + blockIdx.x, + gridDim.x, ...
+// in turn: set one bit per result id, then read the bitmap back in order
+// (block-wide prefix of per-thread bit counts), clearing it for the next one.
 __global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
   __shared__ int s_warp[32];
   __shared__ long long s_nbig;
@@ -1688,7 +1800,7 @@ __global__ void __launch_bounds__(1024) k_memit_big(Common c, Batch b) {
   const long long base0 = b.doffs[0];
   const int64_t per = (b.nw + 1023) / 1024;
   const int64_t w0 = tid * per, w1 = (w0 + per < b.nw) ? w0 + per : b.nw;
-  for (long long r = blockIdx.x; r < s_nbig; r += gridDim.x) {
+  for (long long r = MQ_BIG_SLOTS + blockIdx.x; r < s_nbig; r += gridDim.x) {
     const int j = b.big[r];
     const long long off = b.doffs[j];
     const int cnt = b.qcnt[j];
@@ -2319,6 +2431,8 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
   if (!ws->big) {
     const int64_t nw = idx->n / 32 + 1;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->big, MQ_MAXQ * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->mid, MQ_MAXQ * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bigcnt, (size_t)MQ_BIG_SLOTS * ((nw + 1023) / 1024) * sizeof(int)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bigmaps, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
     RMIPS_TRY_CUDA(cudaMemset(ws->bigmaps, 0, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
   }
@@ -2436,8 +2550,11 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.seglo = dseglo ? dseglo + j0 : nullptr;
     b.seghi = dseghi ? dseghi + j0 : nullptr;
     b.big = ws->big;
+    b.mid = ws->mid;
     b.bigmaps = ws->bigmaps;
+    b.bigcnt = ws->bigcnt;
     b.nw = idx->n / 32 + 1;
+    b.nwc = (b.nw + 1023) / 1024;
     b.doffs = ws->doffs + j0;
     b.out = out;
     b.capacity = capacity;
@@ -2473,6 +2590,10 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     k_mscan<<<1, 1024, 0, st>>>(c, b);
     k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
     k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, st>>>(c, b);
+    k_memit_mid<<<sm_count * 4, 256, 0, st>>>(c, b);
+    k_mbig_mark<<<sm_count * 4, 256, 0, st>>>(c, b);
+    k_mbig_count<<<sm_count * 4, 256, 0, st>>>(c, b);
+    k_mbig_write<<<sm_count * 4, 256, 0, st>>>(c, b);
     k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, st>>>(c, b);
     RMIPS_TRY_CUDA(cudaGetLastError());
   }

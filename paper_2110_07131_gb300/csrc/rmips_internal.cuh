@@ -92,7 +92,8 @@ enum : int {
   C_TODOSUM = 8,    // users sent to the todo list (all queries of the call)
   C_NBIG = 9,       // queries of a batch pass with more than EMIT_SORT_CAP results
   C_DONE = 10,      // CTAs finished (one-launch query)
-  C_NCOUNTERS = 11
+  C_NMID = 11,      // queries of a batch pass with 33 .. MEMIT_MID_CAP results
+  C_NCOUNTERS = 12
 };
 
 // ---------------------------------------------------------------------------
@@ -151,6 +152,8 @@ struct Workspace {
   unsigned long long* wst = nullptr;  // [WST_N] role wait / busy cycles of the TC filter (profiling)
   int64_t cap_gpre = 0;
   int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
+  int32_t* mid = nullptr;        // [MQ_MAXQ] queries of a pass with medium results
+  int* bigcnt = nullptr;         // [MQ_BIG_SLOTS][chunks] ids per 1024-word chunk of a large result
   uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
 
