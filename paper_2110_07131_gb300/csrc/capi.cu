@@ -56,6 +56,7 @@ void destroy_workspace(Workspace* ws) {
   cudaFree(ws->hist);
   cudaFree(ws->big);
   cudaFree(ws->mid);
+  cudaFree(ws->bslot);
   cudaFree(ws->bigcnt);
   cudaFree(ws->bigmaps);
   cudaFree(ws->bcq);

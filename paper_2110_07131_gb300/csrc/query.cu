@@ -1126,6 +1126,7 @@ struct Batch {
   int* gslot0;            // [RMIPS_KMAX_LIMIT + 2] first slot of each k-group
   int32_t* big;           // queries with more than MEMIT_MID_CAP results
   int32_t* mid;           // queries with 33 .. MEMIT_MID_CAP results
+  int32_t* bslot;         // [nq] id-bitmap slot of a query marked through k_mbig_mark, else -1
   uint32_t* bigmaps;      // MQ_BIG_SLOTS id bitmaps of nw words each
   int* bigcnt;            // [MQ_BIG_SLOTS][nwc] ids per 1024-word chunk of each bitmap
   int64_t nw;             // words per id bitmap
@@ -1583,9 +1584,11 @@ __global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
   for (int j = j0; j < j1; ++j) {
     b.doffs[j] = run;
     run += b.qcnt[j];
+    b.bslot[j] = -1;
     if (b.qcnt[j] > MEMIT_MID_CAP) {
       const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
       b.big[r] = j;
+      if (r < MQ_BIG_SLOTS) b.bslot[j] = (int32_t)r;
     } else if (b.qcnt[j] > 32) {
       const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NMID], 1ull);
       b.mid[r] = j;
@@ -1609,6 +1612,7 @@ __global__ void k_mscatter(Common c, Batch b) {
        i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long pr = b.ypairs[i];
     const int j = (int)(pr >> 32);
+    if (b.bslot[j] >= 0) continue;                       // marked straight from the pair list
     const int slot = atomicAdd(&b.qcur[j], 1);
     b.seg[b.doffs[j] - base0 + slot] = (int32_t)(pr & 0xffffffffull);
   }
@@ -1686,23 +1690,20 @@ __global__ void __launch_bounds__(256) k_memit_mid(Common c, Batch b) {
 
 // Queries with more than MEMIT_MID_CAP results, the first MQ_BIG_SLOTS of
 // them, each through an id bitmap of its own and spread over the grid:
-//   mark   every result sets its id's bit;
+//   mark   every yes pair of such a query sets its id's bit (straight from
+//          the pair list: k_mscatter leaves these queries out);
 //   count  ids per 1024-word chunk of every bitmap;
 //   write  each chunk's ids, ascending, at the query's offset plus the ids of
 //          the chunks before it, clearing the words.
 __global__ void __launch_bounds__(256) k_mbig_mark(Common c, Batch b) {
-  if (c.ctr[C_STATUS] != 0) return;
-  const long long nbig = c.ctr[C_NBIG] < MQ_BIG_SLOTS ? c.ctr[C_NBIG] : MQ_BIG_SLOTS;
-  const long long base0 = b.doffs[0];
-  for (long long r = 0; r < nbig; ++r) {
-    const int j = b.big[r];
-    const long long off = b.doffs[j] - base0;
-    const int cnt = b.qcnt[j];
-    uint32_t* bm = b.bigmaps + r * b.nw;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x) {
-      const int32_t v = c.permQ[b.seg[off + i]];
-      atomicOr(&bm[v >> 5], 1u << (v & 31));
-    }
+  if (c.ctr[C_STATUS] != 0 || c.ctr[C_NBIG] == 0) return;
+  const long long cnt = c.ctr[C_YES] < b.cap_y ? c.ctr[C_YES] : b.cap_y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long pr = b.ypairs[i];
+    const int r = b.bslot[(int)(pr >> 32)];
+    if (r < 0) continue;
+    const int32_t v = c.permQ[(int32_t)(pr & 0xffffffffull)];
+    atomicOr(&b.bigmaps[(int64_t)r * b.nw + (v >> 5)], 1u << (v & 31));
   }
 }
 
@@ -2432,6 +2433,7 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
     const int64_t nw = idx->n / 32 + 1;
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->big, MQ_MAXQ * sizeof(int32_t)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->mid, MQ_MAXQ * sizeof(int32_t)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bslot, MQ_MAXQ * sizeof(int32_t)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bigcnt, (size_t)MQ_BIG_SLOTS * ((nw + 1023) / 1024) * sizeof(int)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bigmaps, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
     RMIPS_TRY_CUDA(cudaMemset(ws->bigmaps, 0, (size_t)MQ_BIG_SLOTS * nw * sizeof(uint32_t)));
@@ -2551,6 +2553,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.seghi = dseghi ? dseghi + j0 : nullptr;
     b.big = ws->big;
     b.mid = ws->mid;
+    b.bslot = ws->bslot;
     b.bigmaps = ws->bigmaps;
     b.bigcnt = ws->bigcnt;
     b.nw = idx->n / 32 + 1;
@@ -2586,7 +2589,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used + 1], st));
       ws->ev_used++;
     }
-    k_mresolve<<<sm_count * 2, 256, 0, st>>>(c, b);
+    k_mresolve<<<sm_count * 8, 256, 0, st>>>(c, b);     // one warp per pair: latency-bound, many warps
     k_mscan<<<1, 1024, 0, st>>>(c, b);
     k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
     k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, st>>>(c, b);

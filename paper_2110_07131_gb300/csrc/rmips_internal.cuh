@@ -153,6 +153,7 @@ struct Workspace {
   int64_t cap_gpre = 0;
   int32_t* big = nullptr;        // [MQ_MAXQ] queries of a pass with large results
   int32_t* mid = nullptr;        // [MQ_MAXQ] queries of a pass with medium results
+  int32_t* bslot = nullptr;      // [MQ_MAXQ] id-bitmap slot of a query with a large result, else -1
   int* bigcnt = nullptr;         // [MQ_BIG_SLOTS][chunks] ids per 1024-word chunk of a large result
   uint32_t* bigmaps = nullptr;   // [MQ_BIG_SLOTS][n/32 + 1] all-zero between uses
 };
