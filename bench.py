@@ -67,9 +67,16 @@ def workload(a):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle samples (every 100 ms) around a timed region.
+
+    Started before the warm-up so that sampling is running when the timed
+    region begins; stop(t0, t1) keeps the samples stamped inside [t0, t1]
+    (host wall clock) widened by one sampling period, or, for a region shorter
+    than a period, the samples adjacent to it."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD = 0.1
 
     def __init__(self, gpu: int):
         self.gpu = gpu
@@ -81,25 +88,48 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(int(self.PERIOD * 1000))],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self) -> dict:
+    def _rows(self):
+        import datetime
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            rows.append((ts, parts[1:]))
+        return rows
+
+    def stop(self, t0: float = None, t1: float = None) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        deadline = time.time() + 1.0                  # let one sample land after the region
+        while t1 is not None and time.time() < deadline and not any(ts > t1 for ts, _ in self._rows()):
+            time.sleep(0.02)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = self._rows()
         os.unlink(self.path)
+        window = "timed region"
+        if t0 is not None and t1 is not None:
+            sel = [r for ts, r in rows if t0 - self.PERIOD <= ts <= t1 + self.PERIOD]
+            if not sel:
+                before = [r for ts, r in rows if ts < t0][-1:]
+                after = [r for ts, r in rows if ts > t1][:1]
+                sel, window = before + after, "samples adjacent to a region shorter than the sampling period"
+            rows = sel
+        else:
+            rows = [r for _, r in rows]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -107,7 +137,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "window": window}
 
 
 # --------------------------------------------------------------------------- CPU oracle timing
@@ -279,26 +309,28 @@ def run_ours(a):
         last_offs[0] = offs
         return int(offs[-1])
 
+    sampler = ClockSampler(local)
+    sampler.start()                                  # sampling already runs when the timed region starts
     for i in range(a.warmup):
         step(i)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
     rmips.rmips_profile_enable(index, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
     ev0.record(stream)
     results = 0
     for i in range(a.steps):
         results += step(a.warmup + i)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    t_wall1 = time.time()
     prof = rmips.rmips_profile_read(index)
     rmips.rmips_profile_enable(index, False)
     qstats = rmips.rmips_last_query_stats(index)
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_wall0, t_wall1)
     # pipeline counters of the tensor-core filter: one more step with the
     # instrumented kernel, outside the timed region
     rmips.rmips_profile_enable(index, 2)
