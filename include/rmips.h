@@ -155,6 +155,28 @@ rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
                                int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
                                void* stream);
 
+/*
+ * rmips_query_batch_async -- rmips_query_batch for device-resident inputs and
+ * outputs that does not wait for the GPU (Algorithm 3 for many queries, as
+ * rmips_query_batch; no segments).
+ *
+ * qs [nq][d] float32, ks [nq] int32, out_ids [capacity] int64,
+ * out_offsets [nq + 1] int64 and done [2] int64 are DEVICE pointers.  All work
+ * is queued on `stream` and the call returns; when the stream passes it,
+ * out_offsets holds the CSR offsets, done[0] an rmips_status (RMIPS_OK,
+ * RMIPS_ERR_NONFINITE, RMIPS_ERR_K_RANGE, RMIPS_ERR_CAPACITY with
+ * out_offsets[nq] = the size needed and out_ids unspecified,
+ * RMIPS_ERR_TIMEOUT, RMIPS_ERR_INTERNAL) and done[1] the number of result
+ * ids.  The returned status covers only what the host can check (arguments,
+ * allocations, launches).  The buffers must stay valid until the stream has
+ * passed the call.  Calls on other streams and the other query calls order
+ * themselves after it.  Filter timing and kept pairs reach the profile when
+ * rmips_profile_read is called; rmips_last_query_stats is not updated.
+ */
+rmips_status rmips_query_batch_async(rmips_index* index, const float* qs, int64_t nq, const int32_t* ks,
+                                     int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
+                                     int64_t* done, void* stream);
+
 /* Per-kernel timing of the filter kernels (Lemmas 1-3), for roofline reports. */
 typedef struct {
   int64_t filter_launches;   /* filter launches since profiling was enabled */

@@ -20,6 +20,7 @@ bool is_device_ptr(const void* p) {
 
 void destroy_workspace(Workspace* ws) {
   if (!ws) return;
+  if (ws->done_ev) cudaEventDestroy(ws->done_ev);
   cudaFree(ws->yes);
   cudaFree(ws->todo);
   cudaFree(ws->bitmap);
@@ -100,6 +101,14 @@ Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
     return nullptr;
   }
   return ws;
+}
+
+rmips_status ws_join(Workspace* ws, cudaStream_t st) {
+  if (ws->done_pending) {
+    RMIPS_TRY_CUDA(cudaStreamWaitEvent(st, ws->done_ev, 0));
+    ws->done_pending = false;
+  }
+  return RMIPS_OK;
 }
 
 void release_workspace(rmips_index* idx, Workspace* ws) {
@@ -209,6 +218,9 @@ extern "C" void rmips_free_index(rmips_index* idx) {
   cudaFree(idx->Lb);
   cudaFree(idx->cand);
   cudaFree(idx->cbnd);
+  cudaFree(idx->dprof);
+  for (cudaEvent_t e : idx->pend_ev) cudaEventDestroy(e);
+  idx->pend_ev.clear();
   cudaFree(idx->incomp);
   cudaFree(idx->LB);
   cudaFree(idx->hdr);
@@ -224,16 +236,51 @@ extern "C" int32_t rmips_exact_sign_host(const float* u, const float* a, const f
 
 extern "C" rmips_status rmips_profile_enable(rmips_index* idx, int32_t enable) {
   if (!idx) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != idx->device) cudaSetDevice(idx->device);
   std::lock_guard<std::mutex> lk(idx->mu);
   idx->prof_on = enable == 2 ? 2 : (enable ? 1 : 0);
   idx->prof = rmips_profile{};
+  for (cudaEvent_t e : idx->pend_ev) {
+    cudaEventSynchronize(e);
+    cudaEventDestroy(e);
+  }
+  idx->pend_ev.clear();
+  cudaError_t e = cudaSuccess;
+  if (!idx->dprof) e = cudaMalloc((void**)&idx->dprof, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(idx->dprof, 0, sizeof(unsigned long long));
+  if (prev != idx->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return RMIPS_ERR_CUDA; }
   return RMIPS_OK;
 }
 
+// Folds the filter timing and kept-pair counts of asynchronous batch calls
+// (event pairs and a device counter, waited for here) into the profile.
 extern "C" rmips_status rmips_profile_read(const rmips_index* idx, rmips_profile* out) {
   if (!idx || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
   rmips_index* m = const_cast<rmips_index*>(idx);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != m->device) cudaSetDevice(m->device);
   std::lock_guard<std::mutex> lk(m->mu);
+  for (size_t i = 0; i + 1 < m->pend_ev.size(); i += 2) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(m->pend_ev[i + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, m->pend_ev[i], m->pend_ev[i + 1]) == cudaSuccess) {
+      m->prof.mfilter_launches += 1;
+      m->prof.mfilter_ms += ms;
+    }
+  }
+  for (cudaEvent_t e : m->pend_ev) cudaEventDestroy(e);
+  m->pend_ev.clear();
+  unsigned long long pairs = 0;
+  if (m->dprof && cudaMemcpy(&pairs, m->dprof, sizeof(pairs), cudaMemcpyDeviceToHost) == cudaSuccess && pairs) {
+    m->prof.mfilter_pairs += (int64_t)pairs;
+    m->prof.mfilter_alg_flops += 2.0 * m->d * (double)pairs;
+    cudaMemset(m->dprof, 0, sizeof(unsigned long long));
+  }
   *out = m->prof;
+  if (prev != m->device) cudaSetDevice(prev);
   return RMIPS_OK;
 }

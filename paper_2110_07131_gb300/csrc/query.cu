@@ -2623,6 +2623,7 @@ extern "C" rmips_status rmips_query(rmips_index* idx, const float* q, int32_t k,
   Workspace* ws = acquire_workspace(idx, &s);
   if (!ws) return s;
   WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
   if ((s = ensure_queries(idx, ws, 1)) != RMIPS_OK) return s;
   if (idx->full_p && (!seg || seg->kind != 2)) {
     s = query_fused(idx, ws, q, k, seg, out_ids, capacity, out_count, st);
@@ -2680,6 +2681,7 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   Workspace* ws = acquire_workspace(idx, &s);
   if (!ws) return s;
   WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
   if ((s = ensure_queries(idx, ws, nq)) != RMIPS_OK) return s;
   const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
   long long* out;
@@ -2857,6 +2859,62 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   *out_count = offs[1];
   return status_from_device(h[C_STATUS]);
+}
+
+// Status and result count of an asynchronous batch call, written on the stream.
+__global__ void k_batch_done(const long long* __restrict__ ctr, const long long* __restrict__ doffs, int64_t nq,
+                             int64_t* __restrict__ done, unsigned long long* __restrict__ dprof) {
+  const long long s = ctr[C_STATUS];
+  done[0] = s == ST_OK ? RMIPS_OK
+          : s == ST_NONFINITE ? RMIPS_ERR_NONFINITE
+          : s == ST_CAPACITY ? RMIPS_ERR_CAPACITY
+          : s == ST_TIMEOUT ? RMIPS_ERR_TIMEOUT
+          : s == ST_INTERNAL ? RMIPS_ERR_K_RANGE : RMIPS_ERR_INTERNAL;
+  done[1] = doffs[nq];
+  if (dprof) atomicAdd(dprof, (unsigned long long)ctr[C_TESTED]);
+}
+
+extern "C" rmips_status rmips_query_batch_async(rmips_index* idx, const float* qs, int64_t nq, const int32_t* ks,
+                                                int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
+                                                int64_t* done, void* stream) {
+  if (!idx || nq < 0 || !out_offsets || !done || capacity < 0 || (nq > 0 && (!qs || !ks)) ||
+      (!out_ids && capacity > 0)) {
+    set_error("null argument or negative size");
+    return RMIPS_ERR_ARG;
+  }
+  if (!is_device_ptr(out_offsets) || !is_device_ptr(done) || (nq > 0 && (!is_device_ptr(qs) || !is_device_ptr(ks))) ||
+      (capacity > 0 && !is_device_ptr(out_ids))) {
+    set_error("rmips_query_batch_async takes device buffers only");
+    return RMIPS_ERR_ARG;
+  }
+  DeviceGuard dg(idx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nq == 0) {
+    RMIPS_TRY_CUDA(cudaMemsetAsync(out_offsets, 0, sizeof(int64_t), st));
+    RMIPS_TRY_CUDA(cudaMemsetAsync(done, 0, 2 * sizeof(int64_t), st));
+    return RMIPS_OK;
+  }
+  rmips_status s = RMIPS_OK;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
+  if (!ws->done_ev) RMIPS_TRY_CUDA(cudaEventCreateWithFlags(&ws->done_ev, cudaEventDisableTiming));
+  if ((s = ensure_queries(idx, ws, nq)) != RMIPS_OK) return s;
+  if ((s = stage_inputs(idx, ws, qs, nq, ks, st)) != RMIPS_OK) return s;
+  if ((s = run_batch(idx, ws, nq, (long long*)out_ids, capacity, st, nullptr, nullptr)) != RMIPS_OK) return s;
+  RMIPS_TRY_CUDA(cudaMemcpyAsync(out_offsets, ws->doffs, (nq + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  k_batch_done<<<1, 1, 0, st>>>(ws->ctr, ws->doffs, nq, done, idx->prof_on ? idx->dprof : nullptr);
+  RMIPS_TRY_CUDA(cudaGetLastError());
+  if (ws->ev_used > 0) {                                 // filter timing: read when the profile is read
+    std::lock_guard<std::mutex> lk(idx->mu);
+    idx->pend_ev.insert(idx->pend_ev.end(), ws->ev.begin(), ws->ev.begin() + 2 * ws->ev_used);
+    ws->ev.erase(ws->ev.begin(), ws->ev.begin() + 2 * ws->ev_used);
+    ws->ev_used = 0;
+  }
+  RMIPS_TRY_CUDA(cudaEventRecord(ws->done_ev, st));
+  ws->done_pending = true;
+  return RMIPS_OK;
 }
 
 extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, int32_t lbo,

@@ -119,6 +119,8 @@ struct Workspace {
   float* h_q = nullptr;          // [RMIPS_DMAX] pinned, device-mapped query staging
   long long* h_res = nullptr;    // [2 + C_NCOUNTERS] pinned, device-mapped status / count / counters
   bool ctr_dirty = false;        // counters may be non-zero (multi-kernel paths leave them so)
+  cudaEvent_t done_ev = nullptr; // recorded after the work of an asynchronous call
+  bool done_pending = false;     // a later user joins done_ev on its own stream first
   std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch
   int64_t ev_used = 0;
   // batched (multi-query) path
@@ -192,6 +194,8 @@ struct rmips_index {
   rmips_query_stats last_stats{};
   int prof_on = 0;
   rmips_profile prof{};
+  std::vector<cudaEvent_t> pend_ev;          // filter event pairs of asynchronous calls, read on profile read
+  unsigned long long* dprof = nullptr;       // [1] kept pairs of asynchronous calls (device)
 };
 
 namespace rmips {
@@ -217,6 +221,8 @@ rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long
                           cudaStream_t st, bool with_segments);
 rmips_status device_status(long long s);
 void release_workspace(rmips_index* idx, Workspace* ws);
+// Orders this stream after the last asynchronous call that used ws.
+rmips_status ws_join(Workspace* ws, cudaStream_t st);
 void destroy_workspace(Workspace* ws);
 
 // ---------------------------------------------------------------------------

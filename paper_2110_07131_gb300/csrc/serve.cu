@@ -311,6 +311,10 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
     if (!sl.ws) break;
     if ((st = batch_reserve(idx, sl.ws, o.max_batch)) != RMIPS_OK) break;
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && sl.ws->done_pending) {          // after an asynchronous call's work
+      e = cudaStreamWaitEvent(sl.stream, sl.ws->done_ev, 0);
+      sl.ws->done_pending = false;
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_q, (size_t)o.max_batch * idx->d * sizeof(float), 0);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_k, o.max_batch * sizeof(int32_t), 0);

@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "RmipsError", "Index", "load_library", "rmips_build_index", "rmips_query",
-    "rmips_query_batch", "rmips_index_get_info", "rmips_last_query_stats",
+    "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info", "rmips_last_query_stats",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
     "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
     "FP32", "BF16", "FP16", "Server",
@@ -29,7 +29,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_K_RANGE", 3: "ERR_NONFINITE", 4: "ERR_O
           5: "ERR_CAPACITY", 6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_INTERNAL", 9: "ERR_BUSY"}
 
 EXPORTED_SYMBOLS = [
-    "rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
+    "rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info",
     "rmips_last_query_stats", "rmips_index_export", "rmips_free_index", "rmips_status_string",
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
@@ -108,6 +108,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_build_index.argtypes = [P, I64, P, I64, I32, C.POINTER(BuildOpts), VP, C.POINTER(VP)]
         lib.rmips_query.argtypes = [VP, P, I32, C.POINTER(Segment), P, I64, C.POINTER(I64), VP]
         lib.rmips_query_batch.argtypes = [VP, P, I64, P, C.POINTER(Segment), P, I64, P, VP]
+        lib.rmips_query_batch_async.argtypes = [VP, P, I64, P, P, I64, P, P, VP]
         lib.rmips_index_get_info.argtypes = [VP, C.POINTER(IndexInfo)]
         lib.rmips_last_query_stats.argtypes = [VP, C.POINTER(QueryStats)]
         lib.rmips_index_export.argtypes = [VP, I32, P, I64]
@@ -131,7 +132,8 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_server_wait_many.argtypes = [VP, P, I64, P, I64, P, P, I32]
         lib.rmips_server_destroy.argtypes = [VP]
         lib.rmips_server_destroy.restype = None
-        for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_index_get_info",
+        for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_query_batch_async",
+                     "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
                      "rmips_server_create", "rmips_server_submit", "rmips_server_submit_many",
@@ -318,6 +320,22 @@ def rmips_query_batch(index: Index, qs, ks, segments=None, capacity=None, out=No
             continue
         _check(st)
         return buf[:offs[-1]], offs
+
+
+def rmips_query_batch_async(index: Index, qs, ks, out, offsets, done, stream=None):
+    """Queue a batch on ``stream`` without waiting (torch CUDA tensors only).
+
+    qs float32 [nq, d], ks int32 [nq], out int64 [capacity], offsets int64
+    [nq + 1], done int64 [2]: when the stream has passed the call, offsets is
+    the CSR index of out and done = (status, number of ids)."""
+    for t in (qs, ks, out, offsets, done):
+        if not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
+            raise RmipsError(1, "rmips_query_batch_async takes contiguous CUDA tensors")
+    nq = int(qs.shape[0])
+    if ks.dtype.itemsize != 4 or out.dtype.itemsize != 8 or offsets.numel() < nq + 1 or done.numel() < 2:
+        raise RmipsError(1, "ks int32, out / offsets / done int64, offsets nq + 1, done 2")
+    _check(_lib.rmips_query_batch_async(index.handle, qs.data_ptr(), nq, ks.data_ptr(), out.data_ptr(),
+                                        int(out.numel()), offsets.data_ptr(), done.data_ptr(), _stream(stream)))
 
 
 def rmips_index_get_info(index: Index) -> dict:

@@ -289,3 +289,49 @@ def test_precision_modes_return_identical_sets():
         sample = np.unique(np.concatenate([got[:100], rng.choice(n, 100, replace=False)]))
         truth = O.decide_users(Q, P, qs[j], int(ks[j]), sample)
         assert np.array_equal(np.intersect1d(sample, got), sample[truth])
+
+
+def test_async_batch_matches_sync_and_reports_on_device():
+    torch = pytest.importorskip("torch")
+    Q, P = datagen.make_problem(20000, 5000, 50, 13)
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    qs, _ = datagen.queries_from_items(P, 3000, 13)
+    ks = datagen.random_ks(len(qs), 1, 25, 13)
+    ids_ref, offs_ref = rmips.rmips_query_batch(index, qs, ks)
+    total = int(offs_ref[-1])
+    dev = torch.device("cuda")
+    dq, dk = torch.from_numpy(qs).to(dev), torch.from_numpy(ks).to(dev)
+    stream = torch.cuda.current_stream()
+    rmips.rmips_profile_enable(index, True)
+    outs = []
+    for _ in range(2):                                   # two calls in a row on one workspace
+        out = torch.full((total + 7,), -1, dtype=torch.int64, device=dev)
+        offs = torch.empty(len(qs) + 1, dtype=torch.int64, device=dev)
+        done = torch.full((2,), -1, dtype=torch.int64, device=dev)
+        rmips.rmips_query_batch_async(index, dq, dk, out, offs, done, stream)
+        outs.append((out, offs, done))
+    ids_sync, _ = rmips.rmips_query_batch(index, qs[:100], ks[:100])   # a synchronous call in between
+    torch.cuda.synchronize()
+    for out, offs, done in outs:
+        assert done.tolist() == [0, total]
+        assert np.array_equal(offs.cpu().numpy(), offs_ref)
+        assert np.array_equal(out[:total].cpu().numpy(), ids_ref)
+    assert np.array_equal(ids_sync, ids_ref[:offs_ref[100]])
+    prof = rmips.rmips_profile_read(index)
+    assert prof["mfilter_launches"] >= 2 and prof["mfilter_pairs"] > 0 and prof["mfilter_ms"] > 0
+    rmips.rmips_profile_enable(index, False)
+    # device-side errors arrive in done
+    small = torch.empty(max(1, total // 2), dtype=torch.int64, device=dev)
+    offs = torch.empty(len(qs) + 1, dtype=torch.int64, device=dev)
+    done = torch.empty(2, dtype=torch.int64, device=dev)
+    rmips.rmips_query_batch_async(index, dq, dk, small, offs, done, stream)
+    torch.cuda.synchronize()
+    assert done.tolist() == [5, total] and int(offs[-1]) == total
+    bad = dk.clone()
+    bad[7] = 26
+    rmips.rmips_query_batch_async(index, dq, bad, outs[0][0], offs, done, stream)
+    torch.cuda.synchronize()
+    assert int(done[0]) == 2
+    with pytest.raises(rmips.RmipsError):
+        rmips.rmips_query_batch_async(index, qs, ks, outs[0][0], offs, done, stream)   # host arrays
+    index.close()
