@@ -21,6 +21,12 @@ bool is_device_ptr(const void* p) {
 void destroy_workspace(Workspace* ws) {
   if (!ws) return;
   if (ws->done_ev) cudaEventDestroy(ws->done_ev);
+  for (auto& pg : ws->pgraph) {
+    if (pg.pre) cudaGraphExecDestroy(pg.pre);
+    if (pg.post) cudaGraphExecDestroy(pg.post);
+  }
+  ws->pgraph.clear();
+  if (ws->cap_stream) cudaStreamDestroy(ws->cap_stream);
   cudaFree(ws->yes);
   cudaFree(ws->todo);
   cudaFree(ws->bitmap);

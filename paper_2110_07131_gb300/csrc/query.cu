@@ -669,7 +669,8 @@ cudaError_t filter_dispatch(const rmips_index* idx, const Common& c, int j, int 
 int elem_bytes(int precision) { return precision == RMIPS_FP32 ? 4 : 2; }
 
 Common make_common(const rmips_index* idx, Workspace* ws) {
-  Common c{};
+  Common c;
+  memset(&c, 0, sizeof(c));                        // padding too: graph keys compare the bytes
   c.Qs = idx->Qs;
   c.Qrows = idx->precision == RMIPS_FP32 ? (const void*)idx->Qs : idx->Qh;
   c.Ps = idx->Ps;
@@ -2493,6 +2494,26 @@ rmips_status ensure_segments(Workspace* ws, int64_t nq) {
   return RMIPS_OK;
 }
 
+// Captures what `enqueue` puts on capture stream cs into an executable graph;
+// false (and nothing kept) if any step of the capture fails.
+template <class F>
+bool capture_graph(cudaStream_t cs, F&& enqueue, cudaGraphExec_t* exec) {
+  *exec = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  enqueue(cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    if (*exec) cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+    cudaGetLastError();                            // clear the capture error
+    return false;
+  }
+  return true;
+}
+
 rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
                        cudaStream_t st, const long long* dseglo, const long long* dseghi) {
   ws->ctr_dirty = true;
@@ -2526,7 +2547,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   const int fgrid = (int)(tiles < sm_count * per_sm ? tiles : sm_count * per_sm);
   for (int64_t j0 = 0; j0 < nq; j0 += MQ_MAXQ) {
     const int cnt = (int)((nq - j0) < MQ_MAXQ ? (nq - j0) : MQ_MAXQ);
-    Batch b{};
+    Batch b;
+    memset(&b, 0, sizeof(b));                      // padding too: graph keys compare the bytes
     b.dq = ws->dq + j0 * idx->d;
     b.dk = ws->dk + j0;
     b.dqn = ws->dqn + j0;
@@ -2562,14 +2584,55 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     b.out = out;
     b.capacity = capacity;
     const int nruns = (cnt + RUN - 1) / RUN;
-    RMIPS_TRY_CUDA(cudaMemsetAsync(b.hist, 0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int), st));
-    k_mprep_a<<<(cnt + 255) / 256, 256, 0, st>>>(c, b, idx->precision);
-    k_mprep_groups<<<1, 256, 0, st>>>(c, b);
-    k_mprep_runs<<<nruns, RUN, 0, st>>>(b);
-    k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, st>>>(c, b, nruns);
-    if (!use_tc) k_mprep_c<<<sm_count * 4, 256, 0, st>>>(c, b);
-    if (use_tc) k_mprep_items<<<MQ_ITEMS, 256, 0, st>>>(c, b);
-    if (use_tc) k_mprefix<<<(unsigned)((idx->nb * ngroups_max + 255) / 256), 256, 0, st>>>(c, b, ngroups_max);
+    auto pre = [&](cudaStream_t q) {
+      cudaMemsetAsync(b.hist, 0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int), q);
+      k_mprep_a<<<(cnt + 255) / 256, 256, 0, q>>>(c, b, idx->precision);
+      k_mprep_groups<<<1, 256, 0, q>>>(c, b);
+      k_mprep_runs<<<nruns, RUN, 0, q>>>(b);
+      k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, q>>>(c, b, nruns);
+      if (!use_tc) k_mprep_c<<<sm_count * 4, 256, 0, q>>>(c, b);
+      if (use_tc) k_mprep_items<<<MQ_ITEMS, 256, 0, q>>>(c, b);
+      if (use_tc) k_mprefix<<<(unsigned)((idx->nb * ngroups_max + 255) / 256), 256, 0, q>>>(c, b, ngroups_max);
+    };
+    auto post = [&](cudaStream_t q) {
+      k_mresolve<<<sm_count * 8, 256, 0, q>>>(c, b);     // one warp per pair: latency-bound, many warps
+      k_mscan<<<1, 1024, 0, q>>>(c, b);
+      k_mscatter<<<sm_count * 4, 256, 0, q>>>(c, b);
+      k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, q>>>(c, b);
+      k_memit_mid<<<sm_count * 4, 256, 0, q>>>(c, b);
+      k_mbig_mark<<<sm_count * 4, 256, 0, q>>>(c, b);
+      k_mbig_count<<<sm_count * 4, 256, 0, q>>>(c, b);
+      k_mbig_write<<<sm_count * 4, 256, 0, q>>>(c, b);
+      k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, q>>>(c, b);
+    };
+    // replay the pass's graphs when every kernel argument is as captured
+    const int pass = (int)(j0 / MQ_MAXQ);
+    if ((int)ws->pgraph.size() <= pass) ws->pgraph.resize(pass + 1);
+    Workspace::PassGraph& pg = ws->pgraph[pass];
+    std::vector<unsigned char> key(sizeof(Common) + sizeof(Batch) + 4 * sizeof(int));
+    const int extra[4] = {cnt, use_tc ? 1 : 0, sm_count, ngroups_max};
+    memcpy(key.data(), &c, sizeof(Common));
+    memcpy(key.data() + sizeof(Common), &b, sizeof(Batch));
+    memcpy(key.data() + sizeof(Common) + sizeof(Batch), extra, sizeof(extra));
+    // (a pass seen for the first time runs directly; the second identical one
+    // is captured, so a stream of differing batches never pays for captures)
+    if (key != pg.key) {
+      if (pg.pre) cudaGraphExecDestroy(pg.pre);
+      if (pg.post) cudaGraphExecDestroy(pg.post);
+      pg.pre = pg.post = nullptr;
+      pg.failed = false;
+      pg.key = key;
+    } else if (!pg.pre && !pg.failed) {
+      if (!ws->cap_stream) RMIPS_TRY_CUDA(cudaStreamCreateWithFlags(&ws->cap_stream, cudaStreamNonBlocking));
+      if (!(capture_graph(ws->cap_stream, pre, &pg.pre) && capture_graph(ws->cap_stream, post, &pg.post))) {
+        if (pg.pre) cudaGraphExecDestroy(pg.pre);
+        if (pg.post) cudaGraphExecDestroy(pg.post);
+        pg.pre = pg.post = nullptr;
+        pg.failed = true;
+      }
+    }
+    if (pg.pre) RMIPS_TRY_CUDA(cudaGraphLaunch(pg.pre, st));
+    else pre(st);
     RMIPS_TRY_CUDA(cudaGetLastError());
     const bool prof = idx->prof_on != 0;
     if (prof) {
@@ -2589,15 +2652,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[2 * ws->ev_used + 1], st));
       ws->ev_used++;
     }
-    k_mresolve<<<sm_count * 8, 256, 0, st>>>(c, b);     // one warp per pair: latency-bound, many warps
-    k_mscan<<<1, 1024, 0, st>>>(c, b);
-    k_mscatter<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, st>>>(c, b);
-    k_memit_mid<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_mbig_mark<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_mbig_count<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_mbig_write<<<sm_count * 4, 256, 0, st>>>(c, b);
-    k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, st>>>(c, b);
+    if (pg.post) RMIPS_TRY_CUDA(cudaGraphLaunch(pg.post, st));
+    else post(st);
     RMIPS_TRY_CUDA(cudaGetLastError());
   }
   return RMIPS_OK;

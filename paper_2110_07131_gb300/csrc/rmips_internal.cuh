@@ -119,6 +119,15 @@ struct Workspace {
   float* h_q = nullptr;          // [RMIPS_DMAX] pinned, device-mapped query staging
   long long* h_res = nullptr;    // [2 + C_NCOUNTERS] pinned, device-mapped status / count / counters
   bool ctr_dirty = false;        // counters may be non-zero (multi-kernel paths leave them so)
+  // CUDA graphs of the batched pipeline, one (before, after the filter) pair
+  // per pass, replayed while the pass's kernel arguments stay the same
+  struct PassGraph {
+    std::vector<unsigned char> key;   // arguments of the last pass seen
+    cudaGraphExec_t pre = nullptr, post = nullptr;
+    bool failed = false;              // capture failed for this key: launch directly
+  };
+  std::vector<PassGraph> pgraph;
+  cudaStream_t cap_stream = nullptr;  // capture only (the legacy stream cannot capture)
   cudaEvent_t done_ev = nullptr; // recorded after the work of an asynchronous call
   bool done_pending = false;     // a later user joins done_ev on its own stream first
   std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch

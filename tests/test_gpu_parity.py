@@ -335,3 +335,24 @@ def test_async_batch_matches_sync_and_reports_on_device():
     with pytest.raises(rmips.RmipsError):
         rmips.rmips_query_batch_async(index, qs, ks, outs[0][0], offs, done, stream)   # host arrays
     index.close()
+
+
+def test_graph_replay_with_same_and_changing_batches():
+    """Passes with unchanged arguments replay captured graphs (from the second
+    identical call on); new query data under the same arguments, and changed
+    sizes, must still give the single-query answers."""
+    Q, P = datagen.make_problem(20000, 5000, 50, 17)
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    qa, _ = datagen.queries_from_items(P, 1500, 17)
+    qb, _ = datagen.queries_from_items(P, 1500, 18)
+    ks = datagen.random_ks(1500, 1, 25, 17)
+    ref = {}
+    for name, qs in (("a", qa), ("b", qb)):
+        ref[name] = [rmips.rmips_query(index, qs[j], int(ks[j])) for j in range(0, 1500, 37)]
+    seq = [("a", 1500), ("a", 1500), ("a", 1500), ("b", 1500), ("b", 1500), ("a", 700), ("a", 700), ("b", 1500)]
+    for name, nq in seq:
+        qs = qa if name == "a" else qb
+        ids, offs = rmips.rmips_query_batch(index, qs[:nq], ks[:nq])
+        for r, j in enumerate(range(0, nq, 37)):
+            assert np.array_equal(ids[offs[j]:offs[j + 1]], ref[name][r]), (name, nq, j)
+    index.close()
