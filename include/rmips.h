@@ -177,6 +177,26 @@ rmips_status rmips_query_batch_async(rmips_index* index, const float* qs, int64_
                                      int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
                                      int64_t* done, void* stream);
 
+/*
+ * Index persistence.  rmips_index_save writes the index (sizes, options and
+ * every device array) to a host file; rmips_index_load reads it back onto the
+ * current device, answering exactly as the index that was saved.  The file
+ * format belongs to this library build (native byte order); a file that does
+ * not match its own header is refused with RMIPS_ERR_ARG.  The paper has no
+ * counterpart.
+ */
+rmips_status rmips_index_save(const rmips_index* index, const char* path);
+rmips_status rmips_index_load(const char* path, void* stream, rmips_index** out);
+
+/*
+ * rmips_index_rebuild -- Algorithm 1 again with another k_max (Section 4.1:
+ * the index keeps k_max ranks; a query with a larger k needs a rebuild).
+ * Builds a new index over the same users and items, with the same ids, block
+ * size, P' and precision, taken from `index` itself (the caller's Q and P are
+ * not needed).  `index` is unchanged; the caller frees both.
+ */
+rmips_status rmips_index_rebuild(const rmips_index* index, int32_t k_max, void* stream, rmips_index** out);
+
 /* Per-kernel timing of the filter kernels (Lemmas 1-3), for roofline reports. */
 typedef struct {
   int64_t filter_launches;   /* filter launches since profiling was enabled */

@@ -17,6 +17,7 @@ import numpy as np
 __all__ = [
     "RmipsError", "Index", "load_library", "rmips_build_index", "rmips_query",
     "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info", "rmips_last_query_stats",
+    "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
     "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
     "FP32", "BF16", "FP16", "Server",
@@ -34,7 +35,7 @@ EXPORTED_SYMBOLS = [
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
     "rmips_server_submit_many", "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
-    "rmips_server_destroy",
+    "rmips_server_destroy", "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
 ]
 
 
@@ -109,6 +110,9 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_query.argtypes = [VP, P, I32, C.POINTER(Segment), P, I64, C.POINTER(I64), VP]
         lib.rmips_query_batch.argtypes = [VP, P, I64, P, C.POINTER(Segment), P, I64, P, VP]
         lib.rmips_query_batch_async.argtypes = [VP, P, I64, P, P, I64, P, P, VP]
+        lib.rmips_index_save.argtypes = [VP, C.c_char_p]
+        lib.rmips_index_load.argtypes = [C.c_char_p, VP, C.POINTER(VP)]
+        lib.rmips_index_rebuild.argtypes = [VP, I32, VP, C.POINTER(VP)]
         lib.rmips_index_get_info.argtypes = [VP, C.POINTER(IndexInfo)]
         lib.rmips_last_query_stats.argtypes = [VP, C.POINTER(QueryStats)]
         lib.rmips_index_export.argtypes = [VP, I32, P, I64]
@@ -133,6 +137,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_server_destroy.argtypes = [VP]
         lib.rmips_server_destroy.restype = None
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_query_batch_async",
+                     "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
                      "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
@@ -245,6 +250,29 @@ def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
     out = C.c_void_p()
     _check(_lib.rmips_build_index(qp, n, pp, m, d, C.byref(opts), _stream(stream), C.byref(out)))
     return Index(out.value, n, m, d, int(k_max))
+
+
+def rmips_index_save(index: Index, path: str):
+    """Write the index to a file (see rmips_index_load)."""
+    _check(_lib.rmips_index_save(index.handle, os.fsencode(path)))
+
+
+def rmips_index_load(path: str, stream=None) -> Index:
+    """Read an index written by rmips_index_save onto the current device."""
+    load_library()
+    out = C.c_void_p()
+    _check(_lib.rmips_index_load(os.fsencode(path), _stream(stream), C.byref(out)))
+    h = Index(out.value, 0, 0, 0, 0)
+    info = rmips_index_get_info(h)
+    h.n, h.m, h.d, h.k_max = info["n"], info["m"], info["d"], info["k_max"]
+    return h
+
+
+def rmips_index_rebuild(index: Index, k_max: int, stream=None) -> Index:
+    """A new index over the same users and items with another k_max (Algorithm 1 again)."""
+    out = C.c_void_p()
+    _check(_lib.rmips_index_rebuild(index.handle, int(k_max), _stream(stream), C.byref(out)))
+    return Index(out.value, index.n, index.m, index.d, int(k_max))
 
 
 def rmips_query(index: Index, q, k: int, segment=None, capacity=None, out=None, stream=None) -> np.ndarray:

@@ -80,3 +80,14 @@ def test_exact_sign_full_dimension(lib):
         b = a.copy()
         b[d // 2] = np.nextafter(b[d // 2], np.float32(np.inf))
         assert rmips.rmips_exact_sign_host(u, a, b) == _fsign(u, a, b)
+
+
+def test_index_load_refuses_foreign_files_without_a_gpu(tmp_path):
+    """The file header is checked before any device call."""
+    from paper_2110_07131_gb300 import rmips
+    bogus = tmp_path / "not_an_index.bin"
+    bogus.write_bytes(b"hello, this is not an index" * 10)
+    for path in (str(bogus), str(tmp_path / "missing.bin")):
+        with pytest.raises(rmips.RmipsError) as e:
+            rmips.rmips_index_load(path)
+        assert e.value.status == 1
