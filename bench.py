@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--p-prime", type=int, default=0, help="0 = bounds over all of P")
     ap.add_argument("--block-size", type=int, default=32)
+    ap.add_argument("--no-blocks", action="store_true", help="Lemma 3 off (the paper's without-blocks ablation)")
     ap.add_argument("--batch-kernel", default="tc", choices=["tc", "cuda"],
                     help="batched filter on tensor cores (TF32 tiles) or CUDA cores (FP32 FMA)")
     ap.add_argument("--plain-queries", type=int, default=400)
@@ -60,7 +61,7 @@ def workload(a):
                         f"MF-like lognormal-norm synthetic vectors, queries = random items of P",
             "n_users": a.n, "n_items": a.m, "d": a.d, "k": a.k, "k_max": a.k_max,
             "queries_per_step": a.nq, "index": "full-P" if a.p_prime == 0 else f"P'={a.p_prime}",
-            "block_size": a.block_size, "filter_precision": a.precision,
+            "block_size": a.block_size, "block_filter": not a.no_blocks, "filter_precision": a.precision,
             "batch_filter": "tcgen05 TF32 tiles" if a.batch_kernel == "tc" else "CUDA-core FP32 FMA tiles",
             "l2": "inputs larger than L2 (Q 200 MB fp32 + bounds 200 MB); no flush between steps"}
 
@@ -288,6 +289,7 @@ def run_ours(a):
     Q, P = datagen.make_problem(a.n, a.m, a.d, SEED)
     t0 = time.perf_counter()
     index = rmips.rmips_build_index(Q, P, k_max=a.k_max, block_size=a.block_size, p_prime=a.p_prime,
+                                    block_filter=not a.no_blocks,
                                     precision=a.precision, batch_tensor_cores=(a.batch_kernel == "tc"))
     build_s = time.perf_counter() - t0
     info = index.info()
@@ -419,7 +421,7 @@ def run_ours(a):
     # DRAM bytes (read + write) of one k_mfilter_ws launch on the default
     # workload, from one ncu capture of the current kernel (273.2 MB + 4.9 MB)
     default_workload = (a.n, a.m, a.d, a.k, a.k_max, a.nq) == (1_000_000, 500_000, 50, 10, 25, 10_000)
-    tc_traffic = 278.1e6 if (tc_path and default_workload and a.block_size == 32) else None
+    tc_traffic = 278.1e6 if (tc_path and default_workload and a.block_size == 32 and not a.no_blocks) else None
     if tc_path:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         tf32_peak = bf16 * (1.1 / 2.25)

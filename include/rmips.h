@@ -79,6 +79,10 @@ typedef struct {
 /* rmips_build_index: select each user's candidate items on CUDA cores (float32
    FMA) instead of tensor cores (TF32 tiles, used when d <= 64). */
 #define RMIPS_FLAG_BUILD_CUDA_CORES 2
+/* rmips_build_index: switch the block filter (Lemma 3) off -- every block's
+   bound is -inf, so no block is ever pruned.  Answers are unchanged; this is
+   the "without blocks" ablation of the paper's evaluation. */
+#define RMIPS_FLAG_NO_BLOCK_FILTER 4
 
 /* Optional restriction of a query to a subset of users. */
 typedef struct {

@@ -545,7 +545,7 @@ __global__ void k_finalize(const float* __restrict__ Qs, const float* __restrict
 
 // --- 5. blocks (Equation 1) --------------------------------------------------------
 __global__ void k_blocks(const float2* __restrict__ Lb, const float* __restrict__ unorm, int64_t n, int bs,
-                         int64_t nb, int k_max, float* __restrict__ LB, float* __restrict__ hdr) {
+                         int64_t nb, int k_max, float* __restrict__ LB, float* __restrict__ hdr, int no_blocks) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nb * k_max) return;
   int j = (int)(e / nb);
@@ -553,7 +553,7 @@ __global__ void k_blocks(const float2* __restrict__ Lb, const float* __restrict_
   int64_t lo = b * bs, hi = lo + bs < n ? lo + bs : n;
   float mn = kInf;
   for (int64_t i = lo; i < hi; ++i) mn = fminf(mn, Lb[(int64_t)j * n + i].x);
-  LB[(int64_t)j * nb + b] = mn;
+  LB[(int64_t)j * nb + b] = no_blocks ? -kInf : mn;     // -inf: Lemma 3 never prunes (ablation)
   if (j == 0) hdr[b] = unorm[lo];
 }
 
@@ -617,7 +617,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   int bs = opts->block_size == 0 ? 32 : opts->block_size;
   if (opts->k_max < 1 || opts->k_max > RMIPS_KMAX_LIMIT || !(bs == 32 || bs == 64 || bs == 128 || bs == 256) ||
       opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 ||
-      (opts->flags & ~(RMIPS_FLAG_BATCH_CUDA_CORES | RMIPS_FLAG_BUILD_CUDA_CORES)) != 0) {
+      (opts->flags & ~(RMIPS_FLAG_BATCH_CUDA_CORES | RMIPS_FLAG_BUILD_CUDA_CORES | RMIPS_FLAG_NO_BLOCK_FILTER)) != 0) {
     set_error("invalid build options (k_max 1..28, block_size 32/64/128/256, precision 0..2)");
     return RMIPS_ERR_ARG;
   }
@@ -627,6 +627,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   idx->n = n; idx->m = m; idx->d = d; idx->k_max = opts->k_max; idx->bs = bs;
   idx->precision = opts->precision;
   idx->batch_tc = (opts->flags & RMIPS_FLAG_BATCH_CUDA_CORES) ? 0 : 1;
+  idx->no_blocks = (opts->flags & RMIPS_FLAG_NO_BLOCK_FILTER) ? 1 : 0;
   idx->pp = (opts->p_prime == 0 || opts->p_prime >= m) ? m : opts->p_prime;
   idx->full_p = idx->pp == m ? 1 : 0;
   idx->nb = (n + bs - 1) / bs;
@@ -788,7 +789,7 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     }
     // 5: blocks
     k_blocks<<<grid_for(idx->nb * idx->k_max, 256), 256, 0, st>>>(idx->Lb, idx->unorm, n, bs, idx->nb,
-                                                                   idx->k_max, idx->LB, idx->hdr);
+                                                                   idx->k_max, idx->LB, idx->hdr, idx->no_blocks);
     TRY(cudaGetLastError());
     unsigned long long h_incomp = 0;
     TRY(cudaMemcpyAsync(&h_incomp, d_incomp, sizeof(h_incomp), cudaMemcpyDeviceToHost, st));

@@ -20,7 +20,7 @@ constexpr char kMagic[8] = {'R', 'M', 'I', 'P', 'S', 'I', 'X', '1'};
 struct FileHeader {
   char magic[8];
   int64_t n, m, nb, pp, incomplete;
-  int32_t d, k_max, bs, precision, full_p, batch_tc, has_qh, has_qtc, narrays;
+  int32_t d, k_max, bs, precision, full_p, batch_tc, no_blocks, has_qh, has_qtc, narrays;
   float pn0;
 };
 
@@ -87,7 +87,7 @@ extern "C" rmips_status rmips_index_save(const rmips_index* cidx, const char* pa
   memcpy(h.magic, kMagic, sizeof(kMagic));
   h.n = idx->n; h.m = idx->m; h.nb = idx->nb; h.pp = idx->pp; h.incomplete = idx->incomplete;
   h.d = idx->d; h.k_max = idx->k_max; h.bs = idx->bs; h.precision = idx->precision; h.full_p = idx->full_p;
-  h.batch_tc = idx->batch_tc; h.has_qh = idx->Qh != nullptr; h.has_qtc = idx->Qtc != nullptr;
+  h.batch_tc = idx->batch_tc; h.no_blocks = idx->no_blocks; h.has_qh = idx->Qh != nullptr; h.has_qtc = idx->Qtc != nullptr;
   h.pn0 = idx->pn0;
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh, h.has_qtc);
   h.narrays = (int32_t)a.size();
@@ -122,7 +122,7 @@ extern "C" rmips_status rmips_index_load(const char* path, void* stream, rmips_i
   rmips_index* idx = new rmips_index();
   idx->n = h.n; idx->m = h.m; idx->nb = h.nb; idx->pp = h.pp; idx->incomplete = h.incomplete;
   idx->d = h.d; idx->k_max = h.k_max; idx->bs = h.bs; idx->precision = h.precision; idx->full_p = h.full_p;
-  idx->batch_tc = h.batch_tc; idx->pn0 = h.pn0;
+  idx->batch_tc = h.batch_tc; idx->no_blocks = h.no_blocks; idx->pn0 = h.pn0;
   cudaGetDevice(&idx->device);
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh != 0, h.has_qtc != 0);
   rmips_status s = RMIPS_OK;
@@ -192,7 +192,7 @@ extern "C" rmips_status rmips_index_rebuild(const rmips_index* cidx, int32_t k_m
     o.block_size = idx->bs;
     o.p_prime = idx->full_p ? 0 : idx->pp;
     o.precision = idx->precision;
-    o.flags = idx->batch_tc ? 0 : RMIPS_FLAG_BATCH_CUDA_CORES;
+    o.flags = (idx->batch_tc ? 0 : RMIPS_FLAG_BATCH_CUDA_CORES) | (idx->no_blocks ? RMIPS_FLAG_NO_BLOCK_FILTER : 0);
     s = rmips_build_index(Q, n, P, m, d, &o, stream, out);
   }
   if (Q) cudaFreeAsync(Q, st);

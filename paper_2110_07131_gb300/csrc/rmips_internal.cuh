@@ -177,6 +177,7 @@ struct rmips_index {
   int64_t nb = 0, pp = 0;
   int full_p = 1;
   int batch_tc = 1;             // batched filter on tensor cores (TF32) when eligible
+  int no_blocks = 0;            // Lemma 3 switched off (block bounds at -inf), for the ablation
   int device = 0;
   int64_t incomplete = 0;
   int64_t device_bytes = 0;

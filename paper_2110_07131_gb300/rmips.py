@@ -233,11 +233,12 @@ class Index:
 
 def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
                       precision="fp32", batch_tensor_cores: bool = True, build_tensor_cores: bool = True,
-                      stream=None) -> Index:
+                      block_filter: bool = True, stream=None) -> Index:
     """Build the index of Algorithm 1 from users Q [n, d] and items P [m, d].
 
     ``batch_tensor_cores=False`` keeps the batched filter on CUDA cores;
-    ``build_tensor_cores=False`` selects candidates on CUDA cores."""
+    ``build_tensor_cores=False`` selects candidates on CUDA cores;
+    ``block_filter=False`` switches Lemma 3 off (the no-blocks ablation)."""
     load_library()
     qp, qk = _ptr_f32(Q)
     pp, pk = _ptr_f32(P)
@@ -246,7 +247,8 @@ def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
     if int(pk.shape[1]) != d:
         raise RmipsError(1, "Q and P differ in dimension")
     opts = BuildOpts(int(k_max), int(block_size), int(p_prime), _PREC[precision],
-                     (0 if batch_tensor_cores else 1) | (0 if build_tensor_cores else 2))
+                     (0 if batch_tensor_cores else 1) | (0 if build_tensor_cores else 2) |
+                     (0 if block_filter else 4))
     out = C.c_void_p()
     _check(_lib.rmips_build_index(qp, n, pp, m, d, C.byref(opts), _stream(stream), C.byref(out)))
     return Index(out.value, n, m, d, int(k_max))

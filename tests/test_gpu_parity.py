@@ -356,3 +356,22 @@ def test_graph_replay_with_same_and_changing_batches():
         for r, j in enumerate(range(0, nq, 37)):
             assert np.array_equal(ids[offs[j]:offs[j + 1]], ref[name][r]), (name, nq, j)
     index.close()
+
+
+@pytest.mark.parametrize("bs", [32, 128])
+def test_no_block_filter_gives_the_same_answers(bs):
+    """Lemma 3 only skips work: switching it off (every block bound -inf) must
+    not change any answer, single or batched."""
+    Q, P = datagen.make_problem(6000, 2000, 50, 23)
+    on = rmips.rmips_build_index(Q, P, k_max=25, block_size=bs)
+    off = rmips.rmips_build_index(Q, P, k_max=25, block_size=bs, block_filter=False)
+    assert (rmips.rmips_index_export(off, "LB") == -np.inf).all()
+    qs, _ = datagen.queries_from_items(P, 300, 23)
+    ks = datagen.random_ks(len(qs), 1, 25, 23)
+    a = rmips.rmips_query_batch(on, qs, ks)
+    b = rmips.rmips_query_batch(off, qs, ks)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for j in range(0, len(qs), 29):
+        assert np.array_equal(rmips.rmips_query(off, qs[j], int(ks[j])), a[0][a[1][j]:a[1][j + 1]])
+    on.close()
+    off.close()
