@@ -21,6 +21,9 @@ comparison is within its rounding-error bound, the comparison is redone in exact
 rational arithmetic (``fractions.Fraction``), so the returned sets are those of
 exact arithmetic on the float32 inputs.
 
+``topk_mips`` is Definition 1 itself (the k-MIPS of every user, the join
+that the index's candidates come from).
+
 Parity pins (see ``tests/test_oracle.py``): the printed vectors of Table 1,
 an all-``Fraction`` brute force on tiny inputs, integer fixtures with exact ties,
 monotonicity in k, the identity ``sum_{q in P} |R_k(q)| = n k`` for tie-free
@@ -37,7 +40,7 @@ import numpy as np
 __all__ = [
     "norms_fp64", "norm_order", "exact_dot", "exact_sign_diff",
     "counts_greater", "counts_greater_multi", "reverse_kmips", "reverse_kmips_multi",
-    "decide_users", "build_index", "linear_scan", "simpfer_query", "kth_values",
+    "decide_users", "build_index", "linear_scan", "simpfer_query", "kth_values", "topk_mips",
 ]
 
 _U64 = 2.0 ** -53
@@ -188,6 +191,32 @@ def kth_values(Q, P, k_max: int) -> np.ndarray:
     part = -np.sort(-S, axis=1)[:, :kk]
     out = np.full((Q64.shape[0], k_max), -np.inf)
     out[:, :kk] = part
+    return out
+
+
+def topk_mips(Q, P, k: int) -> np.ndarray:
+    """Definition 1 (k-MIPS) for every user: ``out[i]`` holds the ids of the k
+    items with the largest ``u_i . p``, in descending order of ``u_i . p``;
+    equal products are ordered by ascending item id.  Exact: items whose
+    float64 products lie within the float64 error bound of the k-th largest
+    are ordered in rational arithmetic.  k <= |P|.
+    """
+    Q = np.asarray(Q, dtype=np.float32)
+    P = np.asarray(P, dtype=np.float32)
+    n, m = Q.shape[0], P.shape[0]
+    Q64, P64 = Q.astype(np.float64), P.astype(np.float64)
+    S = Q64 @ P64.T
+    A = np.abs(Q64) @ np.abs(P64).T
+    f = _fp64_bound(Q.shape[1])
+    out = np.empty((n, k), dtype=np.int64)
+    for i in range(n):
+        order = np.lexsort((np.arange(m), -S[i]))
+        kth = S[i, order[k - 1]]
+        slack = f * A[i].max()
+        near = np.nonzero(S[i] >= kth - 2 * slack)[0]      # every item that may rank in the top k
+        exact = {int(j): exact_dot(Q[i], P[j]) for j in near}
+        ranked = sorted(exact, key=lambda j: (-exact[j], j))
+        out[i] = ranked[:k]
     return out
 
 

@@ -277,3 +277,56 @@ def test_linear_scan_reads_negative_products():
     # products: -1, -2, -3 vs u.q = -2.5  -> two items above
     assert O.linear_scan(u, Ps[order], nP[order], q, 2) == 0
     assert O.linear_scan(u, Ps[order], nP[order], q, 3) == 1
+
+
+# ---------------------------------------------------------------------------
+# Definition 1 for every user (top-k MIPS join)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_topk_mips_matches_hand_table(table1, k):
+    g, Q, P = table1
+    hand = g["hand_inner_products"]
+    got = O.topk_mips(Q, P, k)
+    for i in range(4):
+        row = hand[f"u{i + 1}"]
+        want = sorted(row, key=lambda name: (-row[name], int(name[1:])))[:k]
+        assert _names(got[i], "p") == want
+
+
+def test_topk_mips_top1_is_the_printed_mips_column_except_u2(table1):
+    g, Q, P = table1
+    got = O.topk_mips(Q, P, 1)
+    for i in range(4):
+        name = f"u{i + 1}"
+        if name == "u2":        # printed p2, but the printed vectors give p3 (10.00 > 9.85)
+            assert _names(got[i], "p") == ["p3"]
+        else:
+            assert _names(got[i], "p") == [g["printed_mips_column"][name]]
+
+
+def _brute_topk(Q, P, k):
+    out = []
+    for i in range(Q.shape[0]):
+        vals = [(_fdot(Q[i], P[j]), j) for j in range(P.shape[0])]
+        vals.sort(key=lambda t: (-t[0], t[1]))
+        out.append([j for _, j in vals[:k]])
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_topk_mips_matches_rational_brute_force(seed):
+    Q, P = datagen.make_problem(11, 17, 5, seed)
+    Qi, Pi = datagen.integer_problem(9, 14, 4, seed, lim=2)        # many exact ties
+    for A, B in ((Q, P), (Qi, Pi)):
+        for k in (1, 3, 7, B.shape[0]):
+            assert O.topk_mips(A, B, k).tolist() == _brute_topk(A, B, k)
+
+
+def test_topk_mips_agrees_with_reverse_kmips_without_ties():
+    """For tie-free data, p is in the top-k of u exactly when u is in R_k(p)."""
+    Q, P = datagen.make_problem(40, 25, 6, 7)
+    for k in (1, 4, 9):
+        top = O.topk_mips(Q, P, k)
+        for j in range(P.shape[0]):
+            users = set(O.reverse_kmips(Q, P, P[j], k).tolist())
+            assert users == {i for i in range(Q.shape[0]) if j in top[i]}
