@@ -384,6 +384,17 @@ def run_ours(a):
 
     serving = run_serving(rmips, index, qs, a) if a.serve_requests > 0 else None
 
+    # the top-k join over all users (Definition 1 for every user), device output
+    join_s = None
+    if a.p_prime == 0 and a.k <= a.k_max:
+        jout = torch.empty((a.n, a.k), dtype=torch.int64, device=dev)
+        rmips.rmips_topk_join(index, a.k, out=jout)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rmips.rmips_topk_join(index, a.k, out=jout)
+        join_s = time.perf_counter() - t0
+        del jout
+
     # single-query filter timing (HBM-bound kernel), profiled separately from the latency run
     rmips.rmips_profile_enable(index, True)
     for j in range(min(200, a.plain_queries)):
@@ -464,6 +475,7 @@ def run_ours(a):
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain, "serving": serving,
             "batch_latency_ms": ms_max / a.steps,
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
+            "topk_join_s": join_s,
             "index_incomplete_users": info["incomplete"],
             "users_returned_per_query": results / (a.steps * a.nq),
             "result_sizes_last_step": result_sizes(last_offs[0]),

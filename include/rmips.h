@@ -201,6 +201,18 @@ rmips_status rmips_index_load(const char* path, void* stream, rmips_index** out)
  */
 rmips_status rmips_index_rebuild(const rmips_index* index, int32_t k_max, void* stream, rmips_index** out);
 
+/*
+ * rmips_topk_join -- k-MIPS (Definition 1) of every user over all items: the
+ * join whose top-k_max part the index keeps.  out_ids [n][k] (host or device,
+ * row = the caller's user id) receives the caller's ids of the user's k items
+ * with the largest inner products, in descending order; equal products come
+ * in ascending item id.  Needs a full-P index (p_prime = 0; otherwise
+ * RMIPS_ERR_ARG); k in [1, min(k_max, m)] (otherwise RMIPS_ERR_K_RANGE).
+ * Exact: products are ranked in float64 with their error bounds, and in exact
+ * integer arithmetic where two bounds overlap.  Synchronises `stream`.
+ */
+rmips_status rmips_topk_join(const rmips_index* index, int32_t k, int64_t* out_ids, void* stream);
+
 /* Per-kernel timing of the filter kernels (Lemmas 1-3), for roofline reports. */
 typedef struct {
   int64_t filter_launches;   /* filter launches since profiling was enabled */

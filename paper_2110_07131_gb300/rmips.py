@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "RmipsError", "Index", "load_library", "rmips_build_index", "rmips_query",
     "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info", "rmips_last_query_stats",
-    "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
+    "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
     "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
     "FP32", "BF16", "FP16", "Server",
@@ -35,7 +35,7 @@ EXPORTED_SYMBOLS = [
     "rmips_last_error", "rmips_exact_sign_host", "rmips_profile_enable", "rmips_profile_read",
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
     "rmips_server_submit_many", "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
-    "rmips_server_destroy", "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
+    "rmips_server_destroy", "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
 ]
 
 
@@ -113,6 +113,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_index_save.argtypes = [VP, C.c_char_p]
         lib.rmips_index_load.argtypes = [C.c_char_p, VP, C.POINTER(VP)]
         lib.rmips_index_rebuild.argtypes = [VP, I32, VP, C.POINTER(VP)]
+        lib.rmips_topk_join.argtypes = [VP, I32, P, VP]
         lib.rmips_index_get_info.argtypes = [VP, C.POINTER(IndexInfo)]
         lib.rmips_last_query_stats.argtypes = [VP, C.POINTER(QueryStats)]
         lib.rmips_index_export.argtypes = [VP, I32, P, I64]
@@ -137,7 +138,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_server_destroy.argtypes = [VP]
         lib.rmips_server_destroy.restype = None
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_query_batch_async",
-                     "rmips_index_save", "rmips_index_load", "rmips_index_rebuild",
+                     "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
                      "rmips_index_get_info",
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
@@ -275,6 +276,17 @@ def rmips_index_rebuild(index: Index, k_max: int, stream=None) -> Index:
     out = C.c_void_p()
     _check(_lib.rmips_index_rebuild(index.handle, int(k_max), _stream(stream), C.byref(out)))
     return Index(out.value, index.n, index.m, index.d, int(k_max))
+
+
+def rmips_topk_join(index: Index, k: int, out=None, stream=None):
+    """k-MIPS of every user (Definition 1): [n, k] item ids, descending inner product."""
+    if out is None:
+        out = np.empty((index.n, int(k)), dtype=np.int64)
+        _check(_lib.rmips_topk_join(index.handle, int(k), out.ctypes.data, _stream(stream)))
+        return out
+    ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+    _check(_lib.rmips_topk_join(index.handle, int(k), ptr, _stream(stream)))
+    return out
 
 
 def rmips_query(index: Index, q, k: int, segment=None, capacity=None, out=None, stream=None) -> np.ndarray:
