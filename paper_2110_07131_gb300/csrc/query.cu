@@ -1937,6 +1937,23 @@ __device__ __forceinline__ float ws_pick(const float* v, int q) {
   return (q & 16) ? a[1] : a[0];
 }
 
+// Largest of three floats in one instruction (three-input max.f32).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// Largest of 32 accumulators: 17 max operations in a tree four deep.
+__device__ __forceinline__ float ws_max32(const float* v) {
+  float m[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) m[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+  m[10] = fmaxf(v[30], v[31]);
+  const float a = fmax3(m[0], m[1], m[2]), b = fmax3(m[3], m[4], m[5]), c = fmax3(m[6], m[7], m[8]);
+  return fmaxf(fmax3(a, b, c), fmaxf(m[9], m[10]));
+}
+
 // Lemma 1 / hi_k / Lemma 2 classification of up to 32 accumulators v of one
 // user against the queries of cq / qj (live leading ones).  Only columns at or
 // above the fast threshold are tested one by one (a lane has one or two); yes
@@ -1956,11 +1973,11 @@ __device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, con
   while (hit) {
     const int q = __ffs(hit) - 1;
     hit &= hit - 1;
+    const float2 e2 = cq[q];                                               // both loads in flight together
+    const int j = qj[q];
     const float vq = ws_pick(v, q);
-    const float2 e2 = cq[q];
     const float e = __fmaf_ru(un, e2.x, e2.y);
     if (__fadd_ru(vq, e) < L.x) continue;                                  // decided no by Lemma 1
-    const int j = qj[q];
     if (!in_segment(c, b, j, pos)) continue;
     const float lo = __fsub_rd(vq, e);
     if (c.full_p ? (lo >= L.y) : (lo >= pkb)) {
@@ -2314,17 +2331,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
         const float thr = __fsub_rd(L.x, __fmaf_ru(un, itm.c0.x, itm.c0.y));
         bool any = true;
-        if (live == WS_ECOLS) {
-          float m[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) m[i] = v[i];
-#pragma unroll
-          for (int q = 8; q < WS_ECOLS; q += 8)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) m[i] = fmaxf(m[i], v[q + i]);
-          const float mx = fmaxf(fmaxf(fmaxf(m[0], m[1]), fmaxf(m[2], m[3])), fmaxf(fmaxf(m[4], m[5]), fmaxf(m[6], m[7])));
-          any = mx >= thr;
-        }
+        if (live == WS_ECOLS) any = ws_max32(v) >= thr;
         long long t_sl = 0;
         if (PROF) t_sl = clock64();
         if (any) ws_classify<PROF>(c, b, v, live, thr, un, L, kq, cq, qj, pos, st_yes, st_todo, w_atom);
