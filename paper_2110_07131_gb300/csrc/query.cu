@@ -1139,12 +1139,35 @@ struct Batch {
 
 // (a) per query: norm bound, slack, checks, sort key, k histogram.
 __global__ void k_mprep_a(Common c, Batch b, int precision) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= b.nq) return;
-  float qn, eps;
-  const bool fin = query_bounds(b.dq + (int64_t)j * c.d, c.d, precision, &qn, &eps);
+  // eight lanes per query: the sum of squares rounded up in every step (any
+  // order gives an upper bound of ||q||^2), the largest |q_i|, finiteness
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = (int)(t >> 3), sub = (int)(t & 7);
+  const int d = c.d;
+  const bool live = j < b.nq;
+  float acc = 0.f, qmax = 0.f;
+  bool fin = true;
+  if (live) {
+    const float* q = b.dq + (int64_t)j * d;
+    for (int i = sub; i < d; i += 8) {
+      const float v = q[i];
+      fin = fin && isfinite(v);
+      acc = __fmaf_ru(v, v, acc);
+      qmax = fmaxf(qmax, fabsf(v));
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    acc = __fadd_ru(acc, __shfl_xor_sync(FULL, acc, o));
+    qmax = fmaxf(qmax, __shfl_xor_sync(FULL, qmax, o));
+  }
+  const unsigned bad = __ballot_sync(FULL, !fin);
+  if (!live || sub != 0) return;
+  const float qn = __fsqrt_ru(acc);
+  const float lsub = (precision == RMIPS_FP16) ? 0x1p-25f : (precision == RMIPS_BF16 ? 0x1p-133f : 0.f);
+  const float eps = __fmul_ru((float)(d + 2), __fmaf_ru(lsub, qmax, 0x1p-148f));
   int k = b.dk[j];
-  if (!fin) set_status(c.ctr, ST_NONFINITE);
+  if ((bad >> (threadIdx.x & 24)) & 0xffu) set_status(c.ctr, ST_NONFINITE);
   if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_INTERNAL); k = 1; }
   b.dqn[j] = qn;
   b.deps[j] = eps;
@@ -1160,7 +1183,10 @@ __global__ void k_mprep_a(Common c, Batch b, int precision) {
 __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
   __shared__ int first[RMIPS_KMAX_LIMIT + 2];
   __shared__ int slot0[RMIPS_KMAX_LIMIT + 2];
+  __shared__ int hist[RMIPS_KMAX_LIMIT + 2];
   const int tid = threadIdx.x;
+  if (tid < RMIPS_KMAX_LIMIT + 2) hist[tid] = (tid >= 1 && tid <= RMIPS_KMAX_LIMIT) ? b.hist[tid] : 0;
+  __syncthreads();
   if (tid == 0) {
     c.ctr[C_YES] = 0;
     c.ctr[C_TODO] = 0;
@@ -1170,7 +1196,7 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
     for (int k = 0; k <= RMIPS_KMAX_LIMIT + 1; ++k) {
       first[k] = f;
       slot0[k] = s;
-      const int h = (k >= 1 && k <= RMIPS_KMAX_LIMIT) ? b.hist[k] : 0;
+      const int h = hist[k];
       if (h > 0) {
         const int tiles = (h + MQ_TQ - 1) / MQ_TQ;
         if (b.gitem) {                               // tensor-core items: chunks of 128 queries
@@ -1191,7 +1217,7 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
     b.gslot0[tid] = slot0[tid];
   }
   for (int k = 1; k <= RMIPS_KMAX_LIMIT; ++k) {
-    const int h = b.hist[k];
+    const int h = hist[k];
     if (h == 0) continue;
     const int pad = ((h + MQ_TQ - 1) / MQ_TQ) * MQ_TQ;
     for (int r = h + tid; r < pad; r += blockDim.x) {
@@ -1226,26 +1252,34 @@ __global__ void __launch_bounds__(RUN) k_mprep_runs(Batch b) {
   b.runs[g] = keys[tid];
 }
 
-// (d) grid: the final sorted position of each key is its position in its run
-// plus, for every other run, the number of keys below it (keys are distinct),
-// found by binary search; the position gives the query's slot in its k-group.
-__global__ void k_mprep_place(Common c, Batch b, int nruns) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= (int64_t)nruns * RUN) return;
-  const unsigned long long key = b.runs[g];
-  if (key == ~0ull) return;                        // padding
-  const int r = (int)(g / RUN);
-  int64_t rank = g - (int64_t)r * RUN;
-  for (int o = 0; o < nruns; ++o) {
-    if (o == r) continue;
-    const unsigned long long* run = b.runs + (int64_t)o * RUN;
+// (d) one CTA per run: the final sorted position of each key is its position
+// in its run plus, for every other run, the number of keys below it (keys are
+// distinct), found by binary search in a shared-memory copy of that run (the
+// next run's keys are loaded while the current one is searched); the position
+// gives the query's slot in its k-group.
+__global__ void __launch_bounds__(RUN) k_mprep_place(Common c, Batch b, int nruns) {
+  __shared__ unsigned long long other[RUN];
+  const int r = blockIdx.x, tid = threadIdx.x;
+  const unsigned long long key = b.runs[(int64_t)r * RUN + tid];
+  int64_t rank = tid;
+  int o = r == 0 ? 1 : 0;
+  unsigned long long nxt = o < nruns ? b.runs[(int64_t)o * RUN + tid] : 0ull;
+  while (o < nruns) {                                 // uniform over the CTA
+    other[tid] = nxt;
+    int on = o + 1;
+    if (on == r) ++on;
+    if (on < nruns) nxt = b.runs[(int64_t)on * RUN + tid];
+    __syncthreads();
     int lo = 0, hi = RUN;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
-      if (run[mid] < key) lo = mid + 1; else hi = mid;
+      if (other[mid] < key) lo = mid + 1; else hi = mid;
     }
     rank += lo;
+    __syncthreads();
+    o = on;
   }
+  if (key == ~0ull) return;                           // padding
   const int k = (int)(key >> 46);
   const int j = (int)(key & 16383ull);
   const int slot = b.gslot0[k] + (int)(rank - b.gfirst[k]);
@@ -1524,6 +1558,14 @@ __global__ void __launch_bounds__(MQ_THREADS) k_mfilter(Common c, Batch b, int n
   (void)st_lrows;
 }
 
+// Four undecided pairs per warp, eight lanes per pair (four candidates per
+// lane): float32 u.q with its bound against the index's interval of each
+// candidate's u.p decides almost every pair without reading an item row.  A
+// pair with an overlapping interval, or whose user has no candidate proof,
+// goes to the whole-warp exact path (recheck_candidates / verify_scan).
+// Four pairs in flight per warp hide the dependent loads (pair -> user and
+// query rows -> candidate intervals); the yes pairs of a warp take one slot
+// reservation together.
 __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
   __shared__ long long s_cnt;
   __shared__ int s_skip;
@@ -1535,72 +1577,137 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
   __syncthreads();
   if (s_skip) return;
   const long long cnt = s_cnt;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+  const unsigned gbits = 0xffu << (grp * 8);
   const int d = c.d;
+  const float tiny = (d + 2) * 0x1p-148f;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < cnt; t += nw) {
-    const unsigned long long pr = b.tpairs[t];
+  for (int64_t t0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 4; t0 < cnt; t0 += nw * 4) {
+    const int64_t t = t0 + grp;
+    const bool have = t < cnt;
+    const unsigned long long pr = have ? b.tpairs[t] : 0ull;
     const int j = (int)(pr >> 32);
     const int32_t pos = (int32_t)(pr & 0xffffffffull);
-    const float* q = b.dq + (int64_t)j * d;
-    const int k = b.dk[j];
+    const bool quick = have && c.full_p && !c.incomp[pos];
+    const int k = have ? b.dk[j] : 0;
     const float* u = c.Qs + (int64_t)pos * d;
-    bool yes;
-    if (c.full_p && !c.incomp[pos]) {
-      yes = recheck_candidates(u, q, c.cand + (int64_t)pos * RMIPS_KC, c.cbnd + (int64_t)pos * RMIPS_KC, c.Ps, d, k,
-                               c.cg32, c.ctr);
-    } else {
-      yes = verify_scan(u, c.unorm[pos], c, q, k, b.deps[j]);
+    const float* q = b.dq + (int64_t)j * d;
+    float g32 = 0.f, a32 = 0.f;
+    for (int i = sub; quick && i < d; i += 8) {
+      const float x = u[i], y = q[i];
+      g32 = fmaf(x, y, g32);
+      a32 = fmaf(fabsf(x), fabsf(y), a32);
     }
-    if (lane == 0 && yes) {
-      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
-      if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (uint32_t)pos;
-      atomicAdd(&b.qcnt[j], 1);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {                 // within the eight lanes of the pair
+      g32 += __shfl_xor_sync(FULL, g32, o);
+      a32 += __shfl_xor_sync(FULL, a32, o);
+    }
+    const float eg = __fmaf_ru(a32, c.cg32, tiny);
+    const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
+    int ngt = 0;
+    bool overlap = false;
+    if (quick) {
+      const int32_t* crow = c.cand + (int64_t)pos * RMIPS_KC;
+      const float2* cbrow = c.cbnd + (int64_t)pos * RMIPS_KC;
+      int32_t its[RMIPS_KC / 8];
+      float2 cbs[RMIPS_KC / 8];
+#pragma unroll
+      for (int r = 0; r < RMIPS_KC / 8; ++r) {
+        its[r] = crow[sub + 8 * r];
+        cbs[r] = cbrow[sub + 8 * r];
+      }
+#pragma unroll
+      for (int r = 0; r < RMIPS_KC / 8; ++r) {
+        if (its[r] < 0) continue;
+        if (cbs[r].x > gh) ++ngt;
+        else if (!(cbs[r].y < gl)) overlap = true;
+      }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) ngt += __shfl_xor_sync(FULL, ngt, o);
+    const bool grp_overlap = (__ballot_sync(FULL, overlap) & gbits) != 0;
+    bool yes = quick && !grp_overlap && ngt < k;
+    // the pairs the intervals did not decide, one at a time with the whole warp
+    unsigned slow = __ballot_sync(FULL, sub == 0 && have && !(quick && !grp_overlap));
+    while (slow) {
+      const int src = __ffs(slow) - 1;
+      slow &= slow - 1;
+      const unsigned long long sp = __shfl_sync(FULL, pr, src);
+      const int sj = (int)(sp >> 32);
+      const int32_t spos = (int32_t)(sp & 0xffffffffull);
+      const float* su = c.Qs + (int64_t)spos * d;
+      const float* sq = b.dq + (int64_t)sj * d;
+      const int sk = b.dk[sj];
+      const bool y = (c.full_p && !c.incomp[spos])
+                         ? recheck_candidates(su, sq, c.cand + (int64_t)spos * RMIPS_KC,
+                                              c.cbnd + (int64_t)spos * RMIPS_KC, c.Ps, d, sk, c.cg32, c.ctr)
+                         : verify_scan(su, c.unorm[spos], c, sq, sk, b.deps[sj]);
+      if (lane == src) yes = y;
+    }
+    const unsigned ym = __ballot_sync(FULL, sub == 0 && yes);
+    if (ym) {
+      long long base = 0;
+      if (lane == 0) base = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(ym));
+      base = __shfl_sync(FULL, base, 0);
+      if (sub == 0 && yes) {
+        const long long at = base + __popc(ym & ((1u << lane) - 1u));
+        if (at < b.cap_y) b.ypairs[at] = pr;
+        atomicAdd(&b.qcnt[j], 1);
+      }
     }
   }
 }
 
 // Exclusive scan of per-query counts into absolute offsets.
 __global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
+  constexpr int R = MQ_MAXQ / 1024;                    // chunks of 1024 queries, one count per thread
   __shared__ long long s_warp[32];
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_base = c.ctr[C_CURSOR];
-  __syncthreads();
-  const int per = (b.nq + 1023) / 1024;
-  const int j0 = tid * per, j1 = min(b.nq, j0 + per);
-  long long local = 0;
-  for (int j = j0; j < j1; ++j) local += b.qcnt[j];
-  long long x = local;
-  for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    long long v = s_warp[lane];
-    for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, v, o); if (lane >= o) v += y; }
-    s_warp[lane] = v;
+  int v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {                        // every load issued before the first scan
+    const int j = r * 1024 + tid;
+    v[r] = j < b.nq ? b.qcnt[j] : 0;
   }
   __syncthreads();
-  long long run = s_base + (x - local) + (wid ? s_warp[wid - 1] : 0);
-  for (int j = j0; j < j1; ++j) {
-    b.doffs[j] = run;
-    run += b.qcnt[j];
-    b.bslot[j] = -1;
-    if (b.qcnt[j] > MEMIT_MID_CAP) {
-      const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
-      b.big[r] = j;
-      if (r < MQ_BIG_SLOTS) b.bslot[j] = (int32_t)r;
-    } else if (b.qcnt[j] > 32) {
-      const long long r = atomicAdd((unsigned long long*)&c.ctr[C_NMID], 1ull);
-      b.mid[r] = j;
+  long long run = s_base;                              // results of all earlier chunks
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (r * 1024 >= b.nq) break;                       // uniform
+    long long x = v[r];
+    for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      long long w = s_warp[lane];
+      for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, w, o); if (lane >= o) w += y; }
+      s_warp[lane] = w;
     }
+    __syncthreads();
+    const int j = r * 1024 + tid;
+    if (j < b.nq) {
+      b.doffs[j] = run + (x - v[r]) + (wid ? s_warp[wid - 1] : 0);
+      int32_t slot = -1;
+      if (v[r] > MEMIT_MID_CAP) {
+        const long long q = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
+        b.big[q] = j;
+        if (q < MQ_BIG_SLOTS) slot = (int32_t)q;
+      } else if (v[r] > 32) {
+        const long long q = atomicAdd((unsigned long long*)&c.ctr[C_NMID], 1ull);
+        b.mid[q] = j;
+      }
+      b.bslot[j] = slot;
+    }
+    run += s_warp[31];
+    __syncthreads();                                   // s_warp is rewritten by the next chunk
   }
-  __syncthreads();
   if (tid == 0) {
-    const long long total = s_warp[31];
-    b.doffs[b.nq] = s_base + total;
-    c.ctr[C_CURSOR] = s_base + total;
-    if (s_base + total > b.capacity) set_status(c.ctr, ST_CAPACITY);
+    b.doffs[b.nq] = run;
+    c.ctr[C_CURSOR] = run;
+    if (run > b.capacity) set_status(c.ctr, ST_CAPACITY);
   }
 }
 
@@ -1905,15 +2012,45 @@ size_t ws_smem_bytes(int kind, int ns) {
 
 // Lemma 3 prefix of every (block, k-group): the leading queries of the group
 // (descending norm) whose bound fl_up(h qn) is not below the block's LB.
-__global__ void k_mprefix(Common c, Batch b, int ngroups) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= c.nb * ngroups) return;
-  const int64_t blk = e / ngroups;
-  const int g = (int)(e - blk * ngroups);
-  const int4 G = b.grp[g];
-  int r = 0;
-  if (G.z > 0) r = lemma3_prefix(b.bqn, G.y, G.z, c.hdr[blk], c.LB[(int64_t)(G.x - 1) * c.nb + blk]);
-  b.gpre[e] = r;
+// One thread per block.  The query norms of every group (descending) are
+// sampled at every fourth slot into shared memory; the search over the
+// samples leaves at most three norms between a sample that keeps its query
+// and the next that does not, read at once from global memory.  The test is
+// lemma3_prefix's, on the same values, so the prefix is the same.
+constexpr int MPRE_STRIDE = 4;
+__global__ void __launch_bounds__(256) k_mprefix(Common c, Batch b, int ngroups) {
+  __shared__ float smp[(MQ_SLOTS + MPRE_STRIDE - 1) / MPRE_STRIDE];
+  __shared__ int4 sg[RMIPS_KMAX_LIMIT + 1];
+  const int tid = threadIdx.x;
+  const int total = b.grp[RMIPS_KMAX_LIMIT].y;            // slots of all groups
+  for (int i = tid; i * MPRE_STRIDE < total; i += blockDim.x) smp[i] = b.bqn[i * MPRE_STRIDE];
+  for (int g = tid; g < ngroups; g += blockDim.x) sg[g] = b.grp[g];
+  __syncthreads();
+  const int64_t blk = blockIdx.x * (int64_t)blockDim.x + tid;
+  if (blk >= c.nb) return;
+  const float h = c.hdr[blk];
+  for (int g = 0; g < ngroups; ++g) {
+    const int4 G = sg[g];
+    if (G.z <= 0) break;                                  // the non-empty groups come first
+    const float lb = c.LB[(int64_t)(G.x - 1) * c.nb + blk];
+    // samples inside the group: slots MPRE_STRIDE*i, i in [i0, i1)
+    const int i0 = (G.y + MPRE_STRIDE - 1) / MPRE_STRIDE, i1 = (G.y + G.z + MPRE_STRIDE - 1) / MPRE_STRIDE;
+    int lo = i0, hi = i1;                                 // first sample whose query Lemma 3 drops
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__fmul_ru(h, smp[mid]) < lb) hi = mid; else lo = mid + 1;
+    }
+    const int rhi = lo < i1 ? lo * MPRE_STRIDE - G.y : G.z;           // dropped (or the group's end)
+    const int rlo = lo > i0 ? (lo - 1) * MPRE_STRIDE - G.y : -1;      // kept (or before the start)
+    float v[MPRE_STRIDE - 1];
+#pragma unroll
+    for (int t = 0; t < MPRE_STRIDE - 1; ++t) v[t] = rlo + 1 + t < rhi ? b.bqn[G.y + rlo + 1 + t] : 0.f;
+    int r = rhi;
+#pragma unroll
+    for (int t = MPRE_STRIDE - 2; t >= 0; --t)
+      if (rlo + 1 + t < rhi && __fmul_ru(h, v[t]) < lb) r = rlo + 1 + t;
+    b.gpre[blk * ngroups + g] = r;
+  }
 }
 
 // Queries of item t of a group whose tile prefix is gmax, rounded up to the
@@ -2593,16 +2730,16 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     const int nruns = (cnt + RUN - 1) / RUN;
     auto pre = [&](cudaStream_t q) {
       cudaMemsetAsync(b.hist, 0, (RMIPS_KMAX_LIMIT + 2) * sizeof(int), q);
-      k_mprep_a<<<(cnt + 255) / 256, 256, 0, q>>>(c, b, idx->precision);
+      k_mprep_a<<<(cnt * 8 + 255) / 256, 256, 0, q>>>(c, b, idx->precision);
       k_mprep_groups<<<1, 256, 0, q>>>(c, b);
       k_mprep_runs<<<nruns, RUN, 0, q>>>(b);
-      k_mprep_place<<<(nruns * RUN + 255) / 256, 256, 0, q>>>(c, b, nruns);
+      k_mprep_place<<<nruns, RUN, 0, q>>>(c, b, nruns);
       if (!use_tc) k_mprep_c<<<sm_count * 4, 256, 0, q>>>(c, b);
       if (use_tc) k_mprep_items<<<MQ_ITEMS, 256, 0, q>>>(c, b);
-      if (use_tc) k_mprefix<<<(unsigned)((idx->nb * ngroups_max + 255) / 256), 256, 0, q>>>(c, b, ngroups_max);
+      if (use_tc) k_mprefix<<<(unsigned)((idx->nb + 255) / 256), 256, 0, q>>>(c, b, ngroups_max);
     };
     auto post = [&](cudaStream_t q) {
-      k_mresolve<<<sm_count * 8, 256, 0, q>>>(c, b);     // one warp per pair: latency-bound, many warps
+      k_mresolve<<<sm_count * 4, 256, 0, q>>>(c, b);     // 64 registers: four CTAs per SM, one wave
       k_mscan<<<1, 1024, 0, q>>>(c, b);
       k_mscatter<<<sm_count * 4, 256, 0, q>>>(c, b);
       k_memit<<<(cnt + MEMIT_Q - 1) / MEMIT_Q, 256, 0, q>>>(c, b);
