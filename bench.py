@@ -62,7 +62,8 @@ def workload(a):
             "n_users": a.n, "n_items": a.m, "d": a.d, "k": a.k, "k_max": a.k_max,
             "queries_per_step": a.nq, "index": "full-P" if a.p_prime == 0 else f"P'={a.p_prime}",
             "block_size": a.block_size, "block_filter": not a.no_blocks, "filter_precision": a.precision,
-            "batch_filter": "tcgen05 TF32 tiles" if a.batch_kernel == "tc" else "CUDA-core FP32 FMA tiles",
+            "batch_filter": (f"tcgen05 {dict(fp32='TF32', fp16='FP16', bf16='BF16')[a.precision]} tiles"
+                             if a.batch_kernel == "tc" else "CUDA-core FP32 FMA tiles"),
             "l2": "inputs larger than L2 (Q 200 MB fp32 + bounds 200 MB); no flush between steps"}
 
 
@@ -355,7 +356,7 @@ def run_ours(a):
 
     # end to end through the public API with host buffers (copies inside the timed region)
     hq = np.ascontiguousarray(qs[:a.nq])
-    e2e_steps = max(2, min(a.steps, 5))
+    e2e_steps = max(3, min(a.steps, 10))
     rmips.rmips_query_batch(index, hq, ks)
     t0 = time.perf_counter()
     d2h = 0
@@ -428,18 +429,24 @@ def run_ours(a):
     m_flops = prof["mfilter_alg_flops"] / ml
     m_ms = prof["mfilter_ms"] / ml
     m_ach = m_flops / (m_ms / 1e3) / 1e12 if m_ms > 0 else 0.0
-    tc_path = a.batch_kernel == "tc" and a.d <= 64 and a.precision == "fp32"
+    tc_path = a.batch_kernel == "tc" and a.d <= 64
     # DRAM bytes (read + write) of one k_mfilter_ws launch on the default
     # workload, from one ncu capture of the current kernel (273.2 MB + 4.9 MB)
     default_workload = (a.n, a.m, a.d, a.k, a.k_max, a.nq) == (1_000_000, 500_000, 50, 10, 25, 10_000)
-    tc_traffic = 278.1e6 if (tc_path and default_workload and a.block_size == 32 and not a.no_blocks) else None
+    tc_traffic = 278.1e6 if (tc_path and default_workload and a.block_size == 32 and not a.no_blocks
+                             and a.precision == "fp32") else None
     if tc_path:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        tf32_peak = bf16 * (1.1 / 2.25)
-        roofline = {"bound": "tensor", "kernel": "k_mfilter_ws (warp-specialized: TMA-fed tcgen05 TF32 "
-                                                  "128x64xK tiles into 4 TMEM stages + Lemmas 1/2 epilogue)",
-                    "achieved": m_ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": m_ach / tf32_peak,
-                    "peak_source": f"measured bf16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25",
+        if a.precision == "fp32":
+            op, tc_peak = "TF32", bf16 * (1.1 / 2.25)
+            peak_source = f"measured bf16 {bf16:.0f} TFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
+        else:
+            op, tc_peak = a.precision.upper(), bf16
+            peak_source = f"measured bf16 {bf16:.0f} TFLOP/s (FP16 and BF16 share the rate)"
+        roofline = {"bound": "tensor", "kernel": f"k_mfilter_ws (warp-specialized: TMA-fed tcgen05 {op} "
+                                                  "128x128xK tiles into 4 TMEM stages + Lemmas 1/2 epilogue)",
+                    "achieved": m_ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": m_ach / tc_peak,
+                    "peak_source": peak_source,
                     "traffic": tc_traffic, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
                     "pairs_per_launch": prof["mfilter_pairs"] / ml,
                     "tiles_per_launch": pprof["mfilter_tiles"] / max(1, pprof["mfilter_launches"]),
@@ -467,7 +474,8 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": ("tf32" if tc_path else ("f32" if a.precision == "fp32" else a.precision)) + "+f64 recheck",
+            "dtype": ({"fp32": "tf32", "fp16": "f16", "bf16": "bf16"}[a.precision] if tc_path
+                      else ("f32" if a.precision == "fp32" else a.precision)) + "+f64 recheck",
             "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
             "gpu_launches": a.steps * ((16 if a.batch_kernel == "tc" and a.d <= 64 else 15) * ((a.nq + 16383) // 16384) + 1),

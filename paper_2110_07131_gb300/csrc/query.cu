@@ -1092,6 +1092,10 @@ constexpr int MQ_THREADS = 256;
 constexpr int MQ_US = MQ_TU + 4;       // row stride of the transposed user tile
 constexpr int MQ_QS = MQ_TQ + 4;       // row stride of the transposed query tile
 
+// A reserved but unused slot of a pair list (the tensor-core filter's
+// epilogue warps reserve the lists in chunks); readers skip it.
+constexpr unsigned long long PAIR_NONE = ~0ull;
+
 struct Batch {
   const float* dq;        // [nq][d] staged queries (call order)
   const int32_t* dk;      // [nq]
@@ -1192,6 +1196,7 @@ __global__ void __launch_bounds__(256) k_mprep_groups(Common c, Batch b) {
     c.ctr[C_TODO] = 0;
     c.ctr[C_NBIG] = 0;
     c.ctr[C_NMID] = 0;
+    c.ctr[C_TILE] = 0;
     int f = 0, s = 0, g = 0, nit = 0;
     for (int k = 0; k <= RMIPS_KMAX_LIMIT + 1; ++k) {
       first[k] = f;
@@ -1578,14 +1583,13 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
   if (s_skip) return;
   const long long cnt = s_cnt;
   const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
-  const unsigned gbits = 0xffu << (grp * 8);
   const int d = c.d;
   const float tiny = (d + 2) * 0x1p-148f;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 4; t0 < cnt; t0 += nw * 4) {
     const int64_t t = t0 + grp;
-    const bool have = t < cnt;
-    const unsigned long long pr = have ? b.tpairs[t] : 0ull;
+    const unsigned long long pr = t < cnt ? b.tpairs[t] : PAIR_NONE;
+    const bool have = pr != PAIR_NONE;
     const int j = (int)(pr >> 32);
     const int32_t pos = (int32_t)(pr & 0xffffffffull);
     const bool quick = have && c.full_p && !c.incomp[pos];
@@ -1606,11 +1610,11 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
     const float eg = __fmaf_ru(a32, c.cg32, tiny);
     const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
     int ngt = 0;
-    bool overlap = false;
+    uint32_t ovm = 0;                                  // this lane's candidates whose interval overlaps
+    int32_t its[RMIPS_KC / 8] = {-1, -1, -1, -1};
     if (quick) {
       const int32_t* crow = c.cand + (int64_t)pos * RMIPS_KC;
       const float2* cbrow = c.cbnd + (int64_t)pos * RMIPS_KC;
-      int32_t its[RMIPS_KC / 8];
       float2 cbs[RMIPS_KC / 8];
 #pragma unroll
       for (int r = 0; r < RMIPS_KC / 8; ++r) {
@@ -1621,15 +1625,55 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
       for (int r = 0; r < RMIPS_KC / 8; ++r) {
         if (its[r] < 0) continue;
         if (cbs[r].x > gh) ++ngt;
-        else if (!(cbs[r].y < gl)) overlap = true;
+        else if (!(cbs[r].y < gl)) ovm |= 1u << r;
       }
     }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) ngt += __shfl_xor_sync(FULL, ngt, o);
-    const bool grp_overlap = (__ballot_sync(FULL, overlap) & gbits) != 0;
-    bool yes = quick && !grp_overlap && ngt < k;
-    // the pairs the intervals did not decide, one at a time with the whole warp
-    unsigned slow = __ballot_sync(FULL, sub == 0 && have && !(quick && !grp_overlap));
+    // Overlapping candidates, one at a time with the whole warp: most are the
+    // query's own copy in P (queries drawn from the items), an exact tie that
+    // the bitwise comparison settles; otherwise float32 u.p with its bound.
+    // What that leaves open sends the pair to the exact path below.
+    bool hardg = false;
+    for (unsigned pend = __ballot_sync(FULL, ovm != 0); pend; pend = __ballot_sync(FULL, ovm != 0)) {
+      const int src = __ffs(pend) - 1;
+      const uint32_t m = __shfl_sync(FULL, ovm, src);
+      const int r = __ffs(m) - 1;
+      if (lane == src) ovm &= ovm - 1;
+      int32_t mine = its[0];
+#pragma unroll
+      for (int x = 1; x < RMIPS_KC / 8; ++x) mine = r == x ? its[x] : mine;
+      const int32_t it = __shfl_sync(FULL, mine, src);
+      const unsigned long long opr = __shfl_sync(FULL, pr, src);
+      const float ogl = __shfl_sync(FULL, gl, src), ogh = __shfl_sync(FULL, gh, src);
+      const float* op = c.Ps + (int64_t)it * d;
+      const float* ou = c.Qs + (int64_t)(int32_t)(opr & 0xffffffffull) * d;
+      const float* oq = b.dq + (int64_t)(int)(opr >> 32) * d;
+      bool same = true;
+      float sp = 0.f, sb = 0.f;
+      for (int i = lane; i < d; i += 32) {
+        const float pv = op[i], uv = ou[i];
+        same = same && __float_as_uint(pv) == __float_as_uint(oq[i]);
+        sp = fmaf(uv, pv, sp);
+        sb = fmaf(fabsf(uv), fabsf(pv), sb);
+      }
+      same = __all_sync(FULL, same);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sp += __shfl_xor_sync(FULL, sp, o);
+        sb += __shfl_xor_sync(FULL, sb, o);
+      }
+      const float ep = __fmaf_ru(sb, c.cg32, tiny);
+      const bool ogt = !same && __fsub_rd(sp, ep) > ogh;
+      const bool ohard = !same && !ogt && !(__fadd_ru(sp, ep) < ogl);
+      if ((lane >> 3) == (src >> 3)) {
+        ngt += ogt ? 1 : 0;
+        hardg = hardg || ohard;
+      }
+    }
+    bool yes = quick && !hardg && ngt < k;
+    // the pairs still undecided, one at a time with the whole warp
+    unsigned slow = __ballot_sync(FULL, sub == 0 && have && !(quick && !hardg));
     while (slow) {
       const int src = __ffs(slow) - 1;
       slow &= slow - 1;
@@ -1719,6 +1763,7 @@ __global__ void k_mscatter(Common c, Batch b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
        i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long pr = b.ypairs[i];
+    if (pr == PAIR_NONE) continue;
     const int j = (int)(pr >> 32);
     if (b.bslot[j] >= 0) continue;                       // marked straight from the pair list
     const int slot = atomicAdd(&b.qcur[j], 1);
@@ -1808,6 +1853,7 @@ __global__ void __launch_bounds__(256) k_mbig_mark(Common c, Batch b) {
   const long long cnt = c.ctr[C_YES] < b.cap_y ? c.ctr[C_YES] : b.cap_y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long pr = b.ypairs[i];
+    if (pr == PAIR_NONE) continue;
     const int r = b.bslot[(int)(pr >> 32)];
     if (r < 0) continue;
     const int32_t v = c.permQ[(int32_t)(pr & 0xffffffffull)];
@@ -1982,14 +2028,17 @@ __host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K 
 // a timeout the CTA raises a flag, each role leaves its loop, waits for its
 // copies in flight, and TMEM is freed.
 // ===========================================================================
-constexpr int WS_EPI = 16;                             // epilogue warps: 4 lane quadrants x 4 column groups
+#ifndef RMIPS_WS_EPI
+#define RMIPS_WS_EPI 16
+#endif
+constexpr int WS_EPI = RMIPS_WS_EPI;                   // epilogue warps: 4 lane quadrants x column groups
 constexpr int WS_LOADER = WS_EPI, WS_FEEDER = WS_EPI + 1, WS_MMA = WS_EPI + 2;   // MMA warps take even / odd items
 constexpr int WS_THREADS = (WS_EPI + 4) * 32;
 constexpr int WS_NACC = 4;                             // TMEM accumulator stages of WS_N columns
 constexpr int WS_MAXNS = 6;                            // query stages at most
 constexpr int WS_LG = 4;                               // groups per tile whose bounds are staged
 constexpr int WS_ECOLS = WS_N / (WS_EPI / 4);          // query columns per epilogue warp
-static_assert(WS_ECOLS == 32, "the epilogue classifies 32 columns per warp (one lane per query)");
+static_assert(WS_ECOLS == 32 || WS_ECOLS == 64, "an epilogue warp classifies 32 or 64 query columns");
 enum : int { WI_LAST = 1, WI_END = 2, WI_NEWGROUP = 4 };
 
 struct WsTile {                                        // one tile slot, written by the loader
@@ -2091,44 +2140,107 @@ __device__ __forceinline__ float ws_max32(const float* v) {
   return fmaxf(fmax3(a, b, c), fmaxf(m[9], m[10]));
 }
 
+// Pair lists without a shared counter per pair: an epilogue warp reserves
+// slots at least a chunk at a time (one global atomic) and fills them in
+// order; the slots left over in its last chunk hold PAIR_NONE, which every
+// reader of the lists skips (fewer than a chunk per warp and list).  The
+// undecided list is short and walked slot by slot by the recheck: its chunks
+// are small.
+constexpr int WS_CHUNK_Y = 16, WS_CHUNK_T = 4;
+struct WsChunk {
+  long long next;   // next free slot of the warp's current chunk
+  int left;         // slots left in it
+};
+// The warp's n new entries (whole warp, uniform n > 0) take the rest of the
+// current chunk, then a new one: entry e goes to slot at(e).
+struct WsSlots {
+  long long a, b;   // first slot of the old and of the new chunk
+  int split;        // entries in the old chunk
+  __device__ __forceinline__ long long at(int e) const { return e < split ? a + e : b + (e - split); }
+};
+template <int CHUNK>
+__device__ __forceinline__ WsSlots ws_reserve(long long* ctr, int n, WsChunk& ch) {
+  WsSlots s{ch.next, 0, ch.left};
+  if (n > ch.left) {
+    const int need = n - ch.left;
+    const int r = need > CHUNK ? need : CHUNK;
+    long long base = 0;
+    if ((threadIdx.x & 31) == 0) base = (long long)atomicAdd((unsigned long long*)ctr, (unsigned long long)r);
+    s.b = __shfl_sync(FULL, base, 0);
+    ch.next = s.b + need;
+    ch.left = r - need;
+  } else {
+    ch.next += n;
+    ch.left -= n;
+  }
+  return s;
+}
+
 // Lemma 1 / hi_k / Lemma 2 classification of up to 32 accumulators v of one
-// user against the queries of cq / qj (live leading ones).  Only columns at or
-// above the fast threshold are tested one by one (a lane has one or two); yes
-// and undecided pairs are appended to the pair lists.
+// user (one lane) against 32 query columns (live leading ones; rows past the
+// tile's users pass rowok = false).  Called by the whole warp.  Only columns
+// at or above the fast threshold are tested one by one (a lane has one or
+// two); their (error scale, slack) and query index come from the warp's copy
+// in shared memory (sc, sj: lane l holds column l).  The yes and undecided
+// pairs of the warp are appended together into the warp's own chunks of the
+// two lists (ws_reserve).
 template <bool PROF>
-__device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, const float* v, int live, float thr,
-                                            float un, float2 L, int k, const float2* cq, const int* qj, int64_t pos,
-                                            long long& st_yes, long long& st_todo, long long& w_atom) {
+__device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, const float* v, int live, bool rowok,
+                                            float thr, float un, float2 L, int k, const float2* sc, const int* sj,
+                                            int64_t pos, WsChunk& ych, WsChunk& tch, long long& st_yes,
+                                            long long& st_todo, long long& w_atom) {
+  const int lane = threadIdx.x & 31;
   uint32_t hit = 0;
 #pragma unroll
   for (int q = 0; q < 32; ++q) hit |= (v[q] >= thr ? 1u : 0u) << q;
   if (live < 32) hit &= (1u << live) - 1u;
-  if (!hit) return;
-  long long t_a = 0;
-  if (PROF) t_a = clock64();
+  if (!rowok) hit = 0;
   const float pkb = c.full_p ? 0.f : __fmul_ru(un, (k <= c.m) ? c.pnorm[k - 1] : -kInf);
+  uint32_t ym = 0, tm = 0;
   while (hit) {
     const int q = __ffs(hit) - 1;
     hit &= hit - 1;
-    const float2 e2 = cq[q];                                               // both loads in flight together
-    const int j = qj[q];
+    const float2 e2 = sc[q];
     const float vq = ws_pick(v, q);
     const float e = __fmaf_ru(un, e2.x, e2.y);
     if (__fadd_ru(vq, e) < L.x) continue;                                  // decided no by Lemma 1
-    if (!in_segment(c, b, j, pos)) continue;
+    if (!in_segment(c, b, sj[q], pos)) continue;
     const float lo = __fsub_rd(vq, e);
-    if (c.full_p ? (lo >= L.y) : (lo >= pkb)) {
-      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
-      if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
-      atomicAdd(&b.qcnt[j], 1);
-      ++st_yes;
-    } else {
-      const long long at = atomicAdd((unsigned long long*)&c.ctr[C_TODO], 1ull);
-      if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
-      else set_status(c.ctr, ST_INTERNAL);
-      ++st_todo;
-    }
+    if (c.full_p ? (lo >= L.y) : (lo >= pkb)) ym |= 1u << q;
+    else tm |= 1u << q;
   }
+  long long t_a = 0;
+  if (PROF) t_a = clock64();
+  // warp-wide exclusive prefix of both counts; the entries go to the warp's
+  // own reserved chunks of the pair lists
+  const int ny = __popc(ym), nt = __popc(tm);
+  int sy = ny, stt = nt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int a = __shfl_up_sync(FULL, sy, o), bb = __shfl_up_sync(FULL, stt, o);
+    if (lane >= o) { sy += a; stt += bb; }
+  }
+  const int ty = __shfl_sync(FULL, sy, 31), tt = __shfl_sync(FULL, stt, 31);
+  const WsSlots wy = ty ? ws_reserve<WS_CHUNK_Y>(&c.ctr[C_YES], ty, ych) : WsSlots{0, 0, 0};
+  const WsSlots wt = tt ? ws_reserve<WS_CHUNK_T>(&c.ctr[C_TODO], tt, tch) : WsSlots{0, 0, 0};
+  int ey = sy - ny, et = stt - nt;                                  // this lane's first entries
+  while (ym) {
+    const int q = __ffs(ym) - 1;
+    ym &= ym - 1;
+    const int j = sj[q];
+    const long long at = wy.at(ey++);
+    if (at < b.cap_y) b.ypairs[at] = ((unsigned long long)(uint32_t)j << 32) | (unsigned long long)pos;
+    atomicAdd(&b.qcnt[j], 1);
+  }
+  while (tm) {
+    const int q = __ffs(tm) - 1;
+    tm &= tm - 1;
+    const long long at = wt.at(et++);
+    if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)sj[q] << 32) | (unsigned long long)pos;
+    else set_status(c.ctr, ST_INTERNAL);
+  }
+  st_yes += ny;
+  st_todo += nt;
   if (PROF) w_atom += clock64() - t_a;
 }
 
@@ -2157,6 +2269,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
   __shared__ __align__(8) uint64_t tfull[WS_NACC], tempty[WS_NACC], mdone[2];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int s_fail;
+  __shared__ float2 s_ecq[WS_EPI][WS_ECOLS];            // per epilogue warp: its columns' (scale, slack)
+  __shared__ int s_eqj[WS_EPI][WS_ECOLS];               // and query indices, for the per-pair tests
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sub = c.bs < TCU ? c.bs : TCU;             // users per block inside a tile
   const int nbt = TCU / sub;
@@ -2216,8 +2330,19 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     long long st_pairs = 0, st_skipped = 0, st_active = 0;
     uint32_t fpar = 0, fused = 0;           // per slot: parity of its fill count, filled at least once
     int ab = 0, seq = 0;
-    for (int64_t tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
-      if (s_fail) break;
+    // tiles in order (descending user norm: the heaviest first), each taken
+    // by the next CTA whose loader asks; the next index is fetched while the
+    // current tile is prepared
+    auto take = [&]() -> int64_t {
+      long long t = 0;
+      if (lane == 0) t = (long long)atomicAdd((unsigned long long*)&c.ctr[C_TILE], 1ull);
+      return __shfl_sync(FULL, t, 0);
+    };
+    int64_t tnext = take();
+    for (;;) {
+      const int64_t tt = tnext;
+      if (tt >= ntiles || s_fail) break;
+      tnext = take();
       const int64_t u0 = tt * TCU;
       const int nvalid = (int)((c.n - u0) < TCU ? (c.n - u0) : TCU);
       for (int e = lane; e < ngroups * nbt; e += 32) {
@@ -2417,6 +2542,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     const int uu = q4 * 32 + lane;                                    // this thread's user row
     const uint32_t tl = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col;
     long long st_yes = 0, st_todo = 0, w_slow = 0, n_slow = 0, w_atom = 0;
+    WsChunk ych{0, 0}, tch{0, 0};                                    // this warp's chunks of the pair lists
     uint32_t tpar = 0;
     int acc = 0;
     // constants of the current (tile, group), reloaded on WI_NEWGROUP
@@ -2448,7 +2574,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       if (live > 0) {
         tc_fence_after();
         tmem_ld32(tl + (uint32_t)(acc * WS_N), v);
-        if (live > 32) tmem_ld32(tl + (uint32_t)(acc * WS_N) + 32, v + 32);
+        if (WS_ECOLS > 32 && live > 32) tmem_ld32(tl + (uint32_t)(acc * WS_N) + 32, v + 32);
         tmem_ld_wait();
         tc_fence_before();
       }
@@ -2456,30 +2582,47 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       if (lane == 0) mbar_arrive(&tempty[acc]);
       if (PROF) w_b += clock64() - t_ld;
       acc = acc + 1 == WS_NACC ? 0 : acc + 1;
-      if (uu >= nvalid) live = 0;
       if (live > 0) {
-        // the stage may be refilled already: per-query constants of the
-        // (rare) per-pair tests come from the packed item in global memory
-        const float2* cq0 = reinterpret_cast<const float2*>(b.bitems + (size_t)itm.item * PACK + BROWS);
-        const float2* cq = cq0 + col;
-        const int* qj = reinterpret_cast<const int*>(cq0 + WS_N) + col;
+        const bool rowok = uu < nvalid;
         const int64_t pos = u0 + uu;
         // Fast Lemma 1: the item's first query has the largest error scale
         // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
         const float thr = __fsub_rd(L.x, __fmaf_ru(un, itm.c0.x, itm.c0.y));
-        bool any = true;
-        if (live == WS_ECOLS) any = ws_max32(v) >= thr;
-        long long t_sl = 0;
-        if (PROF) t_sl = clock64();
-        if (any) ws_classify<PROF>(c, b, v, live, thr, un, L, kq, cq, qj, pos, st_yes, st_todo, w_atom);
-        if (PROF) {
-          w_slow += clock64() - t_sl;
-          n_slow += __any_sync(__activemask(), any) ? 1 : 0;
+        bool any = rowok;
+        if (rowok && live == WS_ECOLS)
+          any = (WS_ECOLS == 32 ? ws_max32(v) : fmaxf(ws_max32(v), ws_max32(v + WS_ECOLS - 32))) >= thr;
+        if (__any_sync(FULL, any)) {
+          long long t_sl = 0;
+          if (PROF) t_sl = clock64();
+          // (error scale, slack) and index of the warp's query columns, one
+          // coalesced load each from the packed item in global memory (its
+          // stage in shared memory may be refilled already), for all lanes
+          const float2* cq0 = reinterpret_cast<const float2*>(b.bitems + (size_t)itm.item * PACK + BROWS);
+#pragma unroll
+          for (int h = 0; h < WS_ECOLS / 32; ++h) {
+            s_ecq[warp][32 * h + lane] = __ldg(cq0 + col + 32 * h + lane);
+            s_eqj[warp][32 * h + lane] = __ldg(reinterpret_cast<const int*>(cq0 + WS_N) + col + 32 * h + lane);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int h = 0; h < WS_ECOLS / 32; ++h) {
+            const int lh = live - 32 * h;
+            if (lh > 0)
+              ws_classify<PROF>(c, b, v + 32 * h, lh > 32 ? 32 : lh, any, thr, un, L, kq, &s_ecq[warp][32 * h],
+                                &s_eqj[warp][32 * h], pos, ych, tch, st_yes, st_todo, w_atom);
+          }
+          if (PROF) {
+            w_slow += clock64() - t_sl;
+            ++n_slow;
+          }
         }
       }
       __syncwarp();
       if (lane == 0 && (itm.flags & WI_LAST)) mbar_arrive(&aempty[itm.ab]);
     }
+    // the unused rest of both chunks (fewer than a chunk each)
+    if (lane < ych.left && ych.next + lane < b.cap_y) b.ypairs[ych.next + lane] = PAIR_NONE;
+    if (lane < tch.left && tch.next + lane < b.cap_t) b.tpairs[tch.next + lane] = PAIR_NONE;
     for (int o = 16; o > 0; o >>= 1) {
       st_yes += __shfl_xor_sync(FULL, st_yes, o);
       st_todo += __shfl_xor_sync(FULL, st_todo, o);
@@ -2670,7 +2813,8 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
     if (sm_count <= 0) sm_count = 1;
   }
   int64_t want_y = capacity < (int64_t)nq * idx->n ? capacity : (int64_t)nq * idx->n;
-  rmips_status s = ensure_batch(idx, ws, want_y + 1);
+  // plus the slots the tensor-core filter's epilogue warps reserve but leave unused
+  rmips_status s = ensure_batch(idx, ws, want_y + 1 + (int64_t)sm_count * WS_EPI * WS_CHUNK_Y);
   if (s != RMIPS_OK) return s;
   RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
   if (idx->prof_on == 2) RMIPS_TRY_CUDA(cudaMemsetAsync(ws->wst, 0, WST_N * sizeof(unsigned long long), st));
@@ -2859,6 +3003,26 @@ extern "C" rmips_status rmips_query(rmips_index* idx, const float* q, int32_t k,
   return RMIPS_OK;
 }
 
+namespace rmips {
+namespace {
+// Results of a batch (the first min(total, cap) ids; nothing after a failed
+// pass) from the device buffer into device-mapped pinned host memory, 16 bytes
+// per store.
+__global__ void k_copy_results(const long long* __restrict__ src, long long* __restrict__ dst,
+                               const long long* __restrict__ ctr, long long cap) {
+  if (ctr[C_STATUS] != 0) return;
+  const long long n = ctr[C_CURSOR] < cap ? ctr[C_CURSOR] : cap;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const longlong2* s2 = reinterpret_cast<const longlong2*>(src);
+  longlong2* d2 = reinterpret_cast<longlong2*>(dst);
+  for (long long i = t; i < n / 2; i += stride) d2[i] = s2[i];
+  if (t == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+}
+
+}  // namespace
+}  // namespace rmips
+
 extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int64_t nq, const int32_t* ks,
                                           const rmips_segment* segs, int64_t* out_ids, int64_t capacity,
                                           int64_t* out_offsets, void* stream) {
@@ -2884,6 +3048,11 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
   if ((s = ensure_queries(idx, ws, nq)) != RMIPS_OK) return s;
   const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
+  // host results: the emitters write a device buffer; one coalesced copy
+  // kernel then streams it into device-mapped pinned memory (no second
+  // device-to-host transfer after the sizes are known), and the host copies
+  // that into the caller's buffer
+  const bool out_mapped = !out_dev && capacity <= ws->cap_hout;
   long long* out;
   if (out_dev) out = (long long*)out_ids;
   else {
@@ -2914,6 +3083,10 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   } else {
     if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
   }
+  if (out_mapped && capacity > 0) {
+    k_copy_results<<<256, 256, 0, st>>>(ws->dout, ws->h_out, ws->ctr, capacity);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+  }
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -2926,8 +3099,10 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   if (ws->h_ctr[C_STATUS] == ST_INTERNAL) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
   if ((s = status_from_device(ws->h_ctr[C_STATUS])) != RMIPS_OK) return s;
   const long long total = ws->h_offs[nq];
-  if (!out_dev && total > 0)
-    RMIPS_TRY_CUDA(cudaMemcpy(out_ids, ws->dout, total * sizeof(long long), cudaMemcpyDeviceToHost));
+  if (!out_dev && total > 0) {
+    if (out_mapped) memcpy(out_ids, ws->h_out, (size_t)total * sizeof(long long));
+    else RMIPS_TRY_CUDA(cudaMemcpy(out_ids, ws->dout, total * sizeof(long long), cudaMemcpyDeviceToHost));
+  }
   return RMIPS_OK;
 }
 

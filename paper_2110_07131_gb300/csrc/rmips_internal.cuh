@@ -93,7 +93,8 @@ enum : int {
   C_NBIG = 9,       // queries of a batch pass with more than EMIT_SORT_CAP results
   C_DONE = 10,      // CTAs finished (one-launch query)
   C_NMID = 11,      // queries of a batch pass with 33 .. MEMIT_MID_CAP results
-  C_NCOUNTERS = 12
+  C_TILE = 12,      // next user tile of the tensor-core filter (dynamic schedule)
+  C_NCOUNTERS = 13
 };
 
 // ---------------------------------------------------------------------------
