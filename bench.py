@@ -295,7 +295,7 @@ def run_ours(a):
     build_s = time.perf_counter() - t0
     info = index.info()
 
-    total_q = (a.warmup + a.steps) * a.nq
+    total_q = (a.warmup + 1 + a.steps) * a.nq
     qs, _ = datagen.queries_from_items(P, total_q, SEED + 7919 * rank)
     ks = np.full(a.nq, a.k, np.int32)
     dqs = torch.from_numpy(qs).to(dev)
@@ -312,26 +312,45 @@ def run_ours(a):
         last_offs[0] = offs
         return int(offs[-1])
 
+    # Batches are queued through the asynchronous call on two streams in
+    # turn: consecutive batches are independent, so one batch's short
+    # preparation kernels overlap the previous batch's recheck and emission
+    # (each stream slot has its own workspace and output buffer).
+    streams = [stream, torch.cuda.Stream(dev)]
+    douts = [dout, torch.empty(cap, dtype=torch.int64, device=dev)]
+
+    def run_async(first, count, offs, done):
+        for i in range(count):
+            j = first + i
+            rmips.rmips_query_batch_async(index, dqs[j * a.nq:(j + 1) * a.nq], dks, douts[i & 1], offs[i], done[i],
+                                          streams[i & 1])
+
     sampler = ClockSampler(local)
     sampler.start()                                  # sampling already runs when the timed region starts
-    for i in range(a.warmup):
-        step(i)
+    # warm-up: an even number of batches (at least W), so that each of the two
+    # workspaces has seen the batch shape twice and replays captured graphs
+    n_warm = a.warmup + (a.warmup & 1)
+    w_offs = torch.empty((n_warm, a.nq + 1), dtype=torch.int64, device=dev)
+    w_done = torch.full((n_warm, 2), -1, dtype=torch.int64, device=dev)
+    run_async(0, n_warm, w_offs, w_done)
     torch.cuda.synchronize(dev)
+    if (w_done[:, 0].cpu().numpy() != 0).any():
+        raise RuntimeError("warm-up batch failed")
     if dist:
         dist.barrier()
-    # timed steps through the asynchronous call: the host queues one batch per
-    # step and waits once at the end, so the GPU runs the steps back to back
     a_offs = torch.empty((a.steps, a.nq + 1), dtype=torch.int64, device=dev)
     a_done = torch.full((a.steps, 2), -1, dtype=torch.int64, device=dev)
     rmips.rmips_profile_enable(index, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_side = torch.cuda.Event()
     torch.cuda.synchronize(dev)
     t_wall0 = time.time()
-    ev0.record(stream)
-    for i in range(a.steps):
-        j = a.warmup + i
-        rmips.rmips_query_batch_async(index, dqs[j * a.nq:(j + 1) * a.nq], dks, dout, a_offs[i], a_done[i], stream)
-    ev1.record(stream)
+    ev0.record(streams[0])
+    streams[1].wait_event(ev0)
+    run_async(n_warm, a.steps, a_offs, a_done)
+    ev_side.record(streams[1])
+    streams[0].wait_event(ev_side)
+    ev1.record(streams[0])
     torch.cuda.synchronize(dev)
     t_wall1 = time.time()
     done_h = a_done.cpu().numpy()
@@ -479,6 +498,9 @@ def run_ours(a):
             "data": "synthetic",
             "config": workload(a), "e2e": e2e, "roofline": roofline, "clocks": clocks,
             "gpu_launches": a.steps * ((16 if a.batch_kernel == "tc" and a.d <= 64 else 15) * ((a.nq + 16383) // 16384) + 1),
+            "pipelining": f"each step one asynchronous batch call; batches queued on 2 CUDA streams in turn, "
+                          f"each with its own workspace (independent batches overlap); {n_warm} untimed "
+                          f"warm-up batches",
             "roofline_single_query_filter": roof_single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain, "serving": serving,
             "batch_latency_ms": ms_max / a.steps,

@@ -75,14 +75,34 @@ void destroy_workspace(Workspace* ws) {
   delete ws;
 }
 
+// Idle workspaces are kept in the order they were released.  The oldest
+// whose queued device work has finished is taken; while all of them still
+// have work in flight (asynchronous batches queued back to back, e.g. on two
+// streams in turn), a second workspace is created so that consecutive batches
+// do not wait for each other; beyond that the oldest is taken and the call
+// waits for its work (ws_join).  Taking the oldest keeps a stream of batches
+// cycling through the workspaces in a fixed order, so each one replays its
+// own captured graphs.
+constexpr int kOverlapWorkspaces = 2;
+
 Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
   {
     std::lock_guard<std::mutex> lk(idx->mu);
-    if (!idx->pool.empty()) {
-      Workspace* ws = idx->pool.back();
-      idx->pool.pop_back();
+    for (size_t i = 0; i < idx->pool.size(); ++i) {
+      Workspace* ws = idx->pool[i];
+      if (ws->done_pending && cudaEventQuery(ws->done_ev) != cudaSuccess) {
+        cudaGetLastError();                    // "not ready" is not an error of the next call
+        continue;
+      }
+      idx->pool.erase(idx->pool.begin() + (ptrdiff_t)i);
       return ws;
     }
+    if (!idx->pool.empty() && idx->n_ws >= kOverlapWorkspaces) {
+      Workspace* ws = idx->pool.front();
+      idx->pool.erase(idx->pool.begin());
+      return ws;
+    }
+    ++idx->n_ws;
   }
   Workspace* ws = new Workspace();
   const int64_t n = idx->n;
@@ -104,6 +124,8 @@ Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
     set_error(std::string("workspace allocation: ") + cudaGetErrorString(e));
     *st = e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
     destroy_workspace(ws);
+    std::lock_guard<std::mutex> lk(idx->mu);
+    --idx->n_ws;
     return nullptr;
   }
   return ws;

@@ -201,7 +201,8 @@ struct rmips_index {
   unsigned char* Qtc = nullptr;  // user tiles of the batched tensor-core filter (null: not built)
 
   std::mutex mu;
-  std::vector<rmips::Workspace*> pool;
+  std::vector<rmips::Workspace*> pool;       // idle workspaces (their queued device work may still run)
+  int n_ws = 0;                              // workspaces created for this index
   rmips_query_stats last_stats{};
   int prof_on = 0;
   rmips_profile prof{};
