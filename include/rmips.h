@@ -48,7 +48,9 @@ typedef enum {
   RMIPS_ERR_ARG = 1,        /* bad pointer, size, option or segment */
   RMIPS_ERR_K_RANGE = 2,    /* k < 1 or k > k_max (the paper rebuilds the
                                index for k > k_max, Section 4.1) */
-  RMIPS_ERR_NONFINITE = 3,  /* NaN or Inf in Q, P or a query */
+  RMIPS_ERR_NONFINITE = 3,  /* NaN or Inf in Q, P or a query; for a BF16 / FP16
+                               index also a value of Q or a query whose copy in
+                               that format would overflow (FP16: |x| > 65504) */
   RMIPS_ERR_OOM = 4,        /* device or pinned host allocation failed */
   RMIPS_ERR_CAPACITY = 5,   /* output buffer too small; the required size
                                is reported, nothing is written */

@@ -23,7 +23,9 @@ namespace {
 constexpr float kInf = __builtin_huge_valf();
 
 // --- 1. norms ----------------------------------------------------------------
-__global__ void k_norms(const float* __restrict__ X, int64_t rows, int64_t rows_pad, int d,
+// bad |= 1 for a NaN or infinity, |= 2 for a finite value above vmax (the
+// largest magnitude the filter's storage format holds without overflow).
+__global__ void k_norms(const float* __restrict__ X, int64_t rows, int64_t rows_pad, int d, float vmax,
                         float* __restrict__ nrm_up, unsigned long long* __restrict__ key,
                         int32_t* __restrict__ ids, int* __restrict__ bad) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -35,14 +37,16 @@ __global__ void k_norms(const float* __restrict__ X, int64_t rows, int64_t rows_
   }
   const float* x = X + r * d;
   double acc = 0.0;
-  bool fin = true;
+  bool fin = true, inrange = true;
   for (int i = 0; i < d; ++i) {
     float v = x[i];
     fin = fin && isfinite(v);
+    inrange = inrange && !(fabsf(v) > vmax);
     double dv = (double)v;
     acc = fma(dv, dv, acc);   // dv*dv is exact, so this equals acc + dv*dv rounded once
   }
   if (!fin) atomicOr(bad, 1);
+  else if (!inrange) atomicOr(bad, 2);
   double s = sqrt(acc);
   // Upper bound of the exact norm: the float64 value is within (d/2 + 2) ulps.
   nrm_up[r] = __double2float_ru(__dmul_ru(s, 1.0 + (d + 8) * 0x1p-52));
@@ -559,7 +563,7 @@ __global__ void k_blocks(const float2* __restrict__ Lb, const float* __restrict_
 
 inline unsigned grid_for(int64_t work, int threads) { return (unsigned)((work + threads - 1) / threads); }
 
-rmips_status sort_by_norm(const float* X, int64_t rows, int d, cudaStream_t st, float* nrm_up,
+rmips_status sort_by_norm(const float* X, int64_t rows, int d, float vmax, cudaStream_t st, float* nrm_up,
                           int32_t* order, int* d_bad) {
   int64_t N2 = 1;
   while (N2 < rows) N2 <<= 1;
@@ -567,7 +571,7 @@ rmips_status sort_by_norm(const float* X, int64_t rows, int d, cudaStream_t st, 
   int32_t* ids = nullptr;
   RMIPS_TRY_CUDA(cudaMallocAsync((void**)&key, N2 * sizeof(unsigned long long), st));
   RMIPS_TRY_CUDA(cudaMallocAsync((void**)&ids, N2 * sizeof(int32_t), st));
-  k_norms<<<grid_for(N2, 256), 256, 0, st>>>(X, rows, N2, d, nrm_up, key, ids, d_bad);
+  k_norms<<<grid_for(N2, 256), 256, 0, st>>>(X, rows, N2, d, vmax, nrm_up, key, ids, d_bad);
   for (int64_t kk = 2; kk <= N2; kk <<= 1)
     for (int64_t j = kk >> 1; j > 0; j >>= 1)
       k_bitonic<<<grid_for(N2, 256), 256, 0, st>>>(key, ids, N2, j, kk);
@@ -690,9 +694,11 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
       Psrc = Pin;
     }
     // 1-2: norms and sort
-    s = sort_by_norm(Qsrc, n, d, st, qn, idx->permQ, d_bad);
+    // the users also go into the filter's 16-bit copy (BF16 / FP16 indexes):
+    // their values must stay finite there; the items stay in float32
+    s = sort_by_norm(Qsrc, n, d, filter_max_abs(idx->precision), st, qn, idx->permQ, d_bad);
     if (s != RMIPS_OK) goto cleanup;
-    s = sort_by_norm(Psrc, m, d, st, pn, idx->permP, d_bad);
+    s = sort_by_norm(Psrc, m, d, FLT_MAX, st, pn, idx->permP, d_bad);
     if (s != RMIPS_OK) goto cleanup;
     k_gather<<<grid_for(n * d, 256), 256, 0, st>>>(Qsrc, idx->permQ, n, d, idx->Qs, qn, idx->unorm);
     k_gather<<<grid_for(m * d, 256), 256, 0, st>>>(Psrc, idx->permP, m, d, idx->Ps, pn, idx->pnorm);
@@ -701,7 +707,13 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     TRY(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(&idx->pn0, idx->pnorm, sizeof(float), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    if (h_bad) { set_error("non-finite value in Q or P"); s = RMIPS_ERR_NONFINITE; goto cleanup; }
+    if (h_bad & 1) { set_error("non-finite value in Q or P"); s = RMIPS_ERR_NONFINITE; goto cleanup; }
+    if (h_bad) {
+      set_error(idx->precision == RMIPS_FP16 ? "a value of Q beyond +-65504 does not fit the FP16 filter copy"
+                                             : "a value of Q beyond the BF16 range does not fit the filter copy");
+      s = RMIPS_ERR_NONFINITE;
+      goto cleanup;
+    }
     if (idx->precision != RMIPS_FP32) {
       TRY(dalloc(idx, (uint16_t**)&idx->Qh, n * d + pad));
       TRY(cudaMemsetAsync((uint16_t*)idx->Qh + n * d, 0, pad * 2, st));

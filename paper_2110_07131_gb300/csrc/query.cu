@@ -81,9 +81,10 @@ struct Common {
 __device__ __forceinline__ bool query_bounds(const float* q, int d, int precision, float* qn, float* eps) {
   float acc = 0.f, qmax = 0.f;
   bool fin = true;
+  const float vmax = filter_max_abs(precision);
   for (int i = 0; i < d; ++i) {
     const float v = q[i];
-    fin = fin && isfinite(v);
+    fin = fin && isfinite(v) && !(fabsf(v) > vmax);
     acc = __fmaf_ru(v, v, acc);
     qmax = fmaxf(qmax, fabsf(v));
   }
@@ -816,7 +817,9 @@ rmips_status run_queries(rmips_index* idx, Workspace* ws, int64_t nq, const rmip
 rmips_status status_from_device(long long s) {
   switch ((int)s) {
     case ST_OK: return RMIPS_OK;
-    case ST_NONFINITE: set_error("non-finite value in a query"); return RMIPS_ERR_NONFINITE;
+    case ST_NONFINITE:
+      set_error("non-finite value in a query (or, for a BF16 / FP16 index, one beyond that format's range)");
+      return RMIPS_ERR_NONFINITE;
     case ST_CAPACITY: set_error("output capacity too small"); return RMIPS_ERR_CAPACITY;
     case ST_TIMEOUT: set_error("a device wait timed out"); return RMIPS_ERR_TIMEOUT;
     default: set_error("device-side consistency check failed"); return RMIPS_ERR_INTERNAL;
@@ -1151,11 +1154,12 @@ __global__ void k_mprep_a(Common c, Batch b, int precision) {
   const bool live = j < b.nq;
   float acc = 0.f, qmax = 0.f;
   bool fin = true;
+  const float vmax = filter_max_abs(precision);
   if (live) {
     const float* q = b.dq + (int64_t)j * d;
     for (int i = sub; i < d; i += 8) {
       const float v = q[i];
-      fin = fin && isfinite(v);
+      fin = fin && isfinite(v) && !(fabsf(v) > vmax);
       acc = __fmaf_ru(v, v, acc);
       qmax = fmaxf(qmax, fabsf(v));
     }

@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cfloat>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -70,6 +71,13 @@ void set_error(const std::string& msg);
 
 // Device status word values (first error wins).
 enum : int { ST_OK = 0, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_INTERNAL = 8 };
+
+// Largest magnitude a value may have so that its copy in the filter's
+// storage format (users of BF16 / FP16 indexes, and every query rounded for
+// their filter) stays finite: FP16 65504, BF16 (1 - 2^-8) 2^128.
+__host__ __device__ constexpr float filter_max_abs(int precision) {
+  return precision == RMIPS_FP16 ? 65504.0f : (precision == RMIPS_BF16 ? 0x1.fep127f : FLT_MAX);
+}
 
 // Cycle counters of the tensor-core filter's roles (profiling only).
 enum : int {

@@ -175,6 +175,33 @@ def test_errors(tiny):
     assert e.value.status == 3
 
 
+def test_fp16_index_refuses_values_beyond_its_range(tiny):
+    # an FP16 copy of |x| > 65504 would be infinite and break the filter's
+    # bounds: the build and the queries refuse such values (status 3); a
+    # float32 index answers them exactly
+    Q, P, allq, _ = tiny
+    Qb = Q.copy()
+    Qb[11, 4] = 70000.0
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_build_index(Qb, P, k_max=10, precision="fp16")
+    assert e.value.status == 3
+    index16 = rmips.rmips_build_index(Q, P, k_max=10, precision="fp16")
+    q = allq[2].copy()
+    q[5] = 70000.0
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query(index16, q, 5)
+    assert e.value.status == 3
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.rmips_query_batch(index16, np.stack([allq[0], q]), 5)
+    assert e.value.status == 3
+    ok = rmips.rmips_query(index16, allq[0], 5)           # still usable
+    index32 = rmips.rmips_build_index(Q, P, k_max=10)
+    assert np.array_equal(rmips.rmips_query(index32, allq[0], 5), ok)
+    got = rmips.rmips_query(index32, q, 5)
+    exp = np.nonzero(O.counts_greater_multi(Q, P, q[None, :])[0] < 5)[0]
+    assert np.array_equal(got, exp)
+
+
 def test_segments(tiny):
     Q, P, allq, counts = tiny
     index = rmips.rmips_build_index(Q, P, k_max=25)
