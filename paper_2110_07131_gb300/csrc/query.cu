@@ -2035,14 +2035,16 @@ __host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K 
 #ifndef RMIPS_WS_EPI
 #define RMIPS_WS_EPI 16
 #endif
-constexpr int WS_EPI = RMIPS_WS_EPI;                   // epilogue warps: 4 lane quadrants x column groups
+constexpr int WS_EPI = RMIPS_WS_EPI;                   // epilogue warps: 2 sets x 4 lane quadrants x 2 column halves
 constexpr int WS_LOADER = WS_EPI, WS_FEEDER = WS_EPI + 1, WS_MMA = WS_EPI + 2;   // MMA warps take even / odd items
 constexpr int WS_THREADS = (WS_EPI + 4) * 32;
 constexpr int WS_NACC = 4;                             // TMEM accumulator stages of WS_N columns
 constexpr int WS_MAXNS = 6;                            // query stages at most
 constexpr int WS_LG = 4;                               // groups per tile whose bounds are staged
-constexpr int WS_ECOLS = WS_N / (WS_EPI / 4);          // query columns per epilogue warp
-static_assert(WS_ECOLS == 32 || WS_ECOLS == 64, "an epilogue warp classifies 32 or 64 query columns");
+constexpr int WS_ESET = WS_EPI / 2;                    // epilogue warps per item: the two sets take alternate items
+constexpr int WS_ECOLS = WS_N / (WS_ESET / 4);         // query columns per epilogue warp, read 32 at a time
+static_assert(WS_ECOLS == 64 && WS_NACC % 2 == 0, "two sets of 8 epilogue warps, 64 columns each");
+constexpr int WS_ESLOTS = 3;                           // tile slots of the epilogue's per-tile data
 enum : int { WI_LAST = 1, WI_END = 2, WI_NEWGROUP = 4 };
 
 struct WsTile {                                        // one tile slot, written by the loader
@@ -2054,13 +2056,13 @@ struct WsTile {                                        // one tile slot, written
   int pre[RMIPS_KMAX_LIMIT][4];                        // prefix of each block of the tile
 };
 struct WsItem {                                        // one accumulator stage, written by the mma warp
-  int ab, ga, t, item, flags;
+  int seq, ga, t, item, flags;                         // seq: the tile's position in this CTA's sequence
   float2 c0;                                           // (error scale, slack) of the item's first query
 };
 
 size_t ws_smem_bytes(int kind, int ns) {
-  return 2 * (size_t)tc_a_bytes(kind) + (size_t)ns * ws_pack_bytes(kind) + 2 * (size_t)WS_LG * TCU * 8 +
-         2 * (size_t)TCU * 4;
+  return 2 * (size_t)tc_a_bytes(kind) + (size_t)ns * ws_pack_bytes(kind) + WS_ESLOTS * (size_t)WS_LG * TCU * 8 +
+         WS_ESLOTS * (size_t)TCU * 4;
 }
 
 // Lemma 3 prefix of every (block, k-group): the leading queries of the group
@@ -2260,21 +2262,21 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
   constexpr uint32_t BROWS = 2 * TILE;                 // its query rows; then WS_N (scale, slack), WS_N indices
   static_assert(PACK % 16 == 0 && BROWS == (uint32_t)WS_N * TC_K * tc_esize(KIND), "item layout");
   extern __shared__ __align__(1024) unsigned char wsm[];
-  unsigned char* sA = wsm;                             // 2 user tiles
+  unsigned char* sA = wsm;                             // 2 user tiles (MMA operand slots)
   unsigned char* sB = sA + 2 * ABYTES;                 // ns packed items
-  float2* sL = reinterpret_cast<float2*>(sB + (size_t)ns * PACK);
-  float* sUN = reinterpret_cast<float*>(sL + 2 * WS_LG * TCU);
-  __shared__ WsTile tinfo[2];
+  float2* sL = reinterpret_cast<float2*>(sB + (size_t)ns * PACK);   // WS_ESLOTS tile slots of per-user data
+  float* sUN = reinterpret_cast<float*>(sL + WS_ESLOTS * WS_LG * TCU);
+  __shared__ WsTile tinfo[WS_ESLOTS];
   __shared__ WsItem items[WS_NACC];
   __shared__ int4 sgrp[RMIPS_KMAX_LIMIT];
   __shared__ int sgi[RMIPS_KMAX_LIMIT];
   __shared__ int lpre[RMIPS_KMAX_LIMIT][4];
-  __shared__ __align__(8) uint64_t afull[2], aempty[2], bfull[WS_MAXNS], bempty[WS_MAXNS];
+  __shared__ __align__(8) uint64_t afull[2], aempty[2], eempty[WS_ESLOTS], bfull[WS_MAXNS], bempty[WS_MAXNS];
   __shared__ __align__(8) uint64_t tfull[WS_NACC], tempty[WS_NACC], mdone[2];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int s_fail;
-  __shared__ float2 s_ecq[WS_EPI][WS_ECOLS];            // per epilogue warp: its columns' (scale, slack)
-  __shared__ int s_eqj[WS_EPI][WS_ECOLS];               // and query indices, for the per-pair tests
+  __shared__ float2 s_ecq[WS_EPI][32];                  // per epilogue warp: 32 columns' (scale, slack)
+  __shared__ int s_eqj[WS_EPI][32];                     // and query indices, for the per-pair tests
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sub = c.bs < TCU ? c.bs : TCU;             // users per block inside a tile
   const int nbt = TCU / sub;
@@ -2288,9 +2290,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     sgi[tid] = b.gitem[tid];
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], WS_EPI); }
+    // an operand slot is free once both MMA warps are through its tile; a
+    // tile's per-user data once every epilogue warp has moved past the tile
+    for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 2); }
+    for (int i = 0; i < WS_ESLOTS; ++i) mbar_init(&eempty[i], WS_EPI);
     for (int i = 0; i < ns; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }   // emptied by the MMA commit
-    for (int i = 0; i < WS_NACC; ++i) { mbar_init(&tfull[i], 2); mbar_init(&tempty[i], WS_EPI); }
+    for (int i = 0; i < WS_NACC; ++i) { mbar_init(&tfull[i], 2); mbar_init(&tempty[i], WS_ESET); }
     mbar_init(&mdone[0], 1);
     mbar_init(&mdone[1], 1);
     fence_mbar_init();
@@ -2332,8 +2337,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     // ---------------------------------------------------------------- loader
     const int64_t ntiles = (c.n + TCU - 1) / TCU;
     long long st_pairs = 0, st_skipped = 0, st_active = 0;
-    uint32_t fpar = 0, fused = 0;           // per slot: parity of its fill count, filled at least once
-    int ab = 0, seq = 0;
+    uint32_t fpar = 0, fused = 0;           // per operand slot: parity of its fill count, filled at least once
+    uint32_t epar = 0;                      // per data slot: parity of its fill count
+    int ab = 0, es = 0, seq = 0;
     // tiles in order (descending user norm: the heaviest first), each taken
     // by the next CTA whose loader asks; the next index is fetched while the
     // current tile is prepared
@@ -2371,7 +2377,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         continue;
       }
       if (!wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a)) break;
-      WsTile& T = tinfo[ab];
+      if (!wwait(&eempty[es], ((epar >> es) & 1u) ^ 1u, &w_a)) break;
+      WsTile& T = tinfo[es];
       if (gm > 0) {
         const int ga = __popc(act & ((1u << lane) - 1u));
         T.k[ga] = sgrp[lane].x;
@@ -2386,12 +2393,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         T.end = 0;
         T.seq = seq;
       }
-      for (int r = lane; r < TCU; r += 32) sUN[ab * TCU + r] = r < nvalid ? c.unorm[u0 + r] : 0.f;
+      for (int r = lane; r < TCU; r += 32) sUN[es * TCU + r] = r < nvalid ? c.unorm[u0 + r] : 0.f;
       __syncwarp();
       const int nstage = min(__popc(act), WS_LG);          // further groups' bounds are read from memory
       for (int ga = 0; ga < nstage; ++ga) {
         const float2* src = c.Lb + (int64_t)(T.k[ga] - 1) * c.n + u0;
-        float2* dst = sL + ((size_t)ab * WS_LG + ga) * TCU;
+        float2* dst = sL + ((size_t)es * WS_LG + ga) * TCU;
         for (int r = lane; r < TCU; r += 32) dst[r] = r < nvalid ? src[r] : make_float2(kInf, kInf);
       }
       __threadfence_block();
@@ -2402,13 +2409,16 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       }
       fpar ^= 1u << ab;
       fused |= 1u << ab;
+      epar ^= 1u << es;
       ab ^= 1;
+      es = es + 1 == WS_ESLOTS ? 0 : es + 1;
       ++seq;
       ++st_active;
     }
-    if (!s_fail && wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a)) {  // end marker
+    if (!s_fail && wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a) &&
+        wwait(&eempty[es], ((epar >> es) & 1u) ^ 1u, &w_a)) {            // end marker
       if (lane == 0) {
-        tinfo[ab].end = 1;
+        tinfo[es].end = 1;
         __threadfence_block();
         mbar_arrive(&afull[ab]);
       }
@@ -2429,11 +2439,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     uint32_t wpar = 0;                      // per slot: parity of the next wait
     uint32_t epar = 0;                      // per stage: uses so far (parity)
     uint32_t armed = 0;                     // per stage: a copy was started
-    int stg = 0, ab = 0;
+    int stg = 0, ab = 0, es = 0;
     for (;;) {
       if (!wwait(&afull[ab], (wpar >> ab) & 1u, &w_b)) break;
       wpar ^= 1u << ab;
-      const WsTile& T = tinfo[ab];
+      const WsTile& T = tinfo[es];
       if (T.end) break;
       bool ok = true;
       for (int ga = 0; ga < T.ngact && ok; ++ga) {
@@ -2452,6 +2462,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       }
       if (!ok) break;
       ab ^= 1;
+      es = es + 1 == WS_ESLOTS ? 0 : es + 1;
     }
     for (int x = 0; x < ns; ++x)                                      // copies in flight
       if ((armed >> x) & 1u) mbar_wait_bounded(&bfull[x], ((epar >> x) & 1u) ^ 1u);
@@ -2470,15 +2481,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     const uint64_t bdesc0 = tc_sdesc(smem_u32(sB), TC_LBO, SBO);
     constexpr uint64_t BSTEP = PACK >> 4;                 // descriptor units per stage
     uint32_t wpar = 0, fpar = 0, tpar = 0;                // parities: slots, stages, accumulators
-    int stg = 0, acc = 0, ab = 0, it = 0;
+    int stg = 0, acc = 0, ab = 0, it = 0, es = 0, seq = 0;
     long long w_c = 0, n_items = 0, w_issue = 0;
     for (;;) {
       if (!wwait(&afull[ab], (wpar >> ab) & 1u, &w_c)) break;
       wpar ^= 1u << ab;
-      const WsTile& T = tinfo[ab];
+      const WsTile& T = tinfo[es];
       if (T.end) break;
       const int ngact = T.ngact;
-      bool ok = true;
+      bool ok = true, issued = false;
       for (int ga = 0; ga < ngact && ok; ++ga) {
         const int gmax = T.gmax[ga];
         const int nt = (gmax + WS_N - 1) / WS_N;
@@ -2493,7 +2504,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
             if (lane == 0) {
               const int nq = ws_item_n(gmax, t);
               const float2 c0 = *reinterpret_cast<const float2*>(sB + (size_t)stg * PACK + BROWS);
-              items[acc] = WsItem{ab, ga, t, T.item0[ga] + t,
+              items[acc] = WsItem{seq, ga, t, T.item0[ga] + t,
                                   (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0), c0};
               const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, (uint32_t)nq)
                                                       : tc_idesc_f16(TCU, (uint32_t)nq, KIND == TCK_BF16);
@@ -2513,6 +2524,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
               if (PROF) w_issue += clock64() - t_is;
             }
             __syncwarp();
+            issued = true;
             ++n_items;
           }
           stg = stg + 1 == ns ? 0 : stg + 1;
@@ -2520,13 +2532,26 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         }
       }
       if (!ok) break;
-      ab ^= 1;
-    }
-    // end marker: the warp that owns the next item index writes it
-    if ((it & 1) == me && !s_fail && wwait(&tempty[acc], ((tpar >> acc) & 1u) ^ 1u, &w_b)) {
+      // this warp is through the tile: its operand slot is free once its MMAs
+      // have completed (none issued: at once -- earlier ones read other tiles)
       if (lane == 0) {
-        items[acc].flags = WI_END;
-        mbar_arrive_cnt(&tfull[acc], 2);
+        if (issued) tc_commit(&aempty[ab]);
+        else mbar_arrive(&aempty[ab]);
+      }
+      __syncwarp();
+      ab ^= 1;
+      es = es + 1 == WS_ESLOTS ? 0 : es + 1;
+      ++seq;
+    }
+    // end markers: each warp writes one into the next accumulator stage it
+    // owns, so that both epilogue sets (alternate stages) see one
+    {
+      const int ea = (it & 1) == me ? acc : (acc + 1 == WS_NACC ? 0 : acc + 1);
+      if (!s_fail && wwait(&tempty[ea], ((tpar >> ea) & 1u) ^ 1u, &w_b)) {
+        if (lane == 0) {
+          items[ea].flags = WI_END;
+          mbar_arrive_cnt(&tfull[ea], 2);
+        }
       }
     }
     if (lane == 0) {                                                  // this warp's MMAs in flight
@@ -2542,14 +2567,20 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     }
   } else if (warp < WS_EPI) {
     // ---------------------------------------------------------------- epilogue
-    const int q4 = warp & 3, col = (warp >> 2) * WS_ECOLS;
+    // Two sets of WS_ESET warps take alternate items (set s: accumulator
+    // stages s, s + 2, ...), so each warp has two items' time for one.  In a
+    // set, the warp of lane quadrant q4 and column half h classifies 32 users
+    // x 64 query columns, read from TMEM 32 columns at a time; the stage is
+    // released after both halves (the per-pair tests use the values).
+    const int eset = warp / WS_ESET, q4 = warp & 3, col = ((warp >> 2) & 1) * WS_ECOLS;
     const int uu = q4 * 32 + lane;                                    // this thread's user row
     const uint32_t tl = taddr + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col;
     long long st_yes = 0, st_todo = 0, w_slow = 0, n_slow = 0, w_atom = 0;
     WsChunk ych{0, 0}, tch{0, 0};                                    // this warp's chunks of the pair lists
     uint32_t tpar = 0;
-    int acc = 0;
-    // constants of the current (tile, group), reloaded on WI_NEWGROUP
+    int acc = eset;
+    int cur_seq = 0;                       // first tile whose data this warp has not released
+    int c_seq = -1, c_ga = -1;             // (tile, group) of the constants held
     int pre_w = 0, nvalid = 0, kq = 1;
     long long u0 = 0;
     float un = 0.f;
@@ -2559,70 +2590,68 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       tpar ^= 1u << acc;
       const WsItem itm = items[acc];
       if (itm.flags & WI_END) break;
-      if (itm.flags & WI_NEWGROUP) {
-        const WsTile& T = tinfo[itm.ab];
+      // items come in tile order: the tiles before this item's are done for
+      // this warp, whether or not it had items in them
+      for (; cur_seq < itm.seq; ++cur_seq)
+        if (lane == 0) mbar_arrive(&eempty[cur_seq % WS_ESLOTS]);
+      if (itm.seq != c_seq || itm.ga != c_ga) {
+        const int es = itm.seq % WS_ESLOTS;
+        const WsTile& T = tinfo[es];
         pre_w = T.pre[itm.ga][(q4 * 32) / sub];
         nvalid = T.nvalid;
         u0 = T.u0;
         kq = T.k[itm.ga];
-        un = sUN[itm.ab * TCU + uu];
-        L = itm.ga < WS_LG ? sL[((size_t)itm.ab * WS_LG + itm.ga) * TCU + uu]
+        un = sUN[es * TCU + uu];
+        L = itm.ga < WS_LG ? sL[((size_t)es * WS_LG + itm.ga) * TCU + uu]
                            : (uu < nvalid ? c.Lb[(int64_t)(kq - 1) * c.n + u0 + uu] : make_float2(kInf, kInf));
+        c_seq = itm.seq;
+        c_ga = itm.ga;
       }
       // live queries of this warp's columns for its block (warp-uniform)
       int live = pre_w - itm.t * WS_N - col;
       live = live < 0 ? 0 : (live > WS_ECOLS ? WS_ECOLS : live);
-      float v[WS_ECOLS];
-      long long t_ld = 0;
-      if (PROF) t_ld = clock64();
-      if (live > 0) {
+      const bool rowok = uu < nvalid;
+      const int64_t pos = u0 + uu;
+      // Fast Lemma 1: the item's first query has the largest error scale
+      // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
+      const float thr = __fsub_rd(L.x, __fmaf_ru(un, itm.c0.x, itm.c0.y));
+#pragma unroll
+      for (int h = 0; h < WS_ECOLS / 32; ++h) {
+        int lh = live - 32 * h;
+        if (lh <= 0) break;                                           // warp-uniform
+        lh = lh > 32 ? 32 : lh;
+        float v[32];
+        long long t_ld = 0;
+        if (PROF) t_ld = clock64();
         tc_fence_after();
-        tmem_ld32(tl + (uint32_t)(acc * WS_N), v);
-        if (WS_ECOLS > 32 && live > 32) tmem_ld32(tl + (uint32_t)(acc * WS_N) + 32, v + 32);
+        tmem_ld32(tl + (uint32_t)(acc * WS_N + 32 * h), v);
         tmem_ld_wait();
-        tc_fence_before();
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
-      if (PROF) w_b += clock64() - t_ld;
-      acc = acc + 1 == WS_NACC ? 0 : acc + 1;
-      if (live > 0) {
-        const bool rowok = uu < nvalid;
-        const int64_t pos = u0 + uu;
-        // Fast Lemma 1: the item's first query has the largest error scale
-        // and slack (descending norm), so acc < lo_k - e(u, q_0) proves "no".
-        const float thr = __fsub_rd(L.x, __fmaf_ru(un, itm.c0.x, itm.c0.y));
+        if (PROF) w_b += clock64() - t_ld;
         bool any = rowok;
-        if (rowok && live == WS_ECOLS)
-          any = (WS_ECOLS == 32 ? ws_max32(v) : fmaxf(ws_max32(v), ws_max32(v + WS_ECOLS - 32))) >= thr;
+        if (rowok && lh == 32) any = ws_max32(v) >= thr;
         if (__any_sync(FULL, any)) {
           long long t_sl = 0;
           if (PROF) t_sl = clock64();
-          // (error scale, slack) and index of the warp's query columns, one
+          // (error scale, slack) and index of these 32 query columns, one
           // coalesced load each from the packed item in global memory (its
-          // stage in shared memory may be refilled already), for all lanes
+          // stage in shared memory may be refilled already)
           const float2* cq0 = reinterpret_cast<const float2*>(b.bitems + (size_t)itm.item * PACK + BROWS);
-#pragma unroll
-          for (int h = 0; h < WS_ECOLS / 32; ++h) {
-            s_ecq[warp][32 * h + lane] = __ldg(cq0 + col + 32 * h + lane);
-            s_eqj[warp][32 * h + lane] = __ldg(reinterpret_cast<const int*>(cq0 + WS_N) + col + 32 * h + lane);
-          }
+          s_ecq[warp][lane] = __ldg(cq0 + col + 32 * h + lane);
+          s_eqj[warp][lane] = __ldg(reinterpret_cast<const int*>(cq0 + WS_N) + col + 32 * h + lane);
           __syncwarp();
-#pragma unroll
-          for (int h = 0; h < WS_ECOLS / 32; ++h) {
-            const int lh = live - 32 * h;
-            if (lh > 0)
-              ws_classify<PROF>(c, b, v + 32 * h, lh > 32 ? 32 : lh, any, thr, un, L, kq, &s_ecq[warp][32 * h],
-                                &s_eqj[warp][32 * h], pos, ych, tch, st_yes, st_todo, w_atom);
-          }
+          ws_classify<PROF>(c, b, v, lh, any, thr, un, L, kq, s_ecq[warp], s_eqj[warp], pos, ych, tch, st_yes,
+                            st_todo, w_atom);
+          __syncwarp();
           if (PROF) {
             w_slow += clock64() - t_sl;
             ++n_slow;
           }
         }
       }
+      tc_fence_before();
       __syncwarp();
-      if (lane == 0 && (itm.flags & WI_LAST)) mbar_arrive(&aempty[itm.ab]);
+      if (lane == 0) mbar_arrive(&tempty[acc]);
+      acc = acc + 2 >= WS_NACC ? acc + 2 - WS_NACC : acc + 2;
     }
     // the unused rest of both chunks (fewer than a chunk each)
     if (lane < ych.left && ych.next + lane < b.cap_y) b.ypairs[ych.next + lane] = PAIR_NONE;
