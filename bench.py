@@ -357,18 +357,20 @@ def run_ours(a):
     if (done_h[:, 0] != 0).any():
         raise RuntimeError(f"batch status {done_h[:, 0].tolist()}")
     results = int(done_h[:, 1].sum())
-    last_offs[0] = a_offs[-1].cpu().numpy()
+    timed_offs = a_offs[-1].cpu().numpy()
     prof = rmips.rmips_profile_read(index)
     rmips.rmips_profile_enable(index, False)
-    qstats = rmips.rmips_last_query_stats(index)
     clocks = sampler.stop(t_wall0, t_wall1)
-    # pipeline counters of the tensor-core filter: one more step with the
-    # instrumented kernel, outside the timed region
+    # pipeline counters of the tensor-core filter, and the query statistics
+    # (kept by the synchronous call only): the last timed batch once more,
+    # outside the timed region, with the instrumented kernel
     rmips.rmips_profile_enable(index, 2)
-    step(a.warmup)
+    step(n_warm + a.steps - 1)
     torch.cuda.synchronize(dev)
     pprof = rmips.rmips_profile_read(index)
     rmips.rmips_profile_enable(index, False)
+    qstats = rmips.rmips_last_query_stats(index)
+    last_offs[0] = timed_offs
     ms = ev0.elapsed_time(ev1)
     ms_max, units = reduce_over_ranks(ms, a.steps * a.nq, dist, dev)
     value = units / (ms_max / 1e3)
