@@ -175,9 +175,14 @@ rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
  * RMIPS_ERR_TIMEOUT, RMIPS_ERR_INTERNAL) and done[1] the number of result
  * ids.  The returned status covers only what the host can check (arguments,
  * allocations, launches).  The buffers must stay valid until the stream has
- * passed the call.  Calls on other streams and the other query calls order
- * themselves after it.  Filter timing and kept pairs reach the profile when
- * rmips_profile_read is called; rmips_last_query_stats is not updated.
+ * passed the call.  Each call runs on a workspace of the index (scratch
+ * buffers and captured graphs): the oldest one whose queued work has
+ * finished, else a second one, so a call on another stream may run at the
+ * same time as this one (the index itself is only read; consecutive batches
+ * queued on two streams in turn overlap).  While both workspaces still have
+ * work queued, a call waits on the device for the older one's work.  Filter
+ * timing and kept pairs reach the profile when rmips_profile_read is called;
+ * rmips_last_query_stats is not updated.
  */
 rmips_status rmips_query_batch_async(rmips_index* index, const float* qs, int64_t nq, const int32_t* ks,
                                      int64_t* out_ids, int64_t capacity, int64_t* out_offsets,
