@@ -364,6 +364,41 @@ def test_async_batch_matches_sync_and_reports_on_device():
     index.close()
 
 
+def test_async_batches_on_two_streams_overlap_correctly():
+    # consecutive batches queued on two streams in turn run on two workspaces
+    # at once (each replaying its own graphs after two uses); every batch must
+    # still return exactly the synchronous answer, including batches of
+    # another size in between
+    torch = pytest.importorskip("torch")
+    Q, P = datagen.make_problem(30000, 6000, 50, 29)
+    index = rmips.rmips_build_index(Q, P, k_max=25)
+    qs, _ = datagen.queries_from_items(P, 8 * 1200, 29)
+    ks = datagen.random_ks(len(qs), 1, 25, 29)
+    sizes = [1200, 1200, 1200, 1200, 700, 1200, 1200, 1200]
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    refs = [rmips.rmips_query_batch(index, qs[a:a + n], ks[a:a + n]) for a, n in zip(starts, sizes)]
+    dev = torch.device("cuda")
+    dq, dk = torch.from_numpy(qs).to(dev), torch.from_numpy(ks).to(dev)
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    outs = []
+    for rnd in range(2):
+        for i, (a, n) in enumerate(zip(starts, sizes)):
+            total = int(refs[i][1][-1])
+            out = torch.full((total + 5,), -1, dtype=torch.int64, device=dev)
+            offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+            done = torch.full((2,), -1, dtype=torch.int64, device=dev)
+            rmips.rmips_query_batch_async(index, dq[a:a + n], dk[a:a + n], out, offs, done, streams[i & 1])
+            outs.append((i, out, offs, done))
+    torch.cuda.synchronize()
+    for i, out, offs, done in outs:
+        ids_ref, offs_ref = refs[i]
+        total = int(offs_ref[-1])
+        assert done.tolist() == [0, total], i
+        assert np.array_equal(offs.cpu().numpy(), offs_ref), i
+        assert np.array_equal(out[:total].cpu().numpy(), ids_ref), i
+    index.close()
+
+
 def test_graph_replay_with_same_and_changing_batches():
     """Passes with unchanged arguments replay captured graphs (from the second
     identical call on); new query data under the same arguments, and changed
