@@ -2045,6 +2045,10 @@ constexpr int WS_ESET = WS_EPI / 2;                    // epilogue warps per ite
 constexpr int WS_ECOLS = WS_N / (WS_ESET / 4);         // query columns per epilogue warp, read 32 at a time
 static_assert(WS_ECOLS == 64 && WS_NACC % 2 == 0, "two sets of 8 epilogue warps, 64 columns each");
 constexpr int WS_ESLOTS = 3;                           // tile slots of the epilogue's per-tile data
+// Item record flags.  WI_END ends an epilogue set's loop.  WI_LAST (last
+// item of its tile) and WI_NEWGROUP (first item of a (tile, group)) describe
+// the record only: the epilogue sets see alternate items, so they key their
+// per-tile state on (seq, ga) instead.
 enum : int { WI_LAST = 1, WI_END = 2, WI_NEWGROUP = 4 };
 
 struct WsTile {                                        // one tile slot, written by the loader
