@@ -155,6 +155,11 @@ rmips_status rmips_query(rmips_index* index, const float* q, int32_t k,
  * out_ids[out_offsets[j] .. out_offsets[j+1]).  On RMIPS_ERR_CAPACITY the
  * offsets are still filled (out_offsets[nq] is the size needed) and out_ids
  * is left unspecified.  Synchronises `stream`.
+ * The batched filter lists the (user, query) pairs its O(1) tests leave
+ * undecided; the list holds RMIPS_PAIR_LIST_CAP entries (an environment
+ * variable read when a workspace is created; default 16,777,216).  A pass that
+ * finds more is run again in passes of half the size, down to one query at a
+ * time, so the results do not depend on the list size.
  */
 rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
                                const int32_t* ks, const rmips_segment* segs,
@@ -172,6 +177,8 @@ rmips_status rmips_query_batch(rmips_index* index, const float* qs, int64_t nq,
  * out_offsets holds the CSR offsets, done[0] an rmips_status (RMIPS_OK,
  * RMIPS_ERR_NONFINITE, RMIPS_ERR_K_RANGE, RMIPS_ERR_CAPACITY with
  * out_offsets[nq] = the size needed and out_ids unspecified,
+ * RMIPS_ERR_OOM when the undecided-pair list overflowed -- this call cannot
+ * re-run, so run that batch through rmips_query_batch or in smaller batches --,
  * RMIPS_ERR_TIMEOUT, RMIPS_ERR_INTERNAL) and done[1] the number of result
  * ids.  The returned status covers only what the host can check (arguments,
  * allocations, launches).  The buffers must stay valid until the stream has
@@ -238,8 +245,9 @@ typedef struct {
   int64_t mfilter_pairs;     /* (user, query) pairs kept by Lemma 3 */
   double mfilter_alg_flops;  /* 2 d flops per kept pair (the inner products
                                 the per-user tests need) */
-  int64_t mfilter_tiles;     /* 128 x 64 tensor-core tiles multiplied (the
-                                padded work behind the kept pairs) */
+  int64_t mfilter_tiles;     /* 128-user x 128-query tensor-core items
+                                multiplied (the padded work behind the kept
+                                pairs) */
   double mfilter_wait[11];   /* SM clock cycles the tensor-core filter's roles
                                 spent waiting, summed over CTAs: loader (free
                                 tile slot), feeder (free query stage), MMA
@@ -284,7 +292,11 @@ rmips_status rmips_profile_read(const rmips_index* index, rmips_profile* out);
  * q: d floats, host or device.  out_ids: DEVICE memory, capacity int64 slots,
  * receives the ascending result ids.  *out_count (host) receives the result
  * size; on RMIPS_ERR_CAPACITY it is the size needed and out_ids is untouched.
- * The first call on a device looks up the array's device address.
+ * The array belongs to a lazily loaded module of the library; building or
+ * loading an index on a device loads it there (and looks up its address), so
+ * the call itself only reads that cached address.  On an error return after
+ * GPU work was queued, the call waits for that work before it releases the
+ * lock.
  * All calls share the one array, so calls are serialised by a process-wide
  * lock held until the call's GPU work has finished; GPU work of two calls that
  * overlapped would race on the shared scratch.  Synchronises `stream`.
@@ -404,15 +416,14 @@ int32_t rmips_exact_sign_host(const float* u, const float* a, const float* b, in
 /*
  * rmips_debug_tc_tile -- test hook for the tensor-core tiles of the batched
  * filter (no counterpart in the paper).  Runs one 128 x 64 x 64 tile through
- * the shared-memory layout, UMMA descriptors (with the given leading and
- * stride byte offsets; 0 selects the filter's own), tcgen05.mma and TMEM
- * loads the batched filter uses: D[128][64] = A[128][64] * B[64][64]^T.
+ * the shared-memory layout, UMMA descriptors (always the filter's own layout
+ * constants), tcgen05.mma and TMEM loads the batched filter uses:
+ * D[128][64] = A[128][64] * B[64][64]^T.
  * kind: 0 TF32, 1 BF16, 2 FP16 (A and B rounded to nearest into that format).
- * A, B, D: device float32, row-major.  lbo, sbo: 0 or multiples of 16 in
- * [16, 4096].  Synchronises `stream`.  Errors: ARG, TIMEOUT, CUDA.
+ * A, B, D: device float32, row-major.  Synchronises `stream`.
+ * Errors: ARG, TIMEOUT, CUDA.
  */
-rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, int32_t lbo, int32_t sbo,
-                                 void* stream);
+rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, void* stream);
 
 #ifdef __cplusplus
 }

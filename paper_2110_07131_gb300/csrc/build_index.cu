@@ -638,6 +638,11 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   cudaGetDevice(&idx->device);
 
   auto fail = [&](rmips_status s) { rmips_free_index(idx); return s; };
+  {
+    rmips_status pc = check_ptr_device(Q, idx->device, "Q");
+    if (pc == RMIPS_OK) pc = check_ptr_device(P, idx->device, "P");
+    if (pc != RMIPS_OK) return fail(pc);
+  }
   const bool q_dev = is_device_ptr(Q), p_dev = is_device_ptr(P);
   float *Qin = nullptr, *Pin = nullptr, *qn = nullptr, *pn = nullptr, *cval = nullptr;
   float *Pt = nullptr, *cpn = nullptr, *uex = nullptr;
@@ -828,6 +833,10 @@ cleanup:
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("stream synchronisation failed after build");
     return fail(RMIPS_ERR_CUDA);
+  }
+  {
+    const rmips_status ps = noalloc_prepare();       // the allocation-free call's scratch exists from here on
+    if (ps != RMIPS_OK) return fail(ps);
   }
   idx->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = idx;

@@ -18,6 +18,21 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int ptr_class(const void* p, int device) {
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_HOST;
+  }
+  return ptr_class_of((int)a.type, a.device, device);
+}
+
+rmips_status check_ptr_device(const void* p, int device, const char* what) {
+  if (ptr_class(p, device) != PTR_OTHER_DEVICE) return RMIPS_OK;
+  set_error(std::string(what) + " is device memory of another GPU than the index's");
+  return RMIPS_ERR_ARG;
+}
+
 void destroy_workspace(Workspace* ws) {
   if (!ws) return;
   if (ws->done_ev) cudaEventDestroy(ws->done_ev);

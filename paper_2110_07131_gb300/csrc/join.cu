@@ -136,6 +136,7 @@ extern "C" rmips_status rmips_topk_join(const rmips_index* idx, int32_t k, int64
     return RMIPS_ERR_ARG;
   }
   if (k < 1 || k > idx->k_max || k > idx->m) { set_error("k outside [1, min(k_max, m)]"); return RMIPS_ERR_K_RANGE; }
+  if (check_ptr_device(out_ids, idx->device, "out_ids") != RMIPS_OK) return RMIPS_ERR_ARG;
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != idx->device) cudaSetDevice(idx->device);

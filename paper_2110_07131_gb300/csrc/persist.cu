@@ -15,14 +15,61 @@
 namespace rmips {
 namespace {
 
-constexpr char kMagic[8] = {'R', 'M', 'I', 'P', 'S', 'I', 'X', '1'};
+constexpr char kMagic[8] = {'R', 'M', 'I', 'P', 'S', 'I', 'X', '2'};
 
+// File layout: this header, then for every array its byte count (int64), its
+// bytes and their 64-bit FNV-1a hash.  96 bytes, no implicit padding.
 struct FileHeader {
   char magic[8];
   int64_t n, m, nb, pp, incomplete;
   int32_t d, k_max, bs, precision, full_p, batch_tc, no_blocks, has_qh, has_qtc, narrays;
   float pn0;
+  int32_t reserved;
 };
+static_assert(sizeof(FileHeader) == 96, "index file header layout");
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Every field the query kernels size or index with must be what a build of
+// this library could have written; a file that fails is refused before any
+// device call.
+bool header_ok(const FileHeader& h, std::string* why) {
+  auto bad = [&](const char* w) { *why = w; return false; };
+  if (memcmp(h.magic, kMagic, sizeof(kMagic)) != 0) return bad("not an index file of this library");
+  if (h.n < 1 || h.n > INT32_MAX || h.m < 1 || h.m > INT32_MAX) return bad("user or item count out of range");
+  if (h.d < 1 || h.d > RMIPS_DMAX || h.k_max < 1 || h.k_max > RMIPS_KMAX_LIMIT) return bad("d or k_max out of range");
+  if (h.bs != 32 && h.bs != 64 && h.bs != 128 && h.bs != 256) return bad("block size is not 32, 64, 128 or 256");
+  if (h.nb != (h.n + h.bs - 1) / h.bs) return bad("block count does not match n and the block size");
+  if (h.precision < RMIPS_FP32 || h.precision > RMIPS_FP16) return bad("unknown precision");
+  if ((h.full_p != 0 && h.full_p != 1) || (h.batch_tc != 0 && h.batch_tc != 1) ||
+      (h.no_blocks != 0 && h.no_blocks != 1) || (h.has_qh != 0 && h.has_qh != 1) ||
+      (h.has_qtc != 0 && h.has_qtc != 1) || h.reserved != 0)
+    return bad("flag field out of range");
+  if (h.pp < 1 || h.pp > h.m || (h.full_p == 1) != (h.pp == h.m)) return bad("|P'| does not match the index mode");
+  if (h.has_qh != (h.precision != RMIPS_FP32 ? 1 : 0)) return bad("reduced-precision copy does not match the precision");
+  if (h.has_qtc && h.d > 64) return bad("tensor-core tiles need d <= 64");
+  if (h.incomplete < 0 || h.incomplete > h.n || (!h.full_p && h.incomplete != 0)) return bad("incomplete count out of range");
+  if (!(h.pn0 >= 0.f) || !(h.pn0 <= FLT_MAX)) return bad("largest item norm is not finite");
+  return true;
+}
+
+bool is_permutation(const unsigned char* bytes, int64_t n) {
+  std::vector<unsigned char> seen((size_t)n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t v;
+    memcpy(&v, bytes + 4 * i, 4);
+    if (v < 0 || v >= n || seen[(size_t)v]) return false;
+    seen[(size_t)v] = 1;
+  }
+  return true;
+}
 
 // The device arrays of an index in file order: pointer slot and byte size.
 struct ArrayRef {
@@ -89,6 +136,7 @@ extern "C" rmips_status rmips_index_save(const rmips_index* cidx, const char* pa
   h.d = idx->d; h.k_max = idx->k_max; h.bs = idx->bs; h.precision = idx->precision; h.full_p = idx->full_p;
   h.batch_tc = idx->batch_tc; h.no_blocks = idx->no_blocks; h.has_qh = idx->Qh != nullptr; h.has_qtc = idx->Qtc != nullptr;
   h.pn0 = idx->pn0;
+  h.reserved = 0;
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh, h.has_qtc);
   h.narrays = (int32_t)a.size();
   if (cudaDeviceSynchronize() != cudaSuccess) { set_error("device error before save"); return RMIPS_ERR_CUDA; }
@@ -101,61 +149,83 @@ extern "C" rmips_status rmips_index_save(const rmips_index* cidx, const char* pa
     buf.resize((size_t)r.bytes);
     ok = ok && cudaMemcpy(buf.data(), *r.ptr, (size_t)r.bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && fwrite(buf.data(), 1, (size_t)r.bytes, f) == (size_t)r.bytes;
+    const uint64_t hash = fnv1a(buf.data(), buf.size());
+    ok = ok && fwrite(&hash, sizeof(hash), 1, f) == 1;
   }
   ok = (fclose(f) == 0) && ok;
   if (!ok) { set_error(std::string("writing ") + path + " failed"); return RMIPS_ERR_ARG; }
   return RMIPS_OK;
 }
 
+// Reads and checks the whole file on the host (header fields, array sizes,
+// hashes, the two permutations and the candidate item positions) and only
+// then uploads it, so a corrupted or foreign file never reaches a kernel.
 extern "C" rmips_status rmips_index_load(const char* path, void* stream, rmips_index** out) {
   if (out) *out = nullptr;
   if (!path || !out) { set_error("null argument"); return RMIPS_ERR_ARG; }
   FILE* f = fopen(path, "rb");
   if (!f) { set_error(std::string("cannot open ") + path); return RMIPS_ERR_ARG; }
   FileHeader h{};
-  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.n < 1 || h.m < 1 ||
-      h.d < 1 || h.d > RMIPS_DMAX || h.k_max < 1 || h.k_max > RMIPS_KMAX_LIMIT) {
+  std::string why;
+  if (fread(&h, sizeof(h), 1, f) != 1) why = "shorter than an index header";
+  else header_ok(h, &why);
+  if (!why.empty()) {
     fclose(f);
-    set_error(std::string(path) + " is not an index file of this library");
+    set_error(std::string(path) + ": " + why);
     return RMIPS_ERR_ARG;
   }
   rmips_index* idx = new rmips_index();
   idx->n = h.n; idx->m = h.m; idx->nb = h.nb; idx->pp = h.pp; idx->incomplete = h.incomplete;
   idx->d = h.d; idx->k_max = h.k_max; idx->bs = h.bs; idx->precision = h.precision; idx->full_p = h.full_p;
   idx->batch_tc = h.batch_tc; idx->no_blocks = h.no_blocks; idx->pn0 = h.pn0;
-  cudaGetDevice(&idx->device);
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh != 0, h.has_qtc != 0);
-  rmips_status s = RMIPS_OK;
-  if ((int32_t)a.size() != h.narrays) {
-    set_error(std::string(path) + ": array count does not match its header");
-    s = RMIPS_ERR_ARG;
-  }
-  std::vector<unsigned char> buf;
-  for (size_t i = 0; s == RMIPS_OK && i < a.size(); ++i) {
+  std::vector<std::vector<unsigned char>> bufs(a.size());
+  if ((int32_t)a.size() != h.narrays) why = "array count does not match its header";
+  for (size_t i = 0; why.empty() && i < a.size(); ++i) {
     int64_t bytes = -1;
-    if (fread(&bytes, sizeof(bytes), 1, f) != 1 || bytes != a[i].bytes) {
-      set_error(std::string(path) + ": array sizes do not match its header");
-      s = RMIPS_ERR_ARG;
+    uint64_t hash = 0;
+    if (fread(&bytes, sizeof(bytes), 1, f) != 1 || bytes != a[i].bytes) { why = "array sizes do not match its header"; break; }
+    bufs[i].resize((size_t)bytes);
+    if (fread(bufs[i].data(), 1, (size_t)bytes, f) != (size_t)bytes || fread(&hash, sizeof(hash), 1, f) != 1) {
+      why = "truncated";
       break;
     }
-    buf.resize((size_t)bytes);
-    if (fread(buf.data(), 1, (size_t)bytes, f) != (size_t)bytes) {
-      set_error(std::string(path) + " is truncated");
-      s = RMIPS_ERR_ARG;
-      break;
+    if (hash != fnv1a(bufs[i].data(), bufs[i].size())) { why = "array contents do not match their hash"; break; }
+  }
+  if (why.empty() && fgetc(f) != EOF) why = "trailing bytes after the last array";
+  fclose(f);
+  // index arrays that address device memory: permutations, candidate positions
+  for (size_t i = 0; why.empty() && i < a.size(); ++i) {
+    if ((a[i].ptr == (void**)&idx->permQ && !is_permutation(bufs[i].data(), idx->n)) ||
+        (a[i].ptr == (void**)&idx->permP && !is_permutation(bufs[i].data(), idx->m)))
+      why = "a stored order is not a permutation";
+    if (a[i].ptr == (void**)&idx->cand) {
+      const int32_t* c = reinterpret_cast<const int32_t*>(bufs[i].data());
+      for (size_t e = 0; e < bufs[i].size() / 4; ++e)
+        if (c[e] < -1 || c[e] >= idx->m) { why = "a candidate item position is out of range"; break; }
     }
-    cudaError_t e = cudaMalloc(a[i].ptr, (size_t)bytes);
+  }
+  if (!why.empty()) {
+    delete idx;
+    set_error(std::string(path) + ": " + why);
+    return RMIPS_ERR_ARG;
+  }
+  cudaGetDevice(&idx->device);
+  rmips_status s = RMIPS_OK;
+  for (size_t i = 0; s == RMIPS_OK && i < a.size(); ++i) {
+    cudaError_t e = cudaMalloc(a[i].ptr, bufs[i].size());
     if (e == cudaSuccess) {
-      idx->device_bytes += bytes;
-      e = cudaMemcpy(*a[i].ptr, buf.data(), (size_t)bytes, cudaMemcpyHostToDevice);
+      idx->device_bytes += (int64_t)bufs[i].size();
+      e = cudaMemcpy(*a[i].ptr, bufs[i].data(), bufs[i].size(), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
       set_error(cudaGetErrorString(e));
       s = e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
     }
+    std::vector<unsigned char>().swap(bufs[i]);
   }
-  fclose(f);
   (void)stream;
+  if (s == RMIPS_OK) s = noalloc_prepare();          // the allocation-free call's scratch exists from here on
   if (s != RMIPS_OK) {
     rmips_free_index(idx);
     return s;

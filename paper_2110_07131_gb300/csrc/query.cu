@@ -19,6 +19,7 @@
 //              ascending order, capacity check, CSR offsets.
 #include <climits>
 #include <cmath>
+#include <cstdlib>
 
 #include "rmips_internal.cuh"
 #include "tc_common.cuh"
@@ -105,7 +106,7 @@ __global__ void k_qprep(Common c, int64_t nq, int precision) {
     const bool fin = query_bounds(q, c.d, precision, &qn, &eps);
     const int k = c.dk[j];
     if (!fin) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_NONFINITE);
-    if (k < 1 || k > c.k_max) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_INTERNAL);
+    if (k < 1 || k > c.k_max) atomicCAS((unsigned long long*)&c.ctr[C_STATUS], 0ull, (unsigned long long)ST_K_RANGE);
     c.dqn[j] = qn;
     c.deps[j] = eps;
   }
@@ -817,6 +818,10 @@ rmips_status run_queries(rmips_index* idx, Workspace* ws, int64_t nq, const rmip
 rmips_status status_from_device(long long s) {
   switch ((int)s) {
     case ST_OK: return RMIPS_OK;
+    case ST_K_RANGE: set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE;
+    case ST_PAIRS_FULL:
+      set_error("the undecided-pair list of a batched pass is full (RMIPS_PAIR_LIST_CAP)");
+      return RMIPS_ERR_OOM;
     case ST_NONFINITE:
       set_error("non-finite value in a query (or, for a BF16 / FP16 index, one beyond that format's range)");
       return RMIPS_ERR_NONFINITE;
@@ -1013,8 +1018,7 @@ void record_stats(rmips_index* idx, Workspace* ws, const long long* h, int64_t n
 // kinds); D [128][64] = A B^T.
 template <int KIND>
 __global__ void __launch_bounds__(128) k_debug_tc(const float* __restrict__ A, const float* __restrict__ B,
-                                                  float* __restrict__ D, uint32_t lbo, uint32_t sbo,
-                                                  long long* __restrict__ status) {
+                                                  float* __restrict__ D, long long* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   constexpr uint32_t E = KIND == TCK_TF32 ? 4 : 2;
   unsigned char* sA = dsm;                          // 128 x 64
@@ -1049,9 +1053,10 @@ __global__ void __launch_bounds__(128) k_debug_tc(const float* __restrict__ A, c
   const uint32_t taddr = taddr_s;
   if (tid == 0) {
     const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(128, 64) : tc_idesc_f16(128, 64, KIND == TCK_BF16);
+    const uint32_t sbo = KIND == TCK_TF32 ? TC_SBO : TC_SBO16;
     for (uint32_t s = 0; s < TC_K * E / 32; ++s) {
-      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, lbo, sbo);
-      const uint64_t bd = tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, lbo, sbo);
+      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, sbo);
+      const uint64_t bd = tc_sdesc(smem_u32(sB) + s * 2 * TC_LBO, TC_LBO, sbo);
       if (KIND == TCK_TF32) tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
       else tc_mma_f16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
     }
@@ -1176,7 +1181,7 @@ __global__ void k_mprep_a(Common c, Batch b, int precision) {
   const float eps = __fmul_ru((float)(d + 2), __fmaf_ru(lsub, qmax, 0x1p-148f));
   int k = b.dk[j];
   if ((bad >> (threadIdx.x & 24)) & 0xffu) set_status(c.ctr, ST_NONFINITE);
-  if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_INTERNAL); k = 1; }
+  if (k < 1 || k > c.k_max) { set_status(c.ctr, ST_K_RANGE); k = 1; }
   b.dqn[j] = qn;
   b.deps[j] = eps;
   b.qcnt[j] = 0;
@@ -1545,7 +1550,7 @@ __global__ void __launch_bounds__(MQ_THREADS) k_mfilter(Common c, Batch b, int n
               if (tt) {
                 const long long at = base + __popc(bt & lt);
                 if (at < b.cap_t) b.tpairs[at] = pair;
-                else set_status(c.ctr, ST_INTERNAL);
+                else set_status(c.ctr, ST_PAIRS_FULL);
               }
             }
           }
@@ -2247,7 +2252,7 @@ __device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, con
     tm &= tm - 1;
     const long long at = wt.at(et++);
     if (at < b.cap_t) b.tpairs[at] = ((unsigned long long)(uint32_t)sj[q] << 32) | (unsigned long long)pos;
-    else set_status(c.ctr, ST_INTERNAL);
+    else set_status(c.ctr, ST_PAIRS_FULL);
   }
   st_yes += ny;
   st_todo += nt;
@@ -2720,6 +2725,17 @@ cudaError_t launch_mfilter_ws(int kind, const Common& c, const Batch& b, const u
                : launch_ws_prof<false>(kind, c.d, c, b, qtc, ngroups, grid, ns, smem, st);
 }
 
+// Entries of a workspace's undecided-pair list (8 bytes each): 16,777,216, or
+// the value of the environment variable RMIPS_PAIR_LIST_CAP (at least 64) when
+// a workspace is created.  A pass that finds more undecided pairs is run
+// again in smaller passes by the synchronous calls.
+int64_t pair_list_cap() {
+  const char* v = getenv("RMIPS_PAIR_LIST_CAP");
+  long long c = v ? atoll(v) : 0;
+  if (c <= 0) return 16ll << 20;
+  return c < 64 ? 64 : c;
+}
+
 rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
   if (!ws->bq) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bq, (size_t)MQ_SLOTS * idx->d * sizeof(float)));
@@ -2730,7 +2746,7 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->grp, (RMIPS_KMAX_LIMIT + 2) * sizeof(int4)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->qcnt, MQ_MAXQ * sizeof(int32_t)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->qcur, MQ_MAXQ * sizeof(int32_t)));
-    ws->cap_t = 16ll << 20;
+    ws->cap_t = pair_list_cap();
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->tpairs, ws->cap_t * sizeof(unsigned long long)));
   }
   if (!ws->bitems && idx->d <= (int)TC_K) {
@@ -2839,7 +2855,7 @@ bool capture_graph(cudaStream_t cs, F&& enqueue, cudaGraphExec_t* exec) {
 }
 
 rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
-                       cudaStream_t st, const long long* dseglo, const long long* dseghi) {
+                       cudaStream_t st, const long long* dseglo, const long long* dseghi, int pass_max = MQ_MAXQ) {
   ws->ctr_dirty = true;
   Common c = make_common(idx, ws);
   static thread_local int sm_count = 0;
@@ -2870,8 +2886,9 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   if (per_sm < 1) per_sm = 1;
   const int64_t tiles = (idx->n + MQ_TU - 1) / MQ_TU;
   const int fgrid = (int)(tiles < sm_count * per_sm ? tiles : sm_count * per_sm);
-  for (int64_t j0 = 0; j0 < nq; j0 += MQ_MAXQ) {
-    const int cnt = (int)((nq - j0) < MQ_MAXQ ? (nq - j0) : MQ_MAXQ);
+  if (pass_max < 1 || pass_max > MQ_MAXQ) pass_max = MQ_MAXQ;
+  for (int64_t j0 = 0; j0 < nq; j0 += pass_max) {
+    const int cnt = (int)((nq - j0) < pass_max ? (nq - j0) : pass_max);
     Batch b;
     memset(&b, 0, sizeof(b));                      // padding too: graph keys compare the bytes
     b.dq = ws->dq + j0 * idx->d;
@@ -2931,7 +2948,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
       k_memit_big<<<MQ_BIG_SLOTS, 1024, 0, q>>>(c, b);
     };
     // replay the pass's graphs when every kernel argument is as captured
-    const int pass = (int)(j0 / MQ_MAXQ);
+    const int pass = (int)(j0 / pass_max);
     if ((int)ws->pgraph.size() <= pass) ws->pgraph.resize(pass + 1);
     Workspace::PassGraph& pg = ws->pgraph[pass];
     std::vector<unsigned char> key(sizeof(Common) + sizeof(Batch) + 4 * sizeof(int));
@@ -2998,6 +3015,8 @@ extern "C" rmips_status rmips_query(rmips_index* idx, const float* q, int32_t k,
   if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
   rmips_status s = check_segment(idx, seg);
   if (s != RMIPS_OK) return s;
+  if ((s = check_ptr_device(q, idx->device, "q")) != RMIPS_OK) return s;
+  if (capacity > 0 && (s = check_ptr_device(out_ids, idx->device, "out_ids")) != RMIPS_OK) return s;
   DeviceGuard dg(idx->device);
   cudaStream_t st = (cudaStream_t)stream;
   s = RMIPS_OK;
@@ -3070,6 +3089,9 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   out_offsets[0] = 0;
   if (nq == 0) return RMIPS_OK;
   rmips_status s = RMIPS_OK;
+  if ((s = check_ptr_device(qs, idx->device, "qs")) != RMIPS_OK) return s;
+  if ((s = check_ptr_device(ks, idx->device, "ks")) != RMIPS_OK) return s;
+  if (capacity > 0 && (s = check_ptr_device(out_ids, idx->device, "out_ids")) != RMIPS_OK) return s;
   if (segs)
     for (int64_t j = 0; j < nq; ++j)
       if ((s = check_segment(idx, &segs[j])) != RMIPS_OK) return s;
@@ -3100,40 +3122,49 @@ extern "C" rmips_status rmips_query_batch(rmips_index* idx, const float* qs, int
   bool ranges_only = true;
   if (segs)
     for (int64_t j = 0; j < nq; ++j) ranges_only = ranges_only && segs[j].kind != 2;
-  const bool batched = ranges_only;
-  if (batched) {
-    const long long* dlo = nullptr;
-    const long long* dhi = nullptr;
-    if (segs) {
-      if ((s = ensure_segments(ws, nq)) != RMIPS_OK) return s;
-      std::vector<long long> lo(nq), hi(nq);
-      for (int64_t j = 0; j < nq; ++j) {
-        lo[j] = segs[j].kind == 1 ? segs[j].begin : 0;
-        hi[j] = segs[j].kind == 1 ? segs[j].end : INT64_MAX;
-      }
-      RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, lo.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
-      RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, hi.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
-      dlo = ws->dseglo;
-      dhi = ws->dseghi;
+  bool batched = ranges_only;
+  const long long* dlo = nullptr;
+  const long long* dhi = nullptr;
+  if (batched && segs) {
+    if ((s = ensure_segments(ws, nq)) != RMIPS_OK) return s;
+    std::vector<long long> lo(nq), hi(nq);
+    for (int64_t j = 0; j < nq; ++j) {
+      lo[j] = segs[j].kind == 1 ? segs[j].begin : 0;
+      hi[j] = segs[j].kind == 1 ? segs[j].end : INT64_MAX;
     }
-    if ((s = run_batch(idx, ws, nq, out, capacity, st, dlo, dhi)) != RMIPS_OK) return s;
-  } else {
-    if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, lo.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, hi.data(), nq * sizeof(long long), cudaMemcpyHostToDevice, st));
+    RMIPS_TRY_CUDA(cudaStreamSynchronize(st));        // lo / hi leave scope
+    dlo = ws->dseglo;
+    dhi = ws->dseghi;
   }
-  if (out_mapped && capacity > 0) {
-    k_copy_results<<<256, 256, 0, st>>>(ws->dout, ws->h_out, ws->ctr, capacity);
-    RMIPS_TRY_CUDA(cudaGetLastError());
+  // A pass whose undecided pairs overflow the pair list is run again with
+  // passes of half the size; below 64 queries per pass the batch goes
+  // through the per-query path, whose lists hold every user.
+  for (int pass_max = MQ_MAXQ;;) {
+    if (batched) {
+      if ((s = run_batch(idx, ws, nq, out, capacity, st, dlo, dhi, pass_max)) != RMIPS_OK) return s;
+    } else {
+      if ((s = run_queries(idx, ws, nq, segs, out, capacity, st)) != RMIPS_OK) return s;
+    }
+    if (out_mapped && capacity > 0) {
+      k_copy_results<<<256, 256, 0, st>>>(ws->dout, ws->h_out, ws->ctr, capacity);
+      RMIPS_TRY_CUDA(cudaGetLastError());
+    }
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!batched || ws->h_ctr[C_STATUS] != ST_PAIRS_FULL) break;
+    ws->ev_used = 0;                                  // this attempt's filter timing is not kept
+    pass_max = (int)((pass_max < nq ? pass_max : nq) / 2);
+    if (pass_max < 64) batched = false;
   }
-  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
-  RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
-  RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
   for (int64_t j = 0; j <= nq; ++j) out_offsets[j] = ws->h_offs[j];
   record_stats(idx, ws, ws->h_ctr, nq, batched);
   {
     std::lock_guard<std::mutex> lk(idx->mu);
     idx->last_stats.result = ws->h_offs[nq];
   }
-  if (ws->h_ctr[C_STATUS] == ST_INTERNAL) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
   if ((s = status_from_device(ws->h_ctr[C_STATUS])) != RMIPS_OK) return s;
   const long long total = ws->h_offs[nq];
   if (!out_dev && total > 0) {
@@ -3196,6 +3227,19 @@ rmips_status noalloc_base(int dev, unsigned char** out) {
 }
 
 }  // namespace
+
+// Looks the scratch array up on the current device.  The library's device
+// code is loaded lazily, module by module, on first use; this lookup makes the
+// CUDA runtime load this module (and so create the array) when an index is
+// built or loaded, not in the middle of the first allocation-free call.
+rmips_status noalloc_prepare() {
+  int dev = 0;
+  RMIPS_TRY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  unsigned char* base = nullptr;
+  return noalloc_base(dev, &base);
+}
+
 }  // namespace rmips
 
 extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, int32_t k, int64_t* out_ids,
@@ -3209,6 +3253,8 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
     return RMIPS_ERR_ARG;
   }
   if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  if (check_ptr_device(q, idx->device, "q") != RMIPS_OK) return RMIPS_ERR_ARG;
+  if (capacity > 0 && check_ptr_device(out_ids, idx->device, "out_ids") != RMIPS_OK) return RMIPS_ERR_ARG;
   if (capacity > 0 && !is_device_ptr(out_ids)) {
     set_error("rmips_query_noalloc writes ids to device memory only");
     return RMIPS_ERR_ARG;
@@ -3222,6 +3268,15 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
   unsigned char* base = nullptr;
   rmips_status s = noalloc_base(dev, &base);
   if (s != RMIPS_OK) return s;
+  // Declared after the lock, so destroyed before it is released: an error
+  // return after work was queued waits for that work first, so that the
+  // next call cannot find the array still in use.
+  struct DrainOnExit {
+    cudaStream_t st;
+    bool armed = false;
+    ~DrainOnExit() { if (armed) cudaStreamSynchronize(st); }
+  } drain{st};
+  drain.armed = true;
 
   Workspace ws;                                    // views into the scratch array, nothing owned
   ws.ctr = reinterpret_cast<long long*>(base + NA_CTR);
@@ -3269,6 +3324,7 @@ extern "C" rmips_status rmips_query_noalloc(rmips_index* idx, const float* q, in
   RMIPS_TRY_CUDA(cudaMemcpyAsync(h, ws.ctr, sizeof(h), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaMemcpyAsync(offs, ws.doffs, sizeof(offs), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
+  drain.armed = false;
   *out_count = offs[1];
   return status_from_device(h[C_STATUS]);
 }
@@ -3281,7 +3337,8 @@ __global__ void k_batch_done(const long long* __restrict__ ctr, const long long*
           : s == ST_NONFINITE ? RMIPS_ERR_NONFINITE
           : s == ST_CAPACITY ? RMIPS_ERR_CAPACITY
           : s == ST_TIMEOUT ? RMIPS_ERR_TIMEOUT
-          : s == ST_INTERNAL ? RMIPS_ERR_K_RANGE : RMIPS_ERR_INTERNAL;
+          : s == ST_K_RANGE ? RMIPS_ERR_K_RANGE
+          : s == ST_PAIRS_FULL ? RMIPS_ERR_OOM : RMIPS_ERR_INTERNAL;
   done[1] = doffs[nq];
   if (dprof) atomicAdd(dprof, (unsigned long long)ctr[C_TESTED]);
 }
@@ -3294,10 +3351,13 @@ extern "C" rmips_status rmips_query_batch_async(rmips_index* idx, const float* q
     set_error("null argument or negative size");
     return RMIPS_ERR_ARG;
   }
-  if (!is_device_ptr(out_offsets) || !is_device_ptr(done) || (nq > 0 && (!is_device_ptr(qs) || !is_device_ptr(ks))) ||
-      (capacity > 0 && !is_device_ptr(out_ids))) {
-    set_error("rmips_query_batch_async takes device buffers only");
-    return RMIPS_ERR_ARG;
+  {
+    const int dv = idx->device;
+    const auto here = [dv](const void* p) { return ptr_class(p, dv) == PTR_DEVICE; };
+    if (!here(out_offsets) || !here(done) || (nq > 0 && (!here(qs) || !here(ks))) || (capacity > 0 && !here(out_ids))) {
+      set_error("rmips_query_batch_async takes device buffers of the index's GPU only");
+      return RMIPS_ERR_ARG;
+    }
   }
   DeviceGuard dg(idx->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -3329,18 +3389,20 @@ extern "C" rmips_status rmips_query_batch_async(rmips_index* idx, const float* q
   return RMIPS_OK;
 }
 
-extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind, int32_t lbo,
-                                           int32_t sbo, void* stream) {
+extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, float* D, int32_t kind,
+                                           void* stream) {
   if (kind < TCK_TF32 || kind > TCK_FP16) { set_error("bad kind"); return RMIPS_ERR_ARG; }
-  if (lbo == 0) lbo = (int32_t)TC_LBO;
-  if (sbo == 0) sbo = (int32_t)(kind == TCK_TF32 ? TC_SBO : TC_SBO16);
-  if (!A || !B || !D || lbo <= 0 || sbo <= 0 || lbo > 4096 || sbo > 4096 || (lbo & 15) || (sbo & 15)) {
-    set_error("bad argument");
+  if (!A || !B || !D) {
+    set_error("null argument");
     return RMIPS_ERR_ARG;
   }
-  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(D)) {
-    set_error("A, B and D must be device memory");
-    return RMIPS_ERR_ARG;
+  {
+    int dv = 0;
+    RMIPS_TRY_CUDA(cudaGetDevice(&dv));
+    if (ptr_class(A, dv) != PTR_DEVICE || ptr_class(B, dv) != PTR_DEVICE || ptr_class(D, dv) != PTR_DEVICE) {
+      set_error("A, B and D must be device memory of the current GPU");
+      return RMIPS_ERR_ARG;
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   long long* status = nullptr;
@@ -3349,13 +3411,13 @@ extern "C" rmips_status rmips_debug_tc_tile(const float* A, const float* B, floa
   const int dsmem = (int)(192 * TC_K * 4);
   if (kind == TCK_TF32) {
     RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
-    k_debug_tc<TCK_TF32><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+    k_debug_tc<TCK_TF32><<<1, 128, dsmem, st>>>(A, B, D, status);
   } else if (kind == TCK_BF16) {
     RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
-    k_debug_tc<TCK_BF16><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+    k_debug_tc<TCK_BF16><<<1, 128, dsmem, st>>>(A, B, D, status);
   } else {
     RMIPS_TRY_CUDA(cudaFuncSetAttribute(k_debug_tc<TCK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem));
-    k_debug_tc<TCK_FP16><<<1, 128, dsmem, st>>>(A, B, D, (uint32_t)lbo, (uint32_t)sbo, status);
+    k_debug_tc<TCK_FP16><<<1, 128, dsmem, st>>>(A, B, D, status);
   }
   RMIPS_TRY_CUDA(cudaGetLastError());
   long long h = 0;

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "../../include/rmips.h"
+#include "ptr_class.h"
 
 #define RMIPS_KC 32              // candidate slots per user (>= k_max + slack)
 #define RMIPS_KMAX_LIMIT 28      // largest supported k_max
@@ -69,8 +70,12 @@ void set_error(const std::string& msg);
     }                                                                                  \
   } while (0)
 
-// Device status word values (first error wins).
-enum : int { ST_OK = 0, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_INTERNAL = 8 };
+// Device status word values (first error wins).  ST_PAIRS_FULL: a batched
+// pass found more undecided (user, query) pairs than its list holds; the
+// synchronous calls then run the batch again in smaller passes.
+enum : int {
+  ST_OK = 0, ST_K_RANGE = 2, ST_NONFINITE = 3, ST_CAPACITY = 5, ST_TIMEOUT = 6, ST_INTERNAL = 8, ST_PAIRS_FULL = 9
+};
 
 // Largest magnitude a value may have so that its copy in the filter's
 // storage format (users of BF16 / FP16 indexes, and every query rounded for
@@ -231,6 +236,11 @@ cudaError_t dalloc(rmips_index* idx, T** p, size_t count) {
 }
 
 bool is_device_ptr(const void* p);
+// PTR_HOST, PTR_DEVICE (memory of `device`, or managed) or PTR_OTHER_DEVICE.
+int ptr_class(const void* p, int device);
+// RMIPS_ERR_ARG (with a message naming `what`) when p is device memory of a
+// GPU other than `device`; RMIPS_OK otherwise (also for a null p).
+rmips_status check_ptr_device(const void* p, int device, const char* what);
 
 Workspace* acquire_workspace(rmips_index* idx, rmips_status* st);
 // Batched run on a workspace whose ws->dq / ws->dk (and ws->dseglo/dseghi)
@@ -241,6 +251,9 @@ rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long
                           cudaStream_t st, bool with_segments);
 rmips_status device_status(long long s);
 void release_workspace(rmips_index* idx, Workspace* ws);
+// Loads the module that holds rmips_query_noalloc's scratch array on the
+// current device (called when an index is built or loaded).
+rmips_status noalloc_prepare();
 // Orders this stream after the last asynchronous call that used ws.
 rmips_status ws_join(Workspace* ws, cudaStream_t st);
 void destroy_workspace(Workspace* ws);

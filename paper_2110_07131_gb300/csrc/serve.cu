@@ -225,11 +225,14 @@ void completer(rmips_server* S) {
     lk.unlock();
     const int64_t nq = (int64_t)rs.size();
     rmips_status st = sl.launch;
+    bool one_by_one = false;
     if (st == RMIPS_OK) {
       if (cudaEventSynchronize(sl.done) != cudaSuccess) {
         set_error("batch failed on the device");
         st = RMIPS_ERR_CUDA;
       } else {
+        // a full pair list (ties-heavy batch) is retried one request at a time
+        one_by_one = sl.h_ctr[C_STATUS] == ST_PAIRS_FULL;
         st = device_status(sl.h_ctr[C_STATUS]);
       }
     }
@@ -238,7 +241,7 @@ void completer(rmips_server* S) {
     if (st == RMIPS_OK) {
       for (int64_t i = 0; i < nq; ++i)
         res[i].assign(sl.h_out + sl.h_offs[i], sl.h_out + sl.h_offs[i + 1]);
-    } else if (st == RMIPS_ERR_CAPACITY) {
+    } else if (st == RMIPS_ERR_CAPACITY || one_by_one) {
       for (int64_t i = 0; i < nq; ++i) run_single(S, rs[i], res[i], sts[i]);
     }
     const auto now = Clock::now();
@@ -252,8 +255,15 @@ void completer(rmips_server* S) {
 
 rmips_status check_request(const rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg) {
   if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  // the same range rule as the filter: a value whose copy in the index's
+  // filter format would overflow (FP16: |x| > 65504) is refused here, so that
+  // it cannot fail the other requests of its batch
+  const float vmax = filter_max_abs(idx->precision);
   for (int i = 0; i < idx->d; ++i)
-    if (!std::isfinite(q[i])) { set_error("non-finite value in a query"); return RMIPS_ERR_NONFINITE; }
+    if (!std::isfinite(q[i]) || std::fabs(q[i]) > vmax) {
+      set_error("non-finite value in a query (or, for a BF16 / FP16 index, one beyond that format's range)");
+      return RMIPS_ERR_NONFINITE;
+    }
   if (seg) {
     if (seg->reserved != 0 || seg->kind < 0 || seg->kind > 2) { set_error("bad segment"); return RMIPS_ERR_ARG; }
     if (seg->kind == 1 && (seg->begin < 0 || seg->end < seg->begin)) { set_error("bad segment range"); return RMIPS_ERR_ARG; }
@@ -344,6 +354,10 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
 extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* qs, int64_t nq, const int32_t* ks,
                                                  const rmips_segment* segs, int64_t* tickets) {
   if (!S || nq < 0 || (nq > 0 && (!qs || !ks || !tickets))) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  if (nq > 0 && (ptr_class(qs, S->idx->device) != PTR_HOST || ptr_class(ks, S->idx->device) != PTR_HOST)) {
+    set_error("requests are submitted from host memory");
+    return RMIPS_ERR_ARG;
+  }
   const int d = S->idx->d;
   for (int64_t j = 0; j < nq; ++j) {
     rmips_status st = check_request(S->idx, qs + j * d, ks[j], segs ? &segs[j] : nullptr);
@@ -386,6 +400,7 @@ extern "C" rmips_status rmips_server_submit(rmips_server* S, const float* q, int
 extern "C" rmips_status rmips_server_wait(rmips_server* S, int64_t ticket, int64_t* out_ids, int64_t capacity,
                                           int64_t* out_count, double* latency_ms, int32_t timeout_ms) {
   if (!S || !out_count || capacity < 0 || (capacity > 0 && !out_ids)) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  if (capacity > 0 && check_ptr_device(out_ids, S->idx->device, "out_ids") != RMIPS_OK) return RMIPS_ERR_ARG;
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) { set_error("unknown ticket"); return RMIPS_ERR_ARG; }
@@ -425,6 +440,7 @@ extern "C" rmips_status rmips_server_wait_many(rmips_server* S, const int64_t* t
     set_error("null argument");
     return RMIPS_ERR_ARG;
   }
+  if (capacity > 0 && check_ptr_device(out_ids, S->idx->device, "out_ids") != RMIPS_OK) return RMIPS_ERR_ARG;
   std::unique_lock<std::mutex> lk(S->mu);
   std::vector<Request*> rs(nt);
   for (int64_t i = 0; i < nt; ++i) {

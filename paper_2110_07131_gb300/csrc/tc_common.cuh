@@ -92,11 +92,33 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
 }
 
 // Operand kinds of the tensor-core filter: TF32 from float32 rows, or the
-// index's BF16 / FP16 copy.  Relative error bound of one inner product as a
-// multiple of ||a|| ||b|| (operands rounded to nearest with unit roundoff
-// u_in -- TF32 charged 2^-10 for any rounding --, products exact in float32,
-// accumulation over K = 64 charged 65 * 2^-22) and the absolute error unit of
-// operands below the format's normal range.
+// index's BF16 / FP16 copy.
+//
+// tc_rel_err(kind) bounds |D - a.b| / (||a|| ||b||) for one MMA inner product
+// D of two float32 vectors a, b over K <= 64, derived as follows.
+//  1. Operand rounding: a_i' = a_i (1 + e_i), |e_i| <= u_in, where u_in is the
+//     format's relative rounding error -- TF32 (10 fraction bits) 2^-10, which
+//     covers truncation as well as rounding to nearest, BF16 (7 bits, rounded
+//     to nearest) 2^-8, FP16 (10 bits, rounded to nearest) 2^-11.  So
+//     |a_i' b_i' - a_i b_i| <= (2 u_in + u_in^2) |a_i b_i|.
+//  2. Products: two TF32 / BF16 / FP16 significands have at most 22 bits, so
+//     each a_i' b_i' is exact in float32.
+//  3. Accumulation: a float32 sum of K terms that truncates at every step
+//     errs by at most gamma = K 2^-23 / (1 - K 2^-23) times sum |a_i' b_i'|.
+//     ASSUMPTION: the tensor core's accumulation of an MMA chain (internal
+//     order, internal width, truncation) is within twice that of K + 1
+//     sequential truncating float32 additions: 2 (K + 1) 2^-23 = 65 2^-22 for
+//     K = 64.  Nothing documents the internal accumulation; the adversarial
+//     tiles of the GPU tests check the whole bound, and it is the reason for
+//     the factor 2.
+//  4. sum |a_i' b_i'| <= (1 + u_in)^2 sum |a_i b_i| <= (1 + u_in)^2 ||a|| ||b||.
+// Total: (2 u_in + u_in^2) + 65 2^-22 (1 + u_in)^2, rounded up:
+//   TF32 2^-9 + 2^-20 + 65 2^-22 (1 + 2^-10)^2 = 0.0019696  -> 0.00198
+//   BF16 2^-7 + 2^-16 + 65 2^-22 (1 + 2^-8)^2  = 0.0078436  -> 0.00788
+//   FP16 2^-10 + 2^-22 + 65 2^-22 (1 + 2^-11)^2 = 0.0009923 -> 0.000995
+// tc_abs_unit(kind) is the absolute rounding error of an operand below the
+// format's normal range (FP16 subnormals: 2^-25; BF16 and TF32 share float32's
+// range), which the filter charges separately.
 enum : int { TCK_TF32 = 0, TCK_BF16 = 1, TCK_FP16 = 2 };
 __host__ __device__ constexpr float tc_rel_err(int kind) {
   return kind == TCK_TF32 ? 0.00198f : (kind == TCK_BF16 ? 0.00788f : 0.000995f);

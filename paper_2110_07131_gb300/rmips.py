@@ -128,7 +128,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_profile_enable.argtypes = [VP, I32]
         lib.rmips_profile_read.argtypes = [VP, C.POINTER(Profile)]
         lib.rmips_query_noalloc.argtypes = [VP, P, I32, P, I64, C.POINTER(I64), VP]
-        lib.rmips_debug_tc_tile.argtypes = [P, P, P, I32, I32, I32, VP]
+        lib.rmips_debug_tc_tile.argtypes = [P, P, P, I32, VP]
         lib.rmips_server_create.argtypes = [VP, C.POINTER(ServerOpts), C.POINTER(VP)]
         lib.rmips_server_submit.argtypes = [VP, P, I32, C.POINTER(Segment), C.POINTER(I64)]
         lib.rmips_server_submit_many.argtypes = [VP, P, I64, P, C.POINTER(Segment), P]
@@ -322,12 +322,11 @@ def rmips_query_noalloc(index: Index, q, k: int, out, stream=None) -> int:
     return cnt.value
 
 
-def rmips_debug_tc_tile(A, B, D, kind="tf32", lbo: int = 0, sbo: int = 0, stream=None):
+def rmips_debug_tc_tile(A, B, D, kind="tf32", stream=None):
     """One 128x64x64 tensor-core tile (device tensors): D = A @ B.T in TF32, BF16 or FP16."""
     load_library()
     kid = {"tf32": 0, "bf16": 1, "fp16": 2}[kind]
-    _check(_lib.rmips_debug_tc_tile(A.data_ptr(), B.data_ptr(), D.data_ptr(), kid, int(lbo), int(sbo),
-                                    _stream(stream)))
+    _check(_lib.rmips_debug_tc_tile(A.data_ptr(), B.data_ptr(), D.data_ptr(), kid, _stream(stream)))
 
 
 def rmips_query_batch(index: Index, qs, ks, segments=None, capacity=None, out=None, stream=None):

@@ -437,3 +437,28 @@ def test_no_block_filter_gives_the_same_answers(bs):
         assert np.array_equal(rmips.rmips_query(off, qs[j], int(ks[j])), a[0][a[1][j]:a[1][j + 1]])
     on.close()
     off.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pair_list_overflow_splits_the_pass(monkeypatch, precision):
+    # Ties-heavy data leaves many (user, query) pairs undecided by the O(1)
+    # tests.  With the pair list shrunk to 64 entries a whole-batch pass
+    # overflows it; the call runs the batch again in smaller passes (down to
+    # the per-query path) and must still return the oracle's sets.
+    monkeypatch.setenv("RMIPS_PAIR_LIST_CAP", "64")
+    Q, P = datagen.integer_problem(400, 120, 3, 8, lim=1)
+    qs = np.concatenate([P, Q[:40]])
+    counts = O.counts_greater_multi(Q, P, qs)
+    index = rmips.rmips_build_index(Q, P, k_max=12, precision=precision)
+    for k in (1, 4, 12):
+        ids, offs = rmips.rmips_query_batch(index, qs, np.full(len(qs), k, np.int32))
+        for j in range(len(qs)):
+            assert np.array_equal(ids[offs[j]:offs[j + 1]], np.nonzero(counts[j] < k)[0]), (k, j)
+    # with the default list, one pass of the same batch holds more than 64
+    # undecided pairs: the small list really overflowed above
+    monkeypatch.delenv("RMIPS_PAIR_LIST_CAP")
+    big = rmips.rmips_build_index(Q, P, k_max=12, precision=precision)
+    rmips.rmips_query_batch(big, qs, np.full(len(qs), 12, np.int32))
+    assert rmips.rmips_last_query_stats(big)["todo"] > 64
+    big.close()
+    index.close()

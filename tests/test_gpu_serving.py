@@ -119,3 +119,31 @@ def test_small_result_budget_falls_back_per_request(setup):
         srv.wait(12345678)
     assert e.value.status == 1
     srv.close()
+
+
+def test_fp16_out_of_range_request_is_refused_alone():
+    # On an FP16 index a query value beyond 65504 has no FP16 copy.  The
+    # server refuses that request at submission, so the requests it would
+    # have been batched with still complete with their exact answers.
+    Q, P = datagen.make_problem(2000, 1000, 50, 11)
+    index = rmips.rmips_build_index(Q, P, k_max=25, precision="fp16")
+    srv = rmips.Server(index, max_batch=64, max_wait_us=20000, streams=1)
+    qs, _ = datagen.queries_from_items(P, 12, 11)
+    good = [srv.submit(qs[j], 10) for j in range(6)]
+    bad = qs[6].copy()
+    bad[3] = np.float32(70000.0)
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit(bad, 10)
+    assert e.value.status == 3
+    with pytest.raises(rmips.RmipsError) as e:           # all or none: nothing of this call is queued
+        srv.submit_many(np.stack([qs[7], bad]), 10)
+    assert e.value.status == 3
+    good += [srv.submit(qs[j], 10) for j in range(8, 12)]
+    counts = O.counts_greater_multi(Q, P, np.concatenate([qs[:6], qs[8:12]]))
+    for j, t in enumerate(good):
+        ids, _ = srv.wait(t)
+        assert np.array_equal(ids, np.nonzero(counts[j] < 10)[0]), j
+    st = srv.stats()
+    assert st["completed"] == 10 and st["pending"] == 0
+    srv.close()
+    index.close()

@@ -330,3 +330,62 @@ def test_topk_mips_agrees_with_reverse_kmips_without_ties():
         for j in range(P.shape[0]):
             users = set(O.reverse_kmips(Q, P, P[j], k).tolist())
             assert users == {i for i in range(Q.shape[0]) if j in top[i]}
+
+
+# ---------------------------------------------------------------------------
+# kth_values: the j-th largest u.p (Definition 1's ranks, which Algorithm 1's
+# lower-bound array L holds), against a rational sort written here
+# ---------------------------------------------------------------------------
+def _rational_kth(Q, P, k_max):
+    """Exact j-th largest u.p per user (rational sort), None past |P|."""
+    out = []
+    for u in Q:
+        vals = sorted((_fdot(u, p) for p in P), reverse=True)
+        out.append([vals[j] if j < len(vals) else None for j in range(k_max)])
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_kth_values_integer_ties_are_exact(seed):
+    # small-integer vectors: every float64 product sum is exact, and equal
+    # products are frequent, so the j-th value must equal the rational one
+    Q, P = datagen.integer_problem(12, 15, 6, seed, lim=2)
+    got = O.kth_values(Q, P, 9)
+    exp = _rational_kth(Q, P, 9)
+    for i in range(Q.shape[0]):
+        for j in range(9):
+            assert Fraction(got[i, j]) == exp[i][j], (i, j)
+    # the ranks are descending and ties repeat the same value
+    assert np.all(np.diff(got, axis=1) <= 0)
+    assert any(got[i, j] == got[i, j + 1] for i in range(12) for j in range(8))
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_kth_values_mf_within_float64_bound(seed):
+    Q, P = datagen.make_problem(10, 40, 50, seed)
+    k_max = 25
+    got = O.kth_values(Q, P, k_max)
+    exp = _rational_kth(Q, P, k_max)
+    d = Q.shape[1]
+    gam = d * 2.0 ** -53 / (1 - d * 2.0 ** -53)
+    for i in range(Q.shape[0]):
+        # a float64 sum of exact float32 products is within gam * sum|u_i p_i|
+        # of the exact value, so each order statistic moves by at most the
+        # largest such error over the items
+        tol = gam * float(np.max(np.abs(Q[i].astype(np.float64)) @ np.abs(P.astype(np.float64)).T))
+        for j in range(k_max):
+            assert abs(Fraction(got[i, j]) - exp[i][j]) <= Fraction(tol), (i, j)
+    # an off-by-one in the rank would move every entry by a whole gap
+    gaps = [float(exp[0][j] - exp[0][j + 1]) for j in range(k_max - 1)]
+    assert min(gaps) > 1e3 * gam
+
+
+def test_kth_values_pad_with_minus_inf_past_the_item_count():
+    Q, P = datagen.make_problem(6, 4, 8, 5)
+    got = O.kth_values(Q, P, 7)
+    exp = _rational_kth(Q, P, 7)
+    assert got.shape == (6, 7)
+    assert np.all(np.isneginf(got[:, 4:]))
+    for i in range(6):
+        for j in range(4):
+            assert abs(Fraction(got[i, j]) - exp[i][j]) < Fraction(1, 10 ** 9)
