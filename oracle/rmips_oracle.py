@@ -40,7 +40,8 @@ import numpy as np
 __all__ = [
     "norms_fp64", "norm_order", "exact_dot", "exact_sign_diff",
     "counts_greater", "counts_greater_multi", "reverse_kmips", "reverse_kmips_multi",
-    "decide_users", "build_index", "linear_scan", "simpfer_query", "kth_values", "topk_mips",
+    "decide_users", "decide_users_multi", "build_index", "linear_scan", "simpfer_query", "kth_values",
+    "topk_mips",
 ]
 
 _U64 = 2.0 ** -53
@@ -177,6 +178,82 @@ def decide_users(Q, P, q, k: int, users) -> np.ndarray:
     users = np.asarray(users, dtype=np.int64)
     c = counts_greater(np.asarray(Q)[users], P, q)
     return c < k
+
+
+def decide_users_multi(Q, P, qs, ks, users, threads: int = 8, chunk: int = 512) -> np.ndarray:
+    """Yes/no of Definition 2 for every (query j, listed user), many queries at once.
+
+    Uses the identity ``c(u) < k  <=>  v_k(u) <= u.q`` where ``v_k(u)`` is the
+    k-th largest ``u.p`` over P (counted with multiplicity): if the k-th
+    largest product is at most ``u.q``, only the k-1 above it can be strictly
+    above ``u.q``; if it is larger, the k largest all are.  Each listed user's
+    products with all of P are formed once in float64 and its K = max(ks)
+    largest are kept, so every query is decided from them:
+
+    * ``t_k > u.q + E`` (E covers the float64 error of both sides): no;
+    * ``t_k < u.q - E``: yes;
+    * otherwise the items whose product may reach ``u.q`` are compared with q
+      exactly (rational arithmetic), reading the user's whole row again when
+      they do not all lie among the K kept.
+
+    Returns a bool array ``[len(qs), len(users)]``.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+    Q = np.asarray(Q, dtype=np.float32)
+    P = np.asarray(P, dtype=np.float32)
+    qs = np.atleast_2d(np.asarray(qs, dtype=np.float32))
+    users = np.asarray(users, dtype=np.int64)
+    nq, m, d = qs.shape[0], P.shape[0], P.shape[1]
+    ks = np.broadcast_to(np.asarray(ks, dtype=np.int64), (nq,))
+    K = int(min(m, ks.max()))
+    P64 = P.astype(np.float64)
+    q64 = qs.astype(np.float64)
+    G = _fp64_bound(d)
+    pmax = float(norms_fp64(P).max()) * (1 + 1e-12)
+    out = np.zeros((nq, users.shape[0]), dtype=bool)
+
+    def top(rows):
+        S = rows @ P64.T                                  # [r, m]
+        if K >= m:
+            idx = np.broadcast_to(np.arange(m), S.shape)
+        else:
+            idx = np.argpartition(S, m - K, axis=1)[:, m - K:]
+        val = np.take_along_axis(S, idx, axis=1)
+        order = np.argsort(-val, axis=1, kind="stable")
+        return np.take_along_axis(val, order, axis=1), np.take_along_axis(np.asarray(idx), order, axis=1)
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        for c0 in range(0, users.shape[0], chunk):
+            ids = users[c0:c0 + chunk]
+            U = Q[ids]
+            U64 = U.astype(np.float64)
+            parts = np.array_split(np.arange(ids.shape[0]), max(1, min(threads, ids.shape[0])))
+            res = list(ex.map(lambda r: top(U64[r]), parts))
+            tv = np.concatenate([r[0] for r in res])      # [r, K] descending float64 products
+            ti = np.concatenate([r[1] for r in res])      # their items
+            gam = U64 @ q64.T                             # [r, nq] u.q
+            agam = np.abs(U64) @ np.abs(q64).T
+            unorm = norms_fp64(U) * (1 + 1e-12)
+            for j in range(nq):
+                k = int(ks[j])
+                if k > m:                                 # fewer than k items exist: always yes
+                    out[j, c0:c0 + ids.shape[0]] = True
+                    continue
+                E = G * (agam[:, j] + unorm * pmax)       # float64 error of u.q plus that of any u.p
+                tk = tv[:, k - 1]
+                no = tk > gam[:, j] + E
+                yes = tk < gam[:, j] - E
+                out[j, c0:c0 + ids.shape[0]] = yes
+                for r in np.nonzero(~(no | yes))[0].tolist():
+                    lo = gam[r, j] - E[r]
+                    if K < m and tv[r, K - 1] >= lo:      # the band reaches past the kept items
+                        row = P64 @ U64[r]
+                        cand = np.nonzero(row >= lo)[0]
+                    else:
+                        cand = ti[r][tv[r] >= lo]
+                    above = sum(1 for p in cand.tolist() if exact_sign_diff(U[r], P[p], qs[j]) > 0)
+                    out[j, c0 + r] = above < k
+    return out
 
 
 def kth_values(Q, P, k_max: int) -> np.ndarray:

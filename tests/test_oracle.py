@@ -389,3 +389,33 @@ def test_kth_values_pad_with_minus_inf_past_the_item_count():
     for i in range(6):
         for j in range(4):
             assert abs(Fraction(got[i, j]) - exp[i][j]) < Fraction(1, 10 ** 9)
+
+
+# ---------------------------------------------------------------------------
+# decide_users_multi (the k-th-largest form of Definition 2, many queries)
+# against the counting form
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("chunk", [7, 512])
+def test_decide_users_multi_equals_counting_mf(chunk):
+    Q, P = datagen.make_problem(600, 300, 50, 4)
+    qs, _ = datagen.queries_from_items(P, 8, 4)
+    qs = np.concatenate([qs, datagen.random_queries(3, 50, 4), np.zeros((1, 50), np.float32)])
+    counts = O.counts_greater_multi(Q, P, qs)
+    users = np.random.default_rng(0).choice(600, 250, replace=False)
+    for ks in (1, 10, 25, np.arange(1, 13)):
+        kk = np.broadcast_to(np.asarray(ks), (len(qs),))
+        got = O.decide_users_multi(Q, P, qs, kk, users, threads=3, chunk=chunk)
+        exp = counts[:, users] < kk[:, None]
+        assert np.array_equal(got, exp), ks
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_decide_users_multi_equals_counting_integer_ties(seed):
+    # many exact ties at the k-th value: the exact band path decides them
+    Q, P = datagen.integer_problem(200, 60, 4, seed, lim=2)
+    qs = np.concatenate([P[:10], Q[:3]])
+    counts = O.counts_greater_multi(Q, P, qs)
+    users = np.arange(200)
+    for k in (1, 2, 5, 12, 60, 61):
+        got = O.decide_users_multi(Q, P, qs, k, users, threads=2, chunk=64)
+        assert np.array_equal(got, counts < k), k
