@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=60000, help="requests per serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=1.0e6, help="offered load of the paced serving run (q/s)")
+    ap.add_argument("--single-queries", type=int, default=2000,
+                    help="device-resident single queries launched back to back (0: skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the variants, the precision workload, the error report and the CPU Simpfer")
     return ap.parse_args()
 
 
@@ -272,6 +276,152 @@ def run_serving(rmips, index, qs, a):
     return out
 
 
+# --------------------------------------------------------------------------- extras
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def simpfer_cpu_baseline(Q, P, qs, k, k_max, seconds=10.0):
+    """The CPU Simpfer (Algorithms 1-3 in float64 with exact ties, OpenMP over
+    blocks, |P'| = 4 k_max) on all host cores and on one core: queries/s."""
+    from oracle import simpfer_cpu as S
+    t0 = time.perf_counter()
+    idx = S.SimpferCPU(Q, P, k_max=k_max, p_prime=4 * k_max, threads=0)
+    build_s = time.perf_counter() - t0
+    out = {"kind": "cpu simpfer (Algorithm 3 with Algorithm 2, float64, exact ties)", "p_prime": 4 * k_max,
+           "index_build_s": build_s, "cpu_model": cpu_model(), "openmp": bool(S.OPENMP)}
+    for label, threads in (("all_cores", 0), ("one_core", 1)):
+        n_done, t0 = 0, time.perf_counter()
+        while n_done < len(qs) and (time.perf_counter() - t0 < seconds / 2 or n_done < 3):
+            idx.query(qs[n_done], k, threads=threads)
+            n_done += 1
+        el = time.perf_counter() - t0
+        out[label] = {"value": n_done / el, "unit": "queries/s", "queries": n_done,
+                      "cores": S.max_threads() if threads == 0 else 1, "ms_per_query": 1e3 * el / n_done}
+    idx.close()
+    return out
+
+
+def ip_error_report(Q, qs, d, rmips, torch, dev):
+    """Largest error of the tensor-core inner products against float64 on
+    tiles of the workload: the 128 largest-norm users and 128 random users
+    against 64 of the queries, each padded to K = 64, per operand kind."""
+    bound = {"tf32": 0.00198, "bf16": 0.00788, "fp16": 0.000995}
+    un = np.linalg.norm(Q.astype(np.float64), axis=1)
+    rng = np.random.default_rng(0)
+    rep = {}
+    for kind in ("tf32", "bf16", "fp16"):
+        worst_rel, worst_abs = 0.0, 0.0
+        for users in (np.argsort(-un)[:128], rng.choice(Q.shape[0], 128, replace=False)):
+            for q0 in range(0, min(len(qs), 256), 64):
+                A = np.zeros((128, 64), np.float32)
+                B = np.zeros((64, 64), np.float32)
+                A[:, :d] = Q[users]
+                B[:min(64, len(qs) - q0), :d] = qs[q0:q0 + 64]
+                dD = torch.zeros((128, 64), dtype=torch.float32, device=dev)
+                rmips.rmips_debug_tc_tile(torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev), dD, kind=kind)
+                ref = A.astype(np.float64) @ B.astype(np.float64).T
+                nrm = np.linalg.norm(A.astype(np.float64), axis=1)[:, None] * np.linalg.norm(B.astype(np.float64), axis=1)
+                err = np.abs(dD.cpu().numpy().astype(np.float64) - ref)
+                ok = nrm > 0
+                worst_abs = max(worst_abs, float(err.max()))
+                worst_rel = max(worst_rel, float((err[ok] / nrm[ok]).max()))
+        rep[kind] = {"max_abs_ip_err": worst_abs, "max_rel_ip_err": worst_rel, "rel_bound": bound[kind],
+                     "rel_err_over_bound": worst_rel / bound[kind]}
+    rep["note"] = ("relative to ||u|| ||q||; the filter charges every product its bound and rechecks any "
+                   "decision within it exactly, so the sets stay exact")
+    return rep
+
+
+def time_async_batches(rmips, torch, index, dqs, dks, nq, steps, dev, first=0):
+    """Queries/s of `steps` asynchronous batches on two streams (after two warm-up batches)."""
+    streams = [torch.cuda.current_stream(dev), torch.cuda.Stream(dev)]
+    cap = max(1 << 20, nq * 2048)
+    outs = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(2)]
+    offs = torch.empty((steps + 2, nq + 1), dtype=torch.int64, device=dev)
+    done = torch.full((steps + 2, 2), -1, dtype=torch.int64, device=dev)
+    nb = dqs.shape[0] // nq
+
+    def run(i0, cnt):
+        for i in range(cnt):
+            b = (first + i0 + i) % nb
+            rmips.rmips_query_batch_async(index, dqs[b * nq:(b + 1) * nq], dks[:nq], outs[i & 1], offs[i0 + i],
+                                          done[i0 + i], streams[i & 1])
+    run(0, 2)
+    torch.cuda.synchronize(dev)
+    ev0, ev1, side = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), torch.cuda.Event()
+    ev0.record(streams[0])
+    streams[1].wait_event(ev0)
+    run(2, steps)
+    side.record(streams[1])
+    streams[0].wait_event(side)
+    ev1.record(streams[0])
+    torch.cuda.synchronize(dev)
+    d = done.cpu().numpy()
+    if (d[:, 0] != 0).any():
+        raise RuntimeError(f"batch status {d[:, 0].tolist()}")
+    ms = ev0.elapsed_time(ev1)
+    return steps * nq / (ms / 1e3), ms / steps, int(d[2:, 1].sum())
+
+
+def variants_report(a, Q, P, qs, rmips, torch, dev):
+    """The batched step on other indexes of the same workload: the paper's
+    "without blocks" ablation, other block sizes and the BF16 / FP16 filter."""
+    out = {}
+    dqs = torch.from_numpy(qs).to(dev)
+    dks = torch.full((a.nq,), a.k, dtype=torch.int32, device=dev)
+    specs = [("blocks_32_tf32", dict()), ("no_blocks", dict(block_filter=False)),
+             ("blocks_64", dict(block_size=64)), ("blocks_128", dict(block_size=128)),
+             ("blocks_256", dict(block_size=256)), ("bf16_filter", dict(precision="bf16")),
+             ("fp16_filter", dict(precision="fp16"))]
+    for name, kw in specs:
+        index = rmips.rmips_build_index(Q, P, k_max=a.k_max, **kw)
+        rmips.rmips_profile_enable(index, True)
+        qps, ms, ids = time_async_batches(rmips, torch, index, dqs, dks, a.nq, 4, dev)
+        prof = rmips.rmips_profile_read(index)
+        rmips.rmips_profile_enable(index, False)
+        ml = max(1, prof["mfilter_launches"])
+        out[name] = {"queries_per_s": qps, "ms_per_batch": ms, "filter_ms": prof["mfilter_ms"] / ml,
+                     "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (ml * a.nq),
+                     "results_per_query": ids / (4 * a.nq)}
+        index.close()
+    base = out["blocks_32_tf32"]["queries_per_s"]
+    out["blocks_speedup_over_no_blocks"] = base / out["no_blocks"]["queries_per_s"]
+    out["config"] = (f"{a.nq} queries per batch, k = {a.k}, 4 timed batches after 2 warm-up batches on two "
+                     "streams; the paper reports 1.1-3.8x for blocks on its CPU")
+    return out
+
+
+def precision_workload(rmips, torch, dev, steps=3):
+    """The precision workload at its stated size: |Q| = 500k, |P| = 100k,
+    d = 64, k = 10, 2,000 item + 2,000 random queries in one batch, per
+    filter precision, with the tiles' inner-product error."""
+    n, m, d, k, seed = 500_000, 100_000, 64, 10, 2
+    Q, P = datagen.make_problem(n, m, d, seed)
+    qi, _ = datagen.queries_from_items(P, 2000, seed)
+    qs = np.concatenate([qi, datagen.random_queries(2000, d, seed)])
+    dqs = torch.from_numpy(qs).to(dev)
+    dks = torch.full((len(qs),), k, dtype=torch.int32, device=dev)
+    out = {"workload": f"reverse k-MIPS |Q|={n} |P|={m} d={d} k={k}, 2,000 item + 2,000 random queries per batch"}
+    for prec in ("fp32", "bf16", "fp16"):
+        index = rmips.rmips_build_index(Q, P, k_max=25, precision=prec)
+        qps, ms, ids = time_async_batches(rmips, torch, index, dqs, dks, len(qs), steps, dev)
+        ids_h, offs = rmips.rmips_query_batch(index, qs, np.full(len(qs), k, np.int32))
+        st = rmips.rmips_last_query_stats(index)
+        out[prec] = {"queries_per_s": qps, "ms_per_batch": ms, "results": int(offs[-1]),
+                     "pairs_rechecked": st["todo"], "exact_integer_decisions": st["exact_calls"]}
+        index.close()
+    out["ip_error"] = ip_error_report(Q, qs, d, rmips, torch, dev)
+    return out
+
+
 # --------------------------------------------------------------------------- GPU arm
 def run_ours(a):
     import torch
@@ -422,12 +572,38 @@ def run_ours(a):
         join_s = time.perf_counter() - t0
         del jout
 
-    # single-query filter timing (HBM-bound kernel), profiled separately from the latency run
-    rmips.rmips_profile_enable(index, True)
-    for j in range(min(200, a.plain_queries)):
-        rmips.rmips_query(index, qs[j], a.k)
-    sprof = rmips.rmips_profile_read(index)
-    rmips.rmips_profile_enable(index, False)
+    # single queries, one launch each, device-resident: a.single_queries
+    # launches queued back to back on one stream (no host round trip between
+    # them), CUDA events around the sequence; the per-launch filter time for
+    # the roofline comes from the event pairs the library records around each
+    # launch, which back to back span the kernel and its launch gap only
+    single = None
+    sprof = {"filter_launches": 0, "filter_alg_bytes": 0.0, "filter_ms": 0.0, "users_tested": 0,
+             "blocks_pruned": 0, "blocks_total": 1}
+    if a.single_queries > 0:
+        ns1 = min(a.single_queries, dqs.shape[0])
+        sout = torch.empty((2, max(1 << 16, a.n // 8)), dtype=torch.int64, device=dev)
+        sdone = torch.full((ns1, 2), -1, dtype=torch.int64, device=dev)
+        for j in range(20):                                    # warm-up (both workspaces)
+            rmips.rmips_query_async(index, dqs[j], a.k, sout[j & 1], sdone[j], stream=stream)
+        torch.cuda.synchronize(dev)
+        rmips.rmips_profile_enable(index, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(ns1):
+            rmips.rmips_query_async(index, dqs[j], a.k, sout[j & 1], sdone[j], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sprof = rmips.rmips_profile_read(index)
+        rmips.rmips_profile_enable(index, False)
+        sd = sdone.cpu().numpy()
+        if (sd[:, 0] != 0).any():
+            raise RuntimeError(f"single query status {sorted(set(sd[:, 0].tolist()))}")
+        s_total_ms = e0.elapsed_time(e1)
+        single = {"qps": ns1 / (s_total_ms / 1e3), "us_per_query": 1e3 * s_total_ms / ns1, "queries": ns1,
+                  "results_per_query": float(sd[:, 1].mean()),
+                  "api": "rmips_query_async (one k_query1 launch per query), device q and ids, launches queued "
+                         "back to back on one stream"}
 
     peaks = {}
     try:
@@ -440,12 +616,16 @@ def run_ours(a):
     s_bytes = sprof["filter_alg_bytes"] / sl
     s_ms = sprof["filter_ms"] / sl
     s_ach = s_bytes / (s_ms / 1e3) / 1e9 if s_ms > 0 else 0.0
-    roof_single = {"bound": "hbm", "kernel": "k_query1 (one launch per query: Lemmas 1-3 with TMA-staged rows, "
-                                             "then exact recheck and emit in the last CTA)",
+    roof_single = {"bound": "hbm", "kernel": "k_query1 (one launch per query, one CTA per SM: a producer warp "
+                                             "tests Lemma 3 for 32 spans at once and bulk-copies each run of kept "
+                                             "32-user chunks; 8 consumer warps apply Lemmas 1/2 and recheck exactly; "
+                                             "the last CTA emits)",
                    "achieved": s_ach, "peak": hbm, "unit": "GB/s", "frac": s_ach / hbm, "peak_source": peak_src,
                    "traffic": None, "alg_bytes_per_launch": s_bytes, "avg_launch_us": s_ms * 1e3,
+                   "launches": sprof["filter_launches"],
                    "users_tested_per_query": sprof["users_tested"] / sl,
-                   "alpha_blocks_pruned": sprof["blocks_pruned"] / max(1, sprof["blocks_total"])}
+                   "alpha_blocks_pruned": sprof["blocks_pruned"] / max(1, sprof["blocks_total"]),
+                   "timing": "back-to-back device-resident launches (rmips_query_async), CUDA events per launch"}
     # FP32 FMA peak from unit counts and clock: SMs x 128 lanes x 2 flop x clock
     import torch as _t
     sms = _t.cuda.get_device_properties(dev).multi_processor_count
@@ -509,7 +689,7 @@ def run_ours(a):
             "pipelining": f"each step one asynchronous batch call; batches queued on 2 CUDA streams in turn, "
                           f"each with its own workspace (independent batches overlap); {n_warm} untimed "
                           f"warm-up batches",
-            "roofline_single_query_filter": roof_single,
+            "roofline_single_query_filter": roof_single, "single_query_device": single,
             "p50_ms": plain["p50_ms"], "p99_ms": plain["p99_ms"], "plain": plain, "serving": serving,
             "batch_latency_ms": ms_max / a.steps,
             "index_build_s": build_s, "index_device_bytes": info["device_bytes"],
@@ -520,15 +700,24 @@ def run_ours(a):
             "pairs_kept_by_lemma3_per_query": prof["mfilter_pairs"] / (a.steps * a.nq),
             "last_step": {"pairs_decided_yes_in_o1": qstats["yes_fast"], "pairs_rechecked": qstats["todo"],
                           "exact_integer_decisions": qstats["exact_calls"], "results": qstats["result"]}}
+    if rank == 0 and world == 1 and not a.no_extras:
+        line["ip_error"] = ip_error_report(Q, qs[:256], a.d, rmips, torch, dev)
+        index.close()
+        index = None
+        line["variants"] = variants_report(a, Q, P, qs[:4 * a.nq], rmips, torch, dev)
+        line["precision_workload"] = precision_workload(rmips, torch, dev)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         rng = np.random.default_rng(1)
         qps, s, t, cores = oracle_sample(Q, P, qs[0], a.k, a.cpu_seconds, rng)
         line["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one query, {s} random users decided over all {a.m} items "
                                           f"in float64 numpy ({t:.1f} s), scaled to queries/s"}
+        if not a.no_extras:
+            line["cpu_baseline_simpfer"] = simpfer_cpu_baseline(Q, P, qs[:400], a.k, a.k_max)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    index.close()
+    if index is not None:
+        index.close()
     if dist:
         dist.destroy_process_group()
 

@@ -196,6 +196,27 @@ rmips_status rmips_query_batch_async(rmips_index* index, const float* qs, int64_
                                      int64_t* done, void* stream);
 
 /*
+ * rmips_query_async -- rmips_query (Algorithm 3, Section 4.3, for one query)
+ * for device-resident buffers, without waiting for the GPU.
+ *
+ * q [d] float32, out_ids [capacity] int64 and done [2] int64 are DEVICE
+ * pointers of the index's GPU; no segment.  The work is queued on `stream`
+ * (for a full-P index one kernel launch) and the call returns.  When the
+ * stream passes it, out_ids holds the ascending result ids, done[0] an
+ * rmips_status (RMIPS_OK, RMIPS_ERR_NONFINITE, RMIPS_ERR_CAPACITY with
+ * out_ids unspecified, RMIPS_ERR_TIMEOUT, RMIPS_ERR_INTERNAL) and done[1] the
+ * result size (the size needed on RMIPS_ERR_CAPACITY).  The returned status
+ * covers only what the host can check.  The buffers must stay valid until the
+ * stream has passed the call.  Workspaces are taken as for
+ * rmips_query_batch_async, so calls queued back to back run one after the
+ * other on their stream without host round trips.  Filter timing reaches the
+ * profile when rmips_profile_read is called; rmips_last_query_stats is not
+ * updated.
+ */
+rmips_status rmips_query_async(rmips_index* index, const float* q, int32_t k, int64_t* out_ids, int64_t capacity,
+                               int64_t* done, void* stream);
+
+/*
  * Index persistence.  rmips_index_save writes the index (sizes, options and
  * every device array) to a host file; rmips_index_load reads it back onto the
  * current device, answering exactly as the index that was saved.  The file

@@ -57,6 +57,7 @@ void destroy_workspace(Workspace* ws) {
   cudaFreeHost(ws->h_out);
   cudaFreeHost(ws->h_q);
   cudaFreeHost(ws->h_res);
+  cudaFree(ws->dres);
   for (cudaEvent_t e : ws->ev) cudaEventDestroy(e);
   cudaFree(ws->bq);
   cudaFree(ws->bk);
@@ -262,8 +263,11 @@ extern "C" void rmips_free_index(rmips_index* idx) {
   cudaFree(idx->cand);
   cudaFree(idx->cbnd);
   cudaFree(idx->dprof);
+  cudaFree(idx->dprof1);
   for (cudaEvent_t e : idx->pend_ev) cudaEventDestroy(e);
   idx->pend_ev.clear();
+  for (cudaEvent_t e : idx->pend_ev1) cudaEventDestroy(e);
+  idx->pend_ev1.clear();
   cudaFree(idx->incomp);
   cudaFree(idx->LB);
   cudaFree(idx->hdr);
@@ -290,9 +294,16 @@ extern "C" rmips_status rmips_profile_enable(rmips_index* idx, int32_t enable) {
     cudaEventDestroy(e);
   }
   idx->pend_ev.clear();
+  for (cudaEvent_t e : idx->pend_ev1) {
+    cudaEventSynchronize(e);
+    cudaEventDestroy(e);
+  }
+  idx->pend_ev1.clear();
   cudaError_t e = cudaSuccess;
   if (!idx->dprof) e = cudaMalloc((void**)&idx->dprof, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(idx->dprof, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess && !idx->dprof1) e = cudaMalloc((void**)&idx->dprof1, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(idx->dprof1, 0, 4 * sizeof(unsigned long long));
   if (prev != idx->device) cudaSetDevice(prev);
   if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return RMIPS_ERR_CUDA; }
   return RMIPS_OK;
@@ -322,6 +333,26 @@ extern "C" rmips_status rmips_profile_read(const rmips_index* idx, rmips_profile
     m->prof.mfilter_pairs += (int64_t)pairs;
     m->prof.mfilter_alg_flops += 2.0 * m->d * (double)pairs;
     cudaMemset(m->dprof, 0, sizeof(unsigned long long));
+  }
+  // asynchronous single queries: event pairs and the device counters
+  for (size_t i = 0; i + 1 < m->pend_ev1.size(); i += 2) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(m->pend_ev1[i + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, m->pend_ev1[i], m->pend_ev1[i + 1]) == cudaSuccess)
+      m->prof.filter_ms += ms;
+  }
+  for (cudaEvent_t e : m->pend_ev1) cudaEventDestroy(e);
+  m->pend_ev1.clear();
+  unsigned long long acc[4] = {0, 0, 0, 0};
+  if (m->dprof1 && cudaMemcpy(acc, m->dprof1, sizeof(acc), cudaMemcpyDeviceToHost) == cudaSuccess && acc[3]) {
+    const int es = m->precision == RMIPS_FP32 ? 4 : 2;
+    m->prof.filter_launches += (int64_t)acc[3];
+    m->prof.filter_alg_bytes += 8.0 * m->nb * (double)acc[3] + ((double)m->d * es + 8.0) * (double)acc[0] +
+                                4.0 * (double)acc[1];
+    m->prof.users_tested += (int64_t)acc[0];
+    m->prof.blocks_pruned += (int64_t)acc[2] * 32 / m->bs;
+    m->prof.blocks_total += m->nb * (int64_t)acc[3];
+    cudaMemset(m->dprof1, 0, sizeof(acc));
   }
   *out = m->prof;
   if (prev != m->device) cudaSetDevice(prev);

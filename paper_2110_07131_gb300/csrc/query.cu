@@ -569,33 +569,254 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
   }
 }
 
+// Public status code of a device status word (asynchronous calls write it).
+__device__ __forceinline__ int status_code(long long s) {
+  return s == ST_OK ? RMIPS_OK
+       : s == ST_NONFINITE ? RMIPS_ERR_NONFINITE
+       : s == ST_CAPACITY ? RMIPS_ERR_CAPACITY
+       : s == ST_TIMEOUT ? RMIPS_ERR_TIMEOUT
+       : s == ST_K_RANGE ? RMIPS_ERR_K_RANGE
+       : s == ST_PAIRS_FULL ? RMIPS_ERR_OOM : RMIPS_ERR_INTERNAL;
+}
+
 // --- one launch per query (full-P index) ---------------------------------------------
-// Every CTA forms ||q|| itself and runs the filter on its chunks; the last CTA
-// to finish (a device-wide counter taken after a memory fence, nothing waits)
-// rechecks the undecided users, sorts and writes the ids, copies the status,
-// count and counters to `res` (device-visible host memory) and clears the
-// counters for the next call.
+// One CTA per SM.  The users are cut into spans of Q1_SPAN chunks of 32 rows
+// (256 users); CTA c owns spans c, c + G, c + 2G, ... (G CTAs).  Warp
+// Q1_WARPS is the producer: for 32 of its spans at a time (one per lane) it
+// tests Lemma 3 for every block of the span, and for each span that keeps a
+// chunk it takes a shared-memory stage, publishes (span, chunk mask), and
+// copies every run of consecutive kept chunks with ONE bulk copy (a 1-D
+// cp.async.bulk occupies the SM's copy engine for about the same time up to
+// 64 KB, so a whole 51 KB span of float32 rows costs one copy, not eight).
+// Consumer warp w handles chunk w of each stage: it prefetches its users'
+// (lo_k, hi_k) while the rows land, forms u.q with its error bound (Lemma 1:
+// no if u.q + e < lo_k; yes if u.q - e >= hi_k), rechecks undecided users
+// exactly on the spot (one warp per user over its proven candidates), and
+// frees the stage.  Stages are joined by mbarriers: full (the rows landed),
+// info (span and mask published), empty (all consumers done).  Every wait is
+// bounded; a CTA that gives up drains its own copies before it exits.
+// The last CTA to finish (a device-wide counter taken after a memory fence)
+// sorts and writes the ids, copies the status, count and counters to `res`
+// (and status and count to `done` when given) and clears the counters.
 constexpr int RES_STATUS = 0, RES_COUNT = 1, RES_CTR = 2;     // res layout: [2 + C_NCOUNTERS]
+constexpr int Q1_WARPS = 8;                                    // consumer warps = chunks per span
+constexpr int Q1_THREADS = (Q1_WARPS + 1) * 32;
+constexpr int Q1_MAXNS = 6;                                    // stages at most
+constexpr size_t Q1_HEAD = 1024;                               // q, barriers, stage info
+
+__host__ __device__ inline size_t q1_stage_bytes(int d, int es) { return (size_t)Q1_WARPS * 32 * d * es; }
 
 template <class T>
-__global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const float* q_src, int k, int precision,
-                                                     long long* res) {
+__global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, const float* q_src, int k,
+                                                          int precision, int ns, long long* res, long long* done,
+                                                          unsigned long long* pacc) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float* sq = reinterpret_cast<float*>(smem);                        // [RMIPS_DMAX]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 512);          // [FW][2]
-  unsigned char* bufs = smem + 512 + FW * 2 * 8;                     // TMA buffers, later sort keys
+  float* sq = reinterpret_cast<float*>(smem);                             // [RMIPS_DMAX]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 512);               // [Q1_MAXNS]
+  uint64_t* info = full + Q1_MAXNS;                                       // [Q1_MAXNS]
+  uint64_t* empty = info + Q1_MAXNS;                                      // [Q1_MAXNS]
+  int2* sinfo = reinterpret_cast<int2*>(smem + 512 + 3 * Q1_MAXNS * 8);   // [Q1_MAXNS] (span, mask)
+  unsigned char* stages = smem + Q1_HEAD;                                 // ns x stage, later sort keys
   __shared__ float s_qn, s_eps;
-  __shared__ int s_fin, s_last;
+  __shared__ int s_fin, s_last, s_abort;
+  __shared__ int s_fills[Q1_MAXNS];         // phases completed on full[s] by the producer
   __shared__ int s_warp[32];
   __shared__ long long s_total;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = c.d;
+  const int64_t n = c.n;
+  const uint32_t chunk_bytes = 32u * d * (uint32_t)sizeof(T);             // multiple of 16
+  const size_t stage_bytes = (size_t)Q1_WARPS * chunk_bytes;
+  const int64_t nchunks = (n + 31) / 32;
+  const int64_t nspans = (nchunks + Q1_WARPS - 1) / Q1_WARPS;
   for (int i = tid; i < d; i += blockDim.x) sq[i] = q_src[i];
-  init_filter_barriers(bars);
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&info[s], 1);
+      mbar_init(&empty[s], Q1_WARPS);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+    for (int s = 0; s < Q1_MAXNS; ++s) s_fills[s] = 0;
+  }
   __syncthreads();
   if (tid == 0) s_fin = query_bounds(sq, d, precision, &s_qn, &s_eps) ? 1 : 0;
   __syncthreads();
-  if (s_fin) filter_chunks<T, true, true>(c, sq, k, s_qn, s_eps, bars, bufs);
+  const float qn = s_qn, qeps = s_eps;
+  const float2* Lbk = c.Lb + (int64_t)(k - 1) * n;
+  long long pruned = 0, tested = 0, todosum = 0, yesfast = 0;
+  if (s_fin && warp == Q1_WARPS) {
+    // ---------------- producer ----------------
+    const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
+    const int64_t G = gridDim.x;
+    int stage = 0;
+    uint32_t ph = 0;                   // bit s: parity of the next empty wait on stage s
+    uint32_t used = 0;                 // bit s: stage s was filled at least once
+    bool ok = true;
+    for (int64_t base = 0; ok && blockIdx.x + base * G < nspans; base += 32) {
+      const int64_t sp = blockIdx.x + (base + lane) * G;
+      uint32_t mask = 0;
+      if (sp < nspans) {
+#pragma unroll
+        for (int i = 0; i < Q1_WARPS; ++i) {
+          const int64_t ch = sp * Q1_WARPS + i;
+          if (ch < nchunks) {
+            const int64_t blk = (ch * 32) / c.bs;
+            if (!(__fmul_ru(c.hdr[blk], qn) < LBk[blk])) mask |= 1u << i;   // Lemma 3, strict
+          }
+        }
+      }
+      {
+        const int64_t nch = sp < nspans ? ((nchunks - sp * Q1_WARPS) < Q1_WARPS ? (nchunks - sp * Q1_WARPS) : Q1_WARPS) : 0;
+        int pr = (int)nch - __popc(mask);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(FULL, pr, o);
+        pruned += pr;                                          // warp-uniform
+      }
+      for (uint32_t live = __ballot_sync(FULL, mask != 0); live; live &= live - 1) {
+        const int src = __ffs(live) - 1;
+        const uint32_t m = __shfl_sync(FULL, mask, src);
+        const int64_t s_sp = blockIdx.x + (base + src) * G;
+        if (used & (1u << stage)) {                            // wait until the consumers freed it
+          bool w = mbar_wait_bounded(&empty[stage], (ph >> stage) & 1u);
+          w = __all_sync(FULL, w && !*(volatile int*)&s_abort);
+          ph ^= 1u << stage;
+          if (!w) { ok = false; break; }
+        }
+        used |= 1u << stage;
+        if (lane == 0) {
+          unsigned char* dst = stages + (size_t)stage * stage_bytes;
+          const unsigned char* src_rows = reinterpret_cast<const unsigned char*>(c.Qrows) +
+                                          (size_t)s_sp * Q1_WARPS * chunk_bytes;
+          uint32_t tx = 0;
+          for (uint32_t r = m; r;) {                           // runs of consecutive kept chunks
+            const int a = __ffs(r) - 1;
+            int b = a;
+            while (b + 1 < Q1_WARPS && ((r >> (b + 1)) & 1u)) ++b;
+            const int64_t last_row = (s_sp * Q1_WARPS + b + 1) * 32;
+            const int64_t rows = (last_row < n ? last_row : n) - (s_sp * Q1_WARPS + a) * 32;
+            tx += (((uint32_t)(rows * d * sizeof(T))) + 15u) & ~15u;
+            r &= ~(((2u << b) - 1u) & ~((1u << a) - 1u));
+          }
+          sinfo[stage] = make_int2((int)(s_sp), (int)m);
+          mbar_arrive(&info[stage]);
+          fence_proxy_async();
+          s_fills[stage] += 1;
+          mbar_arrive_expect_tx(&full[stage], tx);
+          for (uint32_t r = m; r;) {
+            const int a = __ffs(r) - 1;
+            int b = a;
+            while (b + 1 < Q1_WARPS && ((r >> (b + 1)) & 1u)) ++b;
+            const int64_t last_row = (s_sp * Q1_WARPS + b + 1) * 32;
+            const int64_t rows = (last_row < n ? last_row : n) - (s_sp * Q1_WARPS + a) * 32;
+            const uint32_t bytes = (((uint32_t)(rows * d * sizeof(T))) + 15u) & ~15u;
+            bulk_g2s(dst + (size_t)a * chunk_bytes, src_rows + (size_t)a * chunk_bytes, bytes, &full[stage]);
+            r &= ~(((2u << b) - 1u) & ~((1u << a) - 1u));
+          }
+        }
+        __syncwarp();
+        stage = stage + 1 == ns ? 0 : stage + 1;
+      }
+    }
+    // end marker for the consumers (or, after a failed wait, the abort flag)
+    if (ok && (used & (1u << stage))) {
+      bool w = mbar_wait_bounded(&empty[stage], (ph >> stage) & 1u);
+      w = __all_sync(FULL, w);
+      ph ^= 1u << stage;
+      ok = w;
+    }
+    if (lane == 0) {
+      if (ok) {
+        sinfo[stage] = make_int2(-1, 0);
+        mbar_arrive(&info[stage]);
+        s_fills[stage] += 1;
+        mbar_arrive(&full[stage]);
+      } else {
+        set_status(c.ctr, ST_TIMEOUT);
+        atomicExch(&s_abort, 1);
+      }
+    }
+  } else if (s_fin && warp < Q1_WARPS) {
+    // ---------------- consumers ----------------
+    int stage = 0;
+    uint32_t ph = 0;
+    while (true) {
+      bool w = mbar_wait_bounded(&info[stage], ph);
+      w = __all_sync(FULL, w);
+      if (!w) { if (lane == 0) { set_status(c.ctr, ST_TIMEOUT); atomicExch(&s_abort, 1); } break; }
+      const int2 si = sinfo[stage];
+      if (si.x < 0) break;
+      const bool mine = (si.y >> warp) & 1;
+      const int64_t pos = ((int64_t)si.x * Q1_WARPS + warp) * 32 + lane;
+      const bool valid = mine && pos < n;
+      const float2 L = valid ? Lbk[pos] : make_float2(kInf, kInf);   // prefetched while the rows land
+      w = mbar_wait_bounded(&full[stage], ph);
+      w = __all_sync(FULL, w);
+      if (!w) { if (lane == 0) { set_status(c.ctr, ST_TIMEOUT); atomicExch(&s_abort, 1); } break; }
+      if (mine) {
+        const T* row = reinterpret_cast<const T*>(stages + (size_t)stage * stage_bytes + (size_t)warp * chunk_bytes) +
+                       (size_t)lane * d;
+        float g = 0.f, A = 0.f;
+        int r = lane % d;                     // rotated start: the lanes hit different banks
+        for (int i = 0; i < d; ++i) {
+          const float uv = to_f32<T>(row[r]);
+          const float qv = sq[r];
+          g = fmaf(uv, qv, g);
+          A = fmaf(fabsf(uv), fabsf(qv), A);
+          r = (r + 1 == d) ? 0 : r + 1;
+        }
+        bool yes = false, todo = false;
+        if (valid) {
+          const float e = __fmaf_ru(A, c.cg, qeps);
+          const float hi = __fadd_ru(g, e), lo = __fsub_rd(g, e);
+          if (!(hi < L.x)) {                                              // Lemma 1 (strict)
+            yes = lo >= L.y;                                              // above hi_k
+            todo = !yes;
+          }
+        }
+        __syncwarp();
+        yesfast += __popc(__ballot_sync(FULL, yes));
+        const uint32_t bt = __ballot_sync(FULL, todo);
+        for (uint32_t mm = bt; mm; mm &= mm - 1) {                        // exact recheck on the spot
+          const int l = __ffs(mm) - 1;
+          const int64_t p = ((int64_t)si.x * Q1_WARPS + warp) * 32 + l;
+          const float* u = c.Qs + p * d;
+          const bool y = !c.incomp[p]
+                             ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.cbnd + p * RMIPS_KC, c.Ps, d, k,
+                                                  c.cg32, c.ctr)
+                             : verify_scan(u, c.unorm[p], c, sq, k, qeps);
+          if (y && lane == l) yes = true;
+        }
+        const uint32_t by = __ballot_sync(FULL, yes);
+        if (by) {
+          long long b0 = 0;
+          if (lane == 0) b0 = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
+          b0 = __shfl_sync(FULL, b0, 0);
+          if (yes) c.yes[b0 + __popc(by & ((1u << lane) - 1u))] = (int32_t)pos;
+        }
+        tested += __popc(__ballot_sync(FULL, valid));
+        todosum += __popc(bt);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == ns) { stage = 0; ph ^= 1u; }
+    }
+  }
+  if (lane == 0) {
+    if (pruned) atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)pruned);
+    if (tested) atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)tested);
+    if (todosum) atomicAdd((unsigned long long*)&c.ctr[C_TODOSUM], (unsigned long long)todosum);
+    if (yesfast) atomicAdd((unsigned long long*)&c.ctr[C_YESFAST], (unsigned long long)yesfast);
+  }
+  __syncthreads();
+  // a CTA that gave up waits (bounded) for the copies it may still have in
+  // flight before its shared memory goes away: fill f of stage s is complete
+  // once the phase of parity (f - 1) & 1 has completed
+  if (s_abort && tid == 0) {
+    for (int s = 0; s < ns; ++s)
+      if (s_fills[s] > 0) mbar_wait_bounded(&full[s], (uint32_t)((s_fills[s] - 1) & 1));
+  }
   __threadfence();
   __syncthreads();
   if (tid == 0) s_last = atomicAdd((unsigned long long*)&c.ctr[C_DONE], 1ull) == (unsigned long long)(gridDim.x - 1);
@@ -605,23 +826,7 @@ __global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const 
   long long status = s_fin ? __ldcg(&c.ctr[C_STATUS]) : ST_NONFINITE;
   long long total = 0;
   if (status == 0) {
-    // exact recheck of the undecided users: one warp per user
-    const long long ntodo = __ldcg(&c.ctr[C_TODO]);
-    for (long long t = warp; t < ntodo; t += FW) {
-      const int32_t pos = __ldcg(&c.todo[t]);
-      const float* u = c.Qs + (int64_t)pos * d;
-      const bool yes = !c.incomp[pos]
-                           ? recheck_candidates(u, sq, c.cand + (int64_t)pos * RMIPS_KC, c.cbnd + (int64_t)pos * RMIPS_KC, c.Ps, d, k,
-                                 c.cg32, c.ctr)
-                           : verify_scan(u, c.unorm[pos], c, sq, k, s_eps);
-      if (lane == 0 && yes) {
-        const long long b = atomicAdd((unsigned long long*)&c.ctr[C_YES], 1ull);
-        c.yes[b] = pos;
-      }
-    }
-    __threadfence_block();
-    __syncthreads();
-    total = emit_block(c, e, __ldcg(&c.ctr[C_YES]), 0, reinterpret_cast<int32_t*>(bufs), s_warp, &s_total);
+    total = emit_block(c, e, __ldcg(&c.ctr[C_YES]), 0, reinterpret_cast<int32_t*>(stages), s_warp, &s_total);
     if (total > e.capacity) status = ST_CAPACITY;
   }
   __syncthreads();
@@ -632,7 +837,16 @@ __global__ void __launch_bounds__(FW * 32) k_query1(Common c, EmitArgs e, const 
       res[RES_CTR + i] = c.ctr[i];
       c.ctr[i] = 0;
     }
-    c.ctr[C_DONE] = 0;
+    if (done) {
+      done[0] = status == ST_OK ? RMIPS_OK : (long long)status_code(status);
+      done[1] = total;
+    }
+    if (pacc) {                 // profiling of asynchronous calls: tested users, listed users, pruned chunks
+      atomicAdd(&pacc[0], (unsigned long long)res[RES_CTR + C_TESTED]);
+      atomicAdd(&pacc[1], (unsigned long long)(res[RES_CTR + C_YESFAST] + res[RES_CTR + C_TODOSUM]));
+      atomicAdd(&pacc[2], (unsigned long long)res[RES_CTR + C_PRUNED]);
+      atomicAdd(&pacc[3], 1ull);
+    }
     __threadfence_system();
   }
 }
@@ -832,16 +1046,59 @@ rmips_status status_from_device(long long s) {
 }
 
 template <class T>
-cudaError_t launch_query1(const Common& c, const EmitArgs& e, const float* q, int k, int precision, long long* res,
-                          int grid, size_t smem, cudaStream_t st) {
-  static thread_local bool configured = false;
-  if (!configured) {
-    cudaError_t err = cudaFuncSetAttribute(k_query1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+cudaError_t launch_query1(const Common& c, const EmitArgs& e, const float* q, int k, int precision, int ns,
+                          long long* res, long long* done, unsigned long long* pacc, int grid, size_t smem,
+                          cudaStream_t st) {
+  static thread_local size_t configured = 0;
+  if (configured < smem) {
+    cudaError_t err = cudaFuncSetAttribute(k_query1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    configured = true;
+    configured = smem;
   }
-  k_query1<T><<<grid, FW * 32, smem, st>>>(c, e, q, k, precision, res);
+  k_query1<T><<<grid, Q1_THREADS, smem, st>>>(c, e, q, k, precision, ns, res, done, pacc);
   return cudaGetLastError();
+}
+
+// Launch shape of the one-launch query: one CTA per SM (fewer when there are
+// fewer spans), as many row stages as fit in 220 KB (at most Q1_MAXNS), and
+// room for the emit's sort keys.
+struct Q1Plan {
+  int grid = 1, ns = 1;
+  size_t smem = 0;
+};
+Q1Plan q1_plan(const rmips_index* idx) {
+  static thread_local int sm_count = 0;
+  if (!sm_count) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (sm_count <= 0) sm_count = 1;
+  }
+  Q1Plan p;
+  const size_t stage = q1_stage_bytes(idx->d, elem_bytes(idx->precision));
+  const size_t budget = 220 * 1024 - Q1_HEAD;
+  p.ns = (int)(budget / stage);
+  p.ns = p.ns > Q1_MAXNS ? Q1_MAXNS : (p.ns < 1 ? 1 : p.ns);
+  int64_t keys = 1;
+  while (keys < idx->n && keys < EMIT_SORT_CAP) keys <<= 1;
+  const size_t body = (size_t)p.ns * stage;
+  p.smem = Q1_HEAD + (body > (size_t)keys * 4 ? body : (size_t)keys * 4);
+  const int64_t nspans = ((idx->n + 31) / 32 + Q1_WARPS - 1) / Q1_WARPS;
+  p.grid = (int)(nspans < sm_count ? nspans : sm_count);
+  return p;
+}
+
+cudaError_t q1_dispatch(const rmips_index* idx, const Common& c, const EmitArgs& e, const float* q, int k,
+                        long long* res, long long* done, unsigned long long* pacc, cudaStream_t st) {
+  const Q1Plan p = q1_plan(idx);
+  switch (idx->precision) {
+    case RMIPS_BF16:
+      return launch_query1<__nv_bfloat16>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+    case RMIPS_FP16:
+      return launch_query1<__half>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+    default:
+      return launch_query1<float>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+  }
 }
 
 // Single query in one launch; results land in device-mapped host memory.
@@ -854,21 +1111,6 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
     q_src = ws->h_q;
   }
   Common c = make_common(idx, ws);
-  static thread_local int sm_count = 0;
-  if (!sm_count) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (sm_count <= 0) sm_count = 1;
-  }
-  size_t smem = 512 + FW * 2 * 8 + (size_t)FW * 2 * 32 * d * elem_bytes(idx->precision);
-  const size_t smem_keys = 512 + FW * 2 * 8 + EMIT_SORT_CAP * sizeof(int32_t);
-  if (smem < smem_keys) smem = smem_keys;
-  const int64_t nchunks = (idx->n + 31) / 32;
-  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)(smem + 1024);
-  per_sm = per_sm > 8 ? 8 : (per_sm < 1 ? 1 : per_sm);
-  const int64_t want = (nchunks + FW - 1) / FW;
-  const int grid = (int)(want < sm_count * per_sm ? want : sm_count * per_sm);
   const bool out_dev = capacity > 0 && is_device_ptr(out_ids);
   if (ws->ctr_dirty) {                           // the one-launch kernel needs zero counters
     RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
@@ -891,12 +1133,7 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
     }
     RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[0], st));
   }
-  cudaError_t err;
-  switch (idx->precision) {
-    case RMIPS_BF16: err = launch_query1<__nv_bfloat16>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
-    case RMIPS_FP16: err = launch_query1<__half>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
-    default: err = launch_query1<float>(c, e, q_src, k, idx->precision, ws->h_res, grid, smem, st); break;
-  }
+  const cudaError_t err = q1_dispatch(idx, c, e, q_src, k, ws->h_res, nullptr, nullptr, st);
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
   if (prof) RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[1], st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -3383,6 +3620,72 @@ extern "C" rmips_status rmips_query_batch_async(rmips_index* idx, const float* q
     idx->pend_ev.insert(idx->pend_ev.end(), ws->ev.begin(), ws->ev.begin() + 2 * ws->ev_used);
     ws->ev.erase(ws->ev.begin(), ws->ev.begin() + 2 * ws->ev_used);
     ws->ev_used = 0;
+  }
+  RMIPS_TRY_CUDA(cudaEventRecord(ws->done_ev, st));
+  ws->done_pending = true;
+  return RMIPS_OK;
+}
+
+extern "C" rmips_status rmips_query_async(rmips_index* idx, const float* q, int32_t k, int64_t* out_ids,
+                                          int64_t capacity, int64_t* done, void* stream) {
+  if (!idx || !q || !done || capacity < 0 || (capacity > 0 && !out_ids)) {
+    set_error("null argument or negative capacity");
+    return RMIPS_ERR_ARG;
+  }
+  if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
+  {
+    const int dv = idx->device;
+    if (ptr_class(q, dv) != PTR_DEVICE || ptr_class(done, dv) != PTR_DEVICE ||
+        (capacity > 0 && ptr_class(out_ids, dv) != PTR_DEVICE)) {
+      set_error("rmips_query_async takes device buffers of the index's GPU only");
+      return RMIPS_ERR_ARG;
+    }
+  }
+  DeviceGuard dg(idx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  rmips_status s = RMIPS_OK;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
+  if (!ws->done_ev) RMIPS_TRY_CUDA(cudaEventCreateWithFlags(&ws->done_ev, cudaEventDisableTiming));
+  if (!ws->dres) RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dres, (2 + C_NCOUNTERS) * sizeof(long long)));
+  if ((s = ensure_queries(idx, ws, 1)) != RMIPS_OK) return s;
+  const bool prof = idx->prof_on != 0 && idx->dprof1;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (prof) {
+    RMIPS_TRY_CUDA(cudaEventCreate(&ev[0]));
+    RMIPS_TRY_CUDA(cudaEventCreate(&ev[1]));
+    RMIPS_TRY_CUDA(cudaEventRecord(ev[0], st));
+  }
+  if (idx->full_p) {
+    if (ws->ctr_dirty) {                         // the one-launch kernel needs zero counters
+      RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+      ws->ctr_dirty = false;
+    }
+    Common c = make_common(idx, ws);
+    EmitArgs e{};
+    e.seg_lo = 0;
+    e.seg_hi = INT64_MAX;
+    e.bitmap = ws->bitmap;
+    e.out = (long long*)out_ids;
+    e.capacity = capacity;
+    const cudaError_t err = q1_dispatch(idx, c, e, q, k, ws->dres, (long long*)done, prof ? idx->dprof1 : nullptr, st);
+    if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  } else {                                       // P' index: the multi-kernel path of Algorithm 3
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dq, q, idx->d * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dk, &k, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int64_t ev_before = ws->ev_used;
+    if ((s = run_queries(idx, ws, 1, nullptr, (long long*)out_ids, capacity, st)) != RMIPS_OK) return s;
+    ws->ev_used = ev_before;                     // timed by the pair around the call
+    k_batch_done<<<1, 1, 0, st>>>(ws->ctr, ws->doffs, 1, done, nullptr);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+  }
+  if (prof) {
+    RMIPS_TRY_CUDA(cudaEventRecord(ev[1], st));
+    std::lock_guard<std::mutex> lk(idx->mu);
+    idx->pend_ev1.push_back(ev[0]);
+    idx->pend_ev1.push_back(ev[1]);
   }
   RMIPS_TRY_CUDA(cudaEventRecord(ws->done_ev, st));
   ws->done_pending = true;

@@ -132,6 +132,7 @@ struct Workspace {
   int64_t cap_hout = 0;
   float* h_q = nullptr;          // [RMIPS_DMAX] pinned, device-mapped query staging
   long long* h_res = nullptr;    // [2 + C_NCOUNTERS] pinned, device-mapped status / count / counters
+  long long* dres = nullptr;     // [2 + C_NCOUNTERS] device status / count / counters (asynchronous calls)
   bool ctr_dirty = false;        // counters may be non-zero (multi-kernel paths leave them so)
   // CUDA graphs of the batched pipeline, one (before, after the filter) pair
   // per pass, replayed while the pass's kernel arguments stay the same
@@ -221,6 +222,9 @@ struct rmips_index {
   rmips_profile prof{};
   std::vector<cudaEvent_t> pend_ev;          // filter event pairs of asynchronous calls, read on profile read
   unsigned long long* dprof = nullptr;       // [1] kept pairs of asynchronous calls (device)
+  unsigned long long* dprof1 = nullptr;      // [4] asynchronous single queries: tested users, listed users,
+                                             // pruned chunks, launches (device)
+  std::vector<cudaEvent_t> pend_ev1;         // their filter event pairs
 };
 
 namespace rmips {

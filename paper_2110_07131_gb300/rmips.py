@@ -19,7 +19,7 @@ __all__ = [
     "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info", "rmips_last_query_stats",
     "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
-    "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "EXPORTED_SYMBOLS",
+    "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "rmips_query_async", "EXPORTED_SYMBOLS",
     "FP32", "BF16", "FP16", "Server",
 ]
 
@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = [
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
     "rmips_server_submit_many", "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
     "rmips_server_destroy", "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
+    "rmips_query_async",
 ]
 
 
@@ -110,6 +111,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_query.argtypes = [VP, P, I32, C.POINTER(Segment), P, I64, C.POINTER(I64), VP]
         lib.rmips_query_batch.argtypes = [VP, P, I64, P, C.POINTER(Segment), P, I64, P, VP]
         lib.rmips_query_batch_async.argtypes = [VP, P, I64, P, P, I64, P, P, VP]
+        lib.rmips_query_async.argtypes = [VP, P, I32, P, I64, P, VP]
         lib.rmips_index_save.argtypes = [VP, C.c_char_p]
         lib.rmips_index_load.argtypes = [C.c_char_p, VP, C.POINTER(VP)]
         lib.rmips_index_rebuild.argtypes = [VP, I32, VP, C.POINTER(VP)]
@@ -143,7 +145,8 @@ def load_library(build_if_missing: bool = True):
                      "rmips_last_query_stats", "rmips_index_export", "rmips_profile_enable",
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
                      "rmips_server_create", "rmips_server_submit", "rmips_server_submit_many",
-                     "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats"):
+                     "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
+                     "rmips_query_async"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -377,6 +380,21 @@ def rmips_query_batch_async(index: Index, qs, ks, out, offsets, done, stream=Non
         raise RmipsError(1, "ks int32, out / offsets / done int64, offsets nq + 1, done 2")
     _check(_lib.rmips_query_batch_async(index.handle, qs.data_ptr(), nq, ks.data_ptr(), out.data_ptr(),
                                         int(out.numel()), offsets.data_ptr(), done.data_ptr(), _stream(stream)))
+
+
+def rmips_query_async(index: Index, q, k: int, out, done, stream=None):
+    """Queue one query on ``stream`` without waiting (torch CUDA tensors only).
+
+    q float32 [d], out int64 [capacity], done int64 [2]: when the stream has
+    passed the call, out[:done[1]] holds the ascending ids and done[0] the
+    status."""
+    for t in (q, out, done):
+        if not _is_torch(t) or not t.is_cuda or not t.is_contiguous():
+            raise RmipsError(1, "rmips_query_async takes contiguous CUDA tensors")
+    if q.dtype.itemsize != 4 or out.dtype.itemsize != 8 or done.numel() < 2 or done.dtype.itemsize != 8:
+        raise RmipsError(1, "q float32, out / done int64, done 2")
+    _check(_lib.rmips_query_async(index.handle, q.data_ptr(), int(k), out.data_ptr(), int(out.numel()),
+                                  done.data_ptr(), _stream(stream)))
 
 
 def rmips_index_get_info(index: Index) -> dict:

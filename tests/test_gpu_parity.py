@@ -462,3 +462,53 @@ def test_pair_list_overflow_splits_the_pass(monkeypatch, precision):
     assert rmips.rmips_last_query_stats(big)["todo"] > 64
     big.close()
     index.close()
+
+
+@pytest.mark.parametrize("p_prime", [0, 100])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_async_single_queries_back_to_back(tiny, p_prime, precision):
+    # rmips_query_async: device buffers, no host wait; many calls queued back
+    # to back on one stream (the workspaces alternate) give the oracle's sets
+    torch = pytest.importorskip("torch")
+    Q, P, allq, counts = tiny
+    index = rmips.rmips_build_index(Q, P, k_max=25, p_prime=p_prime, precision=precision)
+    dq = torch.from_numpy(allq).cuda()
+    nq = len(allq)
+    outs = torch.full((nq, 2000), -1, dtype=torch.int64, device="cuda")
+    dones = torch.full((nq, 2), -7, dtype=torch.int64, device="cuda")
+    st = torch.cuda.Stream()
+    ks = [1 + (j * 7) % 25 for j in range(nq)]
+    with torch.cuda.stream(st):
+        for j in range(nq):
+            rmips.rmips_query_async(index, dq[j], ks[j], outs[j], dones[j], stream=st)
+    st.synchronize()
+    d = dones.cpu().numpy()
+    o = outs.cpu().numpy()
+    assert (d[:, 0] == 0).all(), d[:, 0]
+    for j in range(nq):
+        assert np.array_equal(o[j, :d[j, 1]], np.nonzero(counts[j] < ks[j])[0]), (j, ks[j])
+    # too small an output buffer: the status says so and the size needed is reported
+    small = torch.empty(1, dtype=torch.int64, device="cuda")
+    done = torch.zeros(2, dtype=torch.int64, device="cuda")
+    j = int(np.argmax((counts < 25).sum(axis=1)))
+    rmips.rmips_query_async(index, dq[j], 25, small, done)
+    torch.cuda.synchronize()
+    assert done.cpu().tolist() == [5, int((counts[j] < 25).sum())]
+    with pytest.raises(rmips.RmipsError):
+        rmips.rmips_query_async(index, dq[0], 26, outs[0], dones[0])
+    index.close()
+
+
+def test_single_query_kernel_ragged_spans():
+    # users not a multiple of the 256-user span, blocks of every size, and the
+    # largest results (bitmap emit): the one-launch kernel against the oracle
+    for n, m, d, bs in ((1, 3, 5, 32), (255, 40, 50, 32), (257, 60, 50, 64), (9000, 300, 64, 256),
+                        (700, 90, 128, 128)):
+        Q, P = datagen.make_problem(n, m, d, 23)
+        qs = np.concatenate([P[:3] * 6.0, datagen.random_queries(2, d, 5), np.zeros((1, d), np.float32)])
+        counts = O.counts_greater_multi(Q, P, qs)
+        index = rmips.rmips_build_index(Q, P, k_max=min(25, m), block_size=bs)
+        for j in range(len(qs)):
+            for k in sorted({1, min(25, m)}):
+                assert np.array_equal(rmips.rmips_query(index, qs[j], k), np.nonzero(counts[j] < k)[0]), (n, j, k)
+        index.close()
