@@ -73,6 +73,9 @@ typedef struct {
                          p_prime items in descending norm, as in the paper */
   int32_t precision;  /* RMIPS_FP32, RMIPS_BF16 or RMIPS_FP16 */
   int32_t flags;      /* RMIPS_FLAG_* bits; 0 for the defaults */
+  const char* tune_cache;  /* NULL, or a text file of autotuner results: when
+                              set (or with RMIPS_FLAG_AUTOTUNE) the build ends
+                              with rmips_index_tune(index, tune_cache) */
 } rmips_build_opts;
 
 /* rmips_build_opts.flags: run the batched filter on CUDA cores (float32 FMA)
@@ -85,10 +88,15 @@ typedef struct {
    bound is -inf, so no block is ever pruned.  Answers are unchanged; this is
    the "without blocks" ablation of the paper's evaluation. */
 #define RMIPS_FLAG_NO_BLOCK_FILTER 4
+/* rmips_build_index: run the autotuner (rmips_index_tune) at the end of the
+   build, also without a tune_cache file. */
+#define RMIPS_FLAG_AUTOTUNE 8
 
 /* Optional restriction of a query to a subset of users. */
 typedef struct {
-  int32_t kind;       /* 0: all users, 1: ids in [begin, end), 2: id list */
+  int32_t kind;       /* 0: all users, 1: ids in [begin, end), 2: id list,
+                         3: a segment registered with a server (serving only;
+                         begin = the handle of rmips_server_add_segment) */
   int32_t reserved;   /* must be 0 */
   int64_t begin, end; /* kind 1 */
   const int64_t* ids; /* kind 2: host array of n_ids distinct ids */
@@ -104,7 +112,15 @@ typedef struct {
   int64_t incomplete;    /* users whose candidate list could not be proven
                             complete (they fall back to a full scan) */
   int64_t device_bytes;  /* index footprint in device memory */
-  double build_ms;       /* wall time of rmips_build_index */
+  double build_ms;       /* wall time of rmips_build_index (with tuning) */
+  int32_t tuned;         /* 0 not tuned, 1 searched on the device, 2 read
+                            from a tune cache */
+  int32_t batch_stages;  /* query stages of the batched tensor-core filter
+                            (0: as many as fit) */
+  int32_t single_stages; /* row stages of the single-query kernel (0: as
+                            many as fit) */
+  int32_t reserved;
+  double tune_ms;        /* wall time of the tuning */
 } rmips_index_info;
 
 typedef struct {
@@ -131,6 +147,24 @@ typedef struct {
 rmips_status rmips_build_index(const float* Q, int64_t n, const float* P, int64_t m,
                                int32_t d, const rmips_build_opts* opts, void* stream,
                                rmips_index** out);
+
+/*
+ * rmips_index_tune -- the autotuner (no counterpart in the paper, which
+ * leaves the block size of Definition 4 at O(log n) and runs on CPU cores).
+ *
+ * Chooses the block size (32, 64, 128 or 256; the block arrays of Equation 1
+ * are rebuilt from the index's bounds) and the pipeline depths of the batched
+ * tensor-core filter and of the single-query kernel, by timing the index's
+ * own filters on the device: 1,024 items of P spread over the norm order as
+ * queries, k cycling through 1..k_max, then 64 single queries.  None of the
+ * choices changes any answer.  tune_cache: NULL, or a text file; a line for
+ * the same (n, m, d, k_max, precision, P', filter kind, GPU model) is used
+ * instead of searching, and a search appends its result there.  The tuned
+ * choices are saved with the index (rmips_index_save).  No query may run on
+ * the index during the call.  Synchronises `stream`.
+ * Errors: ARG, OOM, CUDA, TIMEOUT.
+ */
+rmips_status rmips_index_tune(rmips_index* index, const char* tune_cache, void* stream);
 
 /*
  * rmips_query -- Algorithm 3 (Section 4.3, "Simpfer") for one query.
@@ -330,16 +364,24 @@ rmips_status rmips_query_noalloc(rmips_index* index, const float* q, int32_t k, 
  * Serving loop: continuous batching of reverse k-MIPS requests on one index
  * (no counterpart in the paper, whose queries arrive one at a time).
  *
- * A dispatcher thread closes a batch when it holds max_batch requests or when
- * its oldest request has waited max_wait_us, and launches it through the
- * batched filter on one of `streams` CUDA streams; requests arriving while
- * batches run join the next batch, and up to `streams` batches overlap on the
- * device.  Results are exactly those of rmips_query for the same request.
- * Admission: at most max_pending requests queued or in flight
- * (RMIPS_ERR_BUSY beyond), and max_result_ids device-visible result slots per
- * batch (a batch that needs more is re-run one request at a time).
- * Requests with an id-list segment are answered through the single-query
- * path.  The index must outlive the server; no other server call may be in
+ * A dispatcher thread closes a batch when it holds max_batch requests, when
+ * their result reservations fill a slot's device result buffer, or when its
+ * oldest request has waited max_wait_us, and launches it through the batched
+ * filter on one of `streams` CUDA streams; requests arriving while batches
+ * run join the next batch, and up to `streams` batches overlap on the device.
+ * Results are exactly those of rmips_query for the same request.  Every
+ * segment kind is answered inside the batch (id ranges on the device; id
+ * lists and registered segments, kind 3, by intersecting the request's exact
+ * result with the list).
+ *
+ * Admission by device memory: each slot owns a device result buffer of
+ * max_device_bytes / (8 x streams) ids; a queued or running request reserves
+ * min(result_ids_per_request, its segment's size) of those ids.  A submission
+ * whose reservation would exceed the buffers' total, or that would exceed
+ * max_pending requests, is refused with RMIPS_ERR_BUSY (nothing is queued).
+ * A batch whose results outgrow its buffer anyway (reservations are
+ * estimates) is answered one request at a time, with the same results.
+ * The index must outlive the server; no other server call may be in
  * progress when rmips_server_destroy is called.
  */
 typedef struct rmips_server rmips_server;
@@ -349,8 +391,13 @@ typedef struct {
   int32_t max_wait_us;      /* batch closing deadline in microseconds (default 200) */
   int32_t streams;          /* batches in flight, 1..16 (default 2) */
   int32_t reserved;         /* must be 0 */
-  int64_t max_pending;      /* admission bound on queued + running requests */
-  int64_t max_result_ids;   /* result slots per batch; 0 = 256 per request */
+  int64_t max_pending;      /* admission bound on queued + running requests
+                               (default 1,048,576) */
+  int64_t max_device_bytes; /* device memory of the result buffers; 0 = an
+                               eighth of the free device memory at creation,
+                               at most 256 MiB */
+  int64_t result_ids_per_request;  /* result ids a request reserves (at most
+                               its segment's size); 0 = 1,024 */
 } rmips_server_opts;
 
 typedef struct {
@@ -358,7 +405,18 @@ typedef struct {
   int64_t batches;
   double mean_batch;        /* requests per launched batch */
   double p50_ms, p99_ms, max_ms;   /* request latency, submit to completion */
+  int64_t reserved_ids;     /* result ids reserved by pending requests */
+  int64_t reservable_ids;   /* total ids of the result buffers (admission bound) */
+  int64_t batches_one_by_one;  /* batches re-run one request at a time */
 } rmips_server_stats;
+
+/*
+ * rmips_server_add_segment -- registers a user segment (host array of n_ids
+ * ids, copied, duplicates dropped) with the server; requests refer to it as
+ * rmips_segment{kind = 3, begin = *handle}, so that large subsets are not
+ * copied with every request.  Handles stay valid for the server's lifetime.
+ */
+rmips_status rmips_server_add_segment(rmips_server* server, const int64_t* ids, int64_t n_ids, int32_t* handle);
 
 /* opts may be NULL for the defaults.  Spawns two host threads. */
 rmips_status rmips_server_create(rmips_index* index, const rmips_server_opts* opts, rmips_server** out);

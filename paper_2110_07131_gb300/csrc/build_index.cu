@@ -606,6 +606,39 @@ cudaError_t launch_topk_list(const float* Qs, const float* Ps, int64_t nlist, in
 }
 
 }  // namespace
+
+rmips_status set_block_size(rmips_index* idx, int bs, cudaStream_t st) {
+  if (!(bs == 32 || bs == 64 || bs == 128 || bs == 256)) { set_error("block size must be 32, 64, 128 or 256"); return RMIPS_ERR_ARG; }
+  if (bs == idx->bs) return RMIPS_OK;
+  const int64_t nb = (idx->n + bs - 1) / bs;
+  float *LB = nullptr, *hdr = nullptr;
+  RMIPS_TRY_CUDA(cudaMalloc((void**)&LB, (size_t)idx->k_max * nb * sizeof(float)));
+  cudaError_t e = cudaMalloc((void**)&hdr, (size_t)nb * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(LB);
+    set_error(cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
+  }
+  k_blocks<<<grid_for(nb * idx->k_max, 256), 256, 0, st>>>(idx->Lb, idx->unorm, idx->n, bs, nb, idx->k_max, LB, hdr,
+                                                          idx->no_blocks);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(LB);
+    cudaFree(hdr);
+    set_error(cudaGetErrorString(e));
+    return RMIPS_ERR_CUDA;
+  }
+  cudaFree(idx->LB);
+  cudaFree(idx->hdr);
+  idx->device_bytes += (int64_t)(idx->k_max + 1) * (nb - idx->nb) * (int64_t)sizeof(float);
+  idx->LB = LB;
+  idx->hdr = hdr;
+  idx->bs = bs;
+  idx->nb = nb;
+  return RMIPS_OK;
+}
+
 }  // namespace rmips
 
 using namespace rmips;
@@ -621,7 +654,8 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   int bs = opts->block_size == 0 ? 32 : opts->block_size;
   if (opts->k_max < 1 || opts->k_max > RMIPS_KMAX_LIMIT || !(bs == 32 || bs == 64 || bs == 128 || bs == 256) ||
       opts->p_prime < 0 || opts->precision < RMIPS_FP32 || opts->precision > RMIPS_FP16 ||
-      (opts->flags & ~(RMIPS_FLAG_BATCH_CUDA_CORES | RMIPS_FLAG_BUILD_CUDA_CORES | RMIPS_FLAG_NO_BLOCK_FILTER)) != 0) {
+      (opts->flags & ~(RMIPS_FLAG_BATCH_CUDA_CORES | RMIPS_FLAG_BUILD_CUDA_CORES | RMIPS_FLAG_NO_BLOCK_FILTER |
+                       RMIPS_FLAG_AUTOTUNE)) != 0) {
     set_error("invalid build options (k_max 1..28, block_size 32/64/128/256, precision 0..2)");
     return RMIPS_ERR_ARG;
   }
@@ -837,6 +871,10 @@ cleanup:
   {
     const rmips_status ps = noalloc_prepare();       // the allocation-free call's scratch exists from here on
     if (ps != RMIPS_OK) return fail(ps);
+  }
+  if ((opts->flags & RMIPS_FLAG_AUTOTUNE) || opts->tune_cache) {
+    const rmips_status ts = tune_index(idx, opts->tune_cache, st);
+    if (ts != RMIPS_OK) return fail(ts);
   }
   idx->build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = idx;

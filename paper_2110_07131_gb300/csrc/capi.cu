@@ -196,6 +196,10 @@ extern "C" rmips_status rmips_index_get_info(const rmips_index* idx, rmips_index
   i.incomplete = idx->incomplete;
   i.device_bytes = idx->device_bytes;
   i.build_ms = idx->build_ms;
+  i.tuned = idx->tuned;
+  i.batch_stages = idx->tune_ws_ns;
+  i.single_stages = idx->tune_q1_ns;
+  i.tune_ms = idx->tune_ms;
   *out = i;
   return RMIPS_OK;
 }

@@ -24,7 +24,7 @@ struct FileHeader {
   int64_t n, m, nb, pp, incomplete;
   int32_t d, k_max, bs, precision, full_p, batch_tc, no_blocks, has_qh, has_qtc, narrays;
   float pn0;
-  int32_t reserved;
+  int32_t tune;            // autotuner choices: batch stages | single stages << 8 | tuned << 16
 };
 static_assert(sizeof(FileHeader) == 96, "index file header layout");
 
@@ -50,8 +50,13 @@ bool header_ok(const FileHeader& h, std::string* why) {
   if (h.precision < RMIPS_FP32 || h.precision > RMIPS_FP16) return bad("unknown precision");
   if ((h.full_p != 0 && h.full_p != 1) || (h.batch_tc != 0 && h.batch_tc != 1) ||
       (h.no_blocks != 0 && h.no_blocks != 1) || (h.has_qh != 0 && h.has_qh != 1) ||
-      (h.has_qtc != 0 && h.has_qtc != 1) || h.reserved != 0)
+      (h.has_qtc != 0 && h.has_qtc != 1))
     return bad("flag field out of range");
+  {
+    const int ws_ns = h.tune & 0xff, q1_ns = (h.tune >> 8) & 0xff, tuned = (h.tune >> 16) & 0xff;
+    if ((h.tune >> 24) != 0 || ws_ns > 6 || (ws_ns & 1) || q1_ns > 8 || tuned > 2)
+      return bad("autotuner field out of range");
+  }
   if (h.pp < 1 || h.pp > h.m || (h.full_p == 1) != (h.pp == h.m)) return bad("|P'| does not match the index mode");
   if (h.has_qh != (h.precision != RMIPS_FP32 ? 1 : 0)) return bad("reduced-precision copy does not match the precision");
   if (h.has_qtc && h.d > 64) return bad("tensor-core tiles need d <= 64");
@@ -136,7 +141,7 @@ extern "C" rmips_status rmips_index_save(const rmips_index* cidx, const char* pa
   h.d = idx->d; h.k_max = idx->k_max; h.bs = idx->bs; h.precision = idx->precision; h.full_p = idx->full_p;
   h.batch_tc = idx->batch_tc; h.no_blocks = idx->no_blocks; h.has_qh = idx->Qh != nullptr; h.has_qtc = idx->Qtc != nullptr;
   h.pn0 = idx->pn0;
-  h.reserved = 0;
+  h.tune = (idx->tune_ws_ns & 0xff) | ((idx->tune_q1_ns & 0xff) << 8) | ((idx->tuned & 0xff) << 16);
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh, h.has_qtc);
   h.narrays = (int32_t)a.size();
   if (cudaDeviceSynchronize() != cudaSuccess) { set_error("device error before save"); return RMIPS_ERR_CUDA; }
@@ -178,6 +183,9 @@ extern "C" rmips_status rmips_index_load(const char* path, void* stream, rmips_i
   idx->n = h.n; idx->m = h.m; idx->nb = h.nb; idx->pp = h.pp; idx->incomplete = h.incomplete;
   idx->d = h.d; idx->k_max = h.k_max; idx->bs = h.bs; idx->precision = h.precision; idx->full_p = h.full_p;
   idx->batch_tc = h.batch_tc; idx->no_blocks = h.no_blocks; idx->pn0 = h.pn0;
+  idx->tune_ws_ns = h.tune & 0xff;
+  idx->tune_q1_ns = (h.tune >> 8) & 0xff;
+  idx->tuned = (h.tune >> 16) & 0xff;
   const std::vector<ArrayRef> a = arrays(idx, h.has_qh != 0, h.has_qtc != 0);
   std::vector<std::vector<unsigned char>> bufs(a.size());
   if ((int32_t)a.size() != h.narrays) why = "array count does not match its header";
@@ -264,6 +272,11 @@ extern "C" rmips_status rmips_index_rebuild(const rmips_index* cidx, int32_t k_m
     o.precision = idx->precision;
     o.flags = (idx->batch_tc ? 0 : RMIPS_FLAG_BATCH_CUDA_CORES) | (idx->no_blocks ? RMIPS_FLAG_NO_BLOCK_FILTER : 0);
     s = rmips_build_index(Q, n, P, m, d, &o, stream, out);
+    if (s == RMIPS_OK) {                                 // the same launch choices
+      (*out)->tune_ws_ns = idx->tune_ws_ns;
+      (*out)->tune_q1_ns = idx->tune_q1_ns;
+      (*out)->tuned = idx->tuned;
+    }
   }
   if (Q) cudaFreeAsync(Q, st);
   if (P) cudaFreeAsync(P, st);

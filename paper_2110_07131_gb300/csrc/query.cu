@@ -603,6 +603,25 @@ constexpr int Q1_WARPS = 8;                                    // consumer warps
 constexpr int Q1_THREADS = (Q1_WARPS + 1) * 32;
 constexpr int Q1_MAXNS = 6;                                    // stages at most
 constexpr size_t Q1_HEAD = 1024;                               // q, barriers, stage info
+constexpr int Q1_YCAP = 256;                                   // yes positions a warp buffers
+constexpr int Q1_TCAP = 64;                                    // undecided positions a warp buffers
+constexpr size_t Q1_BUFS = (size_t)Q1_WARPS * (Q1_YCAP + Q1_TCAP) * sizeof(int32_t);
+
+// Ascending sort of one value per lane (bitonic network over the warp).
+__device__ __forceinline__ int32_t q1_warp_sort(int32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const int32_t y = __shfl_xor_sync(FULL, x, j);
+      const bool up = ((lane & kk) == 0);
+      const bool lower = (lane & j) == 0;
+      x = (lower == up) ? min(x, y) : max(x, y);
+    }
+  }
+  return x;
+}
 
 __host__ __device__ inline size_t q1_stage_bytes(int d, int es) { return (size_t)Q1_WARPS * 32 * d * es; }
 
@@ -616,12 +635,15 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   uint64_t* info = full + Q1_MAXNS;                                       // [Q1_MAXNS]
   uint64_t* empty = info + Q1_MAXNS;                                      // [Q1_MAXNS]
   int2* sinfo = reinterpret_cast<int2*>(smem + 512 + 3 * Q1_MAXNS * 8);   // [Q1_MAXNS] (span, mask)
-  unsigned char* stages = smem + Q1_HEAD;                                 // ns x stage, later sort keys
+  int32_t* ybuf = reinterpret_cast<int32_t*>(smem + Q1_HEAD);            // [Q1_WARPS][Q1_YCAP]
+  int32_t* tbuf = ybuf + Q1_WARPS * Q1_YCAP;                               // [Q1_WARPS][Q1_TCAP]
+  unsigned char* stages = smem + Q1_HEAD + Q1_BUFS;                        // ns x stage, later sort keys
   __shared__ float s_qn, s_eps;
   __shared__ int s_fin, s_last, s_abort;
   __shared__ int s_fills[Q1_MAXNS];         // phases completed on full[s] by the producer
   __shared__ int s_warp[32];
   __shared__ long long s_total;
+  __shared__ long long s_ctr[C_NCOUNTERS];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = c.d;
   const int64_t n = c.n;
@@ -739,6 +761,42 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
     }
   } else if (s_fin && warp < Q1_WARPS) {
     // ---------------- consumers ----------------
+    // Yes positions and undecided positions go to the warp's own buffers in
+    // shared memory: the stream loop holds no round trip to global memory
+    // except the prefetched bounds.  Yes positions are flushed to the list
+    // with one reservation per 256; undecided users are rechecked exactly
+    // after the stream (or when 64 have gathered).
+    int32_t* wy = ybuf + warp * Q1_YCAP;
+    int32_t* wt = tbuf + warp * Q1_TCAP;
+    int ny = 0, nt = 0;                                         // warp-uniform
+    const uint32_t lt = (1u << lane) - 1u;
+    auto flush_yes = [&]() {
+      __syncwarp();
+      long long b0 = 0;
+      if (lane == 0 && ny) b0 = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)ny);
+      b0 = __shfl_sync(FULL, b0, 0);
+      for (int i = lane; i < ny; i += 32) c.yes[b0 + i] = wy[i];
+      __syncwarp();
+      ny = 0;
+    };
+    auto recheck = [&]() {                                      // whole warp, one user at a time
+      __syncwarp();
+      for (int t = 0; t < nt; ++t) {
+        const int64_t p = wt[t];
+        const float* u = c.Qs + p * d;
+        const bool y = !c.incomp[p]
+                           ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.cbnd + p * RMIPS_KC, c.Ps, d, k,
+                                                c.cg32, c.ctr)
+                           : verify_scan(u, c.unorm[p], c, sq, k, qeps);
+        if (y) {
+          if (ny == Q1_YCAP) flush_yes();
+          if (lane == 0) wy[ny] = (int32_t)p;
+          ++ny;
+        }
+      }
+      __syncwarp();
+      nt = 0;
+    };
     int stage = 0;
     uint32_t ph = 0;
     while (true) {
@@ -775,26 +833,18 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
             todo = !yes;
           }
         }
-        __syncwarp();
-        yesfast += __popc(__ballot_sync(FULL, yes));
-        const uint32_t bt = __ballot_sync(FULL, todo);
-        for (uint32_t mm = bt; mm; mm &= mm - 1) {                        // exact recheck on the spot
-          const int l = __ffs(mm) - 1;
-          const int64_t p = ((int64_t)si.x * Q1_WARPS + warp) * 32 + l;
-          const float* u = c.Qs + p * d;
-          const bool y = !c.incomp[p]
-                             ? recheck_candidates(u, sq, c.cand + p * RMIPS_KC, c.cbnd + p * RMIPS_KC, c.Ps, d, k,
-                                                  c.cg32, c.ctr)
-                             : verify_scan(u, c.unorm[p], c, sq, k, qeps);
-          if (y && lane == l) yes = true;
-        }
-        const uint32_t by = __ballot_sync(FULL, yes);
+        const uint32_t by = __ballot_sync(FULL, yes), bt = __ballot_sync(FULL, todo);
         if (by) {
-          long long b0 = 0;
-          if (lane == 0) b0 = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)__popc(by));
-          b0 = __shfl_sync(FULL, b0, 0);
-          if (yes) c.yes[b0 + __popc(by & ((1u << lane) - 1u))] = (int32_t)pos;
+          if (ny + __popc(by) > Q1_YCAP) flush_yes();
+          if (yes) wy[ny + __popc(by & lt)] = (int32_t)pos;
+          ny += __popc(by);
         }
+        if (bt) {
+          if (nt + __popc(bt) > Q1_TCAP) recheck();
+          if (todo) wt[nt + __popc(bt & lt)] = (int32_t)pos;
+          nt += __popc(bt);
+        }
+        yesfast += __popc(by);
         tested += __popc(__ballot_sync(FULL, valid));
         todosum += __popc(bt);
       }
@@ -802,6 +852,8 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       if (lane == 0) mbar_arrive(&empty[stage]);
       if (++stage == ns) { stage = 0; ph ^= 1u; }
     }
+    recheck();
+    flush_yes();
   }
   if (lane == 0) {
     if (pruned) atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)pruned);
@@ -823,28 +875,48 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  long long status = s_fin ? __ldcg(&c.ctr[C_STATUS]) : ST_NONFINITE;
+  // the counters, all at once (one thread each), then the result
+  if (tid < C_NCOUNTERS) s_ctr[tid] = __ldcg(&c.ctr[tid]);
+  __syncthreads();
+  long long status = s_fin ? s_ctr[C_STATUS] : ST_NONFINITE;
+  const long long cnt = s_ctr[C_YES];
   long long total = 0;
-  if (status == 0) {
-    total = emit_block(c, e, __ldcg(&c.ctr[C_YES]), 0, reinterpret_cast<int32_t*>(stages), s_warp, &s_total);
+  if (status == 0 && cnt <= 32) {
+    // a small result: one warp, one id per lane, sorted with shuffles
+    if (warp == 0) {
+      int32_t id = INT_MAX;
+      if (lane < cnt) {
+        const int32_t v = c.permQ[__ldcg(&c.yes[lane])];
+        if (seg_ok(e, v)) id = v;
+      }
+      id = q1_warp_sort(id);
+      const int tot = __popc(__ballot_sync(FULL, id != INT_MAX));
+      if (tot <= e.capacity && id != INT_MAX) e.out[lane] = id;
+      if (lane == 0) s_total = tot;
+    }
+    __syncthreads();
+    total = s_total;
+    if (total > e.capacity) status = ST_CAPACITY;
+  } else if (status == 0) {
+    total = emit_block(c, e, cnt, 0, reinterpret_cast<int32_t*>(stages), s_warp, &s_total);
     if (total > e.capacity) status = ST_CAPACITY;
   }
   __syncthreads();
+  if (tid < C_NCOUNTERS) {
+    res[RES_CTR + tid] = s_ctr[tid];
+    c.ctr[tid] = 0;
+  }
   if (tid == 0) {
     res[RES_STATUS] = status;
     res[RES_COUNT] = total;
-    for (int i = 0; i < C_NCOUNTERS; ++i) {
-      res[RES_CTR + i] = c.ctr[i];
-      c.ctr[i] = 0;
-    }
     if (done) {
       done[0] = status == ST_OK ? RMIPS_OK : (long long)status_code(status);
       done[1] = total;
     }
     if (pacc) {                 // profiling of asynchronous calls: tested users, listed users, pruned chunks
-      atomicAdd(&pacc[0], (unsigned long long)res[RES_CTR + C_TESTED]);
-      atomicAdd(&pacc[1], (unsigned long long)(res[RES_CTR + C_YESFAST] + res[RES_CTR + C_TODOSUM]));
-      atomicAdd(&pacc[2], (unsigned long long)res[RES_CTR + C_PRUNED]);
+      atomicAdd(&pacc[0], (unsigned long long)s_ctr[C_TESTED]);
+      atomicAdd(&pacc[1], (unsigned long long)(s_ctr[C_YESFAST] + s_ctr[C_TODOSUM]));
+      atomicAdd(&pacc[2], (unsigned long long)s_ctr[C_PRUNED]);
       atomicAdd(&pacc[3], 1ull);
     }
     __threadfence_system();
@@ -1076,13 +1148,14 @@ Q1Plan q1_plan(const rmips_index* idx) {
   }
   Q1Plan p;
   const size_t stage = q1_stage_bytes(idx->d, elem_bytes(idx->precision));
-  const size_t budget = 220 * 1024 - Q1_HEAD;
+  const size_t budget = 220 * 1024 - Q1_HEAD - Q1_BUFS;
   p.ns = (int)(budget / stage);
   p.ns = p.ns > Q1_MAXNS ? Q1_MAXNS : (p.ns < 1 ? 1 : p.ns);
+  if (idx->tune_q1_ns > 0 && idx->tune_q1_ns < p.ns) p.ns = idx->tune_q1_ns;    // the autotuner's choice
   int64_t keys = 1;
   while (keys < idx->n && keys < EMIT_SORT_CAP) keys <<= 1;
   const size_t body = (size_t)p.ns * stage;
-  p.smem = Q1_HEAD + (body > (size_t)keys * 4 ? body : (size_t)keys * 4);
+  p.smem = Q1_HEAD + Q1_BUFS + (body > (size_t)keys * 4 ? body : (size_t)keys * 4);
   const int64_t nspans = ((idx->n + 31) / 32 + Q1_WARPS - 1) / Q1_WARPS;
   p.grid = (int)(nspans < sm_count ? nspans : sm_count);
   return p;
@@ -3114,6 +3187,7 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
   int ws_ns = WS_MAXNS;                   // query stages that fit beside the user tiles and bounds
   while (ws_ns > 2 && ws_smem_bytes(tck, ws_ns) > 220 * 1024) --ws_ns;
+  if (idx->tune_ws_ns > 0 && idx->tune_ws_ns < ws_ns) ws_ns = idx->tune_ws_ns;   // the autotuner's choice
   ws_ns &= ~1;                            // even: each MMA warp owns fixed stages
   const size_t smem_ws = ws_smem_bytes(tck, ws_ns);
   const int64_t tc_tiles = (idx->n + TCU - 1) / TCU;
@@ -3743,4 +3817,97 @@ rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long
                    with_segments ? ws->dseghi : nullptr);
 }
 rmips_status device_status(long long s) { return status_from_device(s); }
+
+int max_batch_stages(const rmips_index* idx) {
+  const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
+  int ns = WS_MAXNS;
+  while (ns > 2 && ws_smem_bytes(tck, ns) > 220 * 1024) --ns;
+  return ns & ~1;
+}
+
+int max_single_stages(const rmips_index* idx) {
+  const size_t stage = q1_stage_bytes(idx->d, elem_bytes(idx->precision));
+  int ns = (int)((220 * 1024 - Q1_HEAD - Q1_BUFS) / stage);
+  return ns > Q1_MAXNS ? Q1_MAXNS : (ns < 1 ? 1 : ns);
+}
+
+rmips_status tune_time_batch(rmips_index* idx, const float* dq, const int32_t* dk, int64_t nq, int reps,
+                             cudaStream_t st, float* ms) {
+  rmips_status s = RMIPS_OK;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
+  if ((s = ensure_queries(idx, ws, nq)) != RMIPS_OK) return s;
+  const int64_t cap = idx->n * nq < (8ll << 20) ? idx->n * nq : (8ll << 20);
+  if ((s = ensure_dout(ws, cap)) != RMIPS_OK) return s;
+  if ((s = stage_inputs(idx, ws, dq, nq, dk, st)) != RMIPS_OK) return s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RMIPS_TRY_CUDA(cudaEventCreate(&e0));
+  cudaError_t err = cudaEventCreate(&e1);
+  for (int r = -1; err == cudaSuccess && r < reps; ++r) {       // run -1 is untimed
+    if (r == 0) err = cudaEventRecord(e0, st);
+    if (err == cudaSuccess && (s = run_batch(idx, ws, nq, ws->dout, cap, st, nullptr, nullptr)) != RMIPS_OK) break;
+  }
+  ws->ev_used = 0;
+  if (err == cudaSuccess && s == RMIPS_OK) err = cudaEventRecord(e1, st);
+  if (err == cudaSuccess && s == RMIPS_OK) err = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (err == cudaSuccess && s == RMIPS_OK) err = cudaEventElapsedTime(&t, e0, e1);
+  long long status = 0;
+  if (err == cudaSuccess && s == RMIPS_OK) err = cudaMemcpy(&status, &ws->ctr[C_STATUS], sizeof(status), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s != RMIPS_OK) return s;
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  if (status != ST_OK && status != ST_CAPACITY) return status_from_device(status);
+  *ms = t / (reps > 0 ? reps : 1);
+  return RMIPS_OK;
+}
+
+rmips_status tune_time_single(rmips_index* idx, const float* dq, int64_t nq, int k, cudaStream_t st, float* ms) {
+  rmips_status s = RMIPS_OK;
+  Workspace* ws = acquire_workspace(idx, &s);
+  if (!ws) return s;
+  WsGuard g{idx, ws};
+  if ((s = ws_join(ws, st)) != RMIPS_OK) return s;
+  if (!ws->dres) RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dres, (2 + C_NCOUNTERS) * sizeof(long long)));
+  if ((s = ensure_dout(ws, idx->n)) != RMIPS_OK) return s;
+  if (ws->ctr_dirty) {
+    RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+    ws->ctr_dirty = false;
+  }
+  Common c = make_common(idx, ws);
+  EmitArgs e{};
+  e.seg_lo = 0;
+  e.seg_hi = INT64_MAX;
+  e.bitmap = ws->bitmap;
+  e.out = ws->dout;
+  e.capacity = idx->n;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RMIPS_TRY_CUDA(cudaEventCreate(&e0));
+  cudaError_t err = cudaEventCreate(&e1);
+  const int warm = 4;
+  for (int64_t i = 0; err == cudaSuccess && i < nq + warm; ++i) {
+    if (i == warm) err = cudaEventRecord(e0, st);
+    if (err == cudaSuccess)
+      err = q1_dispatch(idx, c, e, dq + (size_t)((i < warm ? i : i - warm) % nq) * idx->d, k, ws->dres, nullptr,
+                        nullptr, st);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+  long long status = 0;
+  if (err == cudaSuccess) err = cudaMemcpy(&status, &ws->dres[RES_STATUS], sizeof(status), cudaMemcpyDeviceToHost);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  if (status != ST_OK) {
+    if (status == ST_TIMEOUT || status == ST_INTERNAL) ws->ctr_dirty = true;
+    return status_from_device(status);
+  }
+  *ms = t / (float)nq;
+  return RMIPS_OK;
+}
 }  // namespace rmips

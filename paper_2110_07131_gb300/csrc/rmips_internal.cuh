@@ -198,6 +198,11 @@ struct rmips_index {
   int64_t device_bytes = 0;
   double build_ms = 0.0;
   float pn0 = 0.f;              // largest item norm (rounded up)
+  // launch choices of the autotuner (0: as many stages as fit in shared memory)
+  int tune_ws_ns = 0;           // query stages of the batched tensor-core filter (even)
+  int tune_q1_ns = 0;           // row stages of the one-launch single-query kernel
+  int tuned = 0;                // 0 not tuned, 1 searched on the device, 2 read from a tune cache
+  double tune_ms = 0.0;
 
   float* Qs = nullptr;
   void* Qh = nullptr;
@@ -258,6 +263,20 @@ void release_workspace(rmips_index* idx, Workspace* ws);
 // Loads the module that holds rmips_query_noalloc's scratch array on the
 // current device (called when an index is built or loaded).
 rmips_status noalloc_prepare();
+// Block arrays (Equation 1) for another block size, from the index's bounds.
+rmips_status set_block_size(rmips_index* idx, int bs, cudaStream_t st);
+// Autotuner timing hooks: milliseconds per run of the batched path on nq
+// device-resident queries, and per one-launch single query.
+rmips_status tune_time_batch(rmips_index* idx, const float* dq, const int32_t* dk, int64_t nq, int reps,
+                             cudaStream_t st, float* ms);
+rmips_status tune_time_single(rmips_index* idx, const float* dq, int64_t nq, int k, cudaStream_t st, float* ms);
+// Largest number of query stages the batched tensor-core filter can use.
+int max_batch_stages(const rmips_index* idx);
+// Largest number of row stages the single-query kernel can use.
+int max_single_stages(const rmips_index* idx);
+// The autotuner: reads the choices from `cache` (may be NULL) or searches
+// them on the device and appends them to `cache`.
+rmips_status tune_index(rmips_index* idx, const char* cache, cudaStream_t st);
 // Orders this stream after the last asynchronous call that used ws.
 rmips_status ws_join(Workspace* ws, cudaStream_t st);
 void destroy_workspace(Workspace* ws);

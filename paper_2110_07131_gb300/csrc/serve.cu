@@ -1,16 +1,26 @@
 // Serving loop: continuous batching of reverse k-MIPS requests.
 //
-// Requests (q, k, optional id range or id list) are queued by
-// rmips_server_submit.  A dispatcher thread closes a batch when it holds
-// max_batch requests or when its oldest request has waited max_wait_us, and
-// launches it on a free stream slot (each slot owns a workspace, pinned
-// staging buffers and device-mapped result memory); requests that arrive in
-// the meantime wait for the next batch, so up to `streams` batches overlap on
-// the GPU.  A completer thread finishes slots in launch order, copies each
-// request's ids out of the mapped buffer and records its latency (submit to
-// completion).  Admission: at most max_pending requests queued or in flight,
-// and at most max_result_ids result ids per batch (a batch that needs more is
-// re-run one request at a time).
+// Requests (q, k, optional segment) are queued by rmips_server_submit.  A
+// dispatcher thread closes a batch when it holds max_batch requests, when
+// their result reservations fill a slot's result buffer, or when its oldest
+// request has waited max_wait_us, and launches it on a free stream slot (each
+// slot owns a workspace, pinned staging, a device result buffer and a pinned
+// copy of it); requests that arrive in the meantime wait for the next batch,
+// so up to `streams` batches overlap on the GPU.  Every segment kind is
+// answered inside the batch: id ranges on the device, id lists and
+// registered segments by intersecting the request's exact unrestricted
+// result with the (sorted) list afterwards.  A completer thread finishes
+// slots in launch order, copies each request's ids out and records its
+// latency (submit to completion).
+//
+// Admission by device memory: every queued or running request reserves
+// result slots in the slots' device result buffers (min(result_ids_per_request,
+// its segment's size) ids of 8 bytes); a submission whose reservation would
+// take the total past the buffers' capacity (streams x cap_out ids, sized
+// from max_device_bytes, itself by default an eighth of the device's free
+// memory at creation) is refused with RMIPS_ERR_BUSY, as is one past
+// max_pending requests.  A batch whose actual results overflow its buffer
+// (reservations are estimates) is answered one request at a time.
 #include <algorithm>
 #include <chrono>
 #include <climits>
@@ -30,9 +40,11 @@ namespace {
 struct Request {
   std::vector<float> q;
   int32_t k = 1;
-  int kind = 0;                 // 0 all users, 1 id range, 2 id list
+  int kind = 0;                 // 0 all users, 1 id range, 2 id list, 3 registered segment
   int64_t lo = 0, hi = INT64_MAX;
-  std::vector<int64_t> list;
+  std::vector<int64_t> list;    // kind 2: sorted, distinct ids
+  int32_t handle = -1;          // kind 3
+  int64_t reserve = 0;          // result ids reserved (admission)
   Clock::time_point t0;
   int state = 0;                // 0 queued, 1 running, 2 done
   rmips_status st = RMIPS_OK;
@@ -50,7 +62,8 @@ struct Slot {
   long long* h_hi = nullptr;
   long long* h_offs = nullptr;
   long long* h_ctr = nullptr;
-  long long* h_out = nullptr;   // device-mapped pinned result ids
+  long long* d_out = nullptr;   // device result ids of a batch
+  long long* h_out = nullptr;   // pinned, device-mapped copy of them
   int64_t cap_out = 0;
   std::vector<int64_t> tickets;
   bool segments = false;
@@ -59,6 +72,15 @@ struct Slot {
 };
 
 constexpr size_t LAT_CAP = 1 << 20;
+
+// The first min(total, cap) result ids of a batch into mapped host memory.
+__global__ void k_serve_copy(const long long* __restrict__ src, long long* __restrict__ dst,
+                             const long long* __restrict__ ctr, long long cap) {
+  if (ctr[C_STATUS] != 0) return;
+  const long long n = ctr[C_CURSOR] < cap ? ctr[C_CURSOR] : cap;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
 
 }  // namespace
 }  // namespace rmips
@@ -72,10 +94,12 @@ struct rmips_server {
   std::deque<int64_t> queue;
   std::vector<rmips::Slot> slots;
   std::deque<int> inflight;
+  std::vector<std::vector<int64_t>> segs;    // registered segments (sorted, distinct)
   int64_t next = 1, pending = 0;
+  int64_t reserved = 0, capacity = 0;        // result ids reserved / reservable (admission)
   bool stop = false;
   std::thread disp, comp;
-  int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched = 0;
+  int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched = 0, one_by_one = 0;
   std::vector<double> lat;
   size_t lat_n = 0;
 };
@@ -90,14 +114,31 @@ void record_latency(rmips_server* S, double ms) {
   ++S->lat_n;
 }
 
-// One request through the single-query path (list segments, capacity retries).
+const std::vector<int64_t>* seg_list(const rmips_server* S, const Request* r) {
+  if (r->kind == 2) return &r->list;
+  if (r->kind == 3) return &S->segs[(size_t)r->handle];
+  return nullptr;
+}
+
+// ids (ascending) restricted to the request's id list, if it has one.
+void restrict_to_list(const rmips_server* S, const Request* r, std::vector<int64_t>& ids) {
+  const std::vector<int64_t>* L = seg_list(S, r);
+  if (!L) return;
+  size_t w = 0;
+  for (int64_t id : ids)
+    if (std::binary_search(L->begin(), L->end(), id)) ids[w++] = id;
+  ids.resize(w);
+}
+
+// One request through the single-query path (when a batch's results overflow).
 void run_single(rmips_server* S, Request* r, std::vector<int64_t>& ids, rmips_status& st) {
   rmips_segment seg{};
-  seg.kind = r->kind;
+  const std::vector<int64_t>* L = seg_list(S, r);
+  seg.kind = L ? 2 : r->kind;
   seg.begin = r->lo;
   seg.end = r->hi;
-  seg.ids = r->list.data();
-  seg.n_ids = (int64_t)r->list.size();
+  seg.ids = L ? L->data() : nullptr;
+  seg.n_ids = L ? (int64_t)L->size() : 0;
   ids.resize((size_t)S->idx->n);
   int64_t cnt = 0;
   st = rmips_query(S->idx, r->q.data(), r->k, r->kind ? &seg : nullptr, ids.data(), S->idx->n, &cnt, nullptr);
@@ -112,6 +153,7 @@ void finish(rmips_server* S, Request* r, std::vector<int64_t>&& ids, rmips_statu
   record_latency(S, r->ms);
   ++S->completed;
   --S->pending;
+  S->reserved -= r->reserve;
 }
 
 rmips_status launch_slot(rmips_server* S, Slot& sl, int64_t nq) {
@@ -124,8 +166,10 @@ rmips_status launch_slot(rmips_server* S, Slot& sl, int64_t nq) {
     RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, sl.h_lo, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
     RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, sl.h_hi, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
   }
-  rmips_status s = batch_launch(idx, ws, nq, sl.h_out, sl.cap_out, st, sl.segments);
+  rmips_status s = batch_launch(idx, ws, nq, sl.d_out, sl.cap_out, st, sl.segments);
   if (s != RMIPS_OK) return s;
+  k_serve_copy<<<128, 256, 0, st>>>(sl.d_out, sl.h_out, ws->ctr, sl.cap_out);
+  RMIPS_TRY_CUDA(cudaGetLastError());
   RMIPS_TRY_CUDA(cudaMemcpyAsync(sl.h_offs, ws->doffs, (nq + 1) * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaMemcpyAsync(sl.h_ctr, ws->ctr, C_NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost, st));
   RMIPS_TRY_CUDA(cudaEventRecord(sl.done, st));
@@ -154,49 +198,34 @@ void dispatcher(rmips_server* S) {
     sl.busy = true;
     sl.tickets.clear();
     sl.segments = false;
-    std::vector<Request*> batch, singles;
-    std::vector<int64_t> single_t;
+    std::vector<Request*> batch;
+    int64_t ids_reserved = 0;
     while (!S->queue.empty() && (int64_t)batch.size() < S->o.max_batch) {
       const int64_t t = S->queue.front();
-      S->queue.pop_front();
       Request* r = S->reqs[t];
+      if (!batch.empty() && ids_reserved + r->reserve > sl.cap_out) break;   // the slot's result buffer is full
+      S->queue.pop_front();
       r->state = 1;
-      if (r->kind == 2) { singles.push_back(r); single_t.push_back(t); continue; }
+      ids_reserved += r->reserve;
       sl.tickets.push_back(t);
       batch.push_back(r);
       sl.segments = sl.segments || r->kind == 1;
     }
     lk.unlock();
-    // id-list segments: one request at a time through the single-query path
-    for (Request* r : singles) {
-      std::vector<int64_t> ids;
-      rmips_status st;
-      run_single(S, r, ids, st);
-      std::lock_guard<std::mutex> g(S->mu);
-      finish(S, r, std::move(ids), st, Clock::now());
-      S->cv_done.notify_all();
-    }
     const int64_t nq = (int64_t)batch.size();
-    if (nq > 0) {
-      const int d = S->idx->d;
-      for (int64_t i = 0; i < nq; ++i) {
-        memcpy(sl.h_q + i * d, batch[i]->q.data(), d * sizeof(float));
-        sl.h_k[i] = batch[i]->k;
-        sl.h_lo[i] = batch[i]->kind == 1 ? batch[i]->lo : 0;
-        sl.h_hi[i] = batch[i]->kind == 1 ? batch[i]->hi : INT64_MAX;
-      }
-      sl.launch = launch_slot(S, sl, nq);
+    const int d = S->idx->d;
+    for (int64_t i = 0; i < nq; ++i) {
+      memcpy(sl.h_q + i * d, batch[i]->q.data(), d * sizeof(float));
+      sl.h_k[i] = batch[i]->k;
+      sl.h_lo[i] = batch[i]->kind == 1 ? batch[i]->lo : 0;
+      sl.h_hi[i] = batch[i]->kind == 1 ? batch[i]->hi : INT64_MAX;
     }
+    sl.launch = launch_slot(S, sl, nq);
     lk.lock();
-    if (nq > 0) {
-      S->inflight.push_back(si);
-      ++S->batches;
-      S->batched += nq;
-      S->cv_fly.notify_one();
-    } else {
-      sl.busy = false;
-      S->cv_slot.notify_all();
-    }
+    S->inflight.push_back(si);
+    ++S->batches;
+    S->batched += nq;
+    S->cv_fly.notify_one();
   }
   // stopped: fail whatever is still queued
   const auto now = Clock::now();
@@ -231,21 +260,25 @@ void completer(rmips_server* S) {
         set_error("batch failed on the device");
         st = RMIPS_ERR_CUDA;
       } else {
-        // a full pair list (ties-heavy batch) is retried one request at a time
-        one_by_one = sl.h_ctr[C_STATUS] == ST_PAIRS_FULL;
+        // results past the buffer, or a full pair list (ties-heavy batch):
+        // answered one request at a time
+        one_by_one = sl.h_ctr[C_STATUS] == ST_PAIRS_FULL || sl.h_ctr[C_STATUS] == ST_CAPACITY;
         st = device_status(sl.h_ctr[C_STATUS]);
       }
     }
     std::vector<std::vector<int64_t>> res(nq);
     std::vector<rmips_status> sts(nq, st);
     if (st == RMIPS_OK) {
-      for (int64_t i = 0; i < nq; ++i)
+      for (int64_t i = 0; i < nq; ++i) {
         res[i].assign(sl.h_out + sl.h_offs[i], sl.h_out + sl.h_offs[i + 1]);
-    } else if (st == RMIPS_ERR_CAPACITY || one_by_one) {
+        restrict_to_list(S, rs[i], res[i]);
+      }
+    } else if (one_by_one) {
       for (int64_t i = 0; i < nq; ++i) run_single(S, rs[i], res[i], sts[i]);
     }
     const auto now = Clock::now();
     lk.lock();
+    if (one_by_one) S->one_by_one += 1;
     for (int64_t i = 0; i < nq; ++i) finish(S, rs[i], std::move(res[i]), sts[i], now);
     sl.busy = false;
     S->cv_slot.notify_all();
@@ -253,7 +286,11 @@ void completer(rmips_server* S) {
   }
 }
 
-rmips_status check_request(const rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg) {
+// Validates a request; *segment_size receives the number of users its
+// segment allows (for the result reservation).
+rmips_status check_request(const rmips_server* S, const float* q, int32_t k, const rmips_segment* seg,
+                           int64_t* segment_size) {
+  const rmips_index* idx = S->idx;
   if (k < 1 || k > idx->k_max) { set_error("k outside [1, k_max]"); return RMIPS_ERR_K_RANGE; }
   // the same range rule as the filter: a value whose copy in the index's
   // filter format would overflow (FP16: |x| > 65504) is refused here, so that
@@ -264,28 +301,45 @@ rmips_status check_request(const rmips_index* idx, const float* q, int32_t k, co
       set_error("non-finite value in a query (or, for a BF16 / FP16 index, one beyond that format's range)");
       return RMIPS_ERR_NONFINITE;
     }
+  *segment_size = idx->n;
   if (seg) {
-    if (seg->reserved != 0 || seg->kind < 0 || seg->kind > 2) { set_error("bad segment"); return RMIPS_ERR_ARG; }
-    if (seg->kind == 1 && (seg->begin < 0 || seg->end < seg->begin)) { set_error("bad segment range"); return RMIPS_ERR_ARG; }
+    if (seg->reserved != 0 || seg->kind < 0 || seg->kind > 3) { set_error("bad segment"); return RMIPS_ERR_ARG; }
+    if (seg->kind == 1) {
+      if (seg->begin < 0 || seg->end < seg->begin) { set_error("bad segment range"); return RMIPS_ERR_ARG; }
+      const int64_t hi = seg->end < idx->n ? seg->end : idx->n;
+      *segment_size = hi > seg->begin ? hi - seg->begin : 0;
+    }
     if (seg->kind == 2) {
       if (seg->n_ids < 0 || (seg->n_ids > 0 && !seg->ids)) { set_error("bad segment list"); return RMIPS_ERR_ARG; }
       for (int64_t i = 0; i < seg->n_ids; ++i)
         if (seg->ids[i] < 0 || seg->ids[i] >= idx->n) { set_error("segment id out of range"); return RMIPS_ERR_ARG; }
+      *segment_size = seg->n_ids;
+    }
+    if (seg->kind == 3) {
+      if (seg->begin < 0 || seg->begin >= (int64_t)S->segs.size()) { set_error("unknown segment handle"); return RMIPS_ERR_ARG; }
+      *segment_size = (int64_t)S->segs[(size_t)seg->begin].size();
     }
   }
   return RMIPS_OK;
 }
 
-Request* make_request(const rmips_index* idx, const float* q, int32_t k, const rmips_segment* seg) {
+Request* make_request(const rmips_server* S, const float* q, int32_t k, const rmips_segment* seg, int64_t seg_size) {
   Request* r = new Request();
-  r->q.assign(q, q + idx->d);
+  r->q.assign(q, q + S->idx->d);
   r->k = k;
   if (seg) {
     r->kind = seg->kind;
     r->lo = seg->begin;
     r->hi = seg->end;
-    if (seg->kind == 2) r->list.assign(seg->ids, seg->ids + seg->n_ids);
+    if (seg->kind == 2) {
+      r->list.assign(seg->ids, seg->ids + seg->n_ids);
+      std::sort(r->list.begin(), r->list.end());
+      r->list.erase(std::unique(r->list.begin(), r->list.end()), r->list.end());
+    }
+    if (seg->kind == 3) r->handle = (int32_t)seg->begin;
   }
+  const int64_t per = S->o.result_ids_per_request;
+  r->reserve = seg_size < per ? (seg_size > 0 ? seg_size : 1) : per;
   r->t0 = Clock::now();
   return r;
 }
@@ -300,21 +354,30 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
   o.max_wait_us = 200;
   o.streams = 2;
   o.max_pending = 1 << 20;
-  o.max_result_ids = 0;
   if (opts) o = *opts;
   if (o.max_batch < 1 || o.max_batch > MQ_MAXQ || o.max_wait_us < 0 || o.streams < 1 || o.streams > 16 ||
-      o.max_pending < 1 || o.max_result_ids < 0 || o.reserved != 0) {
+      o.max_pending < 1 || o.max_device_bytes < 0 || o.result_ids_per_request < 0 || o.reserved != 0) {
     set_error("bad server options (max_batch 1..16384, streams 1..16)");
     return RMIPS_ERR_ARG;
   }
-  if (o.max_result_ids == 0) o.max_result_ids = (int64_t)o.max_batch * 256;
-  rmips_server* S = new rmips_server();
-  S->idx = idx;
-  S->o = o;
-  S->slots.resize(o.streams);
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(idx->device);
+  if (o.result_ids_per_request == 0) o.result_ids_per_request = 1024;
+  if (o.max_device_bytes == 0) {               // an eighth of the free device memory, at most 256 MiB
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+    const size_t cap = (size_t)256 << 20;
+    o.max_device_bytes = (int64_t)(fr / 8 < cap ? fr / 8 : cap);
+  }
+  // each slot's result buffer: its share of the budget, at least one request's reservation
+  int64_t cap_out = o.max_device_bytes / (8 * (int64_t)o.streams);
+  if (cap_out < o.result_ids_per_request) cap_out = o.result_ids_per_request;
+  rmips_server* S = new rmips_server();
+  S->idx = idx;
+  S->o = o;
+  S->capacity = cap_out * o.streams;
+  S->slots.resize(o.streams);
   rmips_status st = RMIPS_OK;
   for (Slot& sl : S->slots) {
     sl.ws = acquire_workspace(idx, &st);
@@ -332,8 +395,9 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_hi, o.max_batch * sizeof(long long), 0);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_offs, (o.max_batch + 1) * sizeof(long long), 0);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_ctr, C_NCOUNTERS * sizeof(long long), 0);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_out, o.max_result_ids * sizeof(long long), cudaHostAllocMapped);
-    sl.cap_out = o.max_result_ids;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_out, (size_t)cap_out * sizeof(long long));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_out, (size_t)cap_out * sizeof(long long), cudaHostAllocMapped);
+    sl.cap_out = cap_out;
     if (e != cudaSuccess) {
       set_error(std::string("server allocation: ") + cudaGetErrorString(e));
       st = e == cudaErrorMemoryAllocation ? RMIPS_ERR_OOM : RMIPS_ERR_CUDA;
@@ -351,6 +415,21 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
   return RMIPS_OK;
 }
 
+extern "C" rmips_status rmips_server_add_segment(rmips_server* S, const int64_t* ids, int64_t n_ids, int32_t* handle) {
+  if (!S || !handle || n_ids < 0 || (n_ids > 0 && !ids)) { set_error("null argument"); return RMIPS_ERR_ARG; }
+  if (ptr_class(ids, S->idx->device) != PTR_HOST) { set_error("segment ids are given in host memory"); return RMIPS_ERR_ARG; }
+  std::vector<int64_t> v(ids, ids + n_ids);
+  for (int64_t id : v)
+    if (id < 0 || id >= S->idx->n) { set_error("segment id out of range"); return RMIPS_ERR_ARG; }
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->segs.size() >= (size_t)INT32_MAX) { set_error("too many segments"); return RMIPS_ERR_ARG; }
+  S->segs.push_back(std::move(v));
+  *handle = (int32_t)(S->segs.size() - 1);
+  return RMIPS_OK;
+}
+
 extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* qs, int64_t nq, const int32_t* ks,
                                                  const rmips_segment* segs, int64_t* tickets) {
   if (!S || nq < 0 || (nq > 0 && (!qs || !ks || !tickets))) { set_error("null argument"); return RMIPS_ERR_ARG; }
@@ -359,12 +438,20 @@ extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* q
     return RMIPS_ERR_ARG;
   }
   const int d = S->idx->d;
-  for (int64_t j = 0; j < nq; ++j) {
-    rmips_status st = check_request(S->idx, qs + j * d, ks[j], segs ? &segs[j] : nullptr);
-    if (st != RMIPS_OK) return st;
+  std::vector<int64_t> sizes((size_t)nq);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);      // registered segments
+    for (int64_t j = 0; j < nq; ++j) {
+      rmips_status st = check_request(S, qs + j * d, ks[j], segs ? &segs[j] : nullptr, &sizes[j]);
+      if (st != RMIPS_OK) return st;
+    }
   }
   std::vector<Request*> rs(nq);
-  for (int64_t j = 0; j < nq; ++j) rs[j] = make_request(S->idx, qs + j * d, ks[j], segs ? &segs[j] : nullptr);
+  int64_t need = 0;
+  for (int64_t j = 0; j < nq; ++j) {
+    rs[j] = make_request(S, qs + j * d, ks[j], segs ? &segs[j] : nullptr, sizes[j]);
+    need += rs[j]->reserve;
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) {
@@ -372,10 +459,10 @@ extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* q
       set_error("server is stopping");
       return RMIPS_ERR_ARG;
     }
-    if (S->pending + nq > S->o.max_pending) {
+    if (S->pending + nq > S->o.max_pending || S->reserved + need > S->capacity) {
       for (Request* r : rs) delete r;
       S->rejected += nq;
-      set_error("admission refused: too many requests pending");
+      set_error("admission refused: the pending requests' result reservations or count are at the limit");
       return RMIPS_ERR_BUSY;
     }
     for (int64_t j = 0; j < nq; ++j) {
@@ -385,6 +472,7 @@ extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* q
       tickets[j] = t;
     }
     S->pending += nq;
+    S->reserved += need;
     S->submitted += nq;
   }
   S->cv_in.notify_one();
@@ -504,6 +592,9 @@ extern "C" rmips_status rmips_server_get_stats(rmips_server* S, rmips_server_sta
     s.batches = S->batches;
     s.mean_batch = S->batches ? (double)S->batched / S->batches : 0.0;
     s.pending = S->pending;
+    s.reserved_ids = S->reserved;
+    s.reservable_ids = S->capacity;
+    s.batches_one_by_one = S->one_by_one;
   }
   if (!v.empty()) {
     std::sort(v.begin(), v.end());
@@ -539,6 +630,7 @@ extern "C" void rmips_server_destroy(rmips_server* S) {
     cudaFreeHost(sl.h_offs);
     cudaFreeHost(sl.h_ctr);
     cudaFreeHost(sl.h_out);
+    cudaFree(sl.d_out);
   }
   for (auto& kv : S->reqs) delete kv.second;
   delete S;

@@ -19,7 +19,7 @@ __all__ = [
     "rmips_query_batch", "rmips_query_batch_async", "rmips_index_get_info", "rmips_last_query_stats",
     "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
     "rmips_index_export", "rmips_free_index", "rmips_status_string", "rmips_exact_sign_host",
-    "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "rmips_query_async", "EXPORTED_SYMBOLS",
+    "rmips_profile_enable", "rmips_profile_read", "rmips_query_noalloc", "rmips_query_async", "rmips_index_tune", "EXPORTED_SYMBOLS",
     "FP32", "BF16", "FP16", "Server",
 ]
 
@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = [
     "rmips_query_noalloc", "rmips_debug_tc_tile", "rmips_server_create", "rmips_server_submit",
     "rmips_server_submit_many", "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
     "rmips_server_destroy", "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
-    "rmips_query_async",
+    "rmips_query_async", "rmips_index_tune", "rmips_server_add_segment",
 ]
 
 
@@ -48,7 +48,7 @@ class RmipsError(RuntimeError):
 
 class BuildOpts(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("block_size", C.c_int32), ("p_prime", C.c_int64),
-                ("precision", C.c_int32), ("flags", C.c_int32)]
+                ("precision", C.c_int32), ("flags", C.c_int32), ("tune_cache", C.c_char_p)]
 
 
 class Segment(C.Structure):
@@ -60,7 +60,8 @@ class IndexInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("d", C.c_int32), ("k_max", C.c_int32),
                 ("block_size", C.c_int32), ("precision", C.c_int32), ("n_blocks", C.c_int64),
                 ("p_prime", C.c_int64), ("incomplete", C.c_int64), ("device_bytes", C.c_int64),
-                ("build_ms", C.c_double)]
+                ("build_ms", C.c_double), ("tuned", C.c_int32), ("batch_stages", C.c_int32),
+                ("single_stages", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -74,13 +75,15 @@ class Profile(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("streams", C.c_int32),
-                ("reserved", C.c_int32), ("max_pending", C.c_int64), ("max_result_ids", C.c_int64)]
+                ("reserved", C.c_int32), ("max_pending", C.c_int64), ("max_device_bytes", C.c_int64),
+                ("result_ids_per_request", C.c_int64)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64),
                 ("pending", C.c_int64), ("batches", C.c_int64), ("mean_batch", C.c_double),
-                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double)]
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("reserved_ids", C.c_int64), ("reservable_ids", C.c_int64), ("batches_one_by_one", C.c_int64)]
 
 
 class QueryStats(C.Structure):
@@ -112,6 +115,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_query_batch.argtypes = [VP, P, I64, P, C.POINTER(Segment), P, I64, P, VP]
         lib.rmips_query_batch_async.argtypes = [VP, P, I64, P, P, I64, P, P, VP]
         lib.rmips_query_async.argtypes = [VP, P, I32, P, I64, P, VP]
+        lib.rmips_index_tune.argtypes = [VP, C.c_char_p, VP]
         lib.rmips_index_save.argtypes = [VP, C.c_char_p]
         lib.rmips_index_load.argtypes = [C.c_char_p, VP, C.POINTER(VP)]
         lib.rmips_index_rebuild.argtypes = [VP, I32, VP, C.POINTER(VP)]
@@ -138,6 +142,7 @@ def load_library(build_if_missing: bool = True):
         lib.rmips_server_get_stats.argtypes = [VP, C.POINTER(ServerStats)]
         lib.rmips_server_wait_many.argtypes = [VP, P, I64, P, I64, P, P, I32]
         lib.rmips_server_destroy.argtypes = [VP]
+        lib.rmips_server_add_segment.argtypes = [VP, P, I64, C.POINTER(C.c_int32)]
         lib.rmips_server_destroy.restype = None
         for name in ("rmips_build_index", "rmips_query", "rmips_query_batch", "rmips_query_batch_async",
                      "rmips_index_save", "rmips_index_load", "rmips_index_rebuild", "rmips_topk_join",
@@ -146,7 +151,7 @@ def load_library(build_if_missing: bool = True):
                      "rmips_profile_read", "rmips_query_noalloc", "rmips_debug_tc_tile",
                      "rmips_server_create", "rmips_server_submit", "rmips_server_submit_many",
                      "rmips_server_wait", "rmips_server_wait_many", "rmips_server_get_stats",
-                     "rmips_query_async"):
+                     "rmips_query_async", "rmips_index_tune", "rmips_server_add_segment"):
             getattr(lib, name).restype = I32
         _lib = lib
         return lib
@@ -196,7 +201,9 @@ def _segment(seg, keep):
     if seg is None:
         return None
     s = Segment()
-    if isinstance(seg, tuple) and len(seg) == 2:
+    if isinstance(seg, tuple) and len(seg) == 2 and seg[0] == "registered":
+        s.kind, s.begin = 3, int(seg[1])
+    elif isinstance(seg, tuple) and len(seg) == 2:
         s.kind, s.begin, s.end = 1, int(seg[0]), int(seg[1])
     else:
         ids = np.ascontiguousarray(seg, dtype=np.int64)
@@ -237,12 +244,15 @@ class Index:
 
 def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
                       precision="fp32", batch_tensor_cores: bool = True, build_tensor_cores: bool = True,
-                      block_filter: bool = True, stream=None) -> Index:
+                      block_filter: bool = True, autotune: bool = False, tune_cache: str | None = None,
+                      stream=None) -> Index:
     """Build the index of Algorithm 1 from users Q [n, d] and items P [m, d].
 
     ``batch_tensor_cores=False`` keeps the batched filter on CUDA cores;
     ``build_tensor_cores=False`` selects candidates on CUDA cores;
-    ``block_filter=False`` switches Lemma 3 off (the no-blocks ablation)."""
+    ``block_filter=False`` switches Lemma 3 off (the no-blocks ablation);
+    ``autotune=True`` (or a ``tune_cache`` file) ends the build with the
+    autotuner (``rmips_index_tune``)."""
     load_library()
     qp, qk = _ptr_f32(Q)
     pp, pk = _ptr_f32(P)
@@ -252,7 +262,8 @@ def rmips_build_index(Q, P, k_max: int, block_size: int = 32, p_prime: int = 0,
         raise RmipsError(1, "Q and P differ in dimension")
     opts = BuildOpts(int(k_max), int(block_size), int(p_prime), _PREC[precision],
                      (0 if batch_tensor_cores else 1) | (0 if build_tensor_cores else 2) |
-                     (0 if block_filter else 4))
+                     (0 if block_filter else 4) | (8 if autotune else 0),
+                     tune_cache.encode() if tune_cache else None)
     out = C.c_void_p()
     _check(_lib.rmips_build_index(qp, n, pp, m, d, C.byref(opts), _stream(stream), C.byref(out)))
     return Index(out.value, n, m, d, int(k_max))
@@ -397,6 +408,12 @@ def rmips_query_async(index: Index, q, k: int, out, done, stream=None):
                                   done.data_ptr(), _stream(stream)))
 
 
+def rmips_index_tune(index: Index, tune_cache: str | None = None, stream=None) -> dict:
+    """Run the autotuner on an index; returns the index info with the choices."""
+    _check(_lib.rmips_index_tune(index.handle, tune_cache.encode() if tune_cache else None, _stream(stream)))
+    return rmips_index_get_info(index)
+
+
 def rmips_index_get_info(index: Index) -> dict:
     info = IndexInfo()
     _check(_lib.rmips_index_get_info(index.handle, C.byref(info)))
@@ -465,14 +482,21 @@ class Server:
     """Continuous-batching request loop over an index (see ``include/rmips.h``)."""
 
     def __init__(self, index: Index, max_batch: int = 4096, max_wait_us: int = 200, streams: int = 2,
-                 max_pending: int = 1 << 20, max_result_ids: int = 0):
+                 max_pending: int = 1 << 20, max_device_bytes: int = 0, result_ids_per_request: int = 0):
         load_library()
         self.index = index                       # keeps the index alive
         opts = ServerOpts(int(max_batch), int(max_wait_us), int(streams), 0, int(max_pending),
-                          int(max_result_ids))
+                          int(max_device_bytes), int(result_ids_per_request))
         h = C.c_void_p()
         _check(_lib.rmips_server_create(index.handle, C.byref(opts), C.byref(h)))
         self.handle = h
+
+    def add_segment(self, ids) -> int:
+        """Registers a user segment; use it as the segment ``("registered", handle)``."""
+        a = np.ascontiguousarray(ids, np.int64)
+        h = C.c_int32(0)
+        _check(_lib.rmips_server_add_segment(self.handle, a.ctypes.data, a.shape[0], C.byref(h)))
+        return h.value
 
     def submit(self, q, k: int, segment=None) -> int:
         keep = []

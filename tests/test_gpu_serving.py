@@ -110,7 +110,10 @@ def test_admission_and_bad_requests_do_not_stop_the_loop(setup):
 def test_small_result_budget_falls_back_per_request(setup):
     Q, P, index = setup
     qs, ks, _ = _requests(P, 40, 3)
-    srv = rmips.Server(index, max_batch=40, max_wait_us=2000, streams=1, max_result_ids=8)
+    # a result budget of 64 ids per slot, with reservations of 8 ids: most
+    # batches hold more results than their buffer and are re-run request by request
+    srv = rmips.Server(index, max_batch=40, max_wait_us=2000, streams=1, max_device_bytes=64 * 8,
+                       result_ids_per_request=8)
     tickets = srv.submit_many(qs, ks.astype(np.int32))
     for j, t in enumerate(tickets):
         ids, _ = srv.wait(int(t))
@@ -147,3 +150,51 @@ def test_fp16_out_of_range_request_is_refused_alone():
     assert st["completed"] == 10 and st["pending"] == 0
     srv.close()
     index.close()
+
+
+def test_registered_segments_and_id_lists_are_answered_in_the_batch(setup):
+    Q, P, index = setup
+    rng = np.random.default_rng(21)
+    srv = rmips.Server(index, max_batch=256, max_wait_us=3000, streams=2)
+    subsets = [np.sort(rng.choice(3000, s, replace=False)) for s in (5, 700, 2999)]
+    handles = [srv.add_segment(np.concatenate([x, x[:3]])) for x in subsets]   # duplicates are dropped
+    qs, ks, _ = _requests(P, 90, 22)
+    segs = [("registered", handles[j % 3]) if j % 2 == 0 else subsets[j % 3] for j in range(len(qs))]
+    tickets = srv.submit_many(qs, ks.astype(np.int32), segs)
+    ids, offs, _ = srv.wait_many(tickets)
+    for j in range(len(qs)):
+        alone = rmips.rmips_query(index, qs[j], int(ks[j]), segment=subsets[j % 3])
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], alone), j
+    st = srv.stats()
+    assert st["batches"] <= 3 and st["batches_one_by_one"] == 0     # no single-query detour
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit(qs[0], 5, ("registered", 17))
+    assert e.value.status == 1
+    srv.close()
+
+
+def test_admission_by_result_memory(setup):
+    Q, P, index = setup
+    # one stream, a result buffer of 200 ids, 50 ids reserved per request:
+    # at most four requests can be queued or running at once
+    srv = rmips.Server(index, max_batch=64, max_wait_us=200000, streams=1, max_device_bytes=200 * 8,
+                       result_ids_per_request=50)
+    st = srv.stats()
+    assert st["reservable_ids"] == 200
+    t4 = srv.submit_many(P[:4], 10)
+    assert srv.stats()["reserved_ids"] == 200
+    with pytest.raises(rmips.RmipsError) as e:
+        srv.submit(P[4], 10)
+    assert e.value.status == 9
+    # a request whose segment is smaller reserves less
+    small = srv.stats()
+    ids, offs, _ = srv.wait_many(t4)
+    for j in range(4):
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], rmips.rmips_query(index, P[j], 10))
+    assert srv.stats()["reserved_ids"] == 0
+    t = srv.submit(P[5], 10, segment=(0, 20))               # 20 users: reserves 20 ids
+    assert srv.stats()["reserved_ids"] == 20
+    got, _ = srv.wait(t)
+    assert np.array_equal(got, rmips.rmips_query(index, P[5], 10, segment=(0, 20)))
+    assert small["rejected"] == 1
+    srv.close()
