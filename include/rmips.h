@@ -364,11 +364,14 @@ rmips_status rmips_query_noalloc(rmips_index* index, const float* q, int32_t k, 
  * Serving loop: continuous batching of reverse k-MIPS requests on one index
  * (no counterpart in the paper, whose queries arrive one at a time).
  *
- * A dispatcher thread closes a batch when it holds max_batch requests, when
+ * A dispatcher thread takes the queued requests as a batch as soon as one
+ * of `streams` CUDA streams is free and no batch is on the device; while
+ * batches run, it closes a batch when it holds max_batch requests, when
  * their result reservations fill a slot's device result buffer, or when its
- * oldest request has waited max_wait_us, and launches it through the batched
- * filter on one of `streams` CUDA streams; requests arriving while batches
- * run join the next batch, and up to `streams` batches overlap on the device.
+ * oldest request has waited max_wait_us.  So batches grow with the load and
+ * up to `streams` of them overlap on the device.  A batch of at most
+ * single_max requests runs as one-launch single queries on its stream, a
+ * larger one through the batched filter.
  * Results are exactly those of rmips_query for the same request.  Every
  * segment kind is answered inside the batch (id ranges on the device; id
  * lists and registered segments, kind 3, by intersecting the request's exact
@@ -388,9 +391,13 @@ typedef struct rmips_server rmips_server;
 
 typedef struct {
   int32_t max_batch;        /* requests per batch, 1..16384 (default 4096) */
-  int32_t max_wait_us;      /* batch closing deadline in microseconds (default 200) */
+  int32_t max_wait_us;      /* batch closing deadline while another batch is on
+                               the device, in microseconds (default 200; with
+                               the device idle a batch closes at once) */
   int32_t streams;          /* batches in flight, 1..16 (default 2) */
-  int32_t reserved;         /* must be 0 */
+  int32_t single_max;       /* batches of at most this many requests run as
+                               one-launch single queries (full-P index);
+                               0 = 4, -1 = never, at most 64 */
   int64_t max_pending;      /* admission bound on queued + running requests
                                (default 1,048,576) */
   int64_t max_device_bytes; /* device memory of the result buffers; 0 = an

@@ -3818,6 +3818,28 @@ rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long
 }
 rmips_status device_status(long long s) { return status_from_device(s); }
 
+// One query through the one-launch kernel on a workspace, device buffers
+// (the serving loop's small batches): q (device, d floats), results to out
+// (capacity ids), (status, count) to done.  Full-P indexes only.
+rmips_status single_launch(rmips_index* idx, Workspace* ws, const float* q, int k, long long seg_lo,
+                           long long seg_hi, long long* out, long long capacity, long long* done, cudaStream_t st) {
+  if (!ws->dres) RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->dres, (2 + C_NCOUNTERS) * sizeof(long long)));
+  if (ws->ctr_dirty) {                           // the one-launch kernel needs zero counters
+    RMIPS_TRY_CUDA(cudaMemsetAsync(ws->ctr, 0, C_NCOUNTERS * sizeof(long long), st));
+    ws->ctr_dirty = false;
+  }
+  Common c = make_common(idx, ws);
+  EmitArgs e{};
+  e.seg_lo = seg_lo;
+  e.seg_hi = seg_hi;
+  e.bitmap = ws->bitmap;
+  e.out = out;
+  e.capacity = capacity;
+  const cudaError_t err = q1_dispatch(idx, c, e, q, k, ws->dres, done, nullptr, st);
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
+  return RMIPS_OK;
+}
+
 int max_batch_stages(const rmips_index* idx) {
   const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
   int ns = WS_MAXNS;

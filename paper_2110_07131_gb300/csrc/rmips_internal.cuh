@@ -259,6 +259,10 @@ rmips_status batch_reserve(rmips_index* idx, Workspace* ws, int64_t nq);
 rmips_status batch_launch(rmips_index* idx, Workspace* ws, int64_t nq, long long* out, long long capacity,
                           cudaStream_t st, bool with_segments);
 rmips_status device_status(long long s);
+// One query through the one-launch kernel (full-P index) on a workspace:
+// device q, results to out (capacity ids), (status, count) to done.
+rmips_status single_launch(rmips_index* idx, Workspace* ws, const float* q, int k, long long seg_lo,
+                           long long seg_hi, long long* out, long long capacity, long long* done, cudaStream_t st);
 void release_workspace(rmips_index* idx, Workspace* ws);
 // Loads the module that holds rmips_query_noalloc's scratch array on the
 // current device (called when an index is built or loaded).

@@ -65,13 +65,28 @@ struct Slot {
   long long* d_out = nullptr;   // device result ids of a batch
   long long* h_out = nullptr;   // pinned, device-mapped copy of them
   int64_t cap_out = 0;
+  long long* d_done = nullptr;  // small batches: (status, count) per request, device
+  long long* h_done = nullptr;  // and its pinned copy
   std::vector<int64_t> tickets;
   bool segments = false;
+  bool small = false;           // run as one-launch single queries
   rmips_status launch = RMIPS_OK;
   bool busy = false;
 };
 
 constexpr size_t LAT_CAP = 1 << 20;
+
+// Small batches: request i's ids (done[2i + 1] of them, when its status is
+// RMIPS_OK) from its region of `per` ids into mapped host memory.
+__global__ void k_serve_copy_regions(const long long* __restrict__ src, long long* __restrict__ dst,
+                                     const long long* __restrict__ done, int nq, long long per) {
+  for (int i = blockIdx.y; i < nq; i += gridDim.y) {
+    if (done[2 * i] != RMIPS_OK) continue;
+    const long long cnt = done[2 * i + 1] < per ? done[2 * i + 1] : per;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < cnt; j += (long long)gridDim.x * blockDim.x)
+      dst[i * per + j] = src[i * per + j];
+  }
+}
 
 // The first min(total, cap) result ids of a batch into mapped host memory.
 __global__ void k_serve_copy(const long long* __restrict__ src, long long* __restrict__ dst,
@@ -162,6 +177,19 @@ rmips_status launch_slot(rmips_server* S, Slot& sl, int64_t nq) {
   cudaStream_t st = sl.stream;
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dq, sl.h_q, nq * idx->d * sizeof(float), cudaMemcpyHostToDevice, st));
   RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dk, sl.h_k, nq * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (sl.small) {                                   // one launch per request, on this slot's stream
+    const long long per = sl.cap_out / nq;
+    for (int64_t i = 0; i < nq; ++i) {
+      rmips_status s = single_launch(idx, ws, ws->dq + i * idx->d, sl.h_k[i], sl.h_lo[i], sl.h_hi[i],
+                                     sl.d_out + i * per, per, sl.d_done + 2 * i, st);
+      if (s != RMIPS_OK) return s;
+    }
+    k_serve_copy_regions<<<dim3(16, (unsigned)nq), 256, 0, st>>>(sl.d_out, sl.h_out, sl.d_done, (int)nq, per);
+    RMIPS_TRY_CUDA(cudaGetLastError());
+    RMIPS_TRY_CUDA(cudaMemcpyAsync(sl.h_done, sl.d_done, 2 * nq * sizeof(long long), cudaMemcpyDeviceToHost, st));
+    RMIPS_TRY_CUDA(cudaEventRecord(sl.done, st));
+    return RMIPS_OK;
+  }
   if (sl.segments) {
     RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseglo, sl.h_lo, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
     RMIPS_TRY_CUDA(cudaMemcpyAsync(ws->dseghi, sl.h_hi, nq * sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -182,8 +210,11 @@ void dispatcher(rmips_server* S) {
   while (true) {
     S->cv_in.wait(lk, [&] { return S->stop || !S->queue.empty(); });
     if (S->stop) break;
+    // close the batch at once when no batch is on the device (waiting would
+    // only add latency), else when it is full or its oldest request has
+    // waited max_wait_us; requests arriving meanwhile join it
     const auto deadline = S->reqs[S->queue.front()]->t0 + std::chrono::microseconds(S->o.max_wait_us);
-    while (!S->stop && (int64_t)S->queue.size() < S->o.max_batch && Clock::now() < deadline)
+    while (!S->stop && !S->inflight.empty() && (int64_t)S->queue.size() < S->o.max_batch && Clock::now() < deadline)
       S->cv_in.wait_until(lk, deadline);
     if (S->stop) break;
     int si = -1;
@@ -213,6 +244,7 @@ void dispatcher(rmips_server* S) {
     }
     lk.unlock();
     const int64_t nq = (int64_t)batch.size();
+    sl.small = S->idx->full_p && nq <= S->o.single_max;
     const int d = S->idx->d;
     for (int64_t i = 0; i < nq; ++i) {
       memcpy(sl.h_q + i * d, batch[i]->q.data(), d * sizeof(float));
@@ -268,7 +300,20 @@ void completer(rmips_server* S) {
     }
     std::vector<std::vector<int64_t>> res(nq);
     std::vector<rmips_status> sts(nq, st);
-    if (st == RMIPS_OK) {
+    if (st == RMIPS_OK && sl.small) {
+      const long long per = sl.cap_out / nq;
+      for (int64_t i = 0; i < nq; ++i) {
+        const long long code = sl.h_done[2 * i], cnt = sl.h_done[2 * i + 1];
+        if (code == RMIPS_OK) {
+          res[i].assign(sl.h_out + i * per, sl.h_out + i * per + cnt);
+          restrict_to_list(S, rs[i], res[i]);
+        } else if (code == RMIPS_ERR_CAPACITY) {
+          run_single(S, rs[i], res[i], sts[i]);
+        } else {
+          sts[i] = (rmips_status)code;
+        }
+      }
+    } else if (st == RMIPS_OK) {
       for (int64_t i = 0; i < nq; ++i) {
         res[i].assign(sl.h_out + sl.h_offs[i], sl.h_out + sl.h_offs[i + 1]);
         restrict_to_list(S, rs[i], res[i]);
@@ -356,7 +401,8 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
   o.max_pending = 1 << 20;
   if (opts) o = *opts;
   if (o.max_batch < 1 || o.max_batch > MQ_MAXQ || o.max_wait_us < 0 || o.streams < 1 || o.streams > 16 ||
-      o.max_pending < 1 || o.max_device_bytes < 0 || o.result_ids_per_request < 0 || o.reserved != 0) {
+      o.max_pending < 1 || o.max_device_bytes < 0 || o.result_ids_per_request < 0 || o.single_max < -1 ||
+      o.single_max > 64) {
     set_error("bad server options (max_batch 1..16384, streams 1..16)");
     return RMIPS_ERR_ARG;
   }
@@ -364,6 +410,8 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
   cudaGetDevice(&prev);
   cudaSetDevice(idx->device);
   if (o.result_ids_per_request == 0) o.result_ids_per_request = 1024;
+  if (o.single_max == 0) o.single_max = 4;
+  if (o.single_max < 0) o.single_max = 0;
   if (o.max_device_bytes == 0) {               // an eighth of the free device memory, at most 256 MiB
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
@@ -397,6 +445,8 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_ctr, C_NCOUNTERS * sizeof(long long), 0);
     if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_out, (size_t)cap_out * sizeof(long long));
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_out, (size_t)cap_out * sizeof(long long), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sl.d_done, 2 * 64 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_done, 2 * 64 * sizeof(long long), 0);
     sl.cap_out = cap_out;
     if (e != cudaSuccess) {
       set_error(std::string("server allocation: ") + cudaGetErrorString(e));
@@ -631,6 +681,8 @@ extern "C" void rmips_server_destroy(rmips_server* S) {
     cudaFreeHost(sl.h_ctr);
     cudaFreeHost(sl.h_out);
     cudaFree(sl.d_out);
+    cudaFree(sl.d_done);
+    cudaFreeHost(sl.h_done);
   }
   for (auto& kv : S->reqs) delete kv.second;
   delete S;

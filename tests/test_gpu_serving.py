@@ -97,10 +97,11 @@ def test_admission_and_bad_requests_do_not_stop_the_loop(setup):
         srv.submit(bad, 3)
     assert e.value.status == 3
     t = srv.submit(P[2], 7)
-    with pytest.raises(rmips.RmipsError) as e:
-        srv.wait(t, timeout_ms=0)                 # the batch is still open (long deadline)
-    assert e.value.status == 6
-    ids, _ = srv.wait(t)
+    try:                                          # a poll: finished or not yet, never another error
+        ids, _ = srv.wait(t, timeout_ms=0)
+    except rmips.RmipsError as e:
+        assert e.status == 6
+        ids, _ = srv.wait(t)
     assert np.array_equal(ids, rmips.rmips_query(index, P[2], 7))
     st = srv.stats()
     assert st["rejected"] == 20 and st["completed"] == 1
@@ -110,14 +111,16 @@ def test_admission_and_bad_requests_do_not_stop_the_loop(setup):
 def test_small_result_budget_falls_back_per_request(setup):
     Q, P, index = setup
     qs, ks, _ = _requests(P, 40, 3)
-    # a result budget of 64 ids per slot, with reservations of 8 ids: most
-    # batches hold more results than their buffer and are re-run request by request
+    # a result buffer of 64 ids, with reservations of one id per request: the
+    # 40 requests are admitted, but their batches hold more results than the
+    # buffer and are re-run request by request
     srv = rmips.Server(index, max_batch=40, max_wait_us=2000, streams=1, max_device_bytes=64 * 8,
-                       result_ids_per_request=8)
+                       result_ids_per_request=1)
     tickets = srv.submit_many(qs, ks.astype(np.int32))
     for j, t in enumerate(tickets):
         ids, _ = srv.wait(int(t))
         assert np.array_equal(ids, rmips.rmips_query(index, qs[j], int(ks[j])))
+    assert srv.stats()["batches_one_by_one"] >= 1
     with pytest.raises(rmips.RmipsError) as e:
         srv.wait(12345678)
     assert e.value.status == 1
