@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--plain-queries", type=int, default=400)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU baseline time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=60000, help="requests per serving run (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=1.0e6, help="offered load of the paced serving run (q/s)")
+    ap.add_argument("--serve-requests", type=int, default=100000,
+                    help="largest number of requests of a serving run (0: skip)")
     ap.add_argument("--single-queries", type=int, default=2000,
                     help="device-resident single queries launched back to back (0: skip)")
     ap.add_argument("--no-extras", action="store_true",
@@ -229,50 +229,132 @@ def reduce_over_ranks(ms: float, units: float, dist=None, device=None):
 
 
 # --------------------------------------------------------------------------- serving
-def run_serving(rmips, index, qs, a):
-    """Continuous batching through rmips_server_*: a saturating burst and a
-    paced open-loop run.  Latencies are measured inside the library from
-    submit to completion; a separate warm-up server runs first (its slots'
-    workspaces return to the index and are reused)."""
+def serving_requests(P, n, d, n_req, seed):
+    """The serving workload's requests: q a random item of P or a random
+    N(0, I/d) vector (half each), k uniform in 1..25, and a user segment: none
+    (a third), a contiguous id range of log-uniform size in 1e3..1e6 (a third)
+    or one of 8 random id subsets of log-uniform size in 1e3..1e6 (a third).
+    Returns (qs, ks, segs, subsets); segs[i] is None, (lo, hi) or ("subset", j)."""
+    rng = np.random.default_rng(seed)
+    qi, _ = datagen.queries_from_items(P, n_req, seed)
+    qr = datagen.random_queries(n_req, d, seed)
+    pick = rng.random(n_req) < 0.5
+    qs = np.where(pick[:, None], qi, qr).astype(np.float32)
+    ks = rng.integers(1, 26, n_req).astype(np.int32)
+    hi_size = min(n, 1_000_000)
+    subsets = [np.sort(rng.choice(n, int(min(hi_size, 10 ** rng.uniform(3, 6))), replace=False)) for _ in range(8)]
+    segs = []
+    for i in range(n_req):
+        r = i % 3
+        if r == 0:
+            segs.append(None)
+        elif r == 1:
+            size = int(min(hi_size, 10 ** rng.uniform(3, 6)))
+            lo = int(rng.integers(0, max(1, n - size + 1)))
+            segs.append((lo, lo + size))
+        else:
+            segs.append(("subset", int(rng.integers(0, 8))))
+    return qs, ks, segs, subsets
+
+
+def run_serving(rmips, index, P, a):
+    """Served (rmips_server_*) against plain (one rmips_query per request)
+    latency at the same offered loads.  Arrivals follow a Poisson process at
+    each rate; a request's latency runs from its scheduled arrival to the
+    moment its result is available to the caller (for the server: the
+    library's submit-to-completion time plus the submitter's lag behind the
+    schedule).  The plain path takes the requests in arrival order on one
+    host thread, so at a rate above what it can carry its queue, and its
+    latency, grow for as long as the run lasts."""
     import threading
-    n_req = min(a.serve_requests, len(qs))
+    rates = [20_000.0, 200_000.0, 1_000_000.0]
+    n_serve = {20_000.0: 10_000, 200_000.0: 40_000, 1_000_000.0: 100_000}
+    n_plain = {20_000.0: 10_000, 200_000.0: 4_000, 1_000_000.0: 4_000}
+    n_req = min(a.serve_requests, max(n_serve.values())) if a.serve_requests > 0 else 0
+    qs, ks, segs, subsets = serving_requests(P, a.n, a.d, max(n_req, 1), 41)
     opts = dict(max_batch=4096, max_wait_us=200, streams=2, max_pending=1 << 21)
     warm = rmips.Server(index, **opts)
-    warm.wait_many(warm.submit_many(qs[:4096], a.k))
+    warm.wait_many(warm.submit_many(qs[:4096], ks[:4096]))
     warm.close()
-    out = {}
-    for mode in ("saturated", "paced"):
+    out = {"workload": "Poisson arrivals; q = random item of P or random N(0, I/d) (half each); k uniform in "
+                       "1..25; segment: none / contiguous id range / registered random id subset (a third each), "
+                       "segment sizes log-uniform in 1e3..1e6",
+           "server": "rmips_server: max_batch 4096, max_wait_us 200 while a batch is on the device (a batch "
+                     "closes at once when the device is idle), 2 streams, batches of up to 4 requests as "
+                     "one-launch single queries; admission by device result memory",
+           "plain": "rmips_query per request on one host thread, host q and ids, segments as id ranges / id lists",
+           "rates": []}
+    for rate in rates:
+        nr = min(n_req, n_serve[rate])
+        if nr <= 0:
+            break
+        rng = np.random.default_rng(int(rate))
+        arrive = np.cumsum(rng.exponential(1.0 / rate, nr))
         srv = rmips.Server(index, **opts)
-        chunks = []
-        n_chunks = (n_req + 1023) // 1024
+        handles = [srv.add_segment(x) for x in subsets]
+        sseg = [(("registered", handles[sg[1]]) if isinstance(sg, tuple) and sg[0] == "subset" else sg)
+                for sg in segs[:nr]]
+        groups, lags = [], np.zeros(nr)
+        done_groups = []
 
         def collect():
             i = 0
-            while i < n_chunks:
-                if i < len(chunks):
-                    srv.wait_many(chunks[i])
+            while True:
+                if i < len(groups):
+                    g0, g1, tk = groups[i]
+                    if tk is None:
+                        break
+                    _, _, lat = srv.wait_many(tk)
+                    done_groups.append((g0, g1, lat))
                     i += 1
                 else:
-                    time.sleep(0.0002)
+                    time.sleep(0.0001)
 
         th = threading.Thread(target=collect)
         th.start()
         t0 = time.perf_counter()
-        for c0 in range(0, n_req, 1024):
-            if mode == "paced":
-                due = t0 + c0 / a.serve_rate
-                while time.perf_counter() < due:
-                    pass
-            chunks.append(srv.submit_many(qs[c0:c0 + 1024], a.k))
+        i = 0
+        while i < nr:
+            now = time.perf_counter() - t0
+            if arrive[i] > now:
+                continue
+            j = i
+            while j < nr and arrive[j] <= now and j - i < 1024:
+                j += 1
+            tk = srv.submit_many(qs[i:j], ks[i:j], sseg[i:j])
+            sub = time.perf_counter() - t0
+            lags[i:j] = sub - arrive[i:j]
+            groups.append((i, j, tk))
+            i = j
+        groups.append((nr, nr, None))
         th.join()
         el = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
-        out[mode] = {"qps": n_req / el, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                     "max_ms": st["max_ms"], "mean_batch": st["mean_batch"], "batches": st["batches"],
-                     "requests": n_req, "offered_qps": None if mode == "saturated" else a.serve_rate}
-    out["config"] = ("rmips_server: max_batch 4096, max_wait 200 us, 2 streams; k = 10; queries = random items "
-                     "of P submitted in chunks of 1024 from the host")
+        lat_s = np.zeros(nr)
+        for g0, g1, lat in done_groups:
+            lat_s[g0:g1] = lat + 1e3 * lags[g0:g1]
+        served = {"offered_qps": rate, "requests": nr, "achieved_qps": nr / el,
+                  "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+                  "max_ms": float(lat_s.max()), "mean_batch": st["mean_batch"], "batches": st["batches"],
+                  "mean_submit_lag_ms": float(1e3 * lags.mean())}
+        # plain path on the same schedule
+        npl = min(nr, n_plain[rate])
+        plat = np.zeros(npl)
+        t0 = time.perf_counter()
+        for i in range(npl):
+            while time.perf_counter() - t0 < arrive[i]:
+                pass
+            sg = segs[i]
+            if isinstance(sg, tuple) and sg[0] == "subset":
+                sg = subsets[sg[1]]
+            rmips.rmips_query(index, qs[i], int(ks[i]), segment=sg)
+            plat[i] = (time.perf_counter() - t0) - arrive[i]
+        pel = time.perf_counter() - t0
+        plain = {"offered_qps": rate, "requests": npl, "achieved_qps": npl / pel,
+                 "p50_ms": float(1e3 * np.percentile(plat, 50)), "p99_ms": float(1e3 * np.percentile(plat, 99)),
+                 "max_ms": float(1e3 * plat.max())}
+        out["rates"].append({"served": served, "plain": plain})
     return out
 
 
@@ -559,7 +641,7 @@ def run_ours(a):
              "slowest": [[float(lat_s[i]), int(sizes[skip + i])] for i in slow],
              "largest_result": int(max(sizes))}
 
-    serving = run_serving(rmips, index, qs, a) if a.serve_requests > 0 else None
+    serving = run_serving(rmips, index, P, a) if a.serve_requests > 0 else None
 
     # the top-k join over all users (Definition 1 for every user), device output
     join_s = None

@@ -291,9 +291,10 @@ void completer(rmips_server* S) {
       if (cudaEventSynchronize(sl.done) != cudaSuccess) {
         set_error("batch failed on the device");
         st = RMIPS_ERR_CUDA;
-      } else {
+      } else if (!sl.small) {
         // results past the buffer, or a full pair list (ties-heavy batch):
-        // answered one request at a time
+        // answered one request at a time (small batches carry a status per
+        // request instead)
         one_by_one = sl.h_ctr[C_STATUS] == ST_PAIRS_FULL || sl.h_ctr[C_STATUS] == ST_CAPACITY;
         st = device_status(sl.h_ctr[C_STATUS]);
       }

@@ -201,3 +201,21 @@ def test_admission_by_result_memory(setup):
     assert np.array_equal(got, rmips.rmips_query(index, P[5], 10, segment=(0, 20)))
     assert small["rejected"] == 1
     srv.close()
+
+
+def test_small_batches_run_as_single_launches(setup):
+    # every batch of up to 64 requests goes through the one-launch kernel on
+    # the slot's stream; segments of every kind, mixed k: the same results
+    Q, P, index = setup
+    srv = rmips.Server(index, max_batch=64, max_wait_us=500, streams=2, single_max=64)
+    qs, ks, segs = _requests(P, 160, 31)
+    h = srv.add_segment(np.arange(0, 3000, 3))
+    segs = [("registered", h) if j % 5 == 4 else sg for j, sg in enumerate(segs)]
+    tickets = [srv.submit(qs[j], int(ks[j]), segs[j]) for j in range(len(qs))]
+    for j, t in enumerate(tickets):
+        ids, _ = srv.wait(t)
+        sg = np.arange(0, 3000, 3) if j % 5 == 4 else segs[j]
+        assert np.array_equal(ids, rmips.rmips_query(index, qs[j], int(ks[j]), segment=sg)), j
+    st = srv.stats()
+    assert st["completed"] == len(qs) and st["batches_one_by_one"] == 0
+    srv.close()
