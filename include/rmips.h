@@ -119,7 +119,8 @@ typedef struct {
                             (0: as many as fit) */
   int32_t single_stages; /* row stages of the single-query kernel (0: as
                             many as fit) */
-  int32_t reserved;
+  int32_t build_kind;    /* operands of the build's tensor-core candidate
+                            selection: 0 TF32, 1 BF16, 2 FP16, -1 CUDA cores */
   double tune_ms;        /* wall time of the tuning */
 } rmips_index_info;
 

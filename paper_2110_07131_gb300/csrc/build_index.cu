@@ -269,37 +269,51 @@ __global__ void k_list_incomplete(const uint8_t* __restrict__ incomp, int64_t n,
   if (u < n && incomp[u]) list[atomicAdd(count, 1ull)] = (int32_t)u;
 }
 
-// --- 3'. top-KC candidates per user on tensor cores (TF32, d <= 64) ------------------
-// A CTA keeps 128 users (one per thread, TMEM lane = user) and streams every
-// 64-item tile of P' through one 128 x 64 x 64 TF32 MMA; items arrive by 1-D
-// TMA in the UMMA layout prepared by k_item_tiles.  Each thread keeps its
-// user's KC best (value, position) in shared memory and `uex`, an upper bound
-// on the exact inner product of every item it did not keep: a rejected item
-// adds its TF32 value plus ||u|| * TC_TF32_ERR * ||p|| (for a whole tile, the
-// tile's first item has the largest norm), an evicted item the same.
+// --- 3'. top-KC candidates per user on tensor cores (d <= 64) -------------------------
+// Operands in TF32 (float32 index) or in the index's BF16 / FP16 format, FP32
+// accumulation.  A CTA keeps 128 users (one per thread, TMEM lane = user) and
+// streams every 64-item tile of P' through one 128 x 64 x 64 MMA chain; items
+// arrive by 1-D TMA in the UMMA layout prepared by k_item_tiles.  Each thread
+// keeps its user's KC best (value, position) in shared memory and `uex`, an
+// upper bound on the exact inner product of every item it did not keep: a
+// rejected item adds its tensor-core value plus ||u|| tc_rel_err(kind) ||p||
+// and the absolute term of sub-normal 16-bit operands (for a whole tile, the
+// tile's first item has the largest norm), an evicted item the same.  The
+// float64 re-dot of the kept candidates (k_finalize) then makes the bounds
+// rigorous whatever the selection's precision.
 constexpr int TB_THREADS = 128;
 constexpr int TB_TILE = 64;
 
+template <int KIND>
 __global__ void k_item_tiles(const float* __restrict__ Ps, const float* __restrict__ pnorm, int64_t pp, int d,
-                             int64_t ntiles, float* __restrict__ Pt, float* __restrict__ cp) {
+                             int64_t ntiles, unsigned char* __restrict__ Pt, float* __restrict__ cp) {
+  constexpr uint32_t E = KIND == TCK_TF32 ? 4u : 2u;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e < ntiles * TB_TILE * (int64_t)TC_K) {
     const int64_t tile = e / (TB_TILE * TC_K);
     const int r = (int)((e / TC_K) % TB_TILE), k = (int)(e % TC_K);
     const int64_t p = tile * TB_TILE + r;
-    Pt[tile * (TB_TILE * TC_K) + tc_off(r, k) / 4] = (p < pp && k < d) ? Ps[p * d + k] : 0.f;
+    const float v = (p < pp && k < d) ? Ps[p * d + k] : 0.f;
+    unsigned char* base = Pt + (size_t)tile * (TB_TILE * TC_K * E);
+    if (KIND == TCK_TF32) *reinterpret_cast<float*>(base + tc_off(r, k)) = v;
+    else if (KIND == TCK_BF16) *reinterpret_cast<__nv_bfloat16*>(base + tc_off16(r, k)) = __float2bfloat16_rn(v);
+    else *reinterpret_cast<__half*>(base + tc_off16(r, k)) = __float2half_rn(v);
   }
-  if (e < ntiles * TB_TILE) cp[e] = e < pp ? __fmul_ru(pnorm[e], TC_TF32_ERR) : 0.f;
+  if (e < ntiles * TB_TILE) cp[e] = e < pp ? __fmul_ru(pnorm[e], tc_rel_err(KIND)) : 0.f;
 }
 
-__global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict__ Qs, const float* __restrict__ Pt,
+template <int KIND>
+__global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict__ Qs,
+                                                        const unsigned char* __restrict__ Pt,
                                                         const float* __restrict__ cp, const float* __restrict__ unorm,
-                                                        int64_t n, int64_t pp, int d, float* __restrict__ cval,
-                                                        int32_t* __restrict__ cid, float* __restrict__ uex_out,
-                                                        int* __restrict__ fail) {
+                                                        int64_t n, int64_t pp, int d, float pn0,
+                                                        float* __restrict__ cval, int32_t* __restrict__ cid,
+                                                        float* __restrict__ uex_out, int* __restrict__ fail) {
+  constexpr uint32_t E = KIND == TCK_TF32 ? 4u : 2u;
+  constexpr uint32_t SBO = KIND == TCK_TF32 ? TC_SBO : TC_SBO16;
   extern __shared__ __align__(1024) unsigned char tb[];
-  float* sA = reinterpret_cast<float*>(tb);                                        // 128 x 64 (32 KB)
-  float* sB = reinterpret_cast<float*>(tb + 32768);                                // 2 x (64 x 64)
+  unsigned char* sA = tb;                                                          // 128 x 64 (at most 32 KB)
+  unsigned char* sB = tb + 32768;                                                  // 2 x (64 x 64)
   float (*lv)[TB_THREADS] = reinterpret_cast<float (*)[TB_THREADS]>(tb + 65536);   // [KC][128]
   int32_t (*li)[TB_THREADS] = reinterpret_cast<int32_t (*)[TB_THREADS]>(tb + 65536 + RMIPS_KC * TB_THREADS * 4);
   __shared__ float cps[2][TB_TILE];
@@ -308,7 +322,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
   __shared__ uint32_t taddr_s;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const uint32_t TILE_BYTES = TB_TILE * TC_K * 4;
+  const uint32_t TILE_BYTES = TB_TILE * TC_K * E;
   if (warp == 0) {
     tmem_alloc(&taddr_s, 64);
     tmem_relinquish();
@@ -325,15 +339,14 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
   tc_fence_after();
   const uint32_t taddr = taddr_s;
   const uint32_t tlane = taddr + ((uint32_t)(warp * 32) << 16);
-  const uint32_t idesc = tc_idesc_tf32(128, TB_TILE);
+  const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(128, TB_TILE) : tc_idesc_f16(128, TB_TILE, KIND == TCK_BF16);
   const int64_t ntiles = (pp + TB_TILE - 1) / TB_TILE;
   uint32_t phb = 0, ph_m = 0;
   auto load_tile = [&](int64_t t, int buf) {
     if (tid == 0) {
       fence_proxy_async();
       mbar_arrive_expect_tx(&bar_b[buf], TILE_BYTES);
-      bulk_g2s(reinterpret_cast<unsigned char*>(sB) + (size_t)buf * TILE_BYTES, Pt + t * (TB_TILE * TC_K),
-               TILE_BYTES, &bar_b[buf]);
+      bulk_g2s(sB + (size_t)buf * TILE_BYTES, Pt + t * TILE_BYTES, TILE_BYTES, &bar_b[buf]);
     }
     if (tid < TB_TILE) cps[buf][tid] = cp[t * TB_TILE + tid];
   };
@@ -341,28 +354,53 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
     if (!mbar_wait_bounded(&bar_b[buf], (phb >> buf) & 1u)) return false;
     tc_fence_after();
     const uint32_t bb = smem_u32(sB) + (uint32_t)buf * TILE_BYTES;
-    for (uint32_t s = 0; s < TC_K / 8; ++s)
-      tc_mma_tf32(taddr, tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, TC_SBO),
-                  tc_sdesc(bb + s * 2 * TC_LBO, TC_LBO, TC_SBO), idesc, s > 0 ? 1u : 0u);
+    // one MMA consumes 32 bytes of K per row (8 TF32 or 16 16-bit values)
+    for (uint32_t s = 0; s < TC_K * E / 32; ++s) {
+      const uint64_t ad = tc_sdesc(smem_u32(sA) + s * 2 * TC_LBO, TC_LBO, SBO);
+      const uint64_t bd = tc_sdesc(bb + s * 2 * TC_LBO, TC_LBO, SBO);
+      if (KIND == TCK_TF32) tc_mma_tf32(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+      else tc_mma_f16(taddr, ad, bd, idesc, s > 0 ? 1u : 0u);
+    }
     tc_commit(&bar_m);
     return true;
   };
   for (int64_t u0 = (int64_t)blockIdx.x * TB_THREADS; u0 < n && !s_fail; u0 += (int64_t)gridDim.x * TB_THREADS) {
     const int64_t nvalid = (n - u0) < TB_THREADS ? (n - u0) : TB_THREADS;
     const float* src = Qs + u0 * d;
-    for (int e = tid; e < TB_THREADS * (int)(TC_K / 4); e += TB_THREADS) {
-      const int r = e & (TB_THREADS - 1), k0 = (e >> 7) * 4;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (r < nvalid) {
-        const float* row = src + (int64_t)r * d;
-        if (k0 + 0 < d) v.x = row[k0 + 0];
-        if (k0 + 1 < d) v.y = row[k0 + 1];
-        if (k0 + 2 < d) v.z = row[k0 + 2];
-        if (k0 + 3 < d) v.w = row[k0 + 3];
+    if (KIND == TCK_TF32) {
+      for (int e = tid; e < TB_THREADS * (int)(TC_K / 4); e += TB_THREADS) {
+        const int r = e & (TB_THREADS - 1), k0 = (e >> 7) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < nvalid) {
+          const float* row = src + (int64_t)r * d;
+          if (k0 + 0 < d) v.x = row[k0 + 0];
+          if (k0 + 1 < d) v.y = row[k0 + 1];
+          if (k0 + 2 < d) v.z = row[k0 + 2];
+          if (k0 + 3 < d) v.w = row[k0 + 3];
+        }
+        *reinterpret_cast<float4*>(sA + tc_off(r, k0)) = v;
       }
-      *reinterpret_cast<float4*>(&sA[tc_off(r, k0) / 4]) = v;
+    } else {                                       // the 16-bit copy, rounded to nearest
+      for (int e = tid; e < TB_THREADS * (int)(TC_K / 8); e += TB_THREADS) {
+        const int r = e & (TB_THREADS - 1), k0 = (e >> 7) * 8;
+        uint16_t h[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float v = (r < nvalid && k0 + i < d) ? src[(int64_t)r * d + k0 + i] : 0.f;
+          h[i] = KIND == TCK_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+        }
+        uint4 w;
+        w.x = h[0] | ((uint32_t)h[1] << 16);
+        w.y = h[2] | ((uint32_t)h[3] << 16);
+        w.z = h[4] | ((uint32_t)h[5] << 16);
+        w.w = h[6] | ((uint32_t)h[7] << 16);
+        *reinterpret_cast<uint4*>(sA + tc_off16(r, k0)) = w;
+      }
     }
     const float un = tid < nvalid ? unorm[u0 + tid] : 0.f;
+    // absolute error of operands below the 16-bit format's normal range
+    // (FP16: 2^-25 each), charged to every bound: (d + 2) unit (||u|| + max ||p||)
+    const float ua = __fmul_ru((float)(d + 2), __fmul_ru(tc_abs_unit(KIND), __fadd_ru(un, pn0)));
     for (int s = 0; s < RMIPS_KC; ++s) {
       lv[s][tid] = -kInf;
       li[s][tid] = -1;
@@ -408,7 +446,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
         }
         const float vmax = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
         if (!(vmax > thr)) {                       // every item of the tile is rejected
-          uex = fmaxf(uex, __fmaf_ru(un, cps[buf][0], vmax));
+          uex = fmaxf(uex, __fadd_ru(__fmaf_ru(un, cps[buf][0], vmax), ua));
           done_fast = true;
         }
       }
@@ -421,7 +459,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
         cand |= (uint64_t)in << q;
         vrej = (q < live && !in) ? fmaxf(vrej, acc[q]) : vrej;
       }
-      if (vrej > -kInf) uex = fmaxf(uex, __fmaf_ru(un, cps[buf][0], vrej));
+      if (vrej > -kInf) uex = fmaxf(uex, __fadd_ru(__fmaf_ru(un, cps[buf][0], vrej), ua));
       while (cand) {
         const int q = __ffsll((long long)cand) - 1;
         cand &= cand - 1;
@@ -430,7 +468,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
         for (int i = 1; i < TB_TILE; ++i) v = (i == q) ? acc[i] : v;
         if (v > thr) {
           const int32_t old = li[minslot][tid];
-          if (old >= 0) uex = fmaxf(uex, __fmaf_ru(un, cp[old], lv[minslot][tid]));
+          if (old >= 0) uex = fmaxf(uex, __fadd_ru(__fmaf_ru(un, cp[old], lv[minslot][tid]), ua));
           lv[minslot][tid] = v;
           li[minslot][tid] = (int32_t)(t * TB_TILE + q);
           thr = lv[0][tid];
@@ -440,7 +478,7 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
             if (w < thr) { thr = w; minslot = s; }
           }
         } else {
-          uex = fmaxf(uex, __fmaf_ru(un, cps[buf][q], v));
+          uex = fmaxf(uex, __fadd_ru(__fmaf_ru(un, cps[buf][q], v), ua));
         }
       }
       }
@@ -679,7 +717,8 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
   }
   const bool q_dev = is_device_ptr(Q), p_dev = is_device_ptr(P);
   float *Qin = nullptr, *Pin = nullptr, *qn = nullptr, *pn = nullptr, *cval = nullptr;
-  float *Pt = nullptr, *cpn = nullptr, *uex = nullptr;
+  unsigned char* Pt = nullptr;
+  float *cpn = nullptr, *uex = nullptr;
   int32_t* ulist = nullptr;
   float* sval = nullptr;
   int32_t* sid = nullptr;
@@ -780,17 +819,39 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       const int64_t ntiles = (idx->pp + TB_TILE - 1) / TB_TILE;
-      TRY(cudaMallocAsync((void**)&Pt, (size_t)ntiles * TB_TILE * TC_K * sizeof(float), st));
+      // operand kind of the selection: TF32 for a float32 index, the index's
+      // own 16-bit format otherwise (FP16 only while every item value fits it:
+      // |p_i| <= ||p|| <= the largest item norm)
+      TRY(cudaStreamSynchronize(st));                 // idx->pn0 has landed
+      int kind = TCK_TF32;
+      if (idx->precision == RMIPS_BF16) kind = TCK_BF16;
+      if (idx->precision == RMIPS_FP16 && idx->pn0 <= 65504.0f) kind = TCK_FP16;
+      idx->build_kind = kind;
+      const uint32_t esz = kind == TCK_TF32 ? 4u : 2u;
+      TRY(cudaMallocAsync((void**)&Pt, (size_t)ntiles * TB_TILE * TC_K * esz, st));
       TRY(cudaMallocAsync((void**)&cpn, (size_t)ntiles * TB_TILE * sizeof(float), st));
       TRY(cudaMallocAsync((void**)&uex, (size_t)n * sizeof(float), st));
       TRY(cudaMemsetAsync(d_bad, 0, 16, st));
-      k_item_tiles<<<grid_for(ntiles * TB_TILE * TC_K, 256), 256, 0, st>>>(idx->Ps, idx->pnorm, idx->pp, d, ntiles,
-                                                                           Pt, cpn);
+      const unsigned tiles_grid = grid_for(ntiles * TB_TILE * TC_K, 256);
+      if (kind == TCK_TF32) k_item_tiles<TCK_TF32><<<tiles_grid, 256, 0, st>>>(idx->Ps, idx->pnorm, idx->pp, d, ntiles, Pt, cpn);
+      else if (kind == TCK_BF16) k_item_tiles<TCK_BF16><<<tiles_grid, 256, 0, st>>>(idx->Ps, idx->pnorm, idx->pp, d, ntiles, Pt, cpn);
+      else k_item_tiles<TCK_FP16><<<tiles_grid, 256, 0, st>>>(idx->Ps, idx->pnorm, idx->pp, d, ntiles, Pt, cpn);
       const int smem_tc = 65536 + 2 * RMIPS_KC * TB_THREADS * 4;
-      TRY(cudaFuncSetAttribute(k_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc));
       const int64_t utiles = (n + TB_THREADS - 1) / TB_THREADS;
       const int grid = (int)(utiles < 2 * sms ? utiles : 2 * sms);
-      k_topk_tc<<<grid, TB_THREADS, smem_tc, st>>>(idx->Qs, Pt, cpn, idx->unorm, n, idx->pp, d, cval, cid, uex, d_bad);
+      if (kind == TCK_TF32) {
+        TRY(cudaFuncSetAttribute(k_topk_tc<TCK_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc));
+        k_topk_tc<TCK_TF32><<<grid, TB_THREADS, smem_tc, st>>>(idx->Qs, Pt, cpn, idx->unorm, n, idx->pp, d, idx->pn0,
+                                                               cval, cid, uex, d_bad);
+      } else if (kind == TCK_BF16) {
+        TRY(cudaFuncSetAttribute(k_topk_tc<TCK_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc));
+        k_topk_tc<TCK_BF16><<<grid, TB_THREADS, smem_tc, st>>>(idx->Qs, Pt, cpn, idx->unorm, n, idx->pp, d, idx->pn0,
+                                                               cval, cid, uex, d_bad);
+      } else {
+        TRY(cudaFuncSetAttribute(k_topk_tc<TCK_FP16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_tc));
+        k_topk_tc<TCK_FP16><<<grid, TB_THREADS, smem_tc, st>>>(idx->Qs, Pt, cpn, idx->unorm, n, idx->pp, d, idx->pn0,
+                                                               cval, cid, uex, d_bad);
+      }
       TRY(cudaGetLastError());
       int h_fail = 0;
       TRY(cudaMemcpyAsync(&h_fail, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -199,6 +199,7 @@ extern "C" rmips_status rmips_index_get_info(const rmips_index* idx, rmips_index
   i.tuned = idx->tuned;
   i.batch_stages = idx->tune_ws_ns;
   i.single_stages = idx->tune_q1_ns;
+  i.build_kind = idx->build_kind;
   i.tune_ms = idx->tune_ms;
   *out = i;
   return RMIPS_OK;

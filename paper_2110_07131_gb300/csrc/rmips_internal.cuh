@@ -202,6 +202,7 @@ struct rmips_index {
   int tune_ws_ns = 0;           // query stages of the batched tensor-core filter (even)
   int tune_q1_ns = 0;           // row stages of the one-launch single-query kernel
   int tuned = 0;                // 0 not tuned, 1 searched on the device, 2 read from a tune cache
+  int build_kind = -1;          // operand kind of the tensor-core candidate selection (-1: CUDA cores)
   double tune_ms = 0.0;
 
   float* Qs = nullptr;

@@ -61,7 +61,7 @@ class IndexInfo(C.Structure):
                 ("block_size", C.c_int32), ("precision", C.c_int32), ("n_blocks", C.c_int64),
                 ("p_prime", C.c_int64), ("incomplete", C.c_int64), ("device_bytes", C.c_int64),
                 ("build_ms", C.c_double), ("tuned", C.c_int32), ("batch_stages", C.c_int32),
-                ("single_stages", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double)]
+                ("single_stages", C.c_int32), ("build_kind", C.c_int32), ("tune_ms", C.c_double)]
 
 
 class Profile(C.Structure):

@@ -75,11 +75,15 @@ def test_single_query_api_matches(tiny, p_prime):
             assert np.array_equal(ids[offs[0]:offs[1]], got)
 
 
-@pytest.mark.parametrize("build_tc", [True, False])
-def test_index_arrays_match_oracle(tiny, build_tc):
+@pytest.mark.parametrize("build_tc,precision", [(True, "fp32"), (False, "fp32"), (True, "bf16"), (True, "fp16")])
+def test_index_arrays_match_oracle(tiny, build_tc, precision):
+    # the candidate selection runs on tensor cores in TF32, BF16 or FP16 (the
+    # index's precision) or on CUDA cores; the bounds are rigorous either way
     Q, P, _, _ = tiny
     k_max = 25
-    index = rmips.rmips_build_index(Q, P, k_max=k_max, build_tensor_cores=build_tc)
+    index = rmips.rmips_build_index(Q, P, k_max=k_max, build_tensor_cores=build_tc, precision=precision)
+    assert rmips.rmips_index_get_info(index)["build_kind"] == (
+        {"fp32": 0, "bf16": 1, "fp16": 2}[precision] if build_tc else -1)
     permQ = rmips.rmips_index_export(index, "permQ")
     permP = rmips.rmips_index_export(index, "permP")
     assert np.array_equal(permQ, O.norm_order(Q))
