@@ -569,6 +569,108 @@ __global__ void __launch_bounds__(EMIT_THREADS) k_emit(Common c, EmitArgs e, int
   }
 }
 
+// Exact decision of up to four undecided users of one query per warp, eight
+// lanes per user (four candidates per lane): float32 u.q with its bound
+// against the index's interval of each candidate's u.p decides almost every
+// user without reading an item row; overlapping candidates are settled one at
+// a time with the whole warp (bit-identical to q: an exact tie; else float32
+// u.p with its bound); what that leaves open goes to the whole-warp exact
+// path (recheck_candidates, or verify_scan for users without a candidate
+// proof).  pos: this lane's group's user (sorted position), or -1.  Returns
+// the group's yes / no on every lane of the group.
+__device__ bool q1_resolve4(const Common& c, const float* sq, float qeps, int k, int64_t pos) {
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int d = c.d;
+  const float tiny = (d + 2) * 0x1p-148f;
+  const bool have = pos >= 0;
+  const bool quick = have && !c.incomp[pos];
+  const float* u = c.Qs + (have ? pos : 0) * d;
+  float g32 = 0.f, a32 = 0.f;
+  for (int i = sub; quick && i < d; i += 8) {
+    const float x = u[i], y = sq[i];
+    g32 = fmaf(x, y, g32);
+    a32 = fmaf(fabsf(x), fabsf(y), a32);
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {                 // within the eight lanes of the user
+    g32 += __shfl_xor_sync(FULL, g32, o);
+    a32 += __shfl_xor_sync(FULL, a32, o);
+  }
+  const float eg = __fmaf_ru(a32, c.cg32, tiny);
+  const float gl = __fsub_rd(g32, eg), gh = __fadd_ru(g32, eg);
+  int ngt = 0;
+  uint32_t ovm = 0;                                  // this lane's candidates whose interval overlaps
+  int32_t its[RMIPS_KC / 8] = {-1, -1, -1, -1};
+  if (quick) {
+    const int32_t* crow = c.cand + pos * RMIPS_KC;
+    const float2* cbrow = c.cbnd + pos * RMIPS_KC;
+    float2 cbs[RMIPS_KC / 8];
+#pragma unroll
+    for (int r = 0; r < RMIPS_KC / 8; ++r) {
+      its[r] = crow[sub + 8 * r];
+      cbs[r] = cbrow[sub + 8 * r];
+    }
+#pragma unroll
+    for (int r = 0; r < RMIPS_KC / 8; ++r) {
+      if (its[r] < 0) continue;
+      if (cbs[r].x > gh) ++ngt;
+      else if (!(cbs[r].y < gl)) ovm |= 1u << r;
+    }
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) ngt += __shfl_xor_sync(FULL, ngt, o);
+  bool hardg = false;
+  for (unsigned pend = __ballot_sync(FULL, ovm != 0); pend; pend = __ballot_sync(FULL, ovm != 0)) {
+    const int src = __ffs(pend) - 1;
+    const uint32_t m = __shfl_sync(FULL, ovm, src);
+    const int r = __ffs(m) - 1;
+    if (lane == src) ovm &= ovm - 1;
+    int32_t mine = its[0];
+#pragma unroll
+    for (int x = 1; x < RMIPS_KC / 8; ++x) mine = r == x ? its[x] : mine;
+    const int32_t it = __shfl_sync(FULL, mine, src);
+    const long long opos = __shfl_sync(FULL, (long long)pos, src);
+    const float ogl = __shfl_sync(FULL, gl, src), ogh = __shfl_sync(FULL, gh, src);
+    const float* op = c.Ps + (int64_t)it * d;
+    const float* ou = c.Qs + opos * d;
+    bool same = true;
+    float sp = 0.f, sb = 0.f;
+    for (int i = lane; i < d; i += 32) {
+      const float pv = op[i], uv = ou[i];
+      same = same && __float_as_uint(pv) == __float_as_uint(sq[i]);
+      sp = fmaf(uv, pv, sp);
+      sb = fmaf(fabsf(uv), fabsf(pv), sb);
+    }
+    same = __all_sync(FULL, same);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sp += __shfl_xor_sync(FULL, sp, o);
+      sb += __shfl_xor_sync(FULL, sb, o);
+    }
+    const float ep = __fmaf_ru(sb, c.cg32, tiny);
+    const bool ogt = !same && __fsub_rd(sp, ep) > ogh;
+    const bool ohard = !same && !ogt && !(__fadd_ru(sp, ep) < ogl);
+    if ((lane >> 3) == (src >> 3)) {
+      ngt += ogt ? 1 : 0;
+      hardg = hardg || ohard;
+    }
+  }
+  bool yes = quick && !hardg && ngt < k;
+  unsigned slow = __ballot_sync(FULL, sub == 0 && have && !(quick && !hardg));
+  while (slow) {                                     // the users still open, one at a time with the warp
+    const int src = __ffs(slow) - 1;
+    slow &= slow - 1;
+    const int64_t spos = __shfl_sync(FULL, (long long)pos, src);
+    const float* su = c.Qs + spos * d;
+    const bool y = !c.incomp[spos]
+                       ? recheck_candidates(su, sq, c.cand + spos * RMIPS_KC, c.cbnd + spos * RMIPS_KC, c.Ps, d, k,
+                                            c.cg32, c.ctr)
+                       : verify_scan(su, c.unorm[spos], c, sq, k, qeps);
+    if ((lane >> 3) == (src >> 3)) yes = y;
+  }
+  return yes;
+}
+
 // Public status code of a device status word (asynchronous calls write it).
 __device__ __forceinline__ int status_code(long long s) {
   return s == ST_OK ? RMIPS_OK
@@ -604,8 +706,10 @@ constexpr int Q1_THREADS = (Q1_WARPS + 1) * 32;
 constexpr int Q1_MAXNS = 6;                                    // stages at most
 constexpr size_t Q1_HEAD = 1024;                               // q, barriers, stage info
 constexpr int Q1_YCAP = 256;                                   // yes positions a warp buffers
-constexpr int Q1_TCAP = 64;                                    // undecided positions a warp buffers
-constexpr size_t Q1_BUFS = (size_t)Q1_WARPS * (Q1_YCAP + Q1_TCAP) * sizeof(int32_t);
+constexpr int Q1_TCAP = 64;                                    // undecided positions past the CTA's list
+constexpr int Q1_CTCAP = 1024;                                 // undecided positions the CTA lists
+constexpr size_t Q1_BUFS =
+    ((size_t)(Q1_WARPS + 1) * Q1_YCAP + (size_t)Q1_WARPS * Q1_TCAP + Q1_CTCAP) * sizeof(int32_t);
 
 // Ascending sort of one value per lane (bitonic network over the warp).
 __device__ __forceinline__ int32_t q1_warp_sort(int32_t x) {
@@ -635,11 +739,12 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   uint64_t* info = full + Q1_MAXNS;                                       // [Q1_MAXNS]
   uint64_t* empty = info + Q1_MAXNS;                                      // [Q1_MAXNS]
   int2* sinfo = reinterpret_cast<int2*>(smem + 512 + 3 * Q1_MAXNS * 8);   // [Q1_MAXNS] (span, mask)
-  int32_t* ybuf = reinterpret_cast<int32_t*>(smem + Q1_HEAD);            // [Q1_WARPS][Q1_YCAP]
-  int32_t* tbuf = ybuf + Q1_WARPS * Q1_YCAP;                               // [Q1_WARPS][Q1_TCAP]
+  int32_t* ybuf = reinterpret_cast<int32_t*>(smem + Q1_HEAD);            // [Q1_WARPS + 1][Q1_YCAP]
+  int32_t* tbuf = ybuf + (Q1_WARPS + 1) * Q1_YCAP;                         // [Q1_WARPS][Q1_TCAP]
+  int32_t* ctodo = tbuf + Q1_WARPS * Q1_TCAP;                              // [Q1_CTCAP]
   unsigned char* stages = smem + Q1_HEAD + Q1_BUFS;                        // ns x stage, later sort keys
   __shared__ float s_qn, s_eps;
-  __shared__ int s_fin, s_last, s_abort;
+  __shared__ int s_fin, s_last, s_abort, s_ntodo;
   __shared__ int s_fills[Q1_MAXNS];         // phases completed on full[s] by the producer
   __shared__ int s_warp[32];
   __shared__ long long s_total;
@@ -660,6 +765,7 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
     }
     fence_mbar_init();
     s_abort = 0;
+    s_ntodo = 0;
     for (int s = 0; s < Q1_MAXNS; ++s) s_fills[s] = 0;
   }
   __syncthreads();
@@ -668,6 +774,19 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   const float qn = s_qn, qeps = s_eps;
   const float2* Lbk = c.Lb + (int64_t)(k - 1) * n;
   long long pruned = 0, tested = 0, todosum = 0, yesfast = 0;
+  // Yes positions go to the warp's own buffer in shared memory and reach the
+  // global list with one reservation per 256 (every warp has one).
+  int32_t* wy = ybuf + warp * Q1_YCAP;
+  int ny = 0;                                                  // warp-uniform
+  auto flush_yes = [&]() {
+    __syncwarp();
+    long long b0 = 0;
+    if (lane == 0 && ny) b0 = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)ny);
+    b0 = __shfl_sync(FULL, b0, 0);
+    for (int i = lane; i < ny; i += 32) c.yes[b0 + i] = wy[i];
+    __syncwarp();
+    ny = 0;
+  };
   if (s_fin && warp == Q1_WARPS) {
     // ---------------- producer ----------------
     const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
@@ -761,24 +880,14 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
     }
   } else if (s_fin && warp < Q1_WARPS) {
     // ---------------- consumers ----------------
-    // Yes positions and undecided positions go to the warp's own buffers in
-    // shared memory: the stream loop holds no round trip to global memory
-    // except the prefetched bounds.  Yes positions are flushed to the list
-    // with one reservation per 256; undecided users are rechecked exactly
-    // after the stream (or when 64 have gathered).
-    int32_t* wy = ybuf + warp * Q1_YCAP;
+    // The stream loop holds no round trip to global memory except the
+    // prefetched bounds: yes positions go to the warp's buffer, undecided
+    // positions to the CTA's list (resolved by every warp after the stream,
+    // four users per warp), or, past its end, to the warp's own list
+    // (rechecked by the warp when 64 have gathered).
     int32_t* wt = tbuf + warp * Q1_TCAP;
-    int ny = 0, nt = 0;                                         // warp-uniform
+    int nt = 0;                                                 // warp-uniform
     const uint32_t lt = (1u << lane) - 1u;
-    auto flush_yes = [&]() {
-      __syncwarp();
-      long long b0 = 0;
-      if (lane == 0 && ny) b0 = atomicAdd((unsigned long long*)&c.ctr[C_YES], (unsigned long long)ny);
-      b0 = __shfl_sync(FULL, b0, 0);
-      for (int i = lane; i < ny; i += 32) c.yes[b0 + i] = wy[i];
-      __syncwarp();
-      ny = 0;
-    };
     auto recheck = [&]() {                                      // whole warp, one user at a time
       __syncwarp();
       for (int t = 0; t < nt; ++t) {
@@ -840,9 +949,17 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
           ny += __popc(by);
         }
         if (bt) {
-          if (nt + __popc(bt) > Q1_TCAP) recheck();
-          if (todo) wt[nt + __popc(bt & lt)] = (int32_t)pos;
-          nt += __popc(bt);
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s_ntodo, __popc(bt));
+          base = __shfl_sync(FULL, base, 0);
+          const int at = base + __popc(bt & lt);
+          const uint32_t over = __ballot_sync(FULL, todo && at >= Q1_CTCAP);
+          if (todo && at < Q1_CTCAP) ctodo[at] = (int32_t)pos;
+          if (over) {                                  // past the CTA's list: the warp's own
+            if (nt + __popc(over) > Q1_TCAP) recheck();
+            if ((over >> lane) & 1u) wt[nt + __popc(over & lt)] = (int32_t)pos;
+            nt += __popc(over);
+          }
         }
         yesfast += __popc(by);
         tested += __popc(__ballot_sync(FULL, valid));
@@ -853,8 +970,24 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       if (++stage == ns) { stage = 0; ph ^= 1u; }
     }
     recheck();
-    flush_yes();
   }
+  // every warp: the CTA's undecided users, four per warp at a time
+  __syncthreads();
+  if (s_fin && !s_abort) {
+    const int ntodo = s_ntodo < Q1_CTCAP ? s_ntodo : Q1_CTCAP;
+    for (int base = warp * 4; base < ntodo; base += (Q1_WARPS + 1) * 4) {
+      const int at = base + (lane >> 3);
+      const int64_t p = at < ntodo ? (int64_t)ctodo[at] : -1;
+      const bool y = q1_resolve4(c, sq, qeps, k, p);
+      const uint32_t by = __ballot_sync(FULL, (lane & 7) == 0 && p >= 0 && y);
+      if (by) {
+        if (ny + __popc(by) > Q1_YCAP) flush_yes();
+        if ((by >> lane) & 1u) wy[ny + __popc(by & ((1u << lane) - 1u))] = (int32_t)p;
+        ny += __popc(by);
+      }
+    }
+  }
+  flush_yes();
   if (lane == 0) {
     if (pruned) atomicAdd((unsigned long long*)&c.ctr[C_PRUNED], (unsigned long long)pruned);
     if (tested) atomicAdd((unsigned long long*)&c.ctr[C_TESTED], (unsigned long long)tested);
