@@ -924,15 +924,33 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       if (mine) {
         const T* row = reinterpret_cast<const T*>(stages + (size_t)stage * stage_bytes + (size_t)warp * chunk_bytes) +
                        (size_t)lane * d;
-        float g = 0.f, A = 0.f;
-        int r = lane % d;                     // rotated start: the lanes hit different banks
-        for (int i = 0; i < d; ++i) {
-          const float uv = to_f32<T>(row[r]);
-          const float qv = sq[r];
-          g = fmaf(uv, qv, g);
-          A = fmaf(fabsf(uv), fabsf(qv), A);
-          r = (r + 1 == d) ? 0 : r + 1;
+        // u.q over the rotated index r0 + i (mod d), so that the lanes hit
+        // different banks; the index is formed per step (no chain between
+        // steps) and two accumulator pairs keep the loads of several steps
+        // in flight.  Any summation order is within the bound factor cg.
+        float g0 = 0.f, A0 = 0.f, g1 = 0.f, A1 = 0.f;
+        const int r0 = lane % d;
+        int i = 0;
+#pragma unroll 2
+        for (; i + 1 < d; i += 2) {
+          int ra = r0 + i, rb = r0 + i + 1;
+          ra -= ra >= d ? d : 0;
+          rb -= rb >= d ? d : 0;
+          const float ua = to_f32<T>(row[ra]), qa = sq[ra];
+          const float ub = to_f32<T>(row[rb]), qb = sq[rb];
+          g0 = fmaf(ua, qa, g0);
+          A0 = fmaf(fabsf(ua), fabsf(qa), A0);
+          g1 = fmaf(ub, qb, g1);
+          A1 = fmaf(fabsf(ub), fabsf(qb), A1);
         }
+        if (i < d) {
+          int ra = r0 + i;
+          ra -= ra >= d ? d : 0;
+          const float ua = to_f32<T>(row[ra]), qa = sq[ra];
+          g0 = fmaf(ua, qa, g0);
+          A0 = fmaf(fabsf(ua), fabsf(qa), A0);
+        }
+        const float g = g0 + g1, A = A0 + A1;
         bool yes = false, todo = false;
         if (valid) {
           const float e = __fmaf_ru(A, c.cg, qeps);
