@@ -292,7 +292,9 @@ typedef struct {
                                 block header and L^k(B) per block, plus per
                                 tested user its row (d x element size), its
                                 (lo, hi) pair (8 bytes), its norm (4 bytes,
-                                P' index only) and 4 bytes per listed user */
+                                where the filter reads it: the one-launch
+                                query and P' indexes) and 4 bytes per listed
+                                user */
   int64_t users_tested;      /* users of unpruned blocks */
   int64_t blocks_pruned;     /* blocks pruned by Lemma 3 */
   int64_t blocks_total;      /* blocks examined */

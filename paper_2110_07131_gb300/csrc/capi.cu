@@ -352,7 +352,7 @@ extern "C" rmips_status rmips_profile_read(const rmips_index* idx, rmips_profile
   if (m->dprof1 && cudaMemcpy(acc, m->dprof1, sizeof(acc), cudaMemcpyDeviceToHost) == cudaSuccess && acc[3]) {
     const int es = m->precision == RMIPS_FP32 ? 4 : 2;
     m->prof.filter_launches += (int64_t)acc[3];
-    m->prof.filter_alg_bytes += 8.0 * m->nb * (double)acc[3] + ((double)m->d * es + 8.0) * (double)acc[0] +
+    m->prof.filter_alg_bytes += 8.0 * m->nb * (double)acc[3] + ((double)m->d * es + 12.0) * (double)acc[0] +
                                 4.0 * (double)acc[1];
     m->prof.users_tested += (int64_t)acc[0];
     m->prof.blocks_pruned += (int64_t)acc[2] * 32 / m->bs;

@@ -729,6 +729,52 @@ __device__ __forceinline__ int32_t q1_warp_sort(int32_t x) {
 
 __host__ __device__ inline size_t q1_stage_bytes(int d, int es) { return (size_t)Q1_WARPS * 32 * d * es; }
 
+// u.q for this lane's row of a staged chunk (row-major, stride d).  With d
+// even the row is read in pairs: 8-byte words of float32 rows (lane stride
+// 25 words for d = 50: conflict-free per half-warp) or 4-byte pairs of 16-bit
+// values, and q in pairs broadcast to the warp; two accumulators.  With d
+// odd the rotated start r0 = lane mod d keeps the lanes on different banks.
+// Any summation order is within the factor cg of the error bound.
+template <class T>
+__device__ __forceinline__ float q1_dot(const T* __restrict__ row, const float* __restrict__ sq, int d, int lane) {
+  float g0 = 0.f, g1 = 0.f;
+  if ((d & 1) == 0) {
+    const float2* q2 = reinterpret_cast<const float2*>(sq);
+    const int h = d >> 1;
+    if (sizeof(T) == 4) {
+      const float2* r2 = reinterpret_cast<const float2*>(row);
+#pragma unroll 5
+      for (int j = 0; j < h; ++j) {
+        const float2 u = r2[j], q = q2[j];
+        g0 = fmaf(u.x, q.x, g0);
+        g1 = fmaf(u.y, q.y, g1);
+      }
+    } else {
+      const uint32_t* r2 = reinterpret_cast<const uint32_t*>(row);
+#pragma unroll 5
+      for (int j = 0; j < h; ++j) {
+        const uint32_t w = r2[j];
+        T lo_h, hi_h;
+        memcpy(&lo_h, &w, 2);
+        const uint32_t wh = w >> 16;
+        memcpy(&hi_h, &wh, 2);
+        const float2 q = q2[j];
+        g0 = fmaf(to_f32<T>(lo_h), q.x, g0);
+        g1 = fmaf(to_f32<T>(hi_h), q.y, g1);
+      }
+    }
+  } else {
+    const int r0 = lane % d;
+#pragma unroll 2
+    for (int i = 0; i < d; ++i) {
+      int r = r0 + i;
+      r -= r >= d ? d : 0;
+      g0 = fmaf(to_f32<T>(row[r]), sq[r], g0);
+    }
+  }
+  return g0 + g1;
+}
+
 template <class T>
 __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, const float* q_src, int k,
                                                           int precision, int ns, long long* res, long long* done,
@@ -918,42 +964,18 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       const int64_t pos = ((int64_t)si.x * Q1_WARPS + warp) * 32 + lane;
       const bool valid = mine && pos < n;
       const float2 L = valid ? Lbk[pos] : make_float2(kInf, kInf);   // prefetched while the rows land
+      const float un = valid ? c.unorm[pos] : 0.f;
       w = mbar_wait_bounded(&full[stage], ph);
       w = __all_sync(FULL, w);
       if (!w) { if (lane == 0) { set_status(c.ctr, ST_TIMEOUT); atomicExch(&s_abort, 1); } break; }
       if (mine) {
         const T* row = reinterpret_cast<const T*>(stages + (size_t)stage * stage_bytes + (size_t)warp * chunk_bytes) +
                        (size_t)lane * d;
-        // u.q over the rotated index r0 + i (mod d), so that the lanes hit
-        // different banks; the index is formed per step (no chain between
-        // steps) and two accumulator pairs keep the loads of several steps
-        // in flight.  Any summation order is within the bound factor cg.
-        float g0 = 0.f, A0 = 0.f, g1 = 0.f, A1 = 0.f;
-        const int r0 = lane % d;
-        int i = 0;
-#pragma unroll 2
-        for (; i + 1 < d; i += 2) {
-          int ra = r0 + i, rb = r0 + i + 1;
-          ra -= ra >= d ? d : 0;
-          rb -= rb >= d ? d : 0;
-          const float ua = to_f32<T>(row[ra]), qa = sq[ra];
-          const float ub = to_f32<T>(row[rb]), qb = sq[rb];
-          g0 = fmaf(ua, qa, g0);
-          A0 = fmaf(fabsf(ua), fabsf(qa), A0);
-          g1 = fmaf(ub, qb, g1);
-          A1 = fmaf(fabsf(ub), fabsf(qb), A1);
-        }
-        if (i < d) {
-          int ra = r0 + i;
-          ra -= ra >= d ? d : 0;
-          const float ua = to_f32<T>(row[ra]), qa = sq[ra];
-          g0 = fmaf(ua, qa, g0);
-          A0 = fmaf(fabsf(ua), fabsf(qa), A0);
-        }
-        const float g = g0 + g1, A = A0 + A1;
+        const float g = q1_dot<T>(row, sq, d, lane);
         bool yes = false, todo = false;
         if (valid) {
-          const float e = __fmaf_ru(A, c.cg, qeps);
+          // error bound from ||u|| ||q|| >= sum |u_i q_i| (both norms rounded up)
+          const float e = __fmaf_ru(__fmul_ru(un, qn), c.cg, qeps);
           const float hi = __fadd_ru(g, e), lo = __fsub_rd(g, e);
           if (!(hi < L.x)) {                                              // Lemma 1 (strict)
             yes = lo >= L.y;                                              // above hi_k
@@ -1370,7 +1392,7 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
     std::lock_guard<std::mutex> lk(idx->mu);
     idx->prof.filter_launches += 1;
     idx->prof.filter_ms += ms;
-    idx->prof.filter_alg_bytes += 8.0 * idx->nb + ((double)idx->d * es + 8.0) * h[C_TESTED] +
+    idx->prof.filter_alg_bytes += 8.0 * idx->nb + ((double)idx->d * es + 12.0) * h[C_TESTED] +
                                   4.0 * (double)(h[C_YESFAST] + h[C_TODOSUM]);
     idx->prof.users_tested += h[C_TESTED];
     idx->prof.blocks_pruned += h[C_PRUNED] * 32 / idx->bs;
