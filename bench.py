@@ -257,37 +257,12 @@ def serving_requests(P, n, d, n_req, seed):
     return qs, ks, segs, subsets
 
 
-def run_serving(rmips, index, P, a):
-    """Served (rmips_server_*) against plain (one rmips_query per request)
-    latency at the same offered loads.  Arrivals follow a Poisson process at
-    each rate; a request's latency runs from its scheduled arrival to the
-    moment its result is available to the caller (for the server: the
-    library's submit-to-completion time plus the submitter's lag behind the
-    schedule).  The plain path takes the requests in arrival order on one
-    host thread, so at a rate above what it can carry its queue, and its
-    latency, grow for as long as the run lasts."""
+def serve_rates(rmips, index, qs, ks, segs, subsets, rates, n_serve, n_plain, opts):
+    """Served and plain latency at each offered Poisson rate (see run_serving)."""
     import threading
-    rates = [20_000.0, 200_000.0, 1_000_000.0]
-    n_serve = {20_000.0: 10_000, 200_000.0: 40_000, 1_000_000.0: 100_000}
-    n_plain = {20_000.0: 10_000, 200_000.0: 4_000, 1_000_000.0: 4_000}
-    n_req = min(a.serve_requests, max(n_serve.values())) if a.serve_requests > 0 else 0
-    qs, ks, segs, subsets = serving_requests(P, a.n, a.d, max(n_req, 1), 41)
-    opts = dict(max_batch=4096, max_wait_us=200, streams=2, max_pending=1 << 21)
-    warm = rmips.Server(index, **opts)
-    warm.wait_many(warm.submit_many(qs[:4096], ks[:4096]))
-    warm.close()
-    out = {"workload": "Poisson arrivals; q = random item of P or random N(0, I/d) (half each); k uniform in "
-                       "1..25; segment: none / contiguous id range / registered random id subset (a third each), "
-                       "segment sizes log-uniform in 1e3..1e6",
-           "server": "rmips_server: max_batch 4096, max_wait_us 200 while a batch is on the device (a batch "
-                     "closes at once when the device is idle), 2 streams, batches of up to 4 requests as "
-                     "one-launch single queries; admission by device result memory",
-           "plain": "rmips_query per request on one host thread, host q and ids, segments as id ranges / id lists",
-           "rates": []}
+    out = []
     for rate in rates:
-        nr = min(n_req, n_serve[rate])
-        if nr <= 0:
-            break
+        nr = min(len(qs), n_serve[rate])
         rng = np.random.default_rng(int(rate))
         arrive = np.cumsum(rng.exponential(1.0 / rate, nr))
         srv = rmips.Server(index, **opts)
@@ -322,8 +297,7 @@ def run_serving(rmips, index, P, a):
             while j < nr and arrive[j] <= now and j - i < 1024:
                 j += 1
             tk = srv.submit_many(qs[i:j], ks[i:j], sseg[i:j])
-            sub = time.perf_counter() - t0
-            lags[i:j] = sub - arrive[i:j]
+            lags[i:j] = (time.perf_counter() - t0) - arrive[i:j]
             groups.append((i, j, tk))
             i = j
         groups.append((nr, nr, None))
@@ -338,7 +312,6 @@ def run_serving(rmips, index, P, a):
                   "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
                   "max_ms": float(lat_s.max()), "mean_batch": st["mean_batch"], "batches": st["batches"],
                   "mean_submit_lag_ms": float(1e3 * lags.mean())}
-        # plain path on the same schedule
         npl = min(nr, n_plain[rate])
         plat = np.zeros(npl)
         t0 = time.perf_counter()
@@ -354,7 +327,41 @@ def run_serving(rmips, index, P, a):
         plain = {"offered_qps": rate, "requests": npl, "achieved_qps": npl / pel,
                  "p50_ms": float(1e3 * np.percentile(plat, 50)), "p99_ms": float(1e3 * np.percentile(plat, 99)),
                  "max_ms": float(1e3 * plat.max())}
-        out["rates"].append({"served": served, "plain": plain})
+        out.append({"served": served, "plain": plain})
+    return out
+
+
+def run_serving(rmips, index, P, a):
+    """Served (rmips_server_*) against plain (one rmips_query per request)
+    latency at the same offered loads.  Arrivals follow a Poisson process at
+    each rate; a request's latency runs from its scheduled arrival to the
+    moment its result is available to the caller (for the server: the
+    library's submit-to-completion time plus the submitter's lag behind the
+    schedule).  The plain path takes the requests in arrival order on one
+    host thread, so at a rate above what it can carry its queue, and its
+    latency, grow for as long as the run lasts.  Two workloads: the serving
+    workload with segments, and the same requests without segments (which the
+    plain path can carry at 20k requests/s)."""
+    n_req = min(a.serve_requests, 100_000)
+    qs, ks, segs, subsets = serving_requests(P, a.n, a.d, max(n_req, 1), 41)
+    opts = dict(max_batch=4096, max_wait_us=200, streams=2, max_pending=1 << 21)
+    warm = rmips.Server(index, **opts)
+    warm.wait_many(warm.submit_many(qs[:4096], ks[:4096]))
+    warm.close()
+    out = {"workload": "Poisson arrivals; q = random item of P or random N(0, I/d) (half each); k uniform in "
+                       "1..25; segment: none / contiguous id range / registered random id subset (a third each), "
+                       "segment sizes log-uniform in 1e3..1e6",
+           "server": "rmips_server: max_batch 4096, max_wait_us 200 while a batch is on the device (a batch "
+                     "closes at once when the device is idle), 2 streams, batches of up to 4 requests as "
+                     "one-launch single queries; admission by device result memory",
+           "plain": "rmips_query per request on one host thread, host q and ids, segments as id ranges / id lists"}
+    out["with_segments"] = serve_rates(rmips, index, qs, ks, segs, subsets, [20_000.0, 200_000.0, 1_000_000.0],
+                                       {20_000.0: 10_000, 200_000.0: 40_000, 1_000_000.0: n_req},
+                                       {20_000.0: 3_000, 200_000.0: 3_000, 1_000_000.0: 3_000}, opts)
+    none = [None] * len(qs)
+    out["without_segments"] = serve_rates(rmips, index, qs, ks, none, [], [5_000.0, 20_000.0, 200_000.0],
+                                          {5_000.0: 5_000, 20_000.0: 10_000, 200_000.0: 40_000},
+                                          {5_000.0: 5_000, 20_000.0: 10_000, 200_000.0: 4_000}, opts)
     return out
 
 
@@ -672,18 +679,22 @@ def run_ours(a):
         for j in range(20):                                    # warm-up (both workspaces)
             rmips.rmips_query_async(index, dqs[j], a.k, sout[j & 1], sdone[j], stream=stream)
         torch.cuda.synchronize(dev)
-        rmips.rmips_profile_enable(index, True)
-        s_total_ms = 0.0
-        for b0 in range(0, ns1, burst):
-            b1 = min(ns1, b0 + burst)
-            torch.cuda._sleep(int(2e6 * 25))                 # ~25 ms at 2 GHz
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for j in range(b0, b1):
-                rmips.rmips_query_async(index, dqs[j], a.k, sout[j & 1], sdone[j], stream=stream)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            s_total_ms += e0.elapsed_time(e1)
+        def bursts():
+            total = 0.0
+            for b0 in range(0, ns1, burst):
+                b1 = min(ns1, b0 + burst)
+                torch.cuda._sleep(int(2e6 * 25))             # ~25 ms at 2 GHz
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for j in range(b0, b1):
+                    rmips.rmips_query_async(index, dqs[j], a.k, sout[j & 1], sdone[j], stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                total += e0.elapsed_time(e1)
+            return total
+        s_total_ms = bursts()                                  # throughput, profiling off
+        rmips.rmips_profile_enable(index, True)                 # kernel launch times for the roofline
+        bursts()
         sprof = rmips.rmips_profile_read(index)
         rmips.rmips_profile_enable(index, False)
         sd = sdone.cpu().numpy()

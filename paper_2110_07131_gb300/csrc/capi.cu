@@ -149,7 +149,8 @@ Workspace* acquire_workspace(rmips_index* idx, rmips_status* st) {
 
 rmips_status ws_join(Workspace* ws, cudaStream_t st) {
   if (ws->done_pending) {
-    RMIPS_TRY_CUDA(cudaStreamWaitEvent(st, ws->done_ev, 0));
+    // on the stream that queued the work, stream order already joins it
+    if (ws->done_stream != st) RMIPS_TRY_CUDA(cudaStreamWaitEvent(st, ws->done_ev, 0));
     ws->done_pending = false;
   }
   return RMIPS_OK;

@@ -729,6 +729,31 @@ __device__ __forceinline__ int32_t q1_warp_sort(int32_t x) {
 
 __host__ __device__ inline size_t q1_stage_bytes(int d, int es) { return (size_t)Q1_WARPS * 32 * d * es; }
 
+// query_bounds for one warp (every lane calls it, all get the result): the
+// sum of squares rounded up in every step (any order gives an upper bound of
+// ||q||^2), the largest |q_i|, finiteness and the format's range.
+__device__ __forceinline__ bool query_bounds_warp(const float* q, int d, int precision, float* qn, float* eps) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f, qmax = 0.f;
+  bool fin = true;
+  const float vmax = filter_max_abs(precision);
+  for (int i = lane; i < d; i += 32) {
+    const float v = q[i];
+    fin = fin && isfinite(v) && !(fabsf(v) > vmax);
+    acc = __fmaf_ru(v, v, acc);
+    qmax = fmaxf(qmax, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc = __fadd_ru(acc, __shfl_xor_sync(FULL, acc, o));
+    qmax = fmaxf(qmax, __shfl_xor_sync(FULL, qmax, o));
+  }
+  *qn = __fsqrt_ru(acc);
+  const float sub = (precision == RMIPS_FP16) ? 0x1p-25f : (precision == RMIPS_BF16 ? 0x1p-133f : 0.f);
+  *eps = __fmul_ru((float)(d + 2), __fmaf_ru(sub, qmax, 0x1p-148f));
+  return __all_sync(FULL, fin);
+}
+
 // u.q for this lane's row of a staged chunk (row-major, stride d).  With d
 // even the row is read in pairs: 8-byte words of float32 rows (lane stride
 // 25 words for d = 50: conflict-free per half-warp) or 4-byte pairs of 16-bit
@@ -778,7 +803,7 @@ __device__ __forceinline__ float q1_dot(const T* __restrict__ row, const float* 
 template <class T>
 __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, const float* q_src, int k,
                                                           int precision, int ns, long long* res, long long* done,
-                                                          unsigned long long* pacc) {
+                                                          unsigned long long* pacc, int res_host) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* sq = reinterpret_cast<float*>(smem);                             // [RMIPS_DMAX]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + 512);               // [Q1_MAXNS]
@@ -814,8 +839,32 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
     s_ntodo = 0;
     for (int s = 0; s < Q1_MAXNS; ++s) s_fills[s] = 0;
   }
+  // the producer's first round of Lemma 3 loads is issued before the query's
+  // norm is known (it only decides the comparison)
+  const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
+  const int64_t G = gridDim.x;
+  float pre_h[Q1_WARPS], pre_l[Q1_WARPS];
+  if (warp == Q1_WARPS) {
+    const int64_t sp = blockIdx.x + (int64_t)lane * G;
+#pragma unroll
+    for (int i = 0; i < Q1_WARPS; ++i) {
+      const int64_t ch = sp * Q1_WARPS + i;
+      const bool in = sp < nspans && ch < nchunks;
+      const int64_t blk = in ? (ch * 32) / c.bs : 0;
+      pre_h[i] = in ? c.hdr[blk] : 0.f;
+      pre_l[i] = in ? LBk[blk] : 0.f;
+    }
+  }
   __syncthreads();
-  if (tid == 0) s_fin = query_bounds(sq, d, precision, &s_qn, &s_eps) ? 1 : 0;
+  if (warp == 0) {
+    float qn0, eps0;
+    const bool fin = query_bounds_warp(sq, d, precision, &qn0, &eps0);
+    if (lane == 0) {
+      s_qn = qn0;
+      s_eps = eps0;
+      s_fin = fin ? 1 : 0;
+    }
+  }
   __syncthreads();
   const float qn = s_qn, qeps = s_eps;
   const float2* Lbk = c.Lb + (int64_t)(k - 1) * n;
@@ -835,8 +884,6 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   };
   if (s_fin && warp == Q1_WARPS) {
     // ---------------- producer ----------------
-    const float* LBk = c.LB + (int64_t)(k - 1) * c.nb;
-    const int64_t G = gridDim.x;
     int stage = 0;
     uint32_t ph = 0;                   // bit s: parity of the next empty wait on stage s
     uint32_t used = 0;                 // bit s: stage s was filled at least once
@@ -850,7 +897,9 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
           const int64_t ch = sp * Q1_WARPS + i;
           if (ch < nchunks) {
             const int64_t blk = (ch * 32) / c.bs;
-            if (!(__fmul_ru(c.hdr[blk], qn) < LBk[blk])) mask |= 1u << i;   // Lemma 3, strict
+            const float h = base == 0 ? pre_h[i] : c.hdr[blk];
+            const float lb = base == 0 ? pre_l[i] : LBk[blk];
+            if (!(__fmul_ru(h, qn) < lb)) mask |= 1u << i;               // Lemma 3, strict
           }
         }
       }
@@ -1092,7 +1141,7 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       atomicAdd(&pacc[2], (unsigned long long)s_ctr[C_PRUNED]);
       atomicAdd(&pacc[3], 1ull);
     }
-    __threadfence_system();
+    if (res_host) __threadfence_system();                      // res is device-mapped host memory
   }
 }
 
@@ -1292,15 +1341,15 @@ rmips_status status_from_device(long long s) {
 
 template <class T>
 cudaError_t launch_query1(const Common& c, const EmitArgs& e, const float* q, int k, int precision, int ns,
-                          long long* res, long long* done, unsigned long long* pacc, int grid, size_t smem,
-                          cudaStream_t st) {
+                          long long* res, long long* done, unsigned long long* pacc, int res_host, int grid,
+                          size_t smem, cudaStream_t st) {
   static thread_local size_t configured = 0;
   if (configured < smem) {
     cudaError_t err = cudaFuncSetAttribute(k_query1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     configured = smem;
   }
-  k_query1<T><<<grid, Q1_THREADS, smem, st>>>(c, e, q, k, precision, ns, res, done, pacc);
+  k_query1<T><<<grid, Q1_THREADS, smem, st>>>(c, e, q, k, precision, ns, res, done, pacc, res_host);
   return cudaGetLastError();
 }
 
@@ -1335,15 +1384,17 @@ Q1Plan q1_plan(const rmips_index* idx) {
 }
 
 cudaError_t q1_dispatch(const rmips_index* idx, const Common& c, const EmitArgs& e, const float* q, int k,
-                        long long* res, long long* done, unsigned long long* pacc, cudaStream_t st) {
+                        long long* res, long long* done, unsigned long long* pacc, cudaStream_t st,
+                        int res_host = 0) {
   const Q1Plan p = q1_plan(idx);
   switch (idx->precision) {
     case RMIPS_BF16:
-      return launch_query1<__nv_bfloat16>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+      return launch_query1<__nv_bfloat16>(c, e, q, k, idx->precision, p.ns, res, done, pacc, res_host, p.grid,
+                                          p.smem, st);
     case RMIPS_FP16:
-      return launch_query1<__half>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+      return launch_query1<__half>(c, e, q, k, idx->precision, p.ns, res, done, pacc, res_host, p.grid, p.smem, st);
     default:
-      return launch_query1<float>(c, e, q, k, idx->precision, p.ns, res, done, pacc, p.grid, p.smem, st);
+      return launch_query1<float>(c, e, q, k, idx->precision, p.ns, res, done, pacc, res_host, p.grid, p.smem, st);
   }
 }
 
@@ -1379,7 +1430,7 @@ rmips_status query_fused(rmips_index* idx, Workspace* ws, const float* q, int32_
     }
     RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[0], st));
   }
-  const cudaError_t err = q1_dispatch(idx, c, e, q_src, k, ws->h_res, nullptr, nullptr, st);
+  const cudaError_t err = q1_dispatch(idx, c, e, q_src, k, ws->h_res, nullptr, nullptr, st, 1);
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return RMIPS_ERR_CUDA; }
   if (prof) RMIPS_TRY_CUDA(cudaEventRecord(ws->ev[1], st));
   RMIPS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -3870,6 +3921,7 @@ extern "C" rmips_status rmips_query_batch_async(rmips_index* idx, const float* q
   }
   RMIPS_TRY_CUDA(cudaEventRecord(ws->done_ev, st));
   ws->done_pending = true;
+  ws->done_stream = st;
   return RMIPS_OK;
 }
 
@@ -3936,6 +3988,7 @@ extern "C" rmips_status rmips_query_async(rmips_index* idx, const float* q, int3
   }
   RMIPS_TRY_CUDA(cudaEventRecord(ws->done_ev, st));
   ws->done_pending = true;
+  ws->done_stream = st;
   return RMIPS_OK;
 }
 

@@ -145,6 +145,7 @@ struct Workspace {
   cudaStream_t cap_stream = nullptr;  // capture only (the legacy stream cannot capture)
   cudaEvent_t done_ev = nullptr; // recorded after the work of an asynchronous call
   bool done_pending = false;     // a later user joins done_ev on its own stream first
+  cudaStream_t done_stream = nullptr;  // the stream done_ev was recorded on
   std::vector<cudaEvent_t> ev;   // profiling: start/stop pair per filter launch
   int64_t ev_used = 0;
   // batched (multi-query) path
