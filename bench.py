@@ -385,7 +385,7 @@ def simpfer_cpu_baseline(Q, P, qs, k, k_max, seconds=10.0):
     idx = S.SimpferCPU(Q, P, k_max=k_max, p_prime=4 * k_max, threads=0)
     build_s = time.perf_counter() - t0
     out = {"kind": "cpu simpfer (Algorithm 3 with Algorithm 2, float64, exact ties)", "p_prime": 4 * k_max,
-           "index_build_s": build_s, "cpu_model": cpu_model(), "openmp": bool(S.OPENMP)}
+           "index_build_s": build_s, "cpu_model": cpu_model(), "openmp": S.openmp()}
     for label, threads in (("all_cores", 0), ("one_core", 1)):
         n_done, t0 = 0, time.perf_counter()
         while n_done < len(qs) and (time.perf_counter() - t0 < seconds / 2 or n_done < 3):

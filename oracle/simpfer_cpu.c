@@ -188,6 +188,14 @@ int simpfer_max_threads(void) {
 #endif
 }
 
+int simpfer_openmp(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 static void set_threads(int threads) {
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);

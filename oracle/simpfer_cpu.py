@@ -61,12 +61,18 @@ def _load():
         lib.simpfer_query.restype = I64
         lib.simpfer_free.argtypes = [P]
         lib.simpfer_max_threads.restype = I32
+        lib.simpfer_openmp.restype = I32
         lib.simpfer_exact_sign.argtypes = [P, P, P, I32]
         lib.simpfer_exact_sign.restype = I32
         lib.simpfer_blocks.argtypes = [P]
         lib.simpfer_blocks.restype = I64
         _lib = lib
     return _lib
+
+
+def openmp() -> bool:
+    """Whether the loaded library was compiled with OpenMP."""
+    return bool(_load().simpfer_openmp())
 
 
 def max_threads() -> int:
