@@ -2672,23 +2672,6 @@ __device__ __forceinline__ float ws_pick(const float* v, int q) {
   return (q & 16) ? a[1] : a[0];
 }
 
-// Largest of three floats in one instruction (three-input max.f32).
-__device__ __forceinline__ float fmax3(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-
-// Largest of 32 accumulators: 17 max operations in a tree four deep.
-__device__ __forceinline__ float ws_max32(const float* v) {
-  float m[11];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) m[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-  m[10] = fmaxf(v[30], v[31]);
-  const float a = fmax3(m[0], m[1], m[2]), b = fmax3(m[3], m[4], m[5]), c = fmax3(m[6], m[7], m[8]);
-  return fmaxf(fmax3(a, b, c), fmaxf(m[9], m[10]));
-}
-
 // Pair lists without a shared counter per pair: an epilogue warp reserves
 // slots at least a chunk at a time (one global atomic) and fills them in
 // order; the slots left over in its last chunk hold PAIR_NONE, which every
@@ -2883,27 +2866,41 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     uint32_t fpar = 0, fused = 0;           // per operand slot: parity of its fill count, filled at least once
     uint32_t epar = 0;                      // per data slot: parity of its fill count
     int ab = 0, es = 0, seq = 0;
-    // tiles in order (descending user norm: the heaviest first), each taken
-    // by the next CTA whose loader asks; the next index is fetched while the
-    // current tile is prepared
-    auto take = [&]() -> int64_t {
-      long long t = 0;
-      if (lane == 0) t = (long long)atomicAdd((unsigned long long*)&c.ctr[C_TILE], 1ull);
-      return __shfl_sync(FULL, t, 0);
+    // Tiles in a snake order over the CTAs (the norm order puts the heaviest
+    // first; CTA c takes tiles c, 2G - 1 - c, 2G + c, ... of G per round), so
+    // no global counter sits on the loader's path.  A tile's Lemma 3 prefixes
+    // are loaded one tile ahead, and its norms and bounds with every load
+    // issued before the first store: one memory latency per tile.
+    const int64_t G = gridDim.x;
+    auto tile_at = [&](int64_t i) -> int64_t { return i * G + ((i & 1) ? G - 1 - blockIdx.x : blockIdx.x); };
+    auto load_pre = [&](int64_t t, int* pf) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = lane + 32 * i;
+        pf[i] = 0;
+        if (t < ntiles && e < ngroups * nbt) {
+          const int g = e / nbt, sb = e - g * nbt;
+          const int64_t uf = t * TCU + (int64_t)sb * sub;
+          if (uf < c.n && sgrp[g].z > 0) pf[i] = b.gpre[(uf / c.bs) * ngroups + g];
+        }
+      }
     };
-    int64_t tnext = take();
+    static_assert(RMIPS_KMAX_LIMIT * 4 <= 128, "prefixes of a tile: four per lane");
+    int64_t iter = 0, tt = tile_at(0);
+    int pf[4];
+    load_pre(tt, pf);
     for (;;) {
-      const int64_t tt = tnext;
       if (tt >= ntiles || s_fail) break;
-      tnext = take();
-      const int64_t u0 = tt * TCU;
-      const int nvalid = (int)((c.n - u0) < TCU ? (c.n - u0) : TCU);
-      for (int e = lane; e < ngroups * nbt; e += 32) {
-        const int g = e / nbt, sb = e - g * nbt;
-        const int64_t uf = u0 + (int64_t)sb * sub;
-        lpre[g][sb] = (uf < c.n && sgrp[g].z > 0) ? b.gpre[(uf / c.bs) * ngroups + g] : 0;
+      const int64_t tn = tile_at(iter + 1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int e = lane + 32 * i;
+        if (e < ngroups * nbt) lpre[e / nbt][e % nbt] = pf[i];
       }
       __syncwarp();
+      load_pre(tn, pf);                                 // in flight while this tile is prepared
+      const int64_t u0 = tt * TCU;
+      const int nvalid = (int)((c.n - u0) < TCU ? (c.n - u0) : TCU);
       int gm = 0;
       if (lane < ngroups) {
         for (int sb = 0; sb < nbt; ++sb) {
@@ -2914,8 +2911,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         }
       }
       const unsigned act = __ballot_sync(FULL, gm > 0);
+      ++iter;
       if (!act) {
         ++st_skipped;
+        tt = tn;
         __syncwarp();
         continue;
       }
@@ -2936,14 +2935,33 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         T.end = 0;
         T.seq = seq;
       }
-      for (int r = lane; r < TCU; r += 32) sUN[es * TCU + r] = r < nvalid ? c.unorm[u0 + r] : 0.f;
       __syncwarp();
       const int nstage = min(__popc(act), WS_LG);          // further groups' bounds are read from memory
-      for (int ga = 0; ga < nstage; ++ga) {
-        const float2* src = c.Lb + (int64_t)(T.k[ga] - 1) * c.n + u0;
-        float2* dst = sL + ((size_t)es * WS_LG + ga) * TCU;
-        for (int r = lane; r < TCU; r += 32) dst[r] = r < nvalid ? src[r] : make_float2(kInf, kInf);
+      float unv[TCU / 32];
+      float2 lbv[WS_LG][TCU / 32];
+#pragma unroll
+      for (int i = 0; i < TCU / 32; ++i) {
+        const int r = lane + 32 * i;
+        unv[i] = r < nvalid ? c.unorm[u0 + r] : 0.f;
       }
+#pragma unroll
+      for (int ga = 0; ga < WS_LG; ++ga) {
+        const float2* src = c.Lb + (int64_t)((ga < nstage ? T.k[ga] : 1) - 1) * c.n + u0;
+#pragma unroll
+        for (int i = 0; i < TCU / 32; ++i) {
+          const int r = lane + 32 * i;
+          lbv[ga][i] = (ga < nstage && r < nvalid) ? src[r] : make_float2(kInf, kInf);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < TCU / 32; ++i) sUN[es * TCU + lane + 32 * i] = unv[i];
+#pragma unroll
+      for (int ga = 0; ga < WS_LG; ++ga)
+        if (ga < nstage) {
+          float2* dst = sL + ((size_t)es * WS_LG + ga) * TCU;
+#pragma unroll
+          for (int i = 0; i < TCU / 32; ++i) dst[lane + 32 * i] = lbv[ga][i];
+        }
       __threadfence_block();
       __syncwarp();
       if (lane == 0) {
@@ -2957,6 +2975,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       es = es + 1 == WS_ESLOTS ? 0 : es + 1;
       ++seq;
       ++st_active;
+      tt = tn;
     }
     if (!s_fail && wwait(&aempty[ab], ((fpar >> ab) & 1u) ^ 1u, &w_a) &&
         wwait(&eempty[es], ((epar >> es) & 1u) ^ 1u, &w_a)) {            // end marker
@@ -3167,11 +3186,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         long long t_ld = 0;
         if (PROF) t_ld = clock64();
         tc_fence_after();
-        tmem_ld32(tl + (uint32_t)(acc * WS_N + 32 * h), v);
+        const float mx = tmem_ld32_max(tl + (uint32_t)(acc * WS_N + 32 * h), v);
         tmem_ld_wait();
         if (PROF) w_b += clock64() - t_ld;
         bool any = rowok;
-        if (rowok && lh == 32) any = ws_max32(v) >= thr;
+        if (rowok && lh == 32) any = mx >= thr;
         if (__any_sync(FULL, any)) {
           long long t_sl = 0;
           if (PROF) t_sl = clock64();
