@@ -54,7 +54,7 @@ bool header_ok(const FileHeader& h, std::string* why) {
     return bad("flag field out of range");
   {
     const int ws_ns = h.tune & 0xff, q1_ns = (h.tune >> 8) & 0xff, tuned = (h.tune >> 16) & 0xff;
-    if ((h.tune >> 24) != 0 || ws_ns > 6 || (ws_ns & 1) || q1_ns > 8 || tuned > 2)
+    if ((h.tune >> 24) != 0 || ws_ns > RMIPS_WS_MAXNS || (ws_ns & 1) || q1_ns > 8 || tuned > 2)
       return bad("autotuner field out of range");
   }
   if (h.pp < 1 || h.pp > h.m || (h.full_p == 1) != (h.pp == h.m)) return bad("|P'| does not match the index mode");

@@ -2575,10 +2575,12 @@ __host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K 
 #define RMIPS_WS_EPI 16
 #endif
 constexpr int WS_EPI = RMIPS_WS_EPI;                   // epilogue warps: 2 sets x 4 lane quadrants x 2 column halves
-constexpr int WS_LOADER = WS_EPI, WS_FEEDER = WS_EPI + 1, WS_MMA = WS_EPI + 2;   // MMA warps take even / odd items
-constexpr int WS_THREADS = (WS_EPI + 4) * 32;
+constexpr int WS_NMMA = RMIPS_WS_NMMA;                 // MMA warps, taking items in turn
+constexpr int WS_LOADER = WS_EPI, WS_FEEDER = WS_EPI + 1, WS_MMA = WS_EPI + 2;
+constexpr int WS_THREADS = (WS_EPI + 2 + WS_NMMA) * 32;
 constexpr int WS_NACC = 4;                             // TMEM accumulator stages of WS_N columns
-constexpr int WS_MAXNS = 6;                            // query stages at most
+static_assert(WS_NACC % WS_NMMA == 0 && WS_NACC % 2 == 0, "each MMA warp owns fixed accumulators");
+constexpr int WS_MAXNS = RMIPS_WS_MAXNS;               // query stages at most (as many as fit are used)
 constexpr int WS_LG = 4;                               // groups per tile whose bounds are staged
 constexpr int WS_ESET = WS_EPI / 2;                    // epilogue warps per item: the two sets take alternate items
 constexpr int WS_ECOLS = WS_N / (WS_ESET / 4);         // query columns per epilogue warp, read 32 at a time
@@ -2798,7 +2800,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
   __shared__ int sgi[RMIPS_KMAX_LIMIT];
   __shared__ int lpre[RMIPS_KMAX_LIMIT][4];
   __shared__ __align__(8) uint64_t afull[2], aempty[2], eempty[WS_ESLOTS], bfull[WS_MAXNS], bempty[WS_MAXNS];
-  __shared__ __align__(8) uint64_t tfull[WS_NACC], tempty[WS_NACC], mdone[2];
+  __shared__ __align__(8) uint64_t tfull[WS_NACC], tempty[WS_NACC], mdone[WS_NMMA];
   __shared__ uint32_t taddr_s;
   __shared__ volatile int s_fail;
   __shared__ float2 s_ecq[WS_EPI][32];                  // per epilogue warp: 32 columns' (scale, slack)
@@ -2818,12 +2820,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
   if (tid == 0) {
     // an operand slot is free once both MMA warps are through its tile; a
     // tile's per-user data once every epilogue warp has moved past the tile
-    for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], 2); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&afull[i], 1); mbar_init(&aempty[i], WS_NMMA); }
     for (int i = 0; i < WS_ESLOTS; ++i) mbar_init(&eempty[i], WS_EPI);
     for (int i = 0; i < ns; ++i) { mbar_init(&bfull[i], 1); mbar_init(&bempty[i], 1); }   // emptied by the MMA commit
     for (int i = 0; i < WS_NACC; ++i) { mbar_init(&tfull[i], 2); mbar_init(&tempty[i], WS_ESET); }
-    mbar_init(&mdone[0], 1);
-    mbar_init(&mdone[1], 1);
+    for (int i = 0; i < WS_NMMA; ++i) mbar_init(&mdone[i], 1);
     fence_mbar_init();
     s_fail = 0;
   }
@@ -3029,14 +3030,17 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
     for (int x = 0; x < ns; ++x)                                      // copies in flight
       if ((armed >> x) & 1u) mbar_wait_bounded(&bfull[x], ((epar >> x) & 1u) ^ 1u);
     report(WST_FEEDER_WAIT, -1, WST_FEEDER);
-  } else if (warp == WS_MMA || warp == WS_MMA + 1) {
+  } else if (warp >= WS_MMA && warp < WS_MMA + WS_NMMA) {
     // ---------------------------------------------------------------- mma
     // The tensor core queues almost nothing: every cycle the issuing thread
     // spends between two MMAs (a barrier wait, loop control) leaves it idle.
-    // Two warps therefore issue alternate items -- one waits while the other
-    // issues -- and the K loop has a compile-time trip count.  Items keep the
-    // round-robin stage / accumulator order; with an even ns and WS_NACC each
-    // warp owns fixed stages and accumulators, so parities stay per warp.
+    // WS_NMMA warps therefore issue items in turn -- the others wait while one
+    // issues -- the MMAs go out as soon as the item's waits pass (its record
+    // is written after them), and the K loop has a compile-time trip count.
+    // Items keep the round-robin stage / accumulator order.  ns and WS_NACC
+    // are multiples of WS_NMMA, so warp w owns the stages and accumulators
+    // of items w, w + WS_NMMA, ... and waits on each of their barriers'
+    // phases in order (a barrier is never tested one phase early).
     const int me = warp - WS_MMA;
     const uint64_t adesc0 = tc_sdesc(smem_u32(sA), TC_LBO, SBO);
     const uint64_t adesc1 = tc_sdesc(smem_u32(sA + ABYTES), TC_LBO, SBO);
@@ -3056,18 +3060,16 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
         const int gmax = T.gmax[ga];
         const int nt = (gmax + WS_N - 1) / WS_N;
         for (int t = 0; t < nt; ++t, ++it) {
-          if ((it & 1) == me) {
-            if (!wwait(&bfull[stg], (fpar >> stg) & 1u, &w_a)) { ok = false; break; }
-            if (!wwait(&tempty[acc], ((tpar >> acc) & 1u) ^ 1u, &w_b)) { ok = false; break; }
-            fpar ^= 1u << stg;
-            tpar ^= 1u << acc;
+          const uint32_t fp = (fpar >> stg) & 1u, tp = (tpar >> acc) & 1u;
+          fpar ^= 1u << stg;
+          tpar ^= 1u << acc;
+          if (it % WS_NMMA == me) {
+            if (!wwait(&bfull[stg], fp, &w_a)) { ok = false; break; }
+            if (!wwait(&tempty[acc], tp ^ 1u, &w_b)) { ok = false; break; }
             long long t_is = 0;
             if (PROF) t_is = clock64();
             if (lane == 0) {
               const int nq = ws_item_n(gmax, t);
-              const float2 c0 = *reinterpret_cast<const float2*>(sB + (size_t)stg * PACK + BROWS);
-              items[acc] = WsItem{seq, ga, t, T.item0[ga] + t,
-                                  (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0), c0};
               const uint32_t idesc = KIND == TCK_TF32 ? tc_idesc_tf32(TCU, (uint32_t)nq)
                                                       : tc_idesc_f16(TCU, (uint32_t)nq, KIND == TCK_BF16);
               const uint64_t ad0 = ab ? adesc1 : adesc0, bd0 = bdesc0 + (uint64_t)stg * BSTEP;
@@ -3080,6 +3082,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
                 if (KIND == TCK_TF32) tc_mma_tf32(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
                 else tc_mma_f16(d, ad0 + (uint64_t)(s * 16), bd0 + (uint64_t)(s * 16), idesc, s > 0 ? 1u : 0u);
               }
+              const float2 c0 = *reinterpret_cast<const float2*>(sB + (size_t)stg * PACK + BROWS);
+              items[acc] = WsItem{seq, ga, t, T.item0[ga] + t,
+                                  (ga == ngact - 1 && t == nt - 1 ? WI_LAST : 0) | (t == 0 ? WI_NEWGROUP : 0), c0};
               tc_commit(&bempty[stg]);           // the stage is free once these MMAs have read it
               tc_commit(&tfull[acc]);
               mbar_arrive(&tfull[acc]);
@@ -3105,10 +3110,10 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       es = es + 1 == WS_ESLOTS ? 0 : es + 1;
       ++seq;
     }
-    // end markers: each warp writes one into the next accumulator stage it
-    // owns, so that both epilogue sets (alternate stages) see one
-    {
-      const int ea = (it & 1) == me ? acc : (acc + 1 == WS_NACC ? 0 : acc + 1);
+    // end markers in the next two accumulator stages, so that both epilogue
+    // sets (alternate stages) see one, each written by the stage's owner
+    if (me == acc % WS_NMMA || me == (acc + 1) % WS_NMMA) {
+      const int ea = me == acc % WS_NMMA ? acc : (acc + 1) % WS_NACC;
       if (!s_fail && wwait(&tempty[ea], ((tpar >> ea) & 1u) ^ 1u, &w_b)) {
         if (lane == 0) {
           items[ea].flags = WI_END;
@@ -3428,10 +3433,10 @@ rmips_status run_batch(rmips_index* idx, Workspace* ws, int64_t nq, long long* o
   const bool use_tc = idx->batch_tc && idx->d <= (int)TC_K && idx->Qtc;
   const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
   const size_t smem = (size_t)idx->d * (MQ_US + MQ_QS) * sizeof(float) + (size_t)ngroups_max * MQ_TU * sizeof(float2);
-  int ws_ns = WS_MAXNS;                   // query stages that fit beside the user tiles and bounds
-  while (ws_ns > 2 && ws_smem_bytes(tck, ws_ns) > 220 * 1024) --ws_ns;
+  int ws_ns = max_batch_stages(idx);      // query stages that fit beside the user tiles and bounds
   if (idx->tune_ws_ns > 0 && idx->tune_ws_ns < ws_ns) ws_ns = idx->tune_ws_ns;   // the autotuner's choice
-  ws_ns &= ~1;                            // even: each MMA warp owns fixed stages
+  ws_ns -= ws_ns % WS_NMMA;               // a multiple of the MMA warps: each owns fixed stages
+  if (ws_ns < WS_NMMA) ws_ns = WS_NMMA;
   const size_t smem_ws = ws_smem_bytes(tck, ws_ns);
   const int64_t tc_tiles = (idx->n + TCU - 1) / TCU;
   const int tc_grid = (int)(tc_tiles < sm_count ? tc_tiles : sm_count);
@@ -4088,8 +4093,8 @@ rmips_status single_launch(rmips_index* idx, Workspace* ws, const float* q, int 
 int max_batch_stages(const rmips_index* idx) {
   const int tck = idx->precision == RMIPS_BF16 ? TCK_BF16 : (idx->precision == RMIPS_FP16 ? TCK_FP16 : TCK_TF32);
   int ns = WS_MAXNS;
-  while (ns > 2 && ws_smem_bytes(tck, ns) > 220 * 1024) --ns;
-  return ns & ~1;
+  while (ns > WS_NMMA && ws_smem_bytes(tck, ns) > 220 * 1024) --ns;
+  return ns - ns % WS_NMMA;
 }
 
 int max_single_stages(const rmips_index* idx) {

@@ -38,6 +38,8 @@
 
 #define RMIPS_KC 32              // candidate slots per user (>= k_max + slack)
 #define RMIPS_KMAX_LIMIT 28      // largest supported k_max
+#define RMIPS_WS_MAXNS 12        // query stages of the batched tensor-core filter at most
+#define RMIPS_WS_NMMA 4          // its MMA warps; the query stages are a multiple of this
 #define RMIPS_DMAX 128           // largest supported dimension
 #define MQ_MAXQ 16384            // queries per multi-query pass (14-bit index)
 #define MQ_TQ 64                 // queries per tile

@@ -8,7 +8,7 @@
 // search measures them on the index itself:
 //   * block size b in {32, 64, 128, 256} (the block arrays are rebuilt from
 //     the index's bounds, Equation 1) x query stages of the batched
-//     tensor-core filter in {2, 4, 6} (as many as fit): the batched path's
+//     tensor-core filter in {4, 8, ...} (as many as fit): the batched path's
 //     time on 1,024 items of P spread over the norm order, with k cycling
 //     through 1..k_max;
 //   * then row stages of the single-query kernel in {2, ..., as many as fit}:
@@ -60,7 +60,7 @@ bool cache_read(const char* path, const std::string& key, Choice* c) {
     Choice t;
     if (sscanf(bar + 3, "bs=%d batch_stages=%d single_stages=%d batch_ms=%f single_ms=%f", &t.bs, &t.ws_ns,
                &t.q1_ns, &t.batch_ms, &t.single_ms) == 5 &&
-        (t.bs == 32 || t.bs == 64 || t.bs == 128 || t.bs == 256) && t.ws_ns >= 0 && t.ws_ns <= 6 &&
+        (t.bs == 32 || t.bs == 64 || t.bs == 128 || t.bs == 256) && t.ws_ns >= 0 && t.ws_ns <= RMIPS_WS_MAXNS && (t.ws_ns & 1) == 0 &&
         t.q1_ns >= 0 && t.q1_ns <= 8) {
       *c = t;                       // the last valid line for the key wins
       found = true;
@@ -107,7 +107,7 @@ rmips_status search(rmips_index* idx, cudaStream_t st, Choice* best) {
   for (int bi = 0; s == RMIPS_OK && bi < 4; ++bi) {
     if (idx->no_blocks && sizes[bi] != bs0) continue;          // no block bounds: the size does not matter
     if ((s = set_block_size(idx, sizes[bi], st)) != RMIPS_OK) break;
-    for (int ns = 2; s == RMIPS_OK && ns <= (tc ? ns_max : 2); ns += 2) {
+    for (int ns = RMIPS_WS_NMMA; s == RMIPS_OK && ns <= (tc ? ns_max : RMIPS_WS_NMMA); ns += RMIPS_WS_NMMA) {
       idx->tune_ws_ns = tc ? ns : 0;
       float ms = 0.f;
       if ((s = tune_time_batch(idx, dq, dk, nq, 3, st, &ms)) != RMIPS_OK) break;

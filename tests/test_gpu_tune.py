@@ -35,7 +35,7 @@ def test_tuned_and_default_choices_give_the_oracle_sets(data, tmp_path, precisio
     tuned = rmips.rmips_build_index(Q, P, k_max=25, precision=precision, tune_cache=cache)
     info = rmips.rmips_index_get_info(tuned)
     assert info["tuned"] == 1 and info["block_size"] in (32, 64, 128, 256)
-    assert info["batch_stages"] in (2, 4, 6) and info["single_stages"] >= 1
+    assert info["batch_stages"] in (4, 8, 12) and info["single_stages"] >= 1
     _check(tuned, qs, counts)
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and f"bs={info['block_size']}" in lines[0]
