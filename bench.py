@@ -751,7 +751,7 @@ def run_ours(a):
             peak_source = f"measured bf16 {bf16:.0f} TFLOP/s (FP16 and BF16 share the rate)"
         roofline = {"bound": "tensor", "kernel": f"k_mfilter_ws (warp-specialized: TMA-fed tcgen05 {op} "
                                                   "128x128xK tiles into 4 TMEM stages + Lemmas 1/2 epilogue, "
-                                                  "two epilogue warp sets on alternate items)",
+                                                  "four MMA warps and two epilogue warp sets on alternate items)",
                     "achieved": m_ach, "peak": tc_peak, "unit": "TFLOP/s", "frac": m_ach / tc_peak,
                     "peak_source": peak_source,
                     "traffic": tc_traffic, "alg_flops_per_launch": m_flops, "avg_launch_ms": m_ms,
