@@ -93,14 +93,15 @@ __global__ void k_to_half(const float* __restrict__ src, int64_t count, H* __res
   store_rn(dst + e, src[e]);
 }
 
-// Users in 128-row tiles of the tensor-core operand layout (K-major core
-// matrices, K padded to 64 with zeros): 16-byte chunks, 4 float32 (TF32 kind)
-// or 8 16-bit values; consecutive threads fill consecutive rows of a chunk
-// column.  Rows past n are zero.
+// Users in 128-row tiles of the batched filter's operand layout (wf_off:
+// K-major core matrices, rows of nstep 32-byte K steps, zeros past d):
+// 16-byte chunks, 4 float32 (TF32 kind) or 8 16-bit values; consecutive
+// threads fill consecutive rows of a chunk column.  Rows past n are zero.
 __global__ void k_user_tiles(const float* __restrict__ Qs, const uint16_t* __restrict__ Qh, int64_t n, int d,
-                             unsigned char* __restrict__ out) {
+                             int nstep, unsigned char* __restrict__ out) {
   const int per = Qh ? 8 : 4;                      // values per chunk
-  const int64_t chunks = 128 * (int64_t)(TC_K / per);
+  const int64_t chunks = 128 * (int64_t)(2 * nstep);
+  const uint32_t sbo = wf_sbo(nstep), tb = wf_tile_bytes(nstep);
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t tiles = (n + 127) / 128;
   if (e >= tiles * chunks) return;
@@ -112,7 +113,7 @@ __global__ void k_user_tiles(const float* __restrict__ Qs, const uint16_t* __res
     float v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = (u < n && k0 + i < d) ? Qs[u * d + k0 + i] : 0.f;
-    *reinterpret_cast<float4*>(out + t * (128 * TC_K * 4) + tc_off(r, k0)) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(out + t * tb + wf_off(r, (rem >> 7) * 16, sbo)) = make_float4(v[0], v[1], v[2], v[3]);
   } else {
     uint16_t h[8];
 #pragma unroll
@@ -122,7 +123,7 @@ __global__ void k_user_tiles(const float* __restrict__ Qs, const uint16_t* __res
     w.y = h[2] | ((uint32_t)h[3] << 16);
     w.z = h[4] | ((uint32_t)h[5] << 16);
     w.w = h[6] | ((uint32_t)h[7] << 16);
-    *reinterpret_cast<uint4*>(out + t * (128 * TC_K * 2) + tc_off16(r, k0)) = w;
+    *reinterpret_cast<uint4*>(out + t * tb + wf_off(r, (rem >> 7) * 16, sbo)) = w;
   }
 }
 
@@ -802,11 +803,11 @@ extern "C" rmips_status rmips_build_index(const float* Q, int64_t n, const float
     }
     if (idx->batch_tc && d <= (int)TC_K) {         // operand tiles of the batched tensor-core filter
       const int64_t tiles = (n + 127) / 128;
-      const int64_t tile_bytes = 128 * (int64_t)TC_K * (idx->precision == RMIPS_FP32 ? 4 : 2);
-      TRY(dalloc(idx, &idx->Qtc, (size_t)(tiles * tile_bytes)));
-      const int64_t chunks = tiles * 128 * (TC_K / (idx->precision == RMIPS_FP32 ? 4 : 8));
+      const int nstep = wf_nstep(idx->precision == RMIPS_FP32, d);
+      TRY(dalloc(idx, &idx->Qtc, (size_t)(tiles * wf_tile_bytes(nstep))));
+      const int64_t chunks = tiles * 128 * 2 * nstep;
       k_user_tiles<<<grid_for(chunks, 256), 256, 0, st>>>(
-          idx->Qs, idx->precision == RMIPS_FP32 ? nullptr : (const uint16_t*)idx->Qh, n, d, idx->Qtc);
+          idx->Qs, idx->precision == RMIPS_FP32 ? nullptr : (const uint16_t*)idx->Qh, n, d, nstep, idx->Qtc);
       TRY(cudaGetLastError());
     }
     // 3: candidates

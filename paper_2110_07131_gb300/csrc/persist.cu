@@ -11,11 +11,12 @@
 #include <cstring>
 
 #include "rmips_internal.cuh"
+#include "tc_common.cuh"
 
 namespace rmips {
 namespace {
 
-constexpr char kMagic[8] = {'R', 'M', 'I', 'P', 'S', 'I', 'X', '2'};
+constexpr char kMagic[8] = {'R', 'M', 'I', 'P', 'S', 'I', 'X', '3'};
 
 // File layout: this header, then for every array its byte count (int64), its
 // bytes and their 64-bit FNV-1a hash.  96 bytes, no implicit padding.
@@ -85,7 +86,7 @@ struct ArrayRef {
 std::vector<ArrayRef> arrays(rmips_index* idx, bool has_qh, bool has_qtc) {
   const int64_t n = idx->n, m = idx->m, d = idx->d, pad = 32 * d;
   const int64_t tiles = (n + 127) / 128;
-  const int64_t tile_bytes = 128 * 64 * (idx->precision == RMIPS_FP32 ? 4 : 2);
+  const int64_t tile_bytes = wf_tile_bytes(wf_nstep(idx->precision == RMIPS_FP32, idx->d));
   std::vector<ArrayRef> a = {
       {(void**)&idx->Qs, (n * d + pad) * 4},     {(void**)&idx->Ps, (m * d + pad) * 4},
       {(void**)&idx->unorm, n * 4},              {(void**)&idx->pnorm, m * 4},

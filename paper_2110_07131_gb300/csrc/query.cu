@@ -1856,13 +1856,12 @@ __global__ void k_mprep_c(Common c, Batch b) {
   }
 }
 
-// (f) one CTA per tensor-core item: the item's 128 query rows in the UMMA
-// operand layout (K padded to 64 with zeros; rows past the group are zero),
-// then their 128 (error scale, slack) pairs and 128 query indices (-1 past the
-// group), contiguous so that one bulk copy moves the whole item.
-__host__ __device__ constexpr uint32_t ws_pack_bytes(int kind) {
-  return 128u * TC_K * (kind == TCK_TF32 ? 4u : 2u) + 128u * 12u;
-}
+// (f) one CTA per tensor-core item: the item's 128 query rows in the filter's
+// shared-memory operand layout (wf_off with rows of K = 64, zeros past d;
+// rows past the group are zero), then their 128 (error scale, slack) pairs
+// and 128 query indices (-1 past the group), contiguous so that one bulk copy
+// moves the whole item.
+__host__ __device__ constexpr uint32_t ws_pack_bytes(int nstep) { return wf_tile_bytes(nstep) + 128u * 12u; }
 __global__ void __launch_bounds__(256) k_mprep_items(Common c, Batch b) {
   const int p = blockIdx.x;
   if (p >= b.gitem[RMIPS_KMAX_LIMIT + 1]) return;
@@ -1870,10 +1869,13 @@ __global__ void __launch_bounds__(256) k_mprep_items(Common c, Batch b) {
   const int4 G = b.grp[it.x];
   const int r0 = it.y * 128;                       // first query of the item within its group
   const uint32_t esz = b.tc_kind == TCK_TF32 ? 4u : 2u;
-  unsigned char* dst = b.bitems + (size_t)p * ws_pack_bytes(b.tc_kind);
+  const int nstep = b.tc_kind == TCK_TF32 ? 8 : 4;      // rows of K = 64 (see k_mfilter_ws)
+  const uint32_t sbo = wf_sbo(nstep);
+  unsigned char* dst = b.bitems + (size_t)p * ws_pack_bytes(nstep);
   const int per = 16 / (int)esz;                   // values per 16-byte chunk
-  for (int e = threadIdx.x; e < 128 * (int)(TC_K / per); e += blockDim.x) {
+  for (int e = threadIdx.x; e < 128 * 2 * nstep; e += blockDim.x) {
     const int r = e & 127, k0 = (e >> 7) * per;
+    const uint32_t off = wf_off(r, (e >> 7) * 16, sbo);
     const bool live = r0 + r < G.z;
     const int j = live ? b.bidx[G.y + r0 + r] : -1;
     const float* q = b.dq + (int64_t)(j < 0 ? 0 : j) * c.d;
@@ -1881,7 +1883,7 @@ __global__ void __launch_bounds__(256) k_mprep_items(Common c, Batch b) {
       float v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = (j >= 0 && k0 + i < c.d) ? q[k0 + i] : 0.f;
-      *reinterpret_cast<float4*>(dst + tc_off(r, k0)) = make_float4(v[0], v[1], v[2], v[3]);
+      *reinterpret_cast<float4*>(dst + off) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
       uint16_t h[8];
 #pragma unroll
@@ -1894,10 +1896,10 @@ __global__ void __launch_bounds__(256) k_mprep_items(Common c, Batch b) {
       w.y = h[2] | ((uint32_t)h[3] << 16);
       w.z = h[4] | ((uint32_t)h[5] << 16);
       w.w = h[6] | ((uint32_t)h[7] << 16);
-      *reinterpret_cast<uint4*>(dst + tc_off16(r, k0)) = w;
+      *reinterpret_cast<uint4*>(dst + off) = w;
     }
   }
-  float2* cq = reinterpret_cast<float2*>(dst + 128u * TC_K * esz);
+  float2* cq = reinterpret_cast<float2*>(dst + wf_tile_bytes(nstep));
   int* qj = reinterpret_cast<int*>(cq + 128);
   for (int r = threadIdx.x; r < 128; r += blockDim.x) {
     const bool live = r0 + r < G.z;
@@ -2541,8 +2543,7 @@ constexpr int TCU = 128;                       // users per tile (MMA M)
 constexpr int TCQ = MQ_TQ;                     // queries per laid-out tile
 constexpr int WS_N = 2 * TCQ;                  // queries per item (largest MMA N)
 __host__ __device__ constexpr uint32_t tc_esize(int kind) { return kind == TCK_TF32 ? 4u : 2u; }
-__host__ __device__ constexpr uint32_t tc_tile_bytes(int kind) { return TCQ * TC_K * tc_esize(kind); }
-__host__ __device__ constexpr uint32_t tc_a_bytes(int kind) { return TCU * TC_K * tc_esize(kind); }
+
 
 // ===========================================================================
 // Batched filter on tensor cores, warp-specialized.
@@ -2605,8 +2606,9 @@ struct WsItem {                                        // one accumulator stage,
   float2 c0;                                           // (error scale, slack) of the item's first query
 };
 
-size_t ws_smem_bytes(int kind, int ns) {
-  return 2 * (size_t)tc_a_bytes(kind) + (size_t)ns * ws_pack_bytes(kind) + WS_ESLOTS * (size_t)WS_LG * TCU * 8 +
+size_t ws_smem_bytes(int tck, int ns) {
+  const int ks = tck == TCK_TF32 ? 8 : 4;               // shared-memory rows of K = 64
+  return 2 * (size_t)wf_tile_bytes(ks) + (size_t)ns * ws_pack_bytes(ks) + WS_ESLOTS * (size_t)WS_LG * TCU * 8 +
          WS_ESLOTS * (size_t)TCU * 4;
 }
 
@@ -2781,14 +2783,20 @@ __device__ __forceinline__ void ws_classify(const Common& c, const Batch& b, con
 template <int KIND, int NSTEP, bool PROF>
 __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b, const unsigned char* __restrict__ qtc,
                                                                int ngroups, int ns) {
-  constexpr uint32_t TILE = tc_tile_bytes(KIND);
-  constexpr uint32_t ABYTES = tc_a_bytes(KIND);
-  constexpr uint32_t SBO = KIND == TCK_TF32 ? TC_SBO : TC_SBO16;
+  // In shared memory, user tiles and query items have rows of K = 64 (the
+  // 8-row groups 2048 / 1024 bytes apart, the stride the MMAs read fastest);
+  // the index stores user tiles with rows of the MMA's K only (wf_nstep), and
+  // the loader copies them one 8-row group at a time into the wider rows.
+  constexpr int KS = KIND == TCK_TF32 ? 8 : 4;          // K steps of a shared-memory row
+  static_assert(NSTEP <= KS, "K steps beyond the shared-memory row");
+  constexpr uint32_t ABYTES = wf_tile_bytes(KS);       // a user tile in shared memory
+  constexpr uint32_t SBO = wf_sbo(KS);
+  constexpr uint32_t AGLOB = wf_tile_bytes(NSTEP), SBO_G = wf_sbo(NSTEP);   // a user tile in the index
   constexpr int KSTEP = 32 / (int)tc_esize(KIND);     // K of one MMA
   static_assert(NSTEP * KSTEP <= (int)TC_K, "K steps beyond the padded tile");
-  constexpr uint32_t PACK = ws_pack_bytes(KIND);      // one stage: an item as k_mprep_items packs it
-  constexpr uint32_t BROWS = 2 * TILE;                 // its query rows; then WS_N (scale, slack), WS_N indices
-  static_assert(PACK % 16 == 0 && BROWS == (uint32_t)WS_N * TC_K * tc_esize(KIND), "item layout");
+  constexpr uint32_t PACK = ws_pack_bytes(KS);        // one stage: an item as k_mprep_items packs it
+  constexpr uint32_t BROWS = wf_tile_bytes(KS);        // its query rows; then WS_N (scale, slack), WS_N indices
+  static_assert(PACK % 16 == 0 && SBO_G % 16 == 0 && WS_N == TCU, "item layout");
   extern __shared__ __align__(1024) unsigned char wsm[];
   unsigned char* sA = wsm;                             // 2 user tiles (MMA operand slots)
   unsigned char* sB = sA + 2 * ABYTES;                 // ns packed items
@@ -2966,8 +2974,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1) k_mfilter_ws(Common c, Batch b,
       __threadfence_block();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive_expect_tx(&afull[ab], ABYTES);
-        bulk_g2s(sA + (size_t)ab * ABYTES, qtc + (size_t)tt * ABYTES, ABYTES, &afull[ab]);
+        mbar_arrive_expect_tx(&afull[ab], AGLOB);
+        if (SBO_G == SBO) {
+          bulk_g2s(sA + (size_t)ab * ABYTES, qtc + (size_t)tt * AGLOB, AGLOB, &afull[ab]);
+        } else {
+#pragma unroll 1
+          for (int g = 0; g < TCU / 8; ++g)                         // one 8-row group per copy
+            bulk_g2s(sA + (size_t)ab * ABYTES + (size_t)g * SBO, qtc + (size_t)tt * AGLOB + (size_t)g * SBO_G, SBO_G,
+                     &afull[ab]);
+        }
       }
       fpar ^= 1u << ab;
       fused |= 1u << ab;
@@ -3309,7 +3324,7 @@ rmips_status ensure_batch(rmips_index* idx, Workspace* ws, int64_t cap_y) {
   }
   if (!ws->bitems && idx->d <= (int)TC_K) {
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bcq, (size_t)MQ_SLOTS * sizeof(float2)));
-    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bitems, (size_t)MQ_ITEMS * ws_pack_bytes(TCK_TF32)));
+    RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->bitems, (size_t)MQ_ITEMS * ws_pack_bytes(8)));   // the largest item
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->gitem, (RMIPS_KMAX_LIMIT + 2) * sizeof(int)));
     RMIPS_TRY_CUDA(cudaMalloc((void**)&ws->itemg, (size_t)MQ_ITEMS * sizeof(int2)));
   }

@@ -91,6 +91,23 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
       : "memory");
 }
 
+// Operand layout of the batched tensor-core filter: rows of nstep K steps of
+// 32 bytes (8 TF32 or 16 BF16 / FP16 values) in K-major core matrices
+// (16-byte K chunks LBO = 128 bytes apart, 8-row groups SBO = 8 x 32 x nstep
+// bytes apart); zeros between d and the row's K contribute nothing.  The
+// index keeps its user tiles with rows of exactly the MMA's K (wf_nstep: for
+// d = 50, 7 steps = K 56 for TF32, 4 = K 64 for the 16-bit kinds); in shared
+// memory the filter uses rows of K = 64.
+__host__ __device__ constexpr int wf_nstep(int tf32, int d) {
+  return tf32 ? (d <= 32 ? 4 : (d <= 56 ? 7 : 8)) : (d <= 32 ? 2 : 4);
+}
+__host__ __device__ constexpr uint32_t wf_sbo(int nstep) { return 8u * 32u * (uint32_t)nstep; }
+__host__ __device__ constexpr uint32_t wf_tile_bytes(int nstep) { return 128u * 32u * (uint32_t)nstep; }
+// Byte offset of row r, K byte kb (a multiple of 16 for whole chunks).
+__host__ __device__ __forceinline__ uint32_t wf_off(uint32_t r, uint32_t kb, uint32_t sbo) {
+  return (r >> 3) * sbo + (kb >> 4) * TC_LBO + (r & 7) * 16 + (kb & 15);
+}
+
 // Operand kinds of the tensor-core filter: TF32 from float32 rows, or the
 // index's BF16 / FP16 copy.
 //

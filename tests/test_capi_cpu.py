@@ -150,7 +150,7 @@ def _fnv1a(b: bytes) -> int:
 
 def _index_file(n=4, m=3, d=2, k_max=2, bs=32, nb=None, pp=None, precision=0, full_p=1, batch_tc=1,
                 no_blocks=0, has_qh=0, has_qtc=0, incomplete=0, pn0=1.0, tune=0, narrays=None,
-                permQ=None, permP=None, cand=None, corrupt_hash=False, magic=b"RMIPSIX2"):
+                permQ=None, permP=None, cand=None, corrupt_hash=False, magic=b"RMIPSIX3"):
     import struct
     nb = (n + bs - 1) // bs if nb is None else nb
     pp = m if pp is None else pp
@@ -198,7 +198,7 @@ def test_index_file_crafted_by_the_test_is_accepted_up_to_the_device(tmp_path):
     dict(batch_tc=3), dict(no_blocks=-1), dict(has_qh=1), dict(has_qtc=1, d=80), dict(incomplete=9),
     dict(pn0=float("nan")), dict(tune=1), dict(tune=9 << 8), dict(tune=3 << 16), dict(tune=1 << 24),
     dict(narrays=3), dict(k_max=40), dict(d=0),
-    dict(magic=b"RMIPSIX1"), dict(permQ=[0, 1, 1, 3]), dict(permQ=[0, 1, 2, 4]), dict(permP=[2, 0, -1]),
+    dict(magic=b"RMIPSIX2"), dict(permQ=[0, 1, 1, 3]), dict(permQ=[0, 1, 2, 4]), dict(permP=[2, 0, -1]),
     dict(cand=[5] + [-1] * 127), dict(corrupt_hash=True)])
 def test_index_file_with_an_inconsistent_field_is_refused(tmp_path, field):
     p = tmp_path / "bad.rmips"
