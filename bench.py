@@ -737,9 +737,9 @@ def run_ours(a):
     m_ach = m_flops / (m_ms / 1e3) / 1e12 if m_ms > 0 else 0.0
     tc_path = a.batch_kernel == "tc" and a.d <= 64
     # DRAM bytes (read + write) of one k_mfilter_ws launch on the default
-    # workload, from one ncu capture of the current kernel (273.1 MB + 4.7 MB)
+    # workload, from one ncu capture of the current kernel (241.1 MB + 4.1 MB)
     default_workload = (a.n, a.m, a.d, a.k, a.k_max, a.nq) == (1_000_000, 500_000, 50, 10, 25, 10_000)
-    tc_traffic = 277.9e6 if (tc_path and default_workload and a.block_size == 32 and not a.no_blocks
+    tc_traffic = 245.2e6 if (tc_path and default_workload and a.block_size == 32 and not a.no_blocks
                              and a.precision == "fp32") else None
     if tc_path:
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
