@@ -344,16 +344,17 @@ def run_serving(rmips, index, P, a):
     plain path can carry at 20k requests/s)."""
     n_req = min(a.serve_requests, 100_000)
     qs, ks, segs, subsets = serving_requests(P, a.n, a.d, max(n_req, 1), 41)
-    opts = dict(max_batch=4096, max_wait_us=200, streams=2, max_pending=1 << 21)
+    opts = dict(max_batch=4096, max_wait_us=0, streams=2, max_pending=1 << 21, spin_us=200)
     warm = rmips.Server(index, **opts)
     warm.wait_many(warm.submit_many(qs[:4096], ks[:4096]))
     warm.close()
     out = {"workload": "Poisson arrivals; q = random item of P or random N(0, I/d) (half each); k uniform in "
                        "1..25; segment: none / contiguous id range / registered random id subset (a third each), "
                        "segment sizes log-uniform in 1e3..1e6",
-           "server": "rmips_server: max_batch 4096, max_wait_us 200 while a batch is on the device (a batch "
-                     "closes at once when the device is idle), 2 streams, batches of up to 4 requests as "
-                     "one-launch single queries; admission by device result memory",
+           "server": "rmips_server: max_batch 4096, max_wait_us 0 (a batch closes as soon as one of the 2 "
+                     "stream slots is free; requests queue while both are busy), spin_us 200 (server threads "
+                     "and the waiting caller poll before blocking), batches of up to 4 requests as one-launch "
+                     "single queries; admission by device result memory",
            "plain": "rmips_query per request on one host thread, host q and ids, segments as id ranges / id lists"}
     out["with_segments"] = serve_rates(rmips, index, qs, ks, segs, subsets, [20_000.0, 200_000.0, 1_000_000.0],
                                        {20_000.0: 10_000, 200_000.0: 40_000, 1_000_000.0: n_req},

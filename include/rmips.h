@@ -408,6 +408,12 @@ typedef struct {
                                at most 256 MiB */
   int64_t result_ids_per_request;  /* result ids a request reserves (at most
                                its segment's size); 0 = 1,024 */
+  int32_t spin_us;          /* the dispatcher, the completer and waiting callers
+                               poll for up to this many microseconds before they
+                               block (lower latency at light load, for busy
+                               host cores); 0 = block at once (default),
+                               at most 100,000 */
+  int32_t reserved;         /* must be 0 */
 } rmips_server_opts;
 
 typedef struct {

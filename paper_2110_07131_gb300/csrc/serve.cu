@@ -25,6 +25,7 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <thread>
@@ -105,6 +106,7 @@ struct rmips_server {
   rmips_server_opts o{};
   std::mutex mu;
   std::condition_variable cv_in, cv_slot, cv_fly, cv_done;
+  std::atomic<uint64_t> ver{0};    // bumped on every change a waiter may be waiting for (spin_us)
   std::unordered_map<int64_t, rmips::Request*> reqs;
   std::deque<int64_t> queue;
   std::vector<rmips::Slot> slots;
@@ -204,11 +206,40 @@ rmips_status launch_slot(rmips_server* S, Slot& sl, int64_t nq) {
   return RMIPS_OK;
 }
 
+// Every notification of the server's condition variables goes through here,
+// so that threads spinning on `ver` (spin_us > 0) see the change too.
+void bump(rmips_server* S) { S->ver.fetch_add(1, std::memory_order_release); }
+
+// With spin_us > 0: polls pred (under the lock, after each change of `ver`)
+// for up to spin_us before the caller blocks.  Returns with the lock held;
+// true when pred holds.
+template <class P>
+bool spin_for(rmips_server* S, std::unique_lock<std::mutex>& lk, P pred) {
+  if (pred()) return true;
+  if (S->o.spin_us <= 0) return false;
+  const auto end = Clock::now() + std::chrono::microseconds(S->o.spin_us);
+  uint64_t v = S->ver.load(std::memory_order_acquire);
+  lk.unlock();
+  for (;;) {
+    const uint64_t w = S->ver.load(std::memory_order_acquire);
+    if (w != v) {
+      lk.lock();
+      if (pred()) return true;
+      lk.unlock();
+      v = w;
+    }
+    if (Clock::now() >= end) break;
+  }
+  lk.lock();
+  return pred();
+}
+
 void dispatcher(rmips_server* S) {
   cudaSetDevice(S->idx->device);
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
-    S->cv_in.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+    auto any_in = [&] { return S->stop || !S->queue.empty(); };
+    if (!spin_for(S, lk, any_in)) S->cv_in.wait(lk, any_in);
     if (S->stop) break;
     // close the batch at once when no batch is on the device (waiting would
     // only add latency), else when it is full or its oldest request has
@@ -218,12 +249,13 @@ void dispatcher(rmips_server* S) {
       S->cv_in.wait_until(lk, deadline);
     if (S->stop) break;
     int si = -1;
-    S->cv_slot.wait(lk, [&] {
+    auto free_slot = [&] {
       if (S->stop) return true;
       for (int i = 0; i < (int)S->slots.size(); ++i)
         if (!S->slots[i].busy) { si = i; return true; }
       return false;
-    });
+    };
+    if (!spin_for(S, lk, free_slot)) S->cv_slot.wait(lk, free_slot);
     if (S->stop) break;
     Slot& sl = S->slots[si];
     sl.busy = true;
@@ -258,6 +290,7 @@ void dispatcher(rmips_server* S) {
     ++S->batches;
     S->batched += nq;
     S->cv_fly.notify_one();
+    bump(S);
   }
   // stopped: fail whatever is still queued
   const auto now = Clock::now();
@@ -267,13 +300,15 @@ void dispatcher(rmips_server* S) {
     finish(S, r, {}, RMIPS_ERR_ARG, now);
   }
   S->cv_done.notify_all();
+  bump(S);
 }
 
 void completer(rmips_server* S) {
   cudaSetDevice(S->idx->device);
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
-    S->cv_fly.wait(lk, [&] { return S->stop || !S->inflight.empty(); });
+    auto any_fly = [&] { return S->stop || !S->inflight.empty(); };
+    if (!spin_for(S, lk, any_fly)) S->cv_fly.wait(lk, any_fly);
     if (S->inflight.empty()) {
       if (S->stop) break;
       continue;
@@ -288,6 +323,11 @@ void completer(rmips_server* S) {
     rmips_status st = sl.launch;
     bool one_by_one = false;
     if (st == RMIPS_OK) {
+      if (S->o.spin_us > 0) {                     // poll the batch's event before blocking on it
+        const auto end = Clock::now() + std::chrono::microseconds(S->o.spin_us);
+        while (cudaEventQuery(sl.done) == cudaErrorNotReady && Clock::now() < end) {
+        }
+      }
       if (cudaEventSynchronize(sl.done) != cudaSuccess) {
         set_error("batch failed on the device");
         st = RMIPS_ERR_CUDA;
@@ -329,6 +369,7 @@ void completer(rmips_server* S) {
     sl.busy = false;
     S->cv_slot.notify_all();
     S->cv_done.notify_all();
+    bump(S);
   }
 }
 
@@ -403,8 +444,8 @@ extern "C" rmips_status rmips_server_create(rmips_index* idx, const rmips_server
   if (opts) o = *opts;
   if (o.max_batch < 1 || o.max_batch > MQ_MAXQ || o.max_wait_us < 0 || o.streams < 1 || o.streams > 16 ||
       o.max_pending < 1 || o.max_device_bytes < 0 || o.result_ids_per_request < 0 || o.single_max < -1 ||
-      o.single_max > 64) {
-    set_error("bad server options (max_batch 1..16384, streams 1..16)");
+      o.single_max > 64 || o.spin_us < 0 || o.spin_us > 100000 || o.reserved != 0) {
+    set_error("bad server options (max_batch 1..16384, streams 1..16, spin_us 0..100000)");
     return RMIPS_ERR_ARG;
   }
   int prev = -1;
@@ -527,6 +568,7 @@ extern "C" rmips_status rmips_server_submit_many(rmips_server* S, const float* q
     S->submitted += nq;
   }
   S->cv_in.notify_one();
+  bump(S);
   return RMIPS_OK;
 }
 
@@ -545,7 +587,8 @@ extern "C" rmips_status rmips_server_wait(rmips_server* S, int64_t ticket, int64
   if (it == S->reqs.end()) { set_error("unknown ticket"); return RMIPS_ERR_ARG; }
   Request* r = it->second;
   auto done = [&] { return r->state == 2; };
-  if (timeout_ms < 0) S->cv_done.wait(lk, done);
+  if (timeout_ms != 0 && spin_for(S, lk, done)) {
+  } else if (timeout_ms < 0) S->cv_done.wait(lk, done);
   else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
     set_error("request not finished yet");
     return RMIPS_ERR_TIMEOUT;
@@ -592,7 +635,8 @@ extern "C" rmips_status rmips_server_wait_many(rmips_server* S, const int64_t* t
       if (r->state != 2) return false;
     return true;
   };
-  if (timeout_ms < 0) S->cv_done.wait(lk, all_done);
+  if (timeout_ms != 0 && spin_for(S, lk, all_done)) {
+  } else if (timeout_ms < 0) S->cv_done.wait(lk, all_done);
   else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), all_done)) {
     set_error("requests not finished yet");
     return RMIPS_ERR_TIMEOUT;
@@ -667,6 +711,7 @@ extern "C" void rmips_server_destroy(rmips_server* S) {
   S->cv_in.notify_all();
   S->cv_slot.notify_all();
   S->cv_fly.notify_all();
+  bump(S);
   if (S->disp.joinable()) S->disp.join();
   if (S->comp.joinable()) S->comp.join();
   for (Slot& sl : S->slots) {

@@ -76,7 +76,7 @@ class Profile(C.Structure):
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("streams", C.c_int32),
                 ("single_max", C.c_int32), ("max_pending", C.c_int64), ("max_device_bytes", C.c_int64),
-                ("result_ids_per_request", C.c_int64)]
+                ("result_ids_per_request", C.c_int64), ("spin_us", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -483,11 +483,11 @@ class Server:
 
     def __init__(self, index: Index, max_batch: int = 4096, max_wait_us: int = 200, streams: int = 2,
                  max_pending: int = 1 << 20, max_device_bytes: int = 0, result_ids_per_request: int = 0,
-                 single_max: int = 0):
+                 single_max: int = 0, spin_us: int = 0):
         load_library()
         self.index = index                       # keeps the index alive
         opts = ServerOpts(int(max_batch), int(max_wait_us), int(streams), int(single_max), int(max_pending),
-                          int(max_device_bytes), int(result_ids_per_request))
+                          int(max_device_bytes), int(result_ids_per_request), int(spin_us), 0)
         h = C.c_void_p()
         _check(_lib.rmips_server_create(index.handle, C.byref(opts), C.byref(h)))
         self.handle = h

@@ -219,3 +219,23 @@ def test_small_batches_run_as_single_launches(setup):
     st = srv.stats()
     assert st["completed"] == len(qs) and st["batches_one_by_one"] == 0
     srv.close()
+
+
+def test_spinning_server_and_greedy_dispatch_give_the_same_results(setup):
+    # spin_us polls instead of blocking; max_wait_us = 0 closes a batch as
+    # soon as a stream slot is free: the answers are the same
+    Q, P, index = setup
+    qs, ks, segs = _requests(P, 120, 41)
+    srv = rmips.Server(index, max_batch=64, max_wait_us=0, streams=2, spin_us=300)
+    tickets = [srv.submit(qs[j], int(ks[j]), segs[j]) for j in range(len(qs))]
+    for j, t in enumerate(tickets):
+        ids, _ = srv.wait(t)
+        assert np.array_equal(ids, rmips.rmips_query(index, qs[j], int(ks[j]), segment=segs[j])), j
+    more = srv.submit_many(qs[:40], ks[:40].astype(np.int32))
+    ids, offs, _ = srv.wait_many(more)
+    for j in range(40):
+        assert np.array_equal(ids[offs[j]:offs[j + 1]], rmips.rmips_query(index, qs[j], int(ks[j])))
+    with pytest.raises(rmips.RmipsError) as e:
+        rmips.Server(index, spin_us=-1)
+    assert e.value.status == 1
+    srv.close()
