@@ -426,8 +426,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
       }
       tc_fence_after();
       float acc[TB_TILE];
-#pragma unroll
-      for (int c0 = 0; c0 < TB_TILE; c0 += 16) tmem_ld16(tlane + (uint32_t)c0, acc + c0);
+      // the two loads also return the maxima of their 32 columns
+      const float mx0 = tmem_ld32_max(tlane, acc), mx1 = tmem_ld32_max(tlane + 32u, acc + 32);
       tmem_ld_wait();
       tc_fence_before();
       __syncthreads();
@@ -437,15 +437,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_topk_tc(const float* __restrict_
       const int live = (int)((pp - t * TB_TILE) < TB_TILE ? (pp - t * TB_TILE) : TB_TILE);
       bool done_fast = false;
       if (live == TB_TILE) {                       // fast path: the tile's maximum decides alone
-        float m0 = acc[0], m1 = acc[1], m2 = acc[2], m3 = acc[3];
-#pragma unroll
-        for (int q = 4; q < TB_TILE; q += 4) {
-          m0 = fmaxf(m0, acc[q]);
-          m1 = fmaxf(m1, acc[q + 1]);
-          m2 = fmaxf(m2, acc[q + 2]);
-          m3 = fmaxf(m3, acc[q + 3]);
-        }
-        const float vmax = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+        static_assert(TB_TILE == 64, "two 32-column loads per tile");
+        const float vmax = fmaxf(mx0, mx1);
         if (!(vmax > thr)) {                       // every item of the tile is rejected
           uex = fmaxf(uex, __fadd_ru(__fmaf_ru(un, cps[buf][0], vmax), ua));
           done_fast = true;
