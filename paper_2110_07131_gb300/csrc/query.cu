@@ -2175,46 +2175,44 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
     }
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) ngt += __shfl_xor_sync(FULL, ngt, o);
-    // Overlapping candidates, one at a time with the whole warp: most are the
-    // query's own copy in P (queries drawn from the items), an exact tie that
-    // the bitwise comparison settles; otherwise float32 u.p with its bound.
-    // What that leaves open sends the pair to the exact path below.
+    // Overlapping candidates: each pair's eight lanes take its own, one at a
+    // time, the warp's four pairs side by side.  Most are the query's own
+    // copy in P (queries drawn from the items), an exact tie that the bitwise
+    // comparison settles; otherwise float32 u.p with its bound.  What that
+    // leaves open sends the pair to the exact path below.
     bool hardg = false;
+    const unsigned gmask = 0xffu << (grp * 8);
     for (unsigned pend = __ballot_sync(FULL, ovm != 0); pend; pend = __ballot_sync(FULL, ovm != 0)) {
-      const int src = __ffs(pend) - 1;
+      const unsigned gp = pend & gmask;
+      const bool act = gp != 0;                               // this pair has a candidate left
+      const int src = act ? __ffs(gp) - 1 : lane;
       const uint32_t m = __shfl_sync(FULL, ovm, src);
-      const int r = __ffs(m) - 1;
-      if (lane == src) ovm &= ovm - 1;
+      const int r = act ? __ffs(m) - 1 : 0;
+      if (act && lane == src) ovm &= ovm - 1;
       int32_t mine = its[0];
 #pragma unroll
       for (int x = 1; x < RMIPS_KC / 8; ++x) mine = r == x ? its[x] : mine;
       const int32_t it = __shfl_sync(FULL, mine, src);
-      const unsigned long long opr = __shfl_sync(FULL, pr, src);
-      const float ogl = __shfl_sync(FULL, gl, src), ogh = __shfl_sync(FULL, gh, src);
-      const float* op = c.Ps + (int64_t)it * d;
-      const float* ou = c.Qs + (int64_t)(int32_t)(opr & 0xffffffffull) * d;
-      const float* oq = b.dq + (int64_t)(int)(opr >> 32) * d;
+      const float* op = c.Ps + (int64_t)(act ? it : 0) * d;
       bool same = true;
       float sp = 0.f, sb = 0.f;
-      for (int i = lane; i < d; i += 32) {
-        const float pv = op[i], uv = ou[i];
-        same = same && __float_as_uint(pv) == __float_as_uint(oq[i]);
+      for (int i = sub; act && i < d; i += 8) {
+        const float pv = op[i], uv = u[i];
+        same = same && __float_as_uint(pv) == __float_as_uint(q[i]);
         sp = fmaf(uv, pv, sp);
         sb = fmaf(fabsf(uv), fabsf(pv), sb);
       }
-      same = __all_sync(FULL, same);
+      same = (__ballot_sync(FULL, !same) & gmask) == 0;        // all eight lanes of the pair
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 4; o > 0; o >>= 1) {
         sp += __shfl_xor_sync(FULL, sp, o);
         sb += __shfl_xor_sync(FULL, sb, o);
       }
       const float ep = __fmaf_ru(sb, c.cg32, tiny);
-      const bool ogt = !same && __fsub_rd(sp, ep) > ogh;
-      const bool ohard = !same && !ogt && !(__fadd_ru(sp, ep) < ogl);
-      if ((lane >> 3) == (src >> 3)) {
-        ngt += ogt ? 1 : 0;
-        hardg = hardg || ohard;
-      }
+      const bool ogt = act && !same && __fsub_rd(sp, ep) > gh;
+      const bool ohard = act && !same && !ogt && !(__fadd_ru(sp, ep) < gl);
+      ngt += ogt ? 1 : 0;
+      hardg = hardg || ohard;
     }
     bool yes = quick && !hardg && ngt < k;
     // the pairs still undecided, one at a time with the whole warp
@@ -2250,52 +2248,75 @@ __global__ void __launch_bounds__(256) k_mresolve(Common c, Batch b) {
 
 // Exclusive scan of per-query counts into absolute offsets.
 __global__ void __launch_bounds__(1024) k_mscan(Common c, Batch b) {
-  constexpr int R = MQ_MAXQ / 1024;                    // chunks of 1024 queries, one count per thread
+  // One pass: thread t holds the counts of queries R t .. R t + R - 1; one
+  // block scan gives each query's offset and each mid / large result its
+  // place in the lists (the lists' counters are zero at the pass's start).
+  constexpr int R = MQ_MAXQ / 1024;
+  static_assert(R * 1024 == MQ_MAXQ && MQ_MAXQ < 65536, "ten queries per thread, list counts in 16 bits");
   __shared__ long long s_warp[32];
+  __shared__ int s_wlist[32];
   __shared__ long long s_base;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_base = c.ctr[C_CURSOR];
+  const int j0 = tid * R;
   int v[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {                        // every load issued before the first scan
-    const int j = r * 1024 + tid;
-    v[r] = j < b.nq ? b.qcnt[j] : 0;
-  }
-  __syncthreads();
-  long long run = s_base;                              // results of all earlier chunks
+  long long tsum = 0;
+  int lists = 0;                                       // mid count | large count << 16
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    if (r * 1024 >= b.nq) break;                       // uniform
-    long long x = v[r];
-    for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, x, o); if (lane >= o) x += y; }
-    if (lane == 31) s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      long long w = s_warp[lane];
-      for (int o = 1; o < 32; o <<= 1) { long long y = __shfl_up_sync(FULL, w, o); if (lane >= o) w += y; }
-      s_warp[lane] = w;
+    v[r] = j0 + r < b.nq ? b.qcnt[j0 + r] : 0;
+    tsum += v[r];
+    lists += v[r] > MEMIT_MID_CAP ? (1 << 16) : (v[r] > 32 ? 1 : 0);
+  }
+  long long x = tsum;
+  int y = lists;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long xo = __shfl_up_sync(FULL, x, o);
+    const int yo = __shfl_up_sync(FULL, y, o);
+    if (lane >= o) { x += xo; y += yo; }
+  }
+  if (lane == 31) { s_warp[wid] = x; s_wlist[wid] = y; }
+  __syncthreads();
+  if (wid == 0) {
+    long long w = s_warp[lane];
+    int wl = s_wlist[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long wo = __shfl_up_sync(FULL, w, o);
+      const int wlo = __shfl_up_sync(FULL, wl, o);
+      if (lane >= o) { w += wo; wl += wlo; }
     }
-    __syncthreads();
-    const int j = r * 1024 + tid;
+    s_warp[lane] = w;
+    s_wlist[lane] = wl;
+  }
+  __syncthreads();
+  long long off = s_base + (x - tsum) + (wid ? s_warp[wid - 1] : 0);
+  const int lbase = (y - lists) + (wid ? s_wlist[wid - 1] : 0);
+  int nmid = lbase & 0xffff, nbig = lbase >> 16;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j = j0 + r;
     if (j < b.nq) {
-      b.doffs[j] = run + (x - v[r]) + (wid ? s_warp[wid - 1] : 0);
+      b.doffs[j] = off;
+      off += v[r];
       int32_t slot = -1;
       if (v[r] > MEMIT_MID_CAP) {
-        const long long q = atomicAdd((unsigned long long*)&c.ctr[C_NBIG], 1ull);
-        b.big[q] = j;
-        if (q < MQ_BIG_SLOTS) slot = (int32_t)q;
+        b.big[nbig] = j;
+        if (nbig < MQ_BIG_SLOTS) slot = nbig;
+        ++nbig;
       } else if (v[r] > 32) {
-        const long long q = atomicAdd((unsigned long long*)&c.ctr[C_NMID], 1ull);
-        b.mid[q] = j;
+        b.mid[nmid++] = j;
       }
       b.bslot[j] = slot;
     }
-    run += s_warp[31];
-    __syncthreads();                                   // s_warp is rewritten by the next chunk
   }
   if (tid == 0) {
+    const long long run = s_base + s_warp[31];
     b.doffs[b.nq] = run;
     c.ctr[C_CURSOR] = run;
+    c.ctr[C_NMID] = s_wlist[31] & 0xffff;
+    c.ctr[C_NBIG] = s_wlist[31] >> 16;
     if (run > b.capacity) set_status(c.ctr, ST_CAPACITY);
   }
 }
