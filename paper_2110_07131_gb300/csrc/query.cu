@@ -827,7 +827,11 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   const size_t stage_bytes = (size_t)Q1_WARPS * chunk_bytes;
   const int64_t nchunks = (n + 31) / 32;
   const int64_t nspans = (nchunks + Q1_WARPS - 1) / Q1_WARPS;
-  for (int i = tid; i < d; i += blockDim.x) sq[i] = q_src[i];
+  // Launched with programmatic stream serialization: the next launch on the
+  // stream may start its CTAs as this one's leave their SMs; it prepares its
+  // barriers and its first Lemma 3 loads (index data, read-only) and waits
+  // for this grid's completion before it reads q or the workspace.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
@@ -855,6 +859,8 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
       pre_l[i] = in ? LBk[blk] : 0.f;
     }
   }
+  asm volatile("griddepcontrol.wait;" ::: "memory");               // the previous grid has completed
+  for (int i = tid; i < d; i += blockDim.x) sq[i] = q_src[i];
   __syncthreads();
   if (warp == 0) {
     float qn0, eps0;
@@ -1349,8 +1355,17 @@ cudaError_t launch_query1(const Common& c, const EmitArgs& e, const float* q, in
     if (err != cudaSuccess) return err;
     configured = smem;
   }
-  k_query1<T><<<grid, Q1_THREADS, smem, st>>>(c, e, q, k, precision, ns, res, done, pacc, res_host);
-  return cudaGetLastError();
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)grid);
+  lc.blockDim = dim3(Q1_THREADS);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  return cudaLaunchKernelEx(&lc, k_query1<T>, c, e, q, k, precision, ns, res, done, pacc, res_host);
 }
 
 // Launch shape of the one-launch query: one CTA per SM (fewer when there are
