@@ -617,21 +617,43 @@ def run_ours(a):
 
     # end to end through the public API with host buffers (copies inside the
     # timed region): the queries and their k in pinned host memory (numpy
-    # views of pinned tensors), the results returned as a new host array
+    # views of pinned tensors), the results returned as a new host array.
+    # Three caller threads keep three synchronous calls in flight, each on
+    # its own CUDA stream (the library gives each call its own workspace), so
+    # one call's copies and host work overlap another's kernels.
+    import threading
     hq = torch.empty((a.nq, a.d), dtype=torch.float32, pin_memory=True).numpy()
     hq[:] = qs[:a.nq]
     hks = torch.empty(a.nq, dtype=torch.int32, pin_memory=True).numpy()
     hks[:] = ks
+    e2e_threads = 3
     e2e_steps = max(3, min(a.steps, 10))
-    rmips.rmips_query_batch(index, hq, hks)
+    e2e_streams = [torch.cuda.Stream(dev) for _ in range(e2e_threads)]
+    for s_ in e2e_streams:
+        rmips.rmips_query_batch(index, hq, hks, stream=s_)
+    d2h = [0] * e2e_threads
+    e2e_err = []
+
+    def e2e_worker(i):
+        try:
+            for _ in range(e2e_steps):
+                ids, offs = rmips.rmips_query_batch(index, hq, hks, stream=e2e_streams[i])
+                d2h[i] += ids.nbytes + offs.nbytes
+        except Exception as ex:                          # surfaced below
+            e2e_err.append(ex)
+    workers = [threading.Thread(target=e2e_worker, args=(i,)) for i in range(e2e_threads)]
     t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(e2e_steps):
-        ids, offs = rmips.rmips_query_batch(index, hq, hks)
-        d2h += ids.nbytes + offs.nbytes
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    for w in workers:
+        w.start()
+    for w in workers:
+        w.join()
+    e2e_s = (time.perf_counter() - t0) / (e2e_threads * e2e_steps)
+    if e2e_err:
+        raise e2e_err[0]
     e2e = {"value": a.nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(hq.nbytes + hks.nbytes),
-           "d2h_bytes_per_step": int(d2h // e2e_steps), "inputs": "pinned host memory"}
+           "d2h_bytes_per_step": int(sum(d2h) // (e2e_threads * e2e_steps)), "inputs": "pinned host memory",
+           "api": "rmips_query_batch (synchronous, host arrays in and out) from 3 caller threads, each on its "
+                  "own CUDA stream, 3 calls in flight"}
 
     # plain path: one query per call, host buffers, per-call latency
     lat, sizes = [], []
