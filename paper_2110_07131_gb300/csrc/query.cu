@@ -682,14 +682,16 @@ __device__ __forceinline__ int status_code(long long s) {
 }
 
 // --- one launch per query (full-P index) ---------------------------------------------
-// One CTA per SM.  The users are cut into spans of Q1_SPAN chunks of 32 rows
-// (256 users); CTA c owns spans c, c + G, c + 2G, ... (G CTAs).  Warp
+// One CTA per SM.  The users are cut into spans of Q1_WARPS chunks of 32 rows
+// (320 users); CTA c owns spans c, c + G, c + 2G, ... (G CTAs).  Warp
 // Q1_WARPS is the producer: for 32 of its spans at a time (one per lane) it
 // tests Lemma 3 for every block of the span, and for each span that keeps a
 // chunk it takes a shared-memory stage, publishes (span, chunk mask), and
 // copies every run of consecutive kept chunks with ONE bulk copy (a 1-D
 // cp.async.bulk occupies the SM's copy engine for about the same time up to
-// 64 KB, so a whole 51 KB span of float32 rows costs one copy, not eight).
+// 64 KB, so a whole 64,000-byte span of float32 rows at d = 50 costs one
+// copy, not ten).  Ten consumer warps measured faster than eight (three
+// stages instead of four at d = 50) and than twelve.
 // Consumer warp w handles chunk w of each stage: it prefetches its users'
 // (lo_k, hi_k) while the rows land, forms u.q with its error bound (Lemma 1:
 // no if u.q + e < lo_k; yes if u.q - e >= hi_k), rechecks undecided users
@@ -701,7 +703,7 @@ __device__ __forceinline__ int status_code(long long s) {
 // sorts and writes the ids, copies the status, count and counters to `res`
 // (and status and count to `done` when given) and clears the counters.
 constexpr int RES_STATUS = 0, RES_COUNT = 1, RES_CTR = 2;     // res layout: [2 + C_NCOUNTERS]
-constexpr int Q1_WARPS = 8;                                    // consumer warps = chunks per span
+constexpr int Q1_WARPS = 10;                                   // consumer warps = chunks per span
 constexpr int Q1_THREADS = (Q1_WARPS + 1) * 32;
 constexpr int Q1_MAXNS = 6;                                    // stages at most
 constexpr size_t Q1_HEAD = 1024;                               // q, barriers, stage info
