@@ -504,10 +504,11 @@ def test_async_single_queries_back_to_back(tiny, p_prime, precision):
 
 
 def test_single_query_kernel_ragged_spans():
-    # users not a multiple of the 256-user span, blocks of every size, and the
-    # largest results (bitmap emit): the one-launch kernel against the oracle
-    for n, m, d, bs in ((1, 3, 5, 32), (255, 40, 50, 32), (257, 60, 50, 64), (9000, 300, 64, 256),
-                        (700, 90, 128, 128)):
+    # users not a multiple of the kernel's span (ten chunks of 32 users: 320),
+    # one short of and just past one and two spans, blocks of every size, and
+    # the largest results (bitmap emit): the one-launch kernel against the oracle
+    for n, m, d, bs in ((1, 3, 5, 32), (255, 40, 50, 32), (257, 60, 50, 64), (319, 50, 50, 32),
+                        (321, 60, 50, 64), (641, 70, 50, 32), (9000, 300, 64, 256), (700, 90, 128, 128)):
         Q, P = datagen.make_problem(n, m, d, 23)
         qs = np.concatenate([P[:3] * 6.0, datagen.random_queries(2, d, 5), np.zeros((1, d), np.float32)])
         counts = O.counts_greater_multi(Q, P, qs)
