@@ -1111,7 +1111,9 @@ __global__ void __launch_bounds__(Q1_THREADS, 1) k_query1(Common c, EmitArgs e, 
   long long status = s_fin ? s_ctr[C_STATUS] : ST_NONFINITE;
   const long long cnt = s_ctr[C_YES];
   long long total = 0;
-  if (status == 0 && cnt <= 32) {
+  if (status == 0 && cnt == 0) {
+    // no result (most queries): nothing to sort or write
+  } else if (status == 0 && cnt <= 32) {
     // a small result: one warp, one id per lane, sorted with shuffles
     if (warp == 0) {
       int32_t id = INT_MAX;
